@@ -1,0 +1,318 @@
+"""Pins for the oracle's block hierarchy and multi-level Algorithm 1.
+
+* hierarchy: every rule recomputed by brute force with plain loops over block
+  coordinates (sets of tuples, no array shifts), plus structural invariants;
+* S^neq rescaling: the post-collision non-equilibrium stress measured in the
+  single-level dynamics obeys S'^neq = -c_s^2 (tau - 1)(grad u + grad u^T),
+  which fixes the level-to-level factor; up/down are exact inverses;
+* multi-level: uniform flow stays uniform to rounding through Algorithm 1 and
+  through rebuilds; a shear wave crossing a refinement interface tracks the
+  all-fine single-level solution, and the chosen reading of the rescale factor
+  beats the literal one.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import hierarchy as hy
+from oracle import multilevel as ml
+from oracle import single_level as sl
+from paper_2603_14982_gb300 import workloads as wl
+
+torch.set_default_dtype(torch.float64)
+
+
+# ------------------------------------------------------------ brute-force hierarchy
+
+def _wrap(q, dims, periodic):
+    """Wrap/clip a block coordinate (x, y, z); None if outside a wall."""
+    out = []
+    for a in range(3):
+        n = dims[a]
+        v = q[a]
+        if periodic[a]:
+            v %= n
+        elif v < 0 or v >= n:
+            return None
+        out.append(v)
+    return tuple(out)
+
+
+def brute(O0_set, ext, B, L, periodic):
+    dims = [(ext[0] // (B << l), ext[1] // (B << l), ext[2] // (B << l)) for l in range(L)]
+    allb = [set(itertools.product(range(d[0]), range(d[1]), range(d[2]))) for d in dims]
+    nb = [d for d in itertools.product((-1, 0, 1), repeat=3) if d != (0, 0, 0)]
+    H = [set()]
+    src = O0_set
+    for l in range(1, L):
+        par = {(q[0] // 2, q[1] // 2, q[2] // 2) for q in src}
+        Hl = set(par)
+        for q in par:
+            for d in nb:
+                w = _wrap((q[0] + d[0], q[1] + d[1], q[2] + d[2]), dims[l], periodic)
+                if w is not None:
+                    Hl.add(w)
+        H.append(Hl)
+        src = Hl
+    I = [set()]
+    for l in range(1, L):
+        Il = set()
+        for q in H[l]:
+            ok = True
+            for d in nb:
+                w = _wrap((q[0] + d[0], q[1] + d[1], q[2] + d[2]), dims[l], periodic)
+                if w is not None and w not in H[l]:
+                    ok = False
+            if ok:
+                Il.add(q)
+        I.append(Il)
+    stored = []
+    for l in range(L):
+        if l < L - 1:
+            ch = {(2 * q[0] + a, 2 * q[1] + b, 2 * q[2] + c) for q in H[l + 1]
+                  for a in (0, 1) for b in (0, 1) for c in (0, 1)}
+            stored.append(ch - I[l])
+        else:
+            stored.append(allb[l] - I[l])
+    border = []
+    for l in range(L):
+        bl = set()
+        for q in stored[l]:
+            if q in H[l] or (l < L - 1 and (q[0] // 2, q[1] // 2, q[2] // 2) in stored[l + 1]):
+                bl.add(q)
+        border.append(bl)
+    return H, I, stored, border
+
+
+def _as_set(G):
+    z, y, x = np.nonzero(G)
+    return set(zip(x.tolist(), y.tolist(), z.tolist()))
+
+
+@pytest.mark.parametrize("seed,periodic,L", [(1, (True, True, True), 3), (2, (True, False, True), 3),
+                                              (3, (False, False, False), 2), (4, (True, False, True), 4)])
+def test_hierarchy_matches_brute_force(seed, periodic, L):
+    ext = (64, 64, 64) if L < 4 else (128, 64, 128)
+    g = np.random.default_rng(seed)
+    n = 40
+    pos = g.uniform(0, 1, (n, 3)) * np.array([ext[0], 16, ext[2]]) + np.array([0, 2, 0])
+    h = hy.from_particles(pos.astype(np.float32), ext, 8, L, periodic)
+    O0 = {(int(p[0]) // 8, int(p[1]) // 8, int(p[2]) // 8) for p in pos}
+    assert _as_set(h.O0) == O0
+    H, I, stored, border = brute(O0, ext, 8, L, periodic)
+    for l in range(L):
+        assert _as_set(h.H[l]) == H[l]
+        assert _as_set(h.I[l]) == I[l]
+        assert _as_set(h.stored[l]) == stored[l]
+        assert _as_set(h.border[l]) == border[l]
+        bl = h.blocks(l)
+        slot = [(b[2] * h.dims[l][1] + b[1]) * h.dims[l][2] + b[0] for b in bl.tolist()]
+        assert slot == sorted(slot)
+
+
+def test_hierarchy_invariants_on_falling_cloud():
+    ext, B, L, per = (128, 128, 128), 8, 3, (True, False, True)
+    pos = wl.particle_cloud(128, count=20000, seed=7)
+    prev = None
+    for t in range(0, 120, 12):
+        p = wl.fall(pos, t)
+        h = hy.from_particles(p, ext, B, L, per)
+        # every particle sits in a stored level-0 block
+        b = np.floor(p / 8).astype(int)
+        assert h.stored[0][b[:, 2], b[:, 1], b[:, 0]].all()
+        for l in range(L):
+            assert not (h.stored[l] & h.I[l]).any()
+            if l < L - 1:
+                # every stored block's parent is stored or internal at level l+1
+                par = hy.parent(h.stored[l])
+                assert not (par & ~(h.stored[l + 1] | h.I[l + 1])).any()
+            if l > 0:
+                # coverage: the level-l region covered by finer blocks is H_l
+                assert (hy.parent(h.stored[l - 1] | h.I[l - 1]) == h.H[l]).all()
+        # the domain is partitioned by owned nodes: volumes add up
+        vol = sum(h.owned_nodes(l).sum() * 8 ** l for l in range(L))
+        assert vol == ext[0] * ext[1] * ext[2]
+        # I^d nodes interpolate from stored, non-interface coarse nodes
+        for l in range(L - 1):
+            d = np.nonzero(h.down_nodes(l))
+            upd = h.stored_nodes(l + 1) & ~h.missing_nodes(l + 1)
+            for axis_sel in itertools.product((0, 1), repeat=3):
+                cz = (d[0] + axis_sel[0]) // 2
+                cy = np.minimum((d[1] + axis_sel[1]) // 2, upd.shape[1] - 1)
+                cx = ((d[2] + axis_sel[2]) // 2) % upd.shape[2]
+                cz = cz % upd.shape[0]
+                assert upd[cz, cy, cx].all()
+            # I^u coarse nodes read a stored, non-interface fine node
+            u = np.nonzero(h.up_nodes(l + 1))
+            updf = h.stored_nodes(l) & ~h.missing_nodes(l)
+            assert updf[2 * u[0], 2 * u[1], 2 * u[2]].all()
+        if prev is not None:
+            f = h.flags(1, prev)
+            assert f.dtype == np.uint8 and len(f) == len(h.blocks(1))
+        prev = h
+
+
+def test_empty_occupancy_is_single_coarse_level():
+    ext = (64, 64, 64)
+    h = hy.from_particles(np.zeros((0, 3), np.float32), ext, 8, 3, (True, True, True))
+    assert len(h.blocks(0)) == 0 and len(h.blocks(1)) == 0
+    assert len(h.blocks(2)) == 8
+    assert h.missing_nodes(2).sum() == 0
+
+
+# ------------------------------------------------------------ rescaling
+
+@pytest.mark.parametrize("tau", [0.6, 0.7, 1.3])
+def test_post_collision_sneq_law(tau):
+    """S'^neq_xy / (du_x/dy) = -c_s^2 (tau - 1) in the simulated shear-wave dynamics.
+
+    Measured on the Fourier mode, so the O(k^2) lattice error is 5e-4 at n=64.
+    """
+    n, A = 64, 1e-3
+    M = sl.run(torch.tensor(wl.shear_wave((1, n, 1), A)), 120, tau)
+    k = 2 * math.pi / n
+    y = torch.arange(n)
+    a = (M[1][0, :, 0] * torch.sin(k * y)).sum() * 2 / n
+    b = ((M[7] - M[1] * M[2])[0, :, 0] * torch.cos(k * y)).sum() * 2 / n
+    assert abs((b / (a * k)).item() / (-(tau - 1) / 3) - 1) < 2e-3
+
+
+def test_rescale_factors_inverse_and_level_taus():
+    t = ml.level_taus(0.9, 3)
+    assert t == [0.9, 0.7, 0.6]
+    for mode in ("post", "pre"):
+        ku, kd = ml.rescale_factors(0.9, 0.7, mode)
+        assert abs(ku * kd - 1) < 1e-15
+    ku, kd = ml.rescale_factors(0.9, 0.7, "post")
+    assert abs(ku - 2 * (0.7 - 1) / (0.9 - 1)) < 1e-15
+    # nu_{l+1} = nu_l / 2 in the level's own lattice units (Sec. 4.2)
+    for l in range(2):
+        assert abs((t[l + 1] - 0.5) / 3 - 0.5 * (t[l] - 0.5) / 3) < 1e-15
+
+
+# ------------------------------------------------------------ multi-level dynamics
+
+def _init(m, fn):
+    for l in range(m.L):
+        X, Y, Z = m.node_positions(l)
+        m.set_level(l, fn(X, Y, Z))
+
+
+def test_uniform_flow_uniform_across_levels():
+    # 4^3 blocks keep all three levels non-empty on a small domain
+    ext, L, B = (96, 96, 96), 3, 4
+    O0 = np.zeros(hy.block_dims(ext, B, 0), bool)
+    O0[11:13, 11, 11:14] = True
+    h = hy.Hierarchy(O0, ext, B, L, (True, True, True))
+    assert all(len(h.blocks(l)) > 0 for l in range(L))
+    u = (0.05, -0.02, 0.01)
+    m = ml.MultiLevel(h, 0.9)
+    _init(m, lambda X, Y, Z: wl.equilibrium_field(np.ones_like(X), *(np.full_like(X, v) for v in u)))
+    ref = [m.current(l).clone() for l in range(L)]
+    for _ in range(2):
+        m.coarse_step()
+    for l in range(L):
+        st = m.stored[l]
+        assert ((m.current(l) - ref[l])[:, st]).abs().max() < 1e-14
+
+
+def _shear_setup(tau0, rescale):
+    ext, B, L = (16, 128, 16), 8, 2
+    O0 = np.zeros(hy.block_dims(ext, B, 0), bool)
+    O0[:, 7:9, :] = True
+    h = hy.Hierarchy(O0, ext, B, L, (True, True, True))
+    A = 0.01
+
+    def field(X, Y, Z):
+        ux = A * np.sin(2 * np.pi * Y / 128)
+        z0 = np.zeros_like(ux)
+        return wl.equilibrium_field(np.ones_like(ux), ux, z0, z0)
+
+    m = ml.MultiLevel(h, tau0, rescale=rescale)
+    _init(m, field)
+    z, y, x = np.meshgrid(np.arange(16), np.arange(128), np.arange(16), indexing="ij")
+    return m, torch.tensor(field(x, y, z)), A
+
+
+def test_shear_wave_across_interface_tracks_fine_solution():
+    """u_x = A sin(2 pi y / 128) with a refined slab y in [32, 96): after 120 fine
+    steps both levels track the all-fine single-level solution; the post-collision
+    reading of the S^neq factor has the smallest error, the printed factors the largest."""
+    errs = {}
+    for rescale in ("post", "pre", "paper"):
+        m, ref0, A = _shear_setup(0.8, rescale)
+        ref = sl.run(ref0, 120, 0.8)
+        for _ in range(60):
+            m.coarse_step()
+        e0 = ((m.current(0) - ref)[1][m.update[0]]).abs().max().item() / A
+        e1 = ((m.current(1) - ref[:, 0::2, 0::2, 0::2])[1][m.update[1]]).abs().max().item() / A
+        errs[rescale] = (e0, e1)
+    assert errs["post"][0] < 3e-3 and errs["post"][1] < 2e-3
+    assert errs["post"][1] < errs["pre"][1] < errs["paper"][1]
+    assert errs["post"][0] < errs["paper"][0]
+
+
+def test_rebuild_keeps_uniform_flow_and_sources_every_node():
+    ext, L, B = (96, 96, 96), 3, 4
+    u = (0.03, 0.0, -0.01)
+    fn = lambda X, Y, Z: wl.equilibrium_field(np.ones_like(X), *(np.full_like(X, v) for v in u))
+    O0 = np.zeros(hy.block_dims(ext, B, 0), bool)
+    O0[1, 1, 1] = True
+    h = hy.Hierarchy(O0, ext, B, L, (True, True, True))
+    assert all(len(h.blocks(l)) > 0 for l in range(L))
+    m = ml.MultiLevel(h, 0.9)
+    _init(m, fn)
+    m.coarse_step()
+    for shift in (1, 2, 3):
+        O1 = np.zeros_like(O0)
+        O1[1 + shift // 2, 1, 1 + 2 * shift] = True
+        m.rebuild(hy.Hierarchy(O1, ext, B, L, (True, True, True)))
+        m.coarse_step()
+        for l in range(L):
+            st = m.stored[l]
+            vals = m.current(l)[:, st]
+            assert torch.isfinite(vals).all()
+            assert (vals[1] - u[0]).abs().max() < 1e-13
+
+
+def test_two_level_tgv_close_to_fine_solution():
+    """2D TGV (128^2 x 16) with a refined patch: multi-level vs all-fine, error
+    bounded by a few percent of U0 (interface interpolation order)."""
+    n, nz, u0, tau = 128, 16, 0.02, 0.8
+    ext = (n, n, nz)
+    O0 = np.zeros(hy.block_dims(ext, 8, 0), bool)
+    O0[:, 7:9, 7:9] = True
+    h = hy.Hierarchy(O0, ext, 8, 2, (True, True, True))
+    assert len(h.blocks(1)) > 0
+    m = ml.MultiLevel(h, tau)
+    k = 2 * np.pi / n
+
+    def field(X, Y, Z):
+        ux = u0 * np.sin(k * X) * np.cos(k * Y)
+        uy = -u0 * np.cos(k * X) * np.sin(k * Y)
+        rho = 1.0 - 3.0 * u0 * u0 / 4.0 * (np.cos(2 * k * X) + np.cos(2 * k * Y))
+        return wl.equilibrium_field(rho, ux, uy, np.zeros_like(ux))
+
+    _init(m, field)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(n), np.arange(n), indexing="ij")
+    ref = sl.run(torch.tensor(field(x, y, z)), 40, tau)
+    for _ in range(20):
+        m.coarse_step()
+    e0 = ((m.current(0) - ref)[1:3][:, m.update[0]]).abs().max().item() / u0
+    e1 = ((m.current(1) - ref[:, 0::2, 0::2, 0::2])[1:3][:, m.update[1]]).abs().max().item() / u0
+    assert e0 < 0.02 and e1 < 0.02
+
+
+def test_reduce_partitions_mass():
+    ext, L = (64, 64, 64), 3
+    O0 = np.zeros(hy.block_dims(ext, 8, 0), bool)
+    O0[2, 2, 2] = True
+    h = hy.Hierarchy(O0, ext, 8, L, (True, True, True))
+    m = ml.MultiLevel(h, 0.9)
+    _init(m, lambda X, Y, Z: wl.equilibrium_field(np.full_like(X, 1.25), *(np.zeros_like(X),) * 3))
+    r = m.reduce()
+    assert abs(r[0] - 1.25 * 64 ** 3) < 1e-9
+    assert abs(r[5] + r[6] - r[0]) < 1e-9
