@@ -1,0 +1,150 @@
+/*
+ * homelbm.h -- C ABI of the GB300 moment-encoded multi-level lattice Boltzmann
+ * hot path (libhomelbm.so).
+ *
+ * The library advances the moment set M = {rho, u, S} of the paper's HOME-LBM
+ * scheme (Sec. 3.1, Eq. rho_u_stress and Eq. three_order_f) on a block-sparse,
+ * multi-level D3Q27 lattice (Sec. 4.1, Sec. 5.1), with the sub-cycled advance of
+ * Algorithm 1 and the fine<->coarse transfers of Eq. downward_rescale and
+ * Eq. upload_S, and rebuilds the block hierarchy from a particle cloud through
+ * the level-selection function Phi (Sec. 4.3, Sec. 5.3).
+ *
+ * Conventions
+ *  - Every call returns an hlbm_status (int32).  Nothing aborts and no C++
+ *    exception crosses the ABI.  hlbm_last_error() gives a message owned by the
+ *    handle (valid until the next call on that handle).
+ *  - A handle is not thread-safe; calls on one handle must be serialised.
+ *  - All device work is enqueued on the stream given in hlbm_config (borrowed,
+ *    never destroyed; NULL = the legacy default stream).  Calls that return
+ *    data to host memory synchronise that stream.
+ *  - Blocks are cubes of 8^3 nodes.  A block-major field of one level has the
+ *    layout [n_blocks][rows][512] with the node index x + 8 y + 64 z inside the
+ *    block, blocks in ascending linear slot id bz*(nby*nbx) + by*nbx + bx.
+ *  - Moment rows: 0 rho, 1 u_x, 2 u_y, 3 u_z, 4 S_xx, 5 S_yy, 6 S_zz, 7 S_xy,
+ *    8 S_xz, 9 S_yz.  The stored set is the POST-collision one, so the stored
+ *    velocity is u' = u + F/(2 rho) (Eq. rho_u_stress read with Guo forcing).
+ *  - Level 0 is the finest.  A node of level l sits at fine position
+ *    2^l * index (vertex-aligned levels).
+ */
+#ifndef HOMELBM_H
+#define HOMELBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HLBM_OK = 0,
+  HLBM_E_INVALID_ARG = 1, /* bad pointer, size, level or configuration */
+  HLBM_E_BAD_STATE = 2,   /* call out of order, e.g. step before blocks are set */
+  HLBM_E_OOM = 3,         /* device or host allocation failed */
+  HLBM_E_CUDA = 4,        /* a CUDA runtime call failed; message has the CUDA error */
+  HLBM_E_NONFINITE = 5,   /* an input field or a reduction is not finite */
+  HLBM_E_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+  HLBM_E_UNSUPPORTED = 7  /* valid request this build does not implement */
+} hlbm_status;
+
+typedef enum {
+  HLBM_STORE_F64 = 0,   /* 80 B per node */
+  HLBM_STORE_F32 = 1,   /* 40 B per node */
+  HLBM_STORE_F16S = 2,  /* 20 B per node: fp16 x per-row power-of-two scale */
+  HLBM_STORE_BF16S = 3  /* 20 B per node: bf16 x per-row power-of-two scale */
+} hlbm_storage;
+
+typedef enum {
+  /* S^neq of the stored post-collision moments scales with (tau-1) times the
+     lattice velocity gradient: k_up = 2 (tau_c-1)/(tau_f-1), k_down = 1/k_up. */
+  HLBM_RESCALE_POST = 0,
+  /* Chapman-Enskog scaling of the pre-collision S^neq: k_up = 2 tau_c/tau_f. */
+  HLBM_RESCALE_PRE = 1,
+  /* factors as printed in Eq. upload_S (tau_c/(2 tau_f)) and
+     Eq. downward_rescale (2 tau_c/tau_f). */
+  HLBM_RESCALE_PAPER = 2
+} hlbm_rescale;
+
+typedef struct {
+  int32_t nx, ny, nz;      /* fine-equivalent extent; multiples of 8*2^(L-1) */
+  int32_t block_edge;      /* must be 8 */
+  int32_t num_levels;      /* L >= 1 */
+  double tau_finest;       /* tau_0 > 1/2; tau_{l+1} = tau_l/2 + 1/4 (Sec. 4.2) */
+  int32_t periodic[3];     /* per axis x, y, z; non-periodic faces are half-way bounce-back walls */
+  int32_t storage;         /* hlbm_storage */
+  int32_t rescale_mode;    /* hlbm_rescale */
+  int32_t xyz_literal;     /* 0: third-order xyz weight 1/c_s^6 (Hermite series);
+                              1: 1/(2 c_s^6) as printed after Eq. three_order_f */
+  void *stream;            /* cudaStream_t, borrowed */
+  int32_t device;          /* CUDA device ordinal */
+} hlbm_config;
+
+typedef struct hlbm_lattice hlbm_lattice;
+
+/* Library version string (static). */
+const char *hlbm_version(void);
+
+/* Create a lattice.  No blocks are stored until hlbm_set_blocks,
+   hlbm_set_dense or hlbm_rebuild_from_particles.  *out is NULL on failure. */
+int32_t hlbm_create(const hlbm_config *cfg, hlbm_lattice **out);
+
+/* Free every device and host resource of the handle.  NULL is accepted. */
+int32_t hlbm_destroy(hlbm_lattice *h);
+
+/* Message of the last failed call on h (or of the last failed hlbm_create when
+   h is NULL).  Owned by the library. */
+const char *hlbm_last_error(const hlbm_lattice *h);
+
+/* Store every block of a single-level lattice (L must be 1).  Moments are set
+   to rest (rho = 1, u = 0, S = 0). */
+int32_t hlbm_set_dense(hlbm_lattice *h);
+
+/* Number of stored blocks of a level. */
+int32_t hlbm_num_blocks(const hlbm_lattice *h, int32_t level, int64_t *n);
+
+/* Copy the stored block coordinates (bx, by, bz) of a level into out[cap][3]
+   (host memory), ascending slot order, and optionally one flag byte per block
+   (bit 0 leaf, bit 1 border, bit 2 new, bit 3 refine, bit 4 coarsen; Sec. 5.1,
+   Sec. 5.3).  If cap < n, returns HLBM_E_INVALID_ARG with *n set. */
+int32_t hlbm_get_blocks(const hlbm_lattice *h, int32_t level, int32_t *out, int64_t cap,
+                        int64_t *n, uint8_t *flags_out);
+
+/* Uniform body force F (lattice units) at level 0 (Sec. 4, force F). */
+int32_t hlbm_set_uniform_force(hlbm_lattice *h, double fx, double fy, double fz);
+
+/* Per-node force F[n_blocks0][3][512] and fluid fraction eps[n_blocks0][512]
+   (float32, device memory, level-0 block order) for the forcing and the mixture
+   relaxation time eps*tau of Sec. 4.  Copied device-to-device; eps may be NULL
+   (eps = 1).  F may be NULL to return to the uniform force. */
+int32_t hlbm_set_force(hlbm_lattice *h, const float *F_dev, const float *eps_dev);
+
+/* Solid nodes of a single-level lattice, one byte per fine node (host memory,
+   dense [nz][ny][nx], non-zero = solid).  Solid nodes are frozen at rest and
+   fluid nodes next to them use half-way bounce-back.  NULL clears. */
+int32_t hlbm_set_solid(hlbm_lattice *h, const uint8_t *mask_dense);
+
+/* Write / read the stored moments of a level, block-major [n][10][512].
+   dtype 0 = float64, 1 = float32.  on_device 0 = host pointer, 1 = device
+   pointer.  For reads, physical_u = 1 returns u = u' - F/(2 rho) at level 0. */
+int32_t hlbm_write_moments(hlbm_lattice *h, int32_t level, const void *buf, int32_t dtype,
+                           int32_t on_device);
+int32_t hlbm_read_moments(hlbm_lattice *h, int32_t level, void *buf, int32_t dtype,
+                          int32_t on_device, int32_t physical_u);
+
+/* Advance n_fine_steps finest-level steps (Algorithm 1 called
+   n_fine_steps / 2^(L-1) times); n_fine_steps must be a multiple of 2^(L-1).
+   Asynchronous on the handle's stream. */
+int32_t hlbm_step(hlbm_lattice *h, int32_t n_fine_steps);
+
+/* Wait for the handle's stream. */
+int32_t hlbm_synchronize(hlbm_lattice *h);
+
+/* FP64 reductions over nodes not covered by a finer level, weighted by the
+   cell volume 8^l: out[0] mass, out[1..3] momentum (physical u), out[4]
+   kinetic energy, out[5] mass at level 0, out[6] mass at the other levels.
+   Synchronous.  Returns HLBM_E_NONFINITE if the mass is not finite. */
+int32_t hlbm_reduce(hlbm_lattice *h, double out[7]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOMELBM_H */

@@ -1,0 +1,478 @@
+// api.cu -- the C ABI of libhomelbm.so (declared in include/homelbm.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hlbm_internal.h"
+#include "io_reduce.h"
+#include "lattice_state.h"
+
+using namespace hlbm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(hlbm_lattice* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h)
+    h->err = buf;
+  else
+    g_create_error = buf;
+  return code;
+}
+
+#define HLBM_CUDA(h, call)                                                                      \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) return fail((h), HLBM_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t storage_bytes(int storage) {
+  switch (storage) {
+    case HLBM_STORE_F64: return 8;
+    case HLBM_STORE_F32: return 4;
+    default: return 2;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- helpers (lattice_state.h)
+
+namespace hlbm {
+
+int LatticeOps::set_device(hlbm_lattice* h) {
+  HLBM_CUDA(h, cudaSetDevice(h->cfg.device));
+  return HLBM_OK;
+}
+
+int LatticeOps::alloc(hlbm_lattice* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return HLBM_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(h, HLBM_E_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  return HLBM_OK;
+}
+
+void LatticeOps::release(void*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void LatticeOps::free_level(LevelData& L) {
+  release(L.d_mom[0]);
+  release(L.d_mom[1]);
+  void* v = L.d_nbr;
+  release(v);
+  L.d_nbr = nullptr;
+  v = L.d_bflags;
+  release(v);
+  L.d_bflags = nullptr;
+  v = L.d_solid;
+  release(v);
+  L.d_solid = nullptr;
+  v = L.d_skip;
+  release(v);
+  L.d_skip = nullptr;
+  L.nb = 0;
+  L.coords.clear();
+  L.flags.clear();
+}
+
+// Host-side neighbour table of a block list on the level's block grid.
+void LatticeOps::build_nbr(const hlbm_lattice* h, int level, const std::vector<int32_t>& coords,
+                           const std::vector<int32_t>& slot_to_idx, std::vector<int32_t>& nbr) {
+  int dims[3];
+  h->block_dims(level, dims);
+  const int64_t nb = int64_t(coords.size() / 3);
+  nbr.assign(size_t(nb) * 27, kMissing);
+  for (int64_t b = 0; b < nb; ++b) {
+    for (int d = 0; d < 27; ++d) {
+      const int off[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+      int q[3];
+      bool wall = false;
+      for (int a = 0; a < 3; ++a) {
+        q[a] = coords[b * 3 + a] + off[a];
+        if (q[a] < 0 || q[a] >= dims[a]) {
+          if (h->cfg.periodic[a])
+            q[a] = (q[a] + dims[a]) % dims[a];
+          else
+            wall = true;
+        }
+      }
+      if (wall) {
+        nbr[b * 27 + d] = kWall;
+        continue;
+      }
+      const int64_t slot = (int64_t(q[2]) * dims[1] + q[1]) * dims[0] + q[0];
+      nbr[b * 27 + d] = slot_to_idx[slot];
+    }
+  }
+}
+
+}  // namespace hlbm
+
+// ---------------------------------------------------------------- ABI
+
+extern "C" {
+
+const char* hlbm_version(void) { return "homelbm-gb300 0.1 (sm_103a)"; }
+
+const char* hlbm_last_error(const hlbm_lattice* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int32_t hlbm_create(const hlbm_config* cfg, hlbm_lattice** out) {
+  if (out == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (cfg == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "cfg is NULL");
+  if (cfg->block_edge != 8) return fail(nullptr, HLBM_E_INVALID_ARG, "block_edge must be 8 (got %d)", cfg->block_edge);
+  if (cfg->num_levels < 1 || cfg->num_levels > 8)
+    return fail(nullptr, HLBM_E_INVALID_ARG, "num_levels must be in [1, 8] (got %d)", cfg->num_levels);
+  const int64_t unit = int64_t(8) << (cfg->num_levels - 1);
+  const int32_t ext[3] = {cfg->nx, cfg->ny, cfg->nz};
+  for (int a = 0; a < 3; ++a)
+    if (ext[a] <= 0 || ext[a] % unit != 0)
+      return fail(nullptr, HLBM_E_INVALID_ARG, "extent %d on axis %d is not a positive multiple of %lld", ext[a], a,
+                  (long long)unit);
+  if (!(cfg->tau_finest > 0.5) || !std::isfinite(cfg->tau_finest))
+    return fail(nullptr, HLBM_E_INVALID_ARG, "tau_finest must be finite and > 1/2");
+  if (cfg->storage < HLBM_STORE_F64 || cfg->storage > HLBM_STORE_BF16S)
+    return fail(nullptr, HLBM_E_INVALID_ARG, "unknown storage %d", cfg->storage);
+  if (cfg->storage == HLBM_STORE_F16S || cfg->storage == HLBM_STORE_BF16S)
+    return fail(nullptr, HLBM_E_UNSUPPORTED, "reduced-precision storage is not built yet");
+  if (cfg->rescale_mode < HLBM_RESCALE_POST || cfg->rescale_mode > HLBM_RESCALE_PAPER)
+    return fail(nullptr, HLBM_E_INVALID_ARG, "unknown rescale_mode %d", cfg->rescale_mode);
+  if (cfg->num_levels > 1) return fail(nullptr, HLBM_E_UNSUPPORTED, "multi-level lattices are not built yet");
+  hlbm_lattice* h = new (std::nothrow) hlbm_lattice();
+  if (h == nullptr) return fail(nullptr, HLBM_E_OOM, "host allocation failed");
+  h->cfg = *cfg;
+  h->stream = static_cast<cudaStream_t>(cfg->stream);
+  h->lv.resize(cfg->num_levels);
+  double tau = cfg->tau_finest;
+  for (int l = 0; l < cfg->num_levels; ++l) {
+    h->lv[l].tau = tau;
+    tau = tau / 2.0 + 0.25;  // Sec. 4.2 with k = 1
+  }
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e != cudaSuccess) {
+    fail(nullptr, HLBM_E_CUDA, "cudaSetDevice(%d): %s", cfg->device, cudaGetErrorString(e));
+    delete h;
+    return HLBM_E_CUDA;
+  }
+  *out = h;
+  return HLBM_OK;
+}
+
+int32_t hlbm_destroy(hlbm_lattice* h) {
+  if (h == nullptr) return HLBM_OK;
+  cudaSetDevice(h->cfg.device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& L : h->lv) LatticeOps::free_level(L);
+  LatticeOps::release(h->d_stage);
+  void* v = h->d_red;
+  LatticeOps::release(v);
+  v = h->d_F;
+  LatticeOps::release(v);
+  v = h->d_eps;
+  LatticeOps::release(v);
+  delete h;
+  return HLBM_OK;
+}
+
+int32_t hlbm_set_dense(hlbm_lattice* h) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (h->cfg.num_levels != 1) return fail(h, HLBM_E_INVALID_ARG, "hlbm_set_dense needs a single-level lattice");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  LevelData& L = h->lv[0];
+  LatticeOps::free_level(L);
+  int dims[3];
+  h->block_dims(0, dims);
+  const int64_t nb = int64_t(dims[0]) * dims[1] * dims[2];
+  L.coords.resize(size_t(nb) * 3);
+  std::vector<int32_t> slot_to_idx(static_cast<size_t>(nb));
+  for (int64_t s = 0; s < nb; ++s) {
+    L.coords[s * 3 + 0] = int32_t(s % dims[0]);
+    L.coords[s * 3 + 1] = int32_t((s / dims[0]) % dims[1]);
+    L.coords[s * 3 + 2] = int32_t(s / (int64_t(dims[0]) * dims[1]));
+    slot_to_idx[s] = int32_t(s);
+  }
+  L.flags.assign(size_t(nb), 1);  // leaf
+  std::vector<int32_t> nbr;
+  LatticeOps::build_nbr(h, 0, L.coords, slot_to_idx, nbr);
+  L.nb = nb;
+  const size_t mom_bytes = size_t(nb) * kRows * kCells * storage_bytes(h->cfg.storage);
+  void* p = nullptr;
+  if ((rc = LatticeOps::alloc(h, &p, nbr.size() * sizeof(int32_t)))) return rc;
+  L.d_nbr = static_cast<int32_t*>(p);
+  for (int k = 0; k < 2; ++k)
+    if ((rc = LatticeOps::alloc(h, &L.d_mom[k], mom_bytes))) return rc;
+  HLBM_CUDA(h, cudaMemcpyAsync(L.d_nbr, nbr.data(), nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  // rest state: delta_rho = u = S = 0 is all-zero bits in every storage
+  for (int k = 0; k < 2; ++k) HLBM_CUDA(h, cudaMemsetAsync(L.d_mom[k], 0, mom_bytes, h->stream));
+  L.cur = 0;
+  HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->have_blocks = true;
+  return HLBM_OK;
+}
+
+int32_t hlbm_num_blocks(const hlbm_lattice* h, int32_t level, int64_t* n) {
+  if (h == nullptr || n == nullptr) return HLBM_E_INVALID_ARG;
+  if (level < 0 || level >= h->cfg.num_levels)
+    return fail(const_cast<hlbm_lattice*>(h), HLBM_E_INVALID_ARG, "level %d out of range", level);
+  *n = h->lv[level].nb;
+  return HLBM_OK;
+}
+
+int32_t hlbm_get_blocks(const hlbm_lattice* h, int32_t level, int32_t* out, int64_t cap, int64_t* n,
+                        uint8_t* flags_out) {
+  hlbm_lattice* hm = const_cast<hlbm_lattice*>(h);
+  if (h == nullptr || n == nullptr) return fail(hm, HLBM_E_INVALID_ARG, "NULL argument");
+  if (level < 0 || level >= h->cfg.num_levels) return fail(hm, HLBM_E_INVALID_ARG, "level %d out of range", level);
+  const LevelData& L = h->lv[level];
+  *n = L.nb;
+  if (cap < L.nb) return fail(hm, HLBM_E_INVALID_ARG, "capacity %lld < %lld blocks", (long long)cap, (long long)L.nb);
+  if (L.nb > 0 && out == nullptr) return fail(hm, HLBM_E_INVALID_ARG, "out is NULL");
+  if (L.nb > 0) std::memcpy(out, L.coords.data(), size_t(L.nb) * 3 * sizeof(int32_t));
+  if (flags_out && L.nb > 0) std::memcpy(flags_out, L.flags.data(), size_t(L.nb));
+  return HLBM_OK;
+}
+
+int32_t hlbm_set_uniform_force(hlbm_lattice* h, double fx, double fy, double fz) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (!std::isfinite(fx) || !std::isfinite(fy) || !std::isfinite(fz))
+    return fail(h, HLBM_E_NONFINITE, "force is not finite");
+  h->fu[0] = fx;
+  h->fu[1] = fy;
+  h->fu[2] = fz;
+  return HLBM_OK;
+}
+
+int32_t hlbm_set_force(hlbm_lattice* h, const float* F_dev, const float* eps_dev) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (!h->have_blocks) return fail(h, HLBM_E_BAD_STATE, "set blocks before the force field");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  const int64_t n = h->lv[0].nb * kCells;
+  void* v = h->d_F;
+  LatticeOps::release(v);
+  h->d_F = nullptr;
+  v = h->d_eps;
+  LatticeOps::release(v);
+  h->d_eps = nullptr;
+  if (F_dev) {
+    void* p;
+    if ((rc = LatticeOps::alloc(h, &p, size_t(n) * 3 * sizeof(float)))) return rc;
+    h->d_F = static_cast<float*>(p);
+    HLBM_CUDA(h, cudaMemcpyAsync(h->d_F, F_dev, size_t(n) * 3 * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  }
+  if (eps_dev) {
+    void* p;
+    if ((rc = LatticeOps::alloc(h, &p, size_t(n) * sizeof(float)))) return rc;
+    h->d_eps = static_cast<float*>(p);
+    HLBM_CUDA(h, cudaMemcpyAsync(h->d_eps, eps_dev, size_t(n) * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  }
+  HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return HLBM_OK;
+}
+
+int32_t hlbm_set_solid(hlbm_lattice* h, const uint8_t* mask) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (h->cfg.num_levels != 1) return fail(h, HLBM_E_UNSUPPORTED, "solid nodes need a single-level lattice");
+  if (!h->have_blocks) return fail(h, HLBM_E_BAD_STATE, "set blocks before the solid mask");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  LevelData& L = h->lv[0];
+  void* v = L.d_solid;
+  LatticeOps::release(v);
+  L.d_solid = nullptr;
+  v = L.d_bflags;
+  LatticeOps::release(v);
+  L.d_bflags = nullptr;
+  if (mask == nullptr) return HLBM_OK;
+  int dims[3];
+  h->block_dims(0, dims);
+  const int nx = h->cfg.nx, ny = h->cfg.ny;
+  std::vector<uint8_t> bm(size_t(L.nb) * kCells), own(size_t(L.nb), 0), fl(size_t(L.nb), 0);
+  for (int64_t b = 0; b < L.nb; ++b) {
+    const int bx = L.coords[b * 3], by = L.coords[b * 3 + 1], bz = L.coords[b * 3 + 2];
+    for (int c = 0; c < kCells; ++c) {
+      const int x = bx * 8 + (c & 7), y = by * 8 + ((c >> 3) & 7), z = bz * 8 + (c >> 6);
+      const uint8_t s = mask[(size_t(z) * ny + y) * nx + x] ? 1 : 0;
+      bm[b * kCells + c] = s;
+      own[b] |= s;
+    }
+  }
+  std::vector<int32_t> nbr(size_t(L.nb) * 27);
+  HLBM_CUDA(h, cudaMemcpy(nbr.data(), L.d_nbr, nbr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  for (int64_t b = 0; b < L.nb; ++b)
+    for (int d = 0; d < 27; ++d) {
+      const int32_t q = nbr[b * 27 + d];
+      if (q >= 0 && own[q]) fl[b] = kBlockSolidNear;
+    }
+  void* p;
+  if ((rc = LatticeOps::alloc(h, &p, bm.size()))) return rc;
+  L.d_solid = static_cast<uint8_t*>(p);
+  if ((rc = LatticeOps::alloc(h, &p, fl.size()))) return rc;
+  L.d_bflags = static_cast<uint8_t*>(p);
+  HLBM_CUDA(h, cudaMemcpy(L.d_solid, bm.data(), bm.size(), cudaMemcpyHostToDevice));
+  HLBM_CUDA(h, cudaMemcpy(L.d_bflags, fl.data(), fl.size(), cudaMemcpyHostToDevice));
+  return HLBM_OK;
+}
+
+static int stage(hlbm_lattice* h, size_t bytes) {
+  if (h->stage_bytes >= bytes) return HLBM_OK;
+  LatticeOps::release(h->d_stage);
+  h->stage_bytes = 0;
+  int rc = LatticeOps::alloc(h, &h->d_stage, bytes);
+  if (rc) return rc;
+  h->stage_bytes = bytes;
+  return HLBM_OK;
+}
+
+int32_t hlbm_write_moments(hlbm_lattice* h, int32_t level, const void* buf, int32_t dtype, int32_t on_device) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (level < 0 || level >= h->cfg.num_levels) return fail(h, HLBM_E_INVALID_ARG, "level %d out of range", level);
+  if (dtype != 0 && dtype != 1) return fail(h, HLBM_E_INVALID_ARG, "dtype must be 0 (f64) or 1 (f32)");
+  if (!h->have_blocks) return fail(h, HLBM_E_BAD_STATE, "no blocks are stored");
+  LevelData& L = h->lv[level];
+  const int64_t n = L.nb * kCells;
+  if (n == 0) return HLBM_OK;
+  if (buf == nullptr) return fail(h, HLBM_E_INVALID_ARG, "buffer is NULL");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  const size_t bytes = size_t(n) * kRows * (dtype == 0 ? 8 : 4);
+  const void* src = buf;
+  if (!on_device) {
+    if ((rc = stage(h, bytes))) return rc;
+    HLBM_CUDA(h, cudaMemcpyAsync(h->d_stage, buf, bytes, cudaMemcpyHostToDevice, h->stream));
+    src = h->d_stage;
+  }
+  HLBM_CUDA(h, import_moments(h->cfg.storage, src, dtype, L.d_mom[L.cur], n, nullptr, h->stream));
+  if (!on_device) HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return HLBM_OK;
+}
+
+int32_t hlbm_read_moments(hlbm_lattice* h, int32_t level, void* buf, int32_t dtype, int32_t on_device,
+                          int32_t physical_u) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (level < 0 || level >= h->cfg.num_levels) return fail(h, HLBM_E_INVALID_ARG, "level %d out of range", level);
+  if (dtype != 0 && dtype != 1) return fail(h, HLBM_E_INVALID_ARG, "dtype must be 0 (f64) or 1 (f32)");
+  if (!h->have_blocks) return fail(h, HLBM_E_BAD_STATE, "no blocks are stored");
+  LevelData& L = h->lv[level];
+  const int64_t n = L.nb * kCells;
+  if (n == 0) return HLBM_OK;
+  if (buf == nullptr) return fail(h, HLBM_E_INVALID_ARG, "buffer is NULL");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  const size_t bytes = size_t(n) * kRows * (dtype == 0 ? 8 : 4);
+  void* dst = buf;
+  if (!on_device) {
+    if ((rc = stage(h, bytes))) return rc;
+    dst = h->d_stage;
+  }
+  const bool phys = physical_u && level == 0;
+  HLBM_CUDA(h, export_moments(h->cfg.storage, L.d_mom[L.cur], dst, dtype, n, nullptr, phys ? h->d_F : nullptr,
+                              h->fu, phys ? 1 : 0, h->stream));
+  if (!on_device) {
+    HLBM_CUDA(h, cudaMemcpyAsync(buf, h->d_stage, bytes, cudaMemcpyDeviceToHost, h->stream));
+    HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return HLBM_OK;
+}
+
+int32_t hlbm_step(hlbm_lattice* h, int32_t n_fine_steps) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (!h->have_blocks) return fail(h, HLBM_E_BAD_STATE, "no blocks are stored");
+  const int32_t per = 1 << (h->cfg.num_levels - 1);
+  if (n_fine_steps < 0 || n_fine_steps % per != 0)
+    return fail(h, HLBM_E_INVALID_ARG, "n_fine_steps must be a non-negative multiple of %d", per);
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  LevelData& L = h->lv[0];
+  StepArgs a{};
+  a.nbr = L.d_nbr;
+  a.F = h->d_F;
+  a.eps = h->d_eps;
+  a.solid = L.d_solid;
+  a.bflags = L.d_bflags;
+  a.fu[0] = h->fu[0];
+  a.fu[1] = h->fu[1];
+  a.fu[2] = h->fu[2];
+  a.tau = L.tau;
+  a.kxyz = h->cfg.xyz_literal ? 13.5 : 27.0;
+  a.nb = L.nb;
+  for (int32_t s = 0; s < n_fine_steps; ++s) {
+    a.in = L.d_mom[L.cur];
+    a.out = L.d_mom[1 - L.cur];
+    HLBM_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
+    L.cur = 1 - L.cur;
+  }
+  return HLBM_OK;
+}
+
+int32_t hlbm_synchronize(hlbm_lattice* h) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return HLBM_OK;
+}
+
+int32_t hlbm_reduce(hlbm_lattice* h, double out[7]) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (out == nullptr) return fail(h, HLBM_E_INVALID_ARG, "out is NULL");
+  if (!h->have_blocks) return fail(h, HLBM_E_BAD_STATE, "no blocks are stored");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  int64_t nbmax = 0;
+  for (auto& L : h->lv) nbmax = L.nb > nbmax ? L.nb : nbmax;
+  const size_t need = size_t(nbmax) * 7 + 2 * 8;
+  if (h->red_n < need) {
+    void* v = h->d_red;
+    LatticeOps::release(v);
+    h->d_red = nullptr;
+    h->red_n = 0;
+    void* p;
+    if ((rc = LatticeOps::alloc(h, &p, need * sizeof(double)))) return rc;
+    h->d_red = static_cast<double*>(p);
+    h->red_n = need;
+  }
+  double* d_out = h->d_red + size_t(nbmax) * 7;  // [0..4] this level, [8..15] unused
+  double total[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int l = 0; l < h->cfg.num_levels; ++l) {
+    LevelData& L = h->lv[l];
+    if (L.nb == 0) continue;
+    HLBM_CUDA(h, cudaMemsetAsync(d_out, 0, 8 * sizeof(double), h->stream));
+    const double vol = std::ldexp(1.0, 3 * l);
+    HLBM_CUDA(h, reduce_level(h->cfg.storage, L.d_mom[L.cur], L.nb, nullptr, L.d_skip, l == 0 ? h->d_F : nullptr,
+                              h->fu, vol, h->d_red, d_out, h->stream));
+    double r[8];
+    HLBM_CUDA(h, cudaMemcpyAsync(r, d_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 5; ++k) total[k] += r[k];
+    if (l == 0)
+      total[5] += r[0];
+    else
+      total[6] += r[0];
+  }
+  std::memcpy(out, total, sizeof(total));
+  if (!std::isfinite(total[0])) return fail(h, HLBM_E_NONFINITE, "mass is not finite");
+  return HLBM_OK;
+}
+
+}  // extern "C"

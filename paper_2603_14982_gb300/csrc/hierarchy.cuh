@@ -1,0 +1,57 @@
+// hierarchy.cuh -- device-side block-hierarchy maintenance (Sec. 4.3, Sec. 5.1, Sec. 5.3).
+//
+// All sets live on dense per-level slot grids (uint8 per block slot, slot id
+// bz*(nby*nbx) + by*nbx + bx).  The rules are the declarative ones:
+//   O_0      level-0 blocks holding a particle (Phi = 0 there)
+//   H_1      = dilate(parent(O_0)),  H_l = dilate(parent(H_{l-1}))
+//   I_l      = {b in H_l : every in-domain 26-neighbour in H_l}
+//   stored_l = children(H_{l+1}) \ I_l  (l < L-1),  all \ I_{L-1} (top)
+//   border   = stored and (in H_l or parent stored), else leaf
+// Stored blocks are compacted in ascending slot order with warp ballots and a
+// block-level scan, which makes the lists unique and order-stable.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace hlbm {
+
+struct GridDims {
+  int nx, ny, nz;  // blocks per axis
+  __host__ __device__ int64_t slots() const { return int64_t(nx) * ny * nz; }
+};
+
+constexpr uint8_t kFlagLeaf = 1, kFlagBorder = 2, kFlagNew = 4, kFlagRefine = 8, kFlagCoarsen = 16;
+
+// Occupancy of level-0 blocks from particle positions (fine-cell units, x y z
+// float32); non-finite positions are counted in *bad and ignored.
+cudaError_t occupancy_from_particles(const float* pos, int64_t n, GridDims d0, uint8_t* occ, int* bad, cudaStream_t s);
+// Occupancy from an explicit list of level-0 block coordinates (device, [n][3]).
+cudaError_t occupancy_from_blocks(const int32_t* coords, int64_t n, GridDims d0, uint8_t* occ, int* bad,
+                                  cudaStream_t s);
+// H = dilate(parent(src)) on the coarser grid `d` (src lives on the 2x finer grid).
+cudaError_t dilate_parent(const uint8_t* src, GridDims dsrc, uint8_t* H, GridDims d, const int periodic[3],
+                          cudaStream_t s);
+// internal and stored sets of one level; Hup = H of level l+1 (null at the top).
+cudaError_t internal_stored(const uint8_t* H, const uint8_t* Hup, GridDims d, GridDims dup, const int periodic[3],
+                            bool has_H, uint8_t* I, uint8_t* stored, cudaStream_t s);
+// Per-slot flags (0 for slots that are not stored).
+cudaError_t slot_flags(const uint8_t* stored, const uint8_t* H, const uint8_t* stored_up, GridDims d, GridDims dup,
+                       const uint8_t* old_stored, const uint8_t* old_H, bool has_old, uint8_t* flags,
+                       cudaStream_t s);
+// Stable compaction of stored slots: slot_to_idx[slot] = index or -1, coords[idx] = (bx,by,bz),
+// list_flags[idx] = flags[slot], skip[idx] = H[slot] (covered by finer).  *count written to
+// count_dev (device int64).  scratch: >= ceil(slots/1024)+1 int64.
+cudaError_t compact_slots(const uint8_t* stored, const uint8_t* flags, const uint8_t* H, GridDims d,
+                          int32_t* slot_to_idx, int32_t* coords, uint8_t* list_flags, uint8_t* skip,
+                          int64_t* scratch, int64_t* count_dev, cudaStream_t s);
+// Neighbour table [nb][27] from a compacted level.
+cudaError_t neighbour_table(const int32_t* coords, int64_t nb, const int32_t* slot_to_idx, GridDims d,
+                            const int periodic[3], int32_t* nbr, cudaStream_t s);
+// Interface node lists of one level: nodes with a 26-neighbour in a block that
+// is not stored; those inside H blocks go to `up` (I^u), the others to `down`
+// (I^d).  Entries are (block << 9) | cell, ascending.  scratch >= 2*nb+2 int64.
+cudaError_t interface_nodes(const int32_t* nbr, const uint8_t* skip, int64_t nb, int32_t* down, int32_t* up,
+                            int64_t* scratch, int64_t* counts_dev, cudaStream_t s);
+
+}  // namespace hlbm

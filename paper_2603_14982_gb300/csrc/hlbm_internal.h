@@ -1,0 +1,38 @@
+// hlbm_internal.h -- internal interfaces between the C ABI and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/homelbm.h"
+#include "storage.cuh"
+
+namespace hlbm {
+
+// Neighbour-table sentinels: a stored block index is >= 0.
+constexpr int32_t kMissing = -1;  // inside the domain but not stored at this level
+constexpr int32_t kWall = -2;     // beyond a non-periodic face of the domain
+
+// Per-block flag bits of the step kernel.
+constexpr uint8_t kBlockSolidNear = 1;  // the block or one of its 26 neighbours holds a solid node
+
+// Arguments of one stream-collide launch over the stored blocks of a level.
+struct StepArgs {
+  const void* in;           // storage [nb][10][512]
+  void* out;                // storage [nb][10][512]
+  const int32_t* nbr;       // [nb][27] neighbour block per direction (dx+1)+3(dy+1)+9(dz+1)
+  const float* F;           // [nb][3][512] force, or null (uniform fu)
+  const float* eps;         // [nb][512] fluid fraction, or null (1)
+  const uint8_t* solid;     // [nb][512] solid node mask, or null
+  const uint8_t* bflags;    // [nb] block flags, or null
+  const Scales* scales_in;  // reduced-precision row scales of `in` (device), else null
+  const Scales* scales_out; // row scales of `out` (device), else null
+  double fu[3];             // uniform force when F is null
+  double tau;               // level relaxation time
+  double kxyz;              // third-order xyz weight (27 or 13.5)
+  int64_t nb;               // number of blocks
+};
+
+cudaError_t launch_stream_collide(int storage, const StepArgs& a, cudaStream_t s);
+
+}  // namespace hlbm

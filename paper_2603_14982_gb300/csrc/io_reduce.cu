@@ -1,0 +1,189 @@
+// io_reduce.cu -- moment import/export between user buffers and storage, and
+// the FP64 reductions (mass, momentum, kinetic energy).
+#include "hlbm_internal.h"
+#include "io_reduce.h"
+
+namespace hlbm {
+namespace {
+
+// One thread per node.  src rows are (rho, u, S) as in the public layout.
+template <typename T, typename In>
+__global__ void k_import(const In* __restrict__ src, T* __restrict__ dst, int64_t n_nodes, const Scales* sc) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  const int64_t blk = i / kCells;
+  const int cell = int(i % kCells);
+  const In* p = src + blk * kRows * kCells + cell;
+  using R = typename StorageTraits<T>::R;
+  Mom<R> m;
+  m.drho = R(double(p[0]) - 1.0);
+  m.ux = R(p[1 * kCells]);
+  m.uy = R(p[2 * kCells]);
+  m.uz = R(p[3 * kCells]);
+  m.sxx = R(p[4 * kCells]);
+  m.syy = R(p[5 * kCells]);
+  m.szz = R(p[6 * kCells]);
+  m.sxy = R(p[7 * kCells]);
+  m.sxz = R(p[8 * kCells]);
+  m.syz = R(p[9 * kCells]);
+  store_node<T>(dst, blk, cell, m, sc);
+}
+
+template <typename T, typename Out>
+__global__ void k_export(const T* __restrict__ src, Out* __restrict__ dst, int64_t n_nodes, const Scales* sc,
+                         const float* __restrict__ F, double fx, double fy, double fz, int physical) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  const int64_t blk = i / kCells;
+  const int cell = int(i % kCells);
+  const auto m = load_node<T>(src, blk, cell, sc);
+  Out* p = dst + blk * kRows * kCells + cell;
+  const double rho = 1.0 + double(m.drho);
+  double ux = m.ux, uy = m.uy, uz = m.uz;
+  if (physical) {
+    if (F != nullptr) {
+      const float* Fp = F + blk * 3 * kCells + cell;
+      fx = Fp[0];
+      fy = Fp[kCells];
+      fz = Fp[2 * kCells];
+    }
+    ux -= 0.5 * fx / rho;
+    uy -= 0.5 * fy / rho;
+    uz -= 0.5 * fz / rho;
+  }
+  p[0] = Out(rho);
+  p[1 * kCells] = Out(ux);
+  p[2 * kCells] = Out(uy);
+  p[3 * kCells] = Out(uz);
+  p[4 * kCells] = Out(m.sxx);
+  p[5 * kCells] = Out(m.syy);
+  p[6 * kCells] = Out(m.szz);
+  p[7 * kCells] = Out(m.sxy);
+  p[8 * kCells] = Out(m.sxz);
+  p[9 * kCells] = Out(m.syz);
+}
+
+// Per-block FP64 partial sums: one CTA of 512 threads per block, warp shuffles
+// then shared memory.  Blocks whose `skip` byte is set (covered by a finer
+// level) contribute zero.  part[blk][7] = mass, momentum (3), KE, 0, 0.
+template <typename T>
+__global__ void __launch_bounds__(512) k_reduce_blocks(const T* __restrict__ src, const Scales* sc,
+                                                      const uint8_t* __restrict__ skip, const float* __restrict__ F,
+                                                      double fx, double fy, double fz, double vol,
+                                                      double* __restrict__ part) {
+  const int64_t blk = blockIdx.x;
+  const int t = threadIdx.x;
+  double v[5] = {0, 0, 0, 0, 0};
+  if (skip == nullptr || skip[blk] == 0) {
+    const auto m = load_node<T>(src, blk, t, sc);
+    const double rho = 1.0 + double(m.drho);
+    if (F != nullptr) {
+      const float* Fp = F + blk * 3 * kCells + t;
+      fx = Fp[0];
+      fy = Fp[kCells];
+      fz = Fp[2 * kCells];
+    }
+    const double ux = double(m.ux) - 0.5 * fx / rho;
+    const double uy = double(m.uy) - 0.5 * fy / rho;
+    const double uz = double(m.uz) - 0.5 * fz / rho;
+    v[0] = rho * vol;
+    v[1] = rho * ux * vol;
+    v[2] = rho * uy * vol;
+    v[3] = rho * uz * vol;
+    v[4] = 0.5 * rho * (ux * ux + uy * uy + uz * uz) * vol;
+  }
+  __shared__ double s[16][5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((t & 31) == 0) s[t >> 5][k] = x;
+  }
+  __syncthreads();
+  if (t < 5) {
+    double x = 0;
+    for (int w = 0; w < 16; ++w) x += s[w][t];
+    part[blk * 7 + t] = x;
+  }
+  if (t == 5 || t == 6) part[blk * 7 + t] = 0.0;
+}
+
+// Sum part[n][7] into out[7] (one CTA; fixed order, deterministic).
+__global__ void __launch_bounds__(256) k_reduce_final(const double* __restrict__ part, int64_t n, double* out) {
+  __shared__ double s[256];
+  for (int k = 0; k < 5; ++k) {
+    double x = 0;
+    for (int64_t i = threadIdx.x; i < n; i += 256) x += part[i * 7 + k];
+    s[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] += s[0];
+    __syncthreads();
+  }
+}
+
+template <typename T>
+cudaError_t import_typed(const void* src, int dtype, void* dst, int64_t n_nodes, const Scales* sc, cudaStream_t s) {
+  const unsigned grid = unsigned((n_nodes + 255) / 256);
+  if (n_nodes == 0) return cudaSuccess;
+  if (dtype == 0)
+    k_import<T, double><<<grid, 256, 0, s>>>(static_cast<const double*>(src), static_cast<T*>(dst), n_nodes, sc);
+  else
+    k_import<T, float><<<grid, 256, 0, s>>>(static_cast<const float*>(src), static_cast<T*>(dst), n_nodes, sc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t export_typed(const void* src, void* dst, int dtype, int64_t n_nodes, const Scales* sc, const float* F,
+                         const double* fu, int physical, cudaStream_t s) {
+  const unsigned grid = unsigned((n_nodes + 255) / 256);
+  if (n_nodes == 0) return cudaSuccess;
+  if (dtype == 0)
+    k_export<T, double><<<grid, 256, 0, s>>>(static_cast<const T*>(src), static_cast<double*>(dst), n_nodes, sc, F,
+                                             fu[0], fu[1], fu[2], physical);
+  else
+    k_export<T, float><<<grid, 256, 0, s>>>(static_cast<const T*>(src), static_cast<float*>(dst), n_nodes, sc, F,
+                                            fu[0], fu[1], fu[2], physical);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t reduce_typed(const void* src, int64_t nb, const Scales* sc, const uint8_t* skip, const float* F,
+                         const double* fu, double vol, double* part, double* out, cudaStream_t s) {
+  if (nb == 0) return cudaSuccess;
+  k_reduce_blocks<T><<<unsigned(nb), 512, 0, s>>>(static_cast<const T*>(src), sc, skip, F, fu[0], fu[1], fu[2], vol,
+                                                  part);
+  k_reduce_final<<<1, 256, 0, s>>>(part, nb, out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define HLBM_DISPATCH(storage, fn, ...)                                   \
+  switch (storage) {                                                      \
+    case HLBM_STORE_F64: return fn<double>(__VA_ARGS__);                  \
+    case HLBM_STORE_F32: return fn<float>(__VA_ARGS__);                   \
+    case HLBM_STORE_F16S: return fn<__half>(__VA_ARGS__);                 \
+    case HLBM_STORE_BF16S: return fn<__nv_bfloat16>(__VA_ARGS__);         \
+    default: return cudaErrorInvalidValue;                                \
+  }
+
+cudaError_t import_moments(int storage, const void* src, int dtype, void* dst, int64_t n_nodes, const Scales* sc,
+                           cudaStream_t s) {
+  HLBM_DISPATCH(storage, import_typed, src, dtype, dst, n_nodes, sc, s)
+}
+
+cudaError_t export_moments(int storage, const void* src, void* dst, int dtype, int64_t n_nodes, const Scales* sc,
+                           const float* F, const double* fu, int physical, cudaStream_t s) {
+  HLBM_DISPATCH(storage, export_typed, src, dst, dtype, n_nodes, sc, F, fu, physical, s)
+}
+
+cudaError_t reduce_level(int storage, const void* src, int64_t nb, const Scales* sc, const uint8_t* skip,
+                         const float* F, const double* fu, double vol, double* part, double* out, cudaStream_t s) {
+  HLBM_DISPATCH(storage, reduce_typed, src, nb, sc, skip, F, fu, vol, part, out, s)
+}
+
+}  // namespace hlbm

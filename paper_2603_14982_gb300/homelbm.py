@@ -1,0 +1,246 @@
+"""Thin ctypes binding of libhomelbm.so (C ABI in include/homelbm.h).
+
+Only argument marshalling lives here: every step of the lattice update runs in
+the library's CUDA kernels.  Host buffers are numpy arrays; device buffers are
+torch CUDA tensors (passed by data pointer).  The binding raises if the library
+is missing -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhomelbm.so")
+
+OK, E_INVALID_ARG, E_BAD_STATE, E_OOM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_UNSUPPORTED = range(8)
+STORE_F64, STORE_F32, STORE_F16S, STORE_BF16S = range(4)
+RESCALE_POST, RESCALE_PRE, RESCALE_PAPER = range(3)
+STORAGE_NAMES = {"f64": STORE_F64, "f32": STORE_F32, "f16s": STORE_F16S, "bf16s": STORE_BF16S}
+RESCALE_NAMES = {"post": RESCALE_POST, "pre": RESCALE_PRE, "paper": RESCALE_PAPER}
+FLAG_LEAF, FLAG_BORDER, FLAG_NEW, FLAG_REFINE, FLAG_COARSEN = 1, 2, 4, 8, 16
+
+
+class HlbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("hlbm status %d: %s" % (code, msg))
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("block_edge", ctypes.c_int32), ("num_levels", ctypes.c_int32),
+        ("tau_finest", ctypes.c_double),
+        ("periodic", ctypes.c_int32 * 3),
+        ("storage", ctypes.c_int32), ("rescale_mode", ctypes.c_int32), ("xyz_literal", ctypes.c_int32),
+        ("stream", ctypes.c_void_p), ("device", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "hlbm_version": (ctypes.c_char_p, []),
+    "hlbm_create": (ctypes.c_int32, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]),
+    "hlbm_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "hlbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "hlbm_set_dense": (ctypes.c_int32, [ctypes.c_void_p]),
+    "hlbm_num_blocks": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
+    "hlbm_get_blocks": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]),
+    "hlbm_set_uniform_force": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "hlbm_set_force": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "hlbm_set_solid": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hlbm_write_moments": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_int32]),
+    "hlbm_read_moments": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_int32]),
+    "hlbm_step": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "hlbm_synchronize": (ctypes.c_int32, [ctypes.c_void_p]),
+    "hlbm_reduce": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def exported_symbols():
+    """Names of the C ABI entry points this binding expects."""
+    return sorted(_SIGS)
+
+
+def load(path=LIB_PATH):
+    """Load libhomelbm.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libhomelbm.so not found at %s: run paper_2603_14982_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(buf):
+    """(pointer, on_device) of a numpy array or a torch tensor."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(buf.ctypes.data), 0
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(buf.data_ptr()), 1 if buf.is_cuda else 0
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _dtype_code(buf):
+    name = str(buf.dtype)
+    if name in ("float64", "torch.float64"):
+        return 0
+    if name in ("float32", "torch.float32"):
+        return 1
+    raise TypeError("moment buffers must be float64 or float32, got %s" % name)
+
+
+class Lattice:
+    """One lattice handle (hlbm_lattice*)."""
+
+    def __init__(self, extent, levels=1, tau=0.6, periodic=(True, True, True), storage="f32",
+                 rescale="post", xyz_literal=False, stream=None, device=0):
+        self.lib = load()
+        cfg = Config()
+        cfg.nx, cfg.ny, cfg.nz = (int(v) for v in extent)
+        cfg.block_edge = 8
+        cfg.num_levels = int(levels)
+        cfg.tau_finest = float(tau)
+        for a in range(3):
+            cfg.periodic[a] = 1 if periodic[a] else 0
+        cfg.storage = STORAGE_NAMES[storage] if isinstance(storage, str) else int(storage)
+        cfg.rescale_mode = RESCALE_NAMES[rescale] if isinstance(rescale, str) else int(rescale)
+        cfg.xyz_literal = 1 if xyz_literal else 0
+        cfg.stream = ctypes.c_void_p(int(stream) if stream is not None else 0)
+        cfg.device = int(device)
+        self.cfg = cfg
+        self.extent = tuple(int(v) for v in extent)
+        self.levels = int(levels)
+        h = ctypes.c_void_p()
+        rc = self.lib.hlbm_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != OK:
+            raise HlbmError(rc, self.lib.hlbm_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise HlbmError(rc, self.lib.hlbm_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- blocks
+    def set_dense(self):
+        self._check(self.lib.hlbm_set_dense(self.h))
+
+    def num_blocks(self, level=0):
+        n = ctypes.c_int64()
+        self._check(self.lib.hlbm_num_blocks(self.h, level, ctypes.byref(n)))
+        return n.value
+
+    def blocks(self, level=0):
+        """(coords int32 (n, 3) as (bx, by, bz), flags uint8 (n,)) in slot order."""
+        n = self.num_blocks(level)
+        out = np.zeros((max(n, 1), 3), dtype=np.int32)
+        fl = np.zeros(max(n, 1), dtype=np.uint8)
+        nn = ctypes.c_int64()
+        self._check(self.lib.hlbm_get_blocks(self.h, level, out.ctypes.data, n, ctypes.byref(nn), fl.ctypes.data))
+        return out[:n], fl[:n]
+
+    # ---- inputs
+    def set_uniform_force(self, fx, fy, fz):
+        self._check(self.lib.hlbm_set_uniform_force(self.h, float(fx), float(fy), float(fz)))
+
+    def set_force(self, F=None, eps=None):
+        """F: torch CUDA float32 [n0][3][512] (or None), eps: [n0][512] (or None)."""
+        pF = _ptr(F)[0] if F is not None else None
+        pe = _ptr(eps)[0] if eps is not None else None
+        self._check(self.lib.hlbm_set_force(self.h, pF, pe))
+
+    def set_solid(self, mask_dense):
+        """mask_dense: numpy uint8/bool [nz][ny][nx] (fine nodes), or None."""
+        if mask_dense is None:
+            self._check(self.lib.hlbm_set_solid(self.h, None))
+            return
+        m = np.ascontiguousarray(mask_dense, dtype=np.uint8)
+        self._check(self.lib.hlbm_set_solid(self.h, m.ctypes.data))
+
+    # ---- moments
+    def write_moments(self, buf, level=0):
+        p, dev = _ptr(buf)
+        self._check(self.lib.hlbm_write_moments(self.h, level, p, _dtype_code(buf), dev))
+
+    def read_moments(self, buf=None, level=0, physical_u=False, dtype=np.float64):
+        """Fill ``buf`` (numpy host array or torch CUDA tensor, [n][10][512]) and return it."""
+        if buf is None:
+            buf = np.empty((self.num_blocks(level), 10, 512), dtype=dtype)
+        p, dev = _ptr(buf)
+        self._check(self.lib.hlbm_read_moments(self.h, level, p, _dtype_code(buf), dev, 1 if physical_u else 0))
+        return buf
+
+    # ---- stepping
+    def step(self, n_fine_steps=1):
+        self._check(self.lib.hlbm_step(self.h, int(n_fine_steps)))
+
+    def synchronize(self):
+        self._check(self.lib.hlbm_synchronize(self.h))
+
+    def reduce(self):
+        out = (ctypes.c_double * 7)()
+        self._check(self.lib.hlbm_reduce(self.h, out))
+        return np.array(out[:], dtype=np.float64)
+
+
+# ---- layout marshalling between dense [10][nz][ny][nx] grids and block-major [n][10][512]
+
+def dense_to_blocks(M, coords=None):
+    """Dense (R, nz, ny, nx) -> block-major (n, R, 512) for the given block coords
+    (default: every block in slot order)."""
+    M = np.asarray(M)
+    R, nz, ny, nx = M.shape
+    t = M.reshape(R, nz // 8, 8, ny // 8, 8, nx // 8, 8).transpose(1, 3, 5, 0, 2, 4, 6)
+    t = t.reshape(nz // 8, ny // 8, nx // 8, R, 512)
+    if coords is None:
+        return np.ascontiguousarray(t.reshape(-1, R, 512))
+    c = np.asarray(coords)
+    return np.ascontiguousarray(t[c[:, 2], c[:, 1], c[:, 0]])
+
+
+def blocks_to_dense(Mb, shape, coords=None, fill=np.nan):
+    """Block-major (n, R, 512) -> dense (R, nz, ny, nx); nodes of absent blocks hold ``fill``."""
+    Mb = np.asarray(Mb)
+    nz, ny, nx = shape
+    R = Mb.shape[1]
+    t = np.full((nz // 8, ny // 8, nx // 8, R, 512), fill, dtype=Mb.dtype)
+    if coords is None:
+        t = Mb.reshape(nz // 8, ny // 8, nx // 8, R, 512)
+    else:
+        c = np.asarray(coords)
+        t[c[:, 2], c[:, 1], c[:, 0]] = Mb
+    t = t.reshape(nz // 8, ny // 8, nx // 8, R, 8, 8, 8).transpose(3, 0, 4, 1, 5, 2, 6)
+    return np.ascontiguousarray(t.reshape(R, nz, ny, nx))
