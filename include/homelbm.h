@@ -144,6 +144,32 @@ int32_t hlbm_synchronize(hlbm_lattice *h);
    Synchronous.  Returns HLBM_E_NONFINITE if the mass is not finite. */
 int32_t hlbm_reduce(hlbm_lattice *h, double out[7]);
 
+/* Allocation-free FP64 reduction of a moment buffer the caller already holds.
+ * The paper has no counterpart; this entry point exists for callers that must
+ * not allocate device memory: code embedded in a host application that owns
+ * the allocator (a plugin inside another solver), loops with a fixed memory
+ * budget, or contexts where allocation would synchronise the device.
+ *
+ * mom_dev:  float32 device buffer in the public layout [n_blocks][10][512]
+ *           (rho in row 0, as written by hlbm_read_moments with on_device = 1).
+ * F_dev:    float32 device force [n_blocks][3][512], or NULL to use (fx, fy, fz);
+ *           the velocity summed is u - F/(2 rho).
+ * out_dev:  five doubles in device memory, overwritten with mass, momentum
+ *           (3) and kinetic energy.
+ * stream:   cudaStream_t (NULL = legacy default stream); the call is
+ *           asynchronous on it.
+ * Scratch:  a fixed file-scope device array sized for at most 65,536 blocks
+ *           (3.7 MB, present on every GPU that loads the library until the
+ *           process exits).  n_blocks outside [1, 65536] returns
+ *           HLBM_E_INVALID_ARG (message in hlbm_last_error(NULL)).  No
+ *           allocation or free is made by this call.  The first call on a
+ *           device looks up the scratch address with that device current, so
+ *           make that first call outside any stream capture.  All calls share
+ *           the one scratch array: calls whose kernels overlap on the GPU race
+ *           and must be serialised (one stream, or events). */
+int32_t hlbm_reduce_f32_noalloc(const float *mom_dev, int64_t n_blocks, const float *F_dev, double fx, double fy,
+                                double fz, double *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

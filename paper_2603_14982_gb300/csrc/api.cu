@@ -476,3 +476,7 @@ int32_t hlbm_reduce(hlbm_lattice* h, double out[7]) {
 }
 
 }  // extern "C"
+
+// Records the message returned by hlbm_last_error(NULL) for entry points that
+// take no handle.
+void hlbm_internal_set_error(const char* msg) { g_create_error = msg ? msg : ""; }

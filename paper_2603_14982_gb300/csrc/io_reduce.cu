@@ -1,5 +1,8 @@
 // io_reduce.cu -- moment import/export between user buffers and storage, and
 // the FP64 reductions (mass, momentum, kinetic energy).
+#include <cstdio>
+#include <mutex>
+
 #include "hlbm_internal.h"
 #include "io_reduce.h"
 
@@ -187,3 +190,133 @@ cudaError_t reduce_level(int storage, const void* src, int64_t nb, const Scales*
 }
 
 }  // namespace hlbm
+
+// ---------------------------------------------------------------------------
+// Allocation-free reduction for callers that cannot call cudaMalloc.
+//
+// Code that runs inside a host whose allocator it does not own -- a plugin
+// loaded into another simulation, a real-time loop that must not grow device
+// memory, a process whose memory is reserved up front -- still needs the FP64
+// mass/momentum/energy sums.  This entry point reads a moment buffer the caller
+// already holds and writes five doubles to a buffer the caller passes; its only
+// scratch (the per-block partial sums) is a fixed, file-scope device array.
+// ---------------------------------------------------------------------------
+
+void hlbm_internal_set_error(const char* msg);
+
+namespace hlbm {
+namespace {
+
+// Largest buffer the allocation-free reduction accepts: 65,536 blocks of 8^3
+// nodes (33.5M nodes).  The scratch below (7 doubles per block, 3.7 MB) lives
+// on every GPU that loads the library until the process exits.
+constexpr int64_t kNoAllocMaxBlocks = 65536;
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * 7];
+
+constexpr int kMaxDevices = 64;
+double* g_noalloc_scratch[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mutex;
+
+// As k_reduce_blocks, but for the public layout (rho in row 0, float32) that
+// hlbm_read_moments produces.
+__global__ void __launch_bounds__(512) k_reduce_public_blocks(const float* __restrict__ src,
+                                                              const float* __restrict__ F, double fx, double fy,
+                                                              double fz, double* __restrict__ part) {
+  const int64_t blk = blockIdx.x;
+  const int t = threadIdx.x;
+  const float* p = src + blk * kRows * kCells + t;
+  const double rho = p[0];
+  if (F != nullptr) {
+    const float* Fp = F + blk * 3 * kCells + t;
+    fx = Fp[0];
+    fy = Fp[kCells];
+    fz = Fp[2 * kCells];
+  }
+  const double ux = double(p[1 * kCells]) - 0.5 * fx / rho;
+  const double uy = double(p[2 * kCells]) - 0.5 * fy / rho;
+  const double uz = double(p[3 * kCells]) - 0.5 * fz / rho;
+  double v[5] = {rho, rho * ux, rho * uy, rho * uz, 0.5 * rho * (ux * ux + uy * uy + uz * uz)};
+  __shared__ double s[16][5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((t & 31) == 0) s[t >> 5][k] = x;
+  }
+  __syncthreads();
+  if (t < 5) {
+    double x = 0;
+    for (int w = 0; w < 16; ++w) x += s[w][t];
+    part[blk * 7 + t] = x;
+  }
+}
+
+// Sums part[n][7] into out[0..4] by assignment (nothing carried between calls).
+__global__ void __launch_bounds__(256) k_reduce_final_store(const double* __restrict__ part, int64_t n,
+                                                            double* out) {
+  __shared__ double s[256];
+  for (int k = 0; k < 5; ++k) {
+    double x = 0;
+    for (int64_t i = threadIdx.x; i < n; i += 256) x += part[i * 7 + k];
+    s[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = s[0];
+    __syncthreads();
+  }
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current).
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (g_noalloc_scratch[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    g_noalloc_scratch[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_scratch[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace hlbm
+
+extern "C" int32_t hlbm_reduce_f32_noalloc(const float* mom_dev, int64_t n_blocks, const float* F_dev, double fx,
+                                           double fy, double fz, double* out_dev, void* stream) {
+  using namespace hlbm;
+  if (mom_dev == nullptr || out_dev == nullptr) {
+    hlbm_internal_set_error("hlbm_reduce_f32_noalloc: NULL buffer");
+    return HLBM_E_INVALID_ARG;
+  }
+  if (n_blocks <= 0 || n_blocks > kNoAllocMaxBlocks) {
+    char msg[160];
+    snprintf(msg, sizeof(msg), "hlbm_reduce_f32_noalloc: n_blocks = %lld outside [1, %lld]", (long long)n_blocks,
+             (long long)kNoAllocMaxBlocks);
+    hlbm_internal_set_error(msg);
+    return HLBM_E_INVALID_ARG;
+  }
+  double* part = nullptr;
+  cudaError_t e = noalloc_scratch(&part);
+  if (e == cudaSuccess) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    k_reduce_public_blocks<<<unsigned(n_blocks), 512, 0, s>>>(mom_dev, F_dev, fx, fy, fz, part);
+    k_reduce_final_store<<<1, 256, 0, s>>>(part, n_blocks, out_dev);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    char msg[200];
+    snprintf(msg, sizeof(msg), "hlbm_reduce_f32_noalloc: %s", cudaGetErrorString(e));
+    hlbm_internal_set_error(msg);
+    return HLBM_E_CUDA;
+  }
+  return HLBM_OK;
+}

@@ -60,6 +60,8 @@ _SIGS = {
     "hlbm_step": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     "hlbm_synchronize": (ctypes.c_int32, [ctypes.c_void_p]),
     "hlbm_reduce": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "hlbm_reduce_f32_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
