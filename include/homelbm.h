@@ -98,6 +98,38 @@ const char *hlbm_last_error(const hlbm_lattice *h);
    to rest (rho = 1, u = 0, S = 0). */
 int32_t hlbm_set_dense(hlbm_lattice *h);
 
+/* Declare the level-0 blocks that must be resolved at the finest level (the
+   blocks where the level-selection function Phi of Sec. 4.3 is 0) and build
+   the whole hierarchy from them on the device (same pipeline as
+   hlbm_rebuild_from_particles).  coords_xyz: host int32 [n][3] block
+   coordinates (bx, by, bz) of level 0.  On the first call every stored node is
+   at rest; later calls carry the moments over like a rebuild. */
+int32_t hlbm_set_fine_blocks(hlbm_lattice *h, const int32_t *coords_xyz, int64_t n);
+
+/* Rebuild the block hierarchy from a particle cloud (Sec. 5.3): occupancy of
+   level-0 blocks (Phi), the has-children sets H_l (one-block dilation of the
+   parents of the finer set), internal blocks (not stored), stored / border /
+   leaf sets, flags against the previous hierarchy, stable compaction of the
+   stored blocks, neighbour tables and interface node lists.  Blocks that stay
+   keep their moments; new fine nodes are interpolated from the coarser level
+   (Eq. downward_rescale, spatial part), new coarse nodes take the upward rule
+   of Eq. upload_S from their finer coincident nodes.  pos_xyz: float32 [n][3]
+   positions in fine-node units, host (on_device = 0, copied) or device
+   (on_device = 1, borrowed for the call).  counts_out (host, may be NULL):
+   refined (newly in H), coarsened (newly out of H) and deleted blocks summed
+   over levels.  Must be called at a coarse-step boundary.  The level-0 force
+   field is dropped (set it again for the new block list).  Non-finite
+   positions are ignored and reported with HLBM_E_NONFINITE after the rebuild. */
+int32_t hlbm_rebuild_from_particles(hlbm_lattice *h, const float *pos_xyz, int64_t n, int32_t on_device,
+                                    int64_t counts_out[3]);
+
+/* Interface nodes of a level as (block << 9) | node, ascending: which = 0 the
+   downward set I^d (filled from level+1 by the downward transfer), which = 1
+   the upward set I^u (filled from level-1 by the upward transfer).  Host
+   output; if cap < n returns HLBM_E_INVALID_ARG with *n set. */
+int32_t hlbm_get_interface_nodes(const hlbm_lattice *h, int32_t level, int32_t which, int32_t *out, int64_t cap,
+                                 int64_t *n);
+
 /* Number of stored blocks of a level. */
 int32_t hlbm_num_blocks(const hlbm_lattice *h, int32_t level, int64_t *n);
 

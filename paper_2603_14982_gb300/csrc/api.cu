@@ -16,10 +16,10 @@
 using namespace hlbm;
 
 namespace {
-
 thread_local std::string g_create_error;
+}  // namespace
 
-int fail(hlbm_lattice* h, int code, const char* fmt, ...) {
+int hlbm::fail(hlbm_lattice* h, int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -31,6 +31,8 @@ int fail(hlbm_lattice* h, int code, const char* fmt, ...) {
     g_create_error = buf;
   return code;
 }
+
+namespace {
 
 #define HLBM_CUDA(h, call)                                                                      \
   do {                                                                                          \
@@ -83,15 +85,41 @@ void LatticeOps::free_level(LevelData& L) {
   v = L.d_bflags;
   release(v);
   L.d_bflags = nullptr;
+  v = L.d_bmask;
+  release(v);
+  L.d_bmask = nullptr;
   v = L.d_solid;
   release(v);
   L.d_solid = nullptr;
   v = L.d_skip;
   release(v);
   L.d_skip = nullptr;
+  for (void** q : {(void**)&L.d_coords, (void**)&L.d_slot, (void**)&L.d_H, (void**)&L.d_stored, (void**)&L.d_down,
+                   (void**)&L.d_up}) {
+    release(*q);
+  }
+  L.n_down = L.n_up = 0;
   L.nb = 0;
   L.coords.clear();
   L.flags.clear();
+}
+
+int LatticeOps::bounce(hlbm_lattice* h, LevelData& L) {
+  if (L.nb == 0) return HLBM_OK;
+  int rc;
+  if (L.d_bflags == nullptr) {
+    void* p;
+    if ((rc = alloc(h, &p, size_t(L.nb)))) return rc;
+    L.d_bflags = static_cast<uint8_t*>(p);
+    HLBM_CUDA(h, cudaMemsetAsync(L.d_bflags, 0, size_t(L.nb), h->stream));
+  }
+  if (L.d_bmask == nullptr) {
+    void* p;
+    if ((rc = alloc(h, &p, size_t(L.nb) * kCells * sizeof(uint32_t)))) return rc;
+    L.d_bmask = static_cast<uint32_t*>(p);
+  }
+  HLBM_CUDA(h, compute_bounce_masks(L.d_nbr, L.d_solid, L.d_bflags, L.d_bmask, L.nb, h->stream));
+  return HLBM_OK;
 }
 
 // Host-side neighbour table of a block list on the level's block grid.
@@ -156,7 +184,7 @@ int32_t hlbm_create(const hlbm_config* cfg, hlbm_lattice** out) {
     return fail(nullptr, HLBM_E_UNSUPPORTED, "reduced-precision storage is not built yet");
   if (cfg->rescale_mode < HLBM_RESCALE_POST || cfg->rescale_mode > HLBM_RESCALE_PAPER)
     return fail(nullptr, HLBM_E_INVALID_ARG, "unknown rescale_mode %d", cfg->rescale_mode);
-  if (cfg->num_levels > 1) return fail(nullptr, HLBM_E_UNSUPPORTED, "multi-level lattices are not built yet");
+  if (cfg->num_levels > 4) return fail(nullptr, HLBM_E_UNSUPPORTED, "at most 4 levels are supported");
   hlbm_lattice* h = new (std::nothrow) hlbm_lattice();
   if (h == nullptr) return fail(nullptr, HLBM_E_OOM, "host allocation failed");
   h->cfg = *cfg;
@@ -166,6 +194,25 @@ int32_t hlbm_create(const hlbm_config* cfg, hlbm_lattice** out) {
   for (int l = 0; l < cfg->num_levels; ++l) {
     h->lv[l].tau = tau;
     tau = tau / 2.0 + 0.25;  // Sec. 4.2 with k = 1
+  }
+  for (int l = 0; l + 1 < cfg->num_levels; ++l) {
+    const double tf = h->lv[l].tau, tc = h->lv[l + 1].tau;
+    if (cfg->rescale_mode == HLBM_RESCALE_POST) {
+      if (std::fabs(tf - 1.0) < 1e-9 || std::fabs(tc - 1.0) < 1e-9) {
+        delete h;
+        return fail(nullptr, HLBM_E_INVALID_ARG,
+                    "post-collision rescaling needs tau != 1 on every level (tau_%d = %g, tau_%d = %g)", l, tf, l + 1,
+                    tc);
+      }
+      h->kup[l] = 2.0 * (tc - 1.0) / (tf - 1.0);
+      h->kdown[l] = 1.0 / h->kup[l];
+    } else if (cfg->rescale_mode == HLBM_RESCALE_PRE) {
+      h->kup[l] = 2.0 * tc / tf;
+      h->kdown[l] = 1.0 / h->kup[l];
+    } else {
+      h->kup[l] = tc / (2.0 * tf);    // Eq. upload_S as printed
+      h->kdown[l] = 2.0 * tc / tf;    // Eq. downward_rescale as printed
+    }
   }
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
@@ -183,7 +230,9 @@ int32_t hlbm_destroy(hlbm_lattice* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& L : h->lv) LatticeOps::free_level(L);
   LatticeOps::release(h->d_stage);
-  void* v = h->d_red;
+  void* v = h->d_status;
+  LatticeOps::release(v);
+  v = h->d_red;
   LatticeOps::release(v);
   v = h->d_F;
   LatticeOps::release(v);
@@ -224,6 +273,7 @@ int32_t hlbm_set_dense(hlbm_lattice* h) {
   HLBM_CUDA(h, cudaMemcpyAsync(L.d_nbr, nbr.data(), nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
   // rest state: delta_rho = u = S = 0 is all-zero bits in every storage
   for (int k = 0; k < 2; ++k) HLBM_CUDA(h, cudaMemsetAsync(L.d_mom[k], 0, mom_bytes, h->stream));
+  if ((rc = LatticeOps::bounce(h, L))) return rc;
   L.cur = 0;
   HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->have_blocks = true;
@@ -303,7 +353,7 @@ int32_t hlbm_set_solid(hlbm_lattice* h, const uint8_t* mask) {
   v = L.d_bflags;
   LatticeOps::release(v);
   L.d_bflags = nullptr;
-  if (mask == nullptr) return HLBM_OK;
+  if (mask == nullptr) return LatticeOps::bounce(h, L);
   int dims[3];
   h->block_dims(0, dims);
   const int nx = h->cfg.nx, ny = h->cfg.ny;
@@ -331,6 +381,8 @@ int32_t hlbm_set_solid(hlbm_lattice* h, const uint8_t* mask) {
   L.d_bflags = static_cast<uint8_t*>(p);
   HLBM_CUDA(h, cudaMemcpy(L.d_solid, bm.data(), bm.size(), cudaMemcpyHostToDevice));
   HLBM_CUDA(h, cudaMemcpy(L.d_bflags, fl.data(), fl.size(), cudaMemcpyHostToDevice));
+  if ((rc = LatticeOps::bounce(h, L))) return rc;
+  HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
   return HLBM_OK;
 }
 
@@ -403,6 +455,7 @@ int32_t hlbm_step(hlbm_lattice* h, int32_t n_fine_steps) {
     return fail(h, HLBM_E_INVALID_ARG, "n_fine_steps must be a non-negative multiple of %d", per);
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
+  if (h->device_hierarchy) return ml_advance_coarse(h, n_fine_steps / per);
   LevelData& L = h->lv[0];
   StepArgs a{};
   a.nbr = L.d_nbr;
@@ -410,6 +463,7 @@ int32_t hlbm_step(hlbm_lattice* h, int32_t n_fine_steps) {
   a.eps = h->d_eps;
   a.solid = L.d_solid;
   a.bflags = L.d_bflags;
+  a.bmask = L.d_bmask;
   a.fu[0] = h->fu[0];
   a.fu[1] = h->fu[1];
   a.fu[2] = h->fu[2];
@@ -430,7 +484,7 @@ int32_t hlbm_synchronize(hlbm_lattice* h) {
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
   HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
-  return HLBM_OK;
+  return ml_check_status(h);
 }
 
 int32_t hlbm_reduce(hlbm_lattice* h, double out[7]) {
@@ -471,7 +525,52 @@ int32_t hlbm_reduce(hlbm_lattice* h, double out[7]) {
       total[6] += r[0];
   }
   std::memcpy(out, total, sizeof(total));
+  rc = ml_check_status(h);
+  if (rc) return rc;
   if (!std::isfinite(total[0])) return fail(h, HLBM_E_NONFINITE, "mass is not finite");
+  return HLBM_OK;
+}
+
+int32_t hlbm_set_fine_blocks(hlbm_lattice* h, const int32_t* coords_xyz, int64_t n) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (n < 0 || (n > 0 && coords_xyz == nullptr)) return fail(h, HLBM_E_INVALID_ARG, "bad block list");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  int dims[3];
+  h->block_dims(0, dims);
+  for (int64_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a)
+      if (coords_xyz[3 * i + a] < 0 || coords_xyz[3 * i + a] >= dims[a])
+        return fail(h, HLBM_E_INVALID_ARG, "block %lld coordinate %d = %d outside [0, %d)", (long long)i, a,
+                    coords_xyz[3 * i + a], dims[a]);
+  return ml_rebuild(h, nullptr, 0, 0, coords_xyz, n, nullptr);
+}
+
+int32_t hlbm_rebuild_from_particles(hlbm_lattice* h, const float* pos_xyz, int64_t n, int32_t on_device,
+                                    int64_t counts_out[3]) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (n < 0 || (n > 0 && pos_xyz == nullptr)) return fail(h, HLBM_E_INVALID_ARG, "bad particle buffer");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  return ml_rebuild(h, pos_xyz, n, on_device, nullptr, 0, counts_out);
+}
+
+int32_t hlbm_get_interface_nodes(const hlbm_lattice* h, int32_t level, int32_t which, int32_t* out, int64_t cap,
+                                 int64_t* n) {
+  hlbm_lattice* hm = const_cast<hlbm_lattice*>(h);
+  if (h == nullptr || n == nullptr) return fail(hm, HLBM_E_INVALID_ARG, "NULL argument");
+  if (level < 0 || level >= h->cfg.num_levels) return fail(hm, HLBM_E_INVALID_ARG, "level %d out of range", level);
+  if (which != 0 && which != 1) return fail(hm, HLBM_E_INVALID_ARG, "which must be 0 (down) or 1 (up)");
+  const LevelData& L = h->lv[level];
+  const int64_t cnt = which == 0 ? L.n_down : L.n_up;
+  *n = cnt;
+  if (cap < cnt) return fail(hm, HLBM_E_INVALID_ARG, "capacity %lld < %lld nodes", (long long)cap, (long long)cnt);
+  if (cnt == 0) return HLBM_OK;
+  if (out == nullptr) return fail(hm, HLBM_E_INVALID_ARG, "out is NULL");
+  int rc = LatticeOps::set_device(hm);
+  if (rc) return rc;
+  HLBM_CUDA(hm, cudaMemcpy(out, which == 0 ? L.d_down : L.d_up, size_t(cnt) * sizeof(int32_t),
+                           cudaMemcpyDeviceToHost));
   return HLBM_OK;
 }
 

@@ -1,0 +1,364 @@
+// hierarchy.cu -- block-hierarchy maintenance on the device (Sec. 4.3, Sec. 5.1, Sec. 5.3).
+#include "hierarchy.cuh"
+#include "hlbm_internal.h"
+
+namespace hlbm {
+namespace {
+
+constexpr int kScanCta = 1024;  // slots per compaction CTA
+
+__device__ __forceinline__ int64_t slot_of(const GridDims& d, int x, int y, int z) {
+  return (int64_t(z) * d.ny + y) * d.nx + x;
+}
+
+// Wrap (periodic) or reject (wall) a coordinate along one axis.
+__device__ __forceinline__ bool wrap(int& v, int n, int periodic) {
+  if (v >= 0 && v < n) return true;
+  if (!periodic) return false;
+  v = (v % n + n) % n;
+  return true;
+}
+
+__global__ void k_occ_particles(const float* __restrict__ pos, int64_t n, GridDims d0, uint8_t* occ, int* bad) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
+  if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) {
+    atomicAdd(bad, 1);
+    return;
+  }
+  // floor(p / 8): the division by a power of two is exact
+  int bx = int(floorf(px * 0.125f)), by = int(floorf(py * 0.125f)), bz = int(floorf(pz * 0.125f));
+  bx = min(max(bx, 0), d0.nx - 1);
+  by = min(max(by, 0), d0.ny - 1);
+  bz = min(max(bz, 0), d0.nz - 1);
+  occ[slot_of(d0, bx, by, bz)] = 1;  // benign race: every writer stores 1
+}
+
+__global__ void k_occ_blocks(const int32_t* __restrict__ c, int64_t n, GridDims d0, uint8_t* occ, int* bad) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int bx = c[3 * i], by = c[3 * i + 1], bz = c[3 * i + 2];
+  if (bx < 0 || by < 0 || bz < 0 || bx >= d0.nx || by >= d0.ny || bz >= d0.nz) {
+    atomicAdd(bad, 1);
+    return;
+  }
+  occ[slot_of(d0, bx, by, bz)] = 1;
+}
+
+// H[q] = 1 iff some q' in the 3x3x3 neighbourhood of q (wrapped / clipped) has a
+// child set in src (src on the 2x finer grid).
+__global__ void k_dilate_parent(const uint8_t* __restrict__ src, GridDims ds, uint8_t* __restrict__ H, GridDims d,
+                                int px, int py, int pz) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= d.slots()) return;
+  const int x = int(q % d.nx), y = int((q / d.nx) % d.ny), z = int(q / (int64_t(d.nx) * d.ny));
+  uint8_t hit = 0;
+  for (int dz = -1; dz <= 1 && !hit; ++dz)
+    for (int dy = -1; dy <= 1 && !hit; ++dy)
+      for (int dx = -1; dx <= 1 && !hit; ++dx) {
+        int a = x + dx, b = y + dy, c = z + dz;
+        if (!wrap(a, d.nx, px) || !wrap(b, d.ny, py) || !wrap(c, d.nz, pz)) continue;
+        for (int k = 0; k < 8 && !hit; ++k) {
+          const int cx = 2 * a + (k & 1), cy = 2 * b + ((k >> 1) & 1), cz = 2 * c + (k >> 2);
+          hit = src[slot_of(ds, cx, cy, cz)];
+        }
+      }
+  H[q] = hit ? 1 : 0;
+}
+
+__global__ void k_internal_stored(const uint8_t* __restrict__ H, const uint8_t* __restrict__ Hup, GridDims d,
+                                  GridDims du, int px, int py, int pz, int has_H, uint8_t* __restrict__ I,
+                                  uint8_t* __restrict__ stored) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= d.slots()) return;
+  const int x = int(q % d.nx), y = int((q / d.nx) % d.ny), z = int(q / (int64_t(d.nx) * d.ny));
+  uint8_t in = 0;
+  if (has_H && H[q]) {
+    in = 1;
+    for (int dz = -1; dz <= 1 && in; ++dz)
+      for (int dy = -1; dy <= 1 && in; ++dy)
+        for (int dx = -1; dx <= 1 && in; ++dx) {
+          int a = x + dx, b = y + dy, c = z + dz;
+          if (!wrap(a, d.nx, px) || !wrap(b, d.ny, py) || !wrap(c, d.nz, pz)) continue;  // beyond a wall
+          in = H[slot_of(d, a, b, c)];
+        }
+  }
+  I[q] = in;
+  const uint8_t cover = Hup == nullptr ? 1 : Hup[slot_of(du, x >> 1, y >> 1, z >> 1)];
+  stored[q] = (cover && !in) ? 1 : 0;
+}
+
+__global__ void k_slot_flags(const uint8_t* __restrict__ stored, const uint8_t* __restrict__ H,
+                             const uint8_t* __restrict__ stored_up, GridDims d, GridDims du,
+                             const uint8_t* __restrict__ old_stored, const uint8_t* __restrict__ old_H, int has_old,
+                             uint8_t* __restrict__ flags) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= d.slots()) return;
+  if (!stored[q]) {
+    flags[q] = 0;
+    return;
+  }
+  const int x = int(q % d.nx), y = int((q / d.nx) % d.ny), z = int(q / (int64_t(d.nx) * d.ny));
+  const uint8_t h = H ? H[q] : 0;
+  bool border = h != 0;
+  if (stored_up) border = border || stored_up[slot_of(du, x >> 1, y >> 1, z >> 1)] != 0;
+  uint8_t f = border ? kFlagBorder : kFlagLeaf;
+  if (has_old) {
+    const uint8_t oh = old_H ? old_H[q] : 0;
+    if (!old_stored[q]) f |= kFlagNew;
+    if (h && !oh) f |= kFlagRefine;
+    if (!h && oh) f |= kFlagCoarsen;
+  }
+  flags[q] = f;
+}
+
+// Stable compaction, pass 1: per-CTA count of set slots (warp ballots + popc).
+__global__ void __launch_bounds__(kScanCta) k_compact_count(const uint8_t* __restrict__ stored, int64_t n,
+                                                            int64_t* __restrict__ cta_count) {
+  __shared__ int warp_cnt[kScanCta / 32];
+  const int64_t i = int64_t(blockIdx.x) * kScanCta + threadIdx.x;
+  const bool v = i < n && stored[i];
+  const unsigned b = __ballot_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0) warp_cnt[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < kScanCta / 32; ++w) s += warp_cnt[w];
+    cta_count[blockIdx.x] = s;
+  }
+}
+
+// Exclusive scan of the CTA counts (one CTA, sequential over chunks).
+__global__ void k_compact_scan(int64_t* __restrict__ cta_count, int64_t n_cta, int64_t* __restrict__ total) {
+  if (threadIdx.x != 0) return;
+  int64_t run = 0;
+  for (int64_t c = 0; c < n_cta; ++c) {
+    const int64_t v = cta_count[c];
+    cta_count[c] = run;
+    run += v;
+  }
+  *total = run;
+}
+
+// Pass 2: scatter in slot order.
+__global__ void __launch_bounds__(kScanCta) k_compact_scatter(const uint8_t* __restrict__ stored,
+                                                              const uint8_t* __restrict__ flags,
+                                                              const uint8_t* __restrict__ H, GridDims d,
+                                                              const int64_t* __restrict__ cta_off,
+                                                              int32_t* __restrict__ slot_to_idx,
+                                                              int32_t* __restrict__ coords,
+                                                              uint8_t* __restrict__ list_flags,
+                                                              uint8_t* __restrict__ skip) {
+  __shared__ int warp_off[kScanCta / 32];
+  const int64_t n = d.slots();
+  const int64_t i = int64_t(blockIdx.x) * kScanCta + threadIdx.x;
+  const bool v = i < n && stored[i];
+  const unsigned b = __ballot_sync(0xffffffffu, v);
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) warp_off[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < kScanCta / 32; ++w) {
+      const int c = warp_off[w];
+      warp_off[w] = s;
+      s += c;
+    }
+  }
+  __syncthreads();
+  if (i >= n) return;
+  if (!v) {
+    slot_to_idx[i] = -1;
+    return;
+  }
+  const int64_t idx = cta_off[blockIdx.x] + warp_off[threadIdx.x >> 5] + __popc(b & ((1u << lane) - 1u));
+  slot_to_idx[i] = int32_t(idx);
+  coords[3 * idx + 0] = int32_t(i % d.nx);
+  coords[3 * idx + 1] = int32_t((i / d.nx) % d.ny);
+  coords[3 * idx + 2] = int32_t(i / (int64_t(d.nx) * d.ny));
+  list_flags[idx] = flags[i];
+  skip[idx] = H ? H[i] : 0;
+}
+
+__global__ void k_nbr(const int32_t* __restrict__ coords, int64_t nb, const int32_t* __restrict__ slot_to_idx,
+                      GridDims d, int px, int py, int pz, int32_t* __restrict__ nbr) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= nb * 27) return;
+  const int64_t b = i / 27;
+  const int dir = int(i % 27);
+  int x = coords[3 * b] + dir % 3 - 1, y = coords[3 * b + 1] + (dir / 3) % 3 - 1, z = coords[3 * b + 2] + dir / 9 - 1;
+  if (!wrap(x, d.nx, px) || !wrap(y, d.ny, py) || !wrap(z, d.nz, pz)) {
+    nbr[i] = kWall;
+    return;
+  }
+  nbr[i] = slot_to_idx[slot_of(d, x, y, z)];  // -1 (kMissing) when not stored
+}
+
+// Node classification per block (one CTA of 512 threads): a node is an
+// interface node iff its 26-neighbourhood touches a missing neighbour block.
+__device__ __forceinline__ bool node_missing(int cell, unsigned miss) {
+  const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
+  const unsigned mx = 2u | (x == 0 ? 1u : 0u) | (x == 7 ? 4u : 0u);
+  const unsigned my = 2u | (y == 0 ? 1u : 0u) | (y == 7 ? 4u : 0u);
+  const unsigned mz = 2u | (z == 0 ? 1u : 0u) | (z == 7 ? 4u : 0u);
+  unsigned touched = 0;
+  for (int iz = 0; iz < 3; ++iz)
+    for (int iy = 0; iy < 3; ++iy)
+      if (((mz >> iz) & 1u) && ((my >> iy) & 1u)) touched |= mx << (3 * iy + 9 * iz);
+  return (touched & miss) != 0u;
+}
+
+__device__ __forceinline__ unsigned block_missing_mask(const int32_t* nbr, int64_t b) {
+  unsigned m = 0;
+  for (int d = 0; d < 27; ++d)
+    if (nbr[b * 27 + d] == kMissing) m |= 1u << d;
+  return m;
+}
+
+// counts[2*b] = #down nodes of block b, counts[2*b+1] = #up nodes.
+__global__ void __launch_bounds__(512) k_iface_count(const int32_t* __restrict__ nbr, const uint8_t* __restrict__ skip,
+                                                     int64_t nb, int64_t* __restrict__ counts) {
+  __shared__ unsigned s_miss;
+  __shared__ int s_cnt[16];
+  const int64_t b = blockIdx.x;
+  if (threadIdx.x == 0) s_miss = block_missing_mask(nbr, b);
+  __syncthreads();
+  const bool m = s_miss != 0u && node_missing(threadIdx.x, s_miss);
+  const unsigned bal = __ballot_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < 16; ++w) s += s_cnt[w];
+    const bool up = skip[b] != 0;
+    counts[2 * b] = up ? 0 : s;
+    counts[2 * b + 1] = up ? s : 0;
+  }
+}
+
+__global__ void k_iface_scan(int64_t* __restrict__ counts, int64_t nb, int64_t* __restrict__ totals) {
+  if (threadIdx.x != 0) return;
+  int64_t rd = 0, ru = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    const int64_t cd = counts[2 * b], cu = counts[2 * b + 1];
+    counts[2 * b] = rd;
+    counts[2 * b + 1] = ru;
+    rd += cd;
+    ru += cu;
+  }
+  totals[0] = rd;
+  totals[1] = ru;
+}
+
+__global__ void __launch_bounds__(512) k_iface_scatter(const int32_t* __restrict__ nbr,
+                                                       const uint8_t* __restrict__ skip, int64_t nb,
+                                                       const int64_t* __restrict__ offs, int32_t* __restrict__ down,
+                                                       int32_t* __restrict__ up) {
+  __shared__ unsigned s_miss;
+  __shared__ int s_off[16];
+  const int64_t b = blockIdx.x;
+  if (threadIdx.x == 0) s_miss = block_missing_mask(nbr, b);
+  __syncthreads();
+  const bool m = s_miss != 0u && node_missing(threadIdx.x, s_miss);
+  const unsigned bal = __ballot_sync(0xffffffffu, m);
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) s_off[threadIdx.x >> 5] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < 16; ++w) {
+      const int c = s_off[w];
+      s_off[w] = s;
+      s += c;
+    }
+  }
+  __syncthreads();
+  if (!m) return;
+  const bool isup = skip[b] != 0;
+  const int64_t base = offs[2 * b + (isup ? 1 : 0)];
+  const int64_t k = base + s_off[threadIdx.x >> 5] + __popc(bal & ((1u << lane) - 1u));
+  const int32_t v = int32_t((b << 9) | threadIdx.x);
+  if (isup)
+    up[k] = v;
+  else
+    down[k] = v;
+}
+
+inline unsigned grid_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t occupancy_from_particles(const float* pos, int64_t n, GridDims d0, uint8_t* occ, int* bad,
+                                     cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(occ, 0, size_t(d0.slots()), s);
+  if (e != cudaSuccess || n == 0) return e;
+  k_occ_particles<<<grid_for(n, 256), 256, 0, s>>>(pos, n, d0, occ, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t occupancy_from_blocks(const int32_t* coords, int64_t n, GridDims d0, uint8_t* occ, int* bad,
+                                  cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(occ, 0, size_t(d0.slots()), s);
+  if (e != cudaSuccess || n == 0) return e;
+  k_occ_blocks<<<grid_for(n, 256), 256, 0, s>>>(coords, n, d0, occ, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t dilate_parent(const uint8_t* src, GridDims dsrc, uint8_t* H, GridDims d, const int periodic[3],
+                          cudaStream_t s) {
+  k_dilate_parent<<<grid_for(d.slots(), 256), 256, 0, s>>>(src, dsrc, H, d, periodic[0], periodic[1], periodic[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t internal_stored(const uint8_t* H, const uint8_t* Hup, GridDims d, GridDims dup, const int periodic[3],
+                            bool has_H, uint8_t* I, uint8_t* stored, cudaStream_t s) {
+  k_internal_stored<<<grid_for(d.slots(), 256), 256, 0, s>>>(H, Hup, d, dup, periodic[0], periodic[1], periodic[2],
+                                                             has_H ? 1 : 0, I, stored);
+  return cudaGetLastError();
+}
+
+cudaError_t slot_flags(const uint8_t* stored, const uint8_t* H, const uint8_t* stored_up, GridDims d, GridDims dup,
+                       const uint8_t* old_stored, const uint8_t* old_H, bool has_old, uint8_t* flags,
+                       cudaStream_t s) {
+  k_slot_flags<<<grid_for(d.slots(), 256), 256, 0, s>>>(stored, H, stored_up, d, dup, old_stored, old_H,
+                                                        has_old ? 1 : 0, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t compact_slots(const uint8_t* stored, const uint8_t* flags, const uint8_t* H, GridDims d,
+                          int32_t* slot_to_idx, int32_t* coords, uint8_t* list_flags, uint8_t* skip,
+                          int64_t* scratch, int64_t* count_dev, cudaStream_t s) {
+  const int64_t n = d.slots();
+  const int64_t n_cta = (n + kScanCta - 1) / kScanCta;
+  k_compact_count<<<unsigned(n_cta), kScanCta, 0, s>>>(stored, n, scratch);
+  k_compact_scan<<<1, 32, 0, s>>>(scratch, n_cta, count_dev);
+  k_compact_scatter<<<unsigned(n_cta), kScanCta, 0, s>>>(stored, flags, H, d, scratch, slot_to_idx, coords,
+                                                         list_flags, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t neighbour_table(const int32_t* coords, int64_t nb, const int32_t* slot_to_idx, GridDims d,
+                            const int periodic[3], int32_t* nbr, cudaStream_t s) {
+  if (nb == 0) return cudaSuccess;
+  k_nbr<<<grid_for(nb * 27, 256), 256, 0, s>>>(coords, nb, slot_to_idx, d, periodic[0], periodic[1], periodic[2],
+                                                nbr);
+  return cudaGetLastError();
+}
+
+cudaError_t interface_count(const int32_t* nbr, const uint8_t* skip, int64_t nb, int64_t* scratch,
+                            int64_t* counts_dev, cudaStream_t s) {
+  if (nb == 0) return cudaMemsetAsync(counts_dev, 0, 2 * sizeof(int64_t), s);
+  k_iface_count<<<unsigned(nb), 512, 0, s>>>(nbr, skip, nb, scratch);
+  k_iface_scan<<<1, 32, 0, s>>>(scratch, nb, counts_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t interface_scatter(const int32_t* nbr, const uint8_t* skip, int64_t nb, const int64_t* scratch,
+                              int32_t* down, int32_t* up, cudaStream_t s) {
+  if (nb == 0) return cudaSuccess;
+  k_iface_scatter<<<unsigned(nb), 512, 0, s>>>(nbr, skip, nb, scratch, down, up);
+  return cudaGetLastError();
+}
+
+}  // namespace hlbm

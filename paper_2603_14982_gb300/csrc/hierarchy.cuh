@@ -49,9 +49,13 @@ cudaError_t compact_slots(const uint8_t* stored, const uint8_t* flags, const uin
 cudaError_t neighbour_table(const int32_t* coords, int64_t nb, const int32_t* slot_to_idx, GridDims d,
                             const int periodic[3], int32_t* nbr, cudaStream_t s);
 // Interface node lists of one level: nodes with a 26-neighbour in a block that
-// is not stored; those inside H blocks go to `up` (I^u), the others to `down`
-// (I^d).  Entries are (block << 9) | cell, ascending.  scratch >= 2*nb+2 int64.
-cudaError_t interface_nodes(const int32_t* nbr, const uint8_t* skip, int64_t nb, int32_t* down, int32_t* up,
-                            int64_t* scratch, int64_t* counts_dev, cudaStream_t s);
+// is not stored; those inside H blocks (skip != 0) go to `up` (I^u), the others
+// to `down` (I^d).  Entries are (block << 9) | cell, ascending.
+// interface_count writes per-block offsets to scratch (>= 2*nb int64) and the
+// totals (down, up) to counts_dev; interface_scatter then fills the lists.
+cudaError_t interface_count(const int32_t* nbr, const uint8_t* skip, int64_t nb, int64_t* scratch,
+                            int64_t* counts_dev, cudaStream_t s);
+cudaError_t interface_scatter(const int32_t* nbr, const uint8_t* skip, int64_t nb, const int64_t* scratch,
+                              int32_t* down, int32_t* up, cudaStream_t s);
 
 }  // namespace hlbm

@@ -15,6 +15,7 @@ constexpr int32_t kWall = -2;     // beyond a non-periodic face of the domain
 
 // Per-block flag bits of the step kernel.
 constexpr uint8_t kBlockSolidNear = 1;  // the block or one of its 26 neighbours holds a solid node
+constexpr uint8_t kBlockBounce = 2;     // some node of the block pulls from a wall or a solid node
 
 // Arguments of one stream-collide launch over the stored blocks of a level.
 struct StepArgs {
@@ -25,6 +26,7 @@ struct StepArgs {
   const float* eps;         // [nb][512] fluid fraction, or null (1)
   const uint8_t* solid;     // [nb][512] solid node mask, or null
   const uint8_t* bflags;    // [nb] block flags, or null
+  const uint32_t* bmask;    // [nb][512] bounce-back masks (bit k: pull source x - c_k is wall/solid)
   const Scales* scales_in;  // reduced-precision row scales of `in` (device), else null
   const Scales* scales_out; // row scales of `out` (device), else null
   double fu[3];             // uniform force when F is null
@@ -33,6 +35,13 @@ struct StepArgs {
   int64_t nb;               // number of blocks
 };
 
+// FP64 storage: one node per thread (stream_collide.cu).  Other storages: the
+// packed-FP32 node-pair kernel (stream_collide_f2.cu).
 cudaError_t launch_stream_collide(int storage, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_stream_collide_f2(int storage, const StepArgs& a, cudaStream_t s);
+// Per-node bounce masks and the kBlockBounce flag from a neighbour table and
+// an optional solid mask (bflags must hold kBlockSolidNear where solids are near).
+cudaError_t compute_bounce_masks(const int32_t* nbr, const uint8_t* solid, uint8_t* bflags, uint32_t* bmask,
+                                 int64_t nb, cudaStream_t s);
 
 }  // namespace hlbm

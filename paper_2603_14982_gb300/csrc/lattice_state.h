@@ -18,9 +18,18 @@ struct LevelData {
   void* d_mom[2] = {nullptr, nullptr};  // ping-pong moment buffers [nb][10][512]
   int cur = 0;                     // buffer holding the current state
   double tau = 0;                  // level relaxation time
-  uint8_t* d_bflags = nullptr;     // [nb] step-kernel block flags or null
+  uint8_t* d_bflags = nullptr;     // [nb] step-kernel block flags
+  uint32_t* d_bmask = nullptr;     // [nb][512] bounce-back masks
   uint8_t* d_solid = nullptr;      // [nb][512] solid nodes or null
   uint8_t* d_skip = nullptr;       // [nb] 1 = covered by a finer level (left out of reductions) or null
+  // hierarchy built on the device (multi-level lattices and rebuilds)
+  int32_t* d_coords = nullptr;     // [slots][3] capacity, first nb used
+  int32_t* d_slot = nullptr;       // [slots] slot -> block index or -1
+  uint8_t* d_H = nullptr;          // [slots] block has stored finer children
+  uint8_t* d_stored = nullptr;     // [slots] block is stored
+  int64_t n_down = 0, n_up = 0;    // interface node counts (I^d, I^u)
+  int32_t* d_down = nullptr;       // [n_down] (block << 9) | cell
+  int32_t* d_up = nullptr;         // [n_up]
 };
 
 }  // namespace hlbm
@@ -37,6 +46,9 @@ struct hlbm_lattice {
   size_t stage_bytes = 0;
   double* d_red = nullptr;  // reduction scratch
   size_t red_n = 0;
+  bool device_hierarchy = false;  // levels were built by the device rebuild pipeline
+  double kup[8] = {0}, kdown[8] = {0};  // S^neq factors between level l and l+1
+  int* d_status = nullptr;    // device status word of the transfer kernels (0 = ok)
   std::string err;
 
   void block_dims(int level, int dims[3]) const {
@@ -49,11 +61,22 @@ struct hlbm_lattice {
 
 namespace hlbm {
 
+// Records an error message on h (or the global one when h is NULL) and returns code.
+int fail(hlbm_lattice* h, int code, const char* fmt, ...);
+
+// Multi-level engine (ml_host.cu).
+int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_device, const int32_t* blocks,
+               int64_t n_blocks, int64_t counts_out[3]);
+int ml_advance_coarse(hlbm_lattice* h, int64_t n_coarse);
+int ml_check_status(hlbm_lattice* h);
+
 struct LatticeOps {
   static int set_device(hlbm_lattice* h);
   static int alloc(hlbm_lattice* h, void** p, size_t bytes);
   static void release(void*& p);
   static void free_level(LevelData& L);
+  // (Re)compute d_bflags / d_bmask of a level from its neighbour table and solids.
+  static int bounce(hlbm_lattice* h, LevelData& L);
   static void build_nbr(const hlbm_lattice* h, int level, const std::vector<int32_t>& coords,
                         const std::vector<int32_t>& slot_to_idx, std::vector<int32_t>& nbr);
 };

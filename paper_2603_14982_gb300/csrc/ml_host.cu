@@ -1,0 +1,384 @@
+// ml_host.cu -- host orchestration of the multi-level engine: the rebuild
+// pipeline of Sec. 5.3 (occupancy -> Phi -> sets -> compaction -> tables ->
+// interface lists -> moments of the new blocks) and the sub-cycled advance of
+// Algorithm 1 with its downward and upward transfers.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "hierarchy.cuh"
+#include "hlbm_internal.h"
+#include "lattice_state.h"
+#include "multilevel.cuh"
+
+namespace hlbm {
+namespace {
+
+#define ML_CUDA(h, call)                                                                       \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail((h), HLBM_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define ML_TRY(expr)        \
+  do {                      \
+    int rc_ = (expr);       \
+    if (rc_ != HLBM_OK) return rc_; \
+  } while (0)
+
+size_t storage_size(int storage) { return storage == HLBM_STORE_F64 ? 8 : (storage == HLBM_STORE_F32 ? 4 : 2); }
+
+GridDims dims_of(const hlbm_lattice* h, int l) {
+  int d[3];
+  h->block_dims(l, d);
+  return GridDims{d[0], d[1], d[2]};
+}
+
+template <typename P>
+int alloc_t(hlbm_lattice* h, P** p, size_t count) {
+  void* v = nullptr;
+  int rc = LatticeOps::alloc(h, &v, count * sizeof(P));
+  *p = static_cast<P*>(v);
+  return rc;
+}
+
+LevelView view_of(const LevelData& L, GridDims d) {
+  LevelView v;
+  v.d = d;
+  v.slot = L.d_slot;
+  v.coords = L.d_coords;
+  v.mom = L.d_mom[L.cur];
+  v.mom_other = L.d_mom[1 - L.cur];
+  v.nb = L.nb;
+  return v;
+}
+
+// Transfers of Algorithm 1 ------------------------------------------------------
+
+int downward(hlbm_lattice* h, int l, int s, bool refresh) {
+  LevelData& F = h->lv[l];
+  LevelData& C = h->lv[l + 1];
+  if (F.n_down == 0) return HLBM_OK;
+  TransferArgs a{};
+  a.fine = view_of(F, dims_of(h, l));
+  a.coarse = view_of(C, dims_of(h, l + 1));
+  a.out = F.d_mom[F.cur];
+  a.nodes = F.d_down;
+  a.n_nodes = F.n_down;
+  a.avg = (!refresh && s == 2) ? 1 : 0;
+  a.use_other = (!refresh && s == 1) ? 1 : 0;
+  a.k = h->kdown[l];
+  for (int ax = 0; ax < 3; ++ax) a.periodic[ax] = h->cfg.periodic[ax];
+  a.status = h->d_status;
+  ML_CUDA(h, transfer_down(h->cfg.storage, a, h->stream));
+  return HLBM_OK;
+}
+
+int upward(hlbm_lattice* h, int l) {
+  LevelData& F = h->lv[l];
+  LevelData& C = h->lv[l + 1];
+  if (C.n_up == 0) return HLBM_OK;
+  TransferArgs a{};
+  a.fine = view_of(F, dims_of(h, l));
+  a.coarse = view_of(C, dims_of(h, l + 1));
+  a.out = C.d_mom[C.cur];
+  a.nodes = C.d_up;
+  a.n_nodes = C.n_up;
+  a.k = h->kup[l];
+  for (int ax = 0; ax < 3; ++ax) a.periodic[ax] = h->cfg.periodic[ax];
+  a.status = h->d_status;
+  ML_CUDA(h, transfer_up(h->cfg.storage, a, h->stream));
+  return HLBM_OK;
+}
+
+int streaming_collision(hlbm_lattice* h, int l) {
+  LevelData& L = h->lv[l];
+  if (L.nb == 0) {
+    L.cur = 1 - L.cur;
+    return HLBM_OK;
+  }
+  StepArgs a{};
+  a.in = L.d_mom[L.cur];
+  a.out = L.d_mom[1 - L.cur];
+  a.nbr = L.d_nbr;
+  a.F = l == 0 ? h->d_F : nullptr;
+  a.eps = l == 0 ? h->d_eps : nullptr;
+  a.solid = L.d_solid;
+  a.bflags = L.d_bflags;
+  a.bmask = L.d_bmask;
+  for (int ax = 0; ax < 3; ++ax) a.fu[ax] = l == 0 ? h->fu[ax] : 0.0;
+  a.tau = L.tau;
+  a.kxyz = h->cfg.xyz_literal ? 13.5 : 27.0;
+  a.nb = L.nb;
+  ML_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
+  L.cur = 1 - L.cur;
+  return HLBM_OK;
+}
+
+// AdvanceLBM(l, s) of Algorithm 1.
+int advance(hlbm_lattice* h, int l, int s) {
+  const int L = h->cfg.num_levels;
+  if (l < L - 1) ML_TRY(downward(h, l, s, false));
+  ML_TRY(streaming_collision(h, l));
+  if (l < L - 1 && s == 2) ML_TRY(upward(h, l));
+  if (l > 0) {
+    ML_TRY(advance(h, l - 1, 1));
+    ML_TRY(advance(h, l - 1, 2));
+  }
+  return HLBM_OK;
+}
+
+}  // namespace
+
+int ml_advance_coarse(hlbm_lattice* h, int64_t n_coarse) {
+  for (int64_t i = 0; i < n_coarse; ++i) ML_TRY(advance(h, h->cfg.num_levels - 1, 1));
+  return HLBM_OK;
+}
+
+int ml_check_status(hlbm_lattice* h) {
+  if (h->d_status == nullptr) return HLBM_OK;
+  int st = 0;
+  ML_CUDA(h, cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  ML_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (st == 1) return fail(h, HLBM_E_BAD_STATE, "a transfer stencil reached a node that is not stored");
+  if (st == 2) return fail(h, HLBM_E_BAD_STATE, "rebuild: a new node had no source at any level");
+  return HLBM_OK;
+}
+
+// Rebuild ---------------------------------------------------------------------
+
+int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_device, const int32_t* blocks,
+               int64_t n_blocks, int64_t counts_out[3]) {
+  const int L = h->cfg.num_levels;
+  cudaStream_t st = h->stream;
+  const int per[3] = {h->cfg.periodic[0], h->cfg.periodic[1], h->cfg.periodic[2]};
+  if (h->d_status == nullptr) {
+    ML_TRY(alloc_t(h, &h->d_status, 2));
+    ML_CUDA(h, cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st));
+  }
+  const bool has_old = h->have_blocks && h->device_hierarchy;
+  // 1. every old level at the same time: refill I^d from the coarser level
+  if (has_old)
+    for (int l = L - 2; l >= 0; --l) ML_TRY(downward(h, l, 1, true));
+
+  // 2. occupancy of level-0 blocks (Phi = 0 there)
+  const GridDims d0 = dims_of(h, 0);
+  uint8_t* d_occ = nullptr;
+  int* d_bad = h->d_status + 1;
+  ML_TRY(alloc_t(h, &d_occ, size_t(d0.slots())));
+  std::vector<void*> tmp = {d_occ};
+  auto cleanup = [&]() {
+    for (void*& p : tmp) LatticeOps::release(p);
+  };
+  ML_CUDA(h, cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+  if (blocks != nullptr) {
+    int32_t* d_b = nullptr;
+    if (n_blocks > 0) {
+      ML_TRY(alloc_t(h, &d_b, size_t(n_blocks) * 3));
+      tmp.push_back(d_b);
+      ML_CUDA(h, cudaMemcpyAsync(d_b, blocks, size_t(n_blocks) * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
+    ML_CUDA(h, occupancy_from_blocks(d_b, n_blocks, d0, d_occ, d_bad, st));
+  } else {
+    const float* d_p = pos;
+    if (!pos_on_device && n_pos > 0) {
+      float* d_copy = nullptr;
+      ML_TRY(alloc_t(h, &d_copy, size_t(n_pos) * 3));
+      tmp.push_back(d_copy);
+      ML_CUDA(h, cudaMemcpyAsync(d_copy, pos, size_t(n_pos) * 3 * sizeof(float), cudaMemcpyHostToDevice, st));
+      d_p = d_copy;
+    }
+    ML_CUDA(h, occupancy_from_particles(d_p, n_pos, d0, d_occ, d_bad, st));
+  }
+
+  // 3. H, I, stored, flags on the dense slot grids
+  std::vector<LevelData> nl(L);
+  for (int l = 0; l < L; ++l) nl[l].tau = h->lv[l].tau;
+  auto free_new = [&]() {
+    for (auto& X : nl) LatticeOps::free_level(X);
+  };
+  int rc = HLBM_OK;
+  std::vector<uint8_t*> d_I(L, nullptr), d_fl(L, nullptr);
+  for (int l = 0; l < L && rc == HLBM_OK; ++l) {
+    const size_t ns = size_t(dims_of(h, l).slots());
+    if ((rc = alloc_t(h, &nl[l].d_H, ns))) break;
+    if ((rc = alloc_t(h, &nl[l].d_stored, ns))) break;
+    if ((rc = alloc_t(h, &d_I[l], ns))) break;
+    tmp.push_back(d_I[l]);
+    if ((rc = alloc_t(h, &d_fl[l], ns))) break;
+    tmp.push_back(d_fl[l]);
+  }
+  if (rc) {
+    free_new();
+    cleanup();
+    return rc;
+  }
+  ML_CUDA(h, cudaMemsetAsync(nl[0].d_H, 0, size_t(d0.slots()), st));
+  for (int l = 1; l < L; ++l)
+    ML_CUDA(h, dilate_parent(l == 1 ? d_occ : nl[l - 1].d_H, dims_of(h, l - 1), nl[l].d_H, dims_of(h, l), per, st));
+  for (int l = 0; l < L; ++l)
+    ML_CUDA(h, internal_stored(nl[l].d_H, l < L - 1 ? nl[l + 1].d_H : nullptr, dims_of(h, l),
+                               l < L - 1 ? dims_of(h, l + 1) : dims_of(h, l), per, l >= 1, d_I[l], nl[l].d_stored,
+                               st));
+  for (int l = 0; l < L; ++l)
+    ML_CUDA(h, slot_flags(nl[l].d_stored, nl[l].d_H, l < L - 1 ? nl[l + 1].d_stored : nullptr, dims_of(h, l),
+                          l < L - 1 ? dims_of(h, l + 1) : dims_of(h, l), has_old ? h->lv[l].d_stored : nullptr,
+                          has_old ? h->lv[l].d_H : nullptr, has_old, d_fl[l], st));
+
+  // 4. stable compaction of every level
+  int64_t* d_cnt = nullptr;
+  int64_t max_cta = 0;
+  for (int l = 0; l < L; ++l) max_cta = std::max<int64_t>(max_cta, (dims_of(h, l).slots() + 1023) / 1024);
+  if ((rc = alloc_t(h, &d_cnt, size_t(max_cta) + 4 * L + 8))) {
+    free_new();
+    cleanup();
+    return rc;
+  }
+  tmp.push_back(d_cnt);
+  int64_t* d_tot = d_cnt + max_cta;  // [L] block counts, then [2L] interface counts
+  std::vector<uint8_t*> d_lflags(L, nullptr);
+  for (int l = 0; l < L && rc == HLBM_OK; ++l) {
+    const size_t ns = size_t(dims_of(h, l).slots());
+    if ((rc = alloc_t(h, &nl[l].d_slot, ns))) break;
+    if ((rc = alloc_t(h, &nl[l].d_coords, ns * 3))) break;
+    if ((rc = alloc_t(h, &nl[l].d_skip, ns))) break;
+    if ((rc = alloc_t(h, &d_lflags[l], ns))) break;
+    tmp.push_back(d_lflags[l]);
+    cudaError_t e = compact_slots(nl[l].d_stored, d_fl[l], nl[l].d_H, dims_of(h, l), nl[l].d_slot, nl[l].d_coords,
+                                  d_lflags[l], nl[l].d_skip, d_cnt, d_tot + l, st);
+    if (e != cudaSuccess) rc = fail(h, HLBM_E_CUDA, "compaction: %s", cudaGetErrorString(e));
+  }
+  if (rc) {
+    free_new();
+    cleanup();
+    return rc;
+  }
+  std::vector<int64_t> nb(L);
+  ML_CUDA(h, cudaMemcpyAsync(nb.data(), d_tot, L * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  ML_CUDA(h, cudaStreamSynchronize(st));
+
+  // 5. neighbour tables and interface node lists
+  for (int l = 0; l < L && rc == HLBM_OK; ++l) {
+    nl[l].nb = nb[l];
+    if (nb[l] == 0) continue;
+    if ((rc = alloc_t(h, &nl[l].d_nbr, size_t(nb[l]) * 27))) break;
+    cudaError_t e = neighbour_table(nl[l].d_coords, nb[l], nl[l].d_slot, dims_of(h, l), per, nl[l].d_nbr, st);
+    if (e != cudaSuccess) rc = fail(h, HLBM_E_CUDA, "neighbour table: %s", cudaGetErrorString(e));
+    if (rc == HLBM_OK) rc = LatticeOps::bounce(h, nl[l]);
+  }
+  std::vector<int64_t*> d_ioff(L, nullptr);
+  for (int l = 0; l < L && rc == HLBM_OK; ++l) {
+    if (nb[l] == 0) continue;
+    if ((rc = alloc_t(h, &d_ioff[l], size_t(nb[l]) * 2 + 2))) break;
+    tmp.push_back(d_ioff[l]);
+    cudaError_t e = interface_count(nl[l].d_nbr, nl[l].d_skip, nb[l], d_ioff[l], d_tot + L + 2 * l, st);
+    if (e != cudaSuccess) rc = fail(h, HLBM_E_CUDA, "interface count: %s", cudaGetErrorString(e));
+  }
+  if (rc) {
+    free_new();
+    cleanup();
+    return rc;
+  }
+  std::vector<int64_t> ic(2 * L, 0);
+  for (int l = 0; l < L; ++l)
+    if (nb[l] == 0) ML_CUDA(h, cudaMemsetAsync(d_tot + L + 2 * l, 0, 2 * sizeof(int64_t), st));
+  ML_CUDA(h, cudaMemcpyAsync(ic.data(), d_tot + L, 2 * L * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  ML_CUDA(h, cudaStreamSynchronize(st));
+  for (int l = 0; l < L && rc == HLBM_OK; ++l) {
+    nl[l].n_down = ic[2 * l];
+    nl[l].n_up = ic[2 * l + 1];
+    if (nb[l] == 0) continue;
+    if ((rc = alloc_t(h, &nl[l].d_down, size_t(nl[l].n_down) + 1))) break;
+    if ((rc = alloc_t(h, &nl[l].d_up, size_t(nl[l].n_up) + 1))) break;
+    cudaError_t e = interface_scatter(nl[l].d_nbr, nl[l].d_skip, nb[l], d_ioff[l], nl[l].d_down, nl[l].d_up, st);
+    if (e != cudaSuccess) rc = fail(h, HLBM_E_CUDA, "interface scatter: %s", cudaGetErrorString(e));
+  }
+
+  // 6. moments: survivors keep theirs, new nodes take the transfer rules
+  const size_t node_bytes = kRows * storage_size(h->cfg.storage);
+  for (int l = 0; l < L && rc == HLBM_OK; ++l)
+    for (int k = 0; k < 2 && rc == HLBM_OK; ++k)
+      rc = LatticeOps::alloc(h, &nl[l].d_mom[k], size_t(nb[l]) * kCells * node_bytes);
+  if (rc) {
+    free_new();
+    cleanup();
+    return rc;
+  }
+  if (has_old) {
+    OldHierarchy o{};
+    o.L = L;
+    for (int l = 0; l < L; ++l) {
+      o.lv[l] = view_of(h->lv[l], dims_of(h, l));
+      o.kup[l] = h->kup[l];
+      o.kdown[l] = h->kdown[l];
+    }
+    for (int ax = 0; ax < 3; ++ax) o.periodic[ax] = per[ax];
+    o.ext[0] = h->cfg.nx;
+    o.ext[1] = h->cfg.ny;
+    o.ext[2] = h->cfg.nz;
+    for (int l = 0; l < L; ++l)
+      ML_CUDA(h, init_new_level(h->cfg.storage, o, l, nl[l].d_coords, nb[l], nl[l].d_mom[0], h->d_status, st));
+  } else {
+    for (int l = 0; l < L; ++l)
+      if (nb[l]) ML_CUDA(h, cudaMemsetAsync(nl[l].d_mom[0], 0, size_t(nb[l]) * kCells * node_bytes, st));
+  }
+  for (int l = 0; l < L; ++l)
+    if (nb[l])
+      ML_CUDA(h, cudaMemcpyAsync(nl[l].d_mom[1], nl[l].d_mom[0], size_t(nb[l]) * kCells * node_bytes,
+                                 cudaMemcpyDeviceToDevice, st));
+
+  // 7. host copies of the lists; counts of refined / coarsened / deleted blocks
+  int64_t refined = 0, coarsened = 0, deleted = 0;
+  for (int l = 0; l < L; ++l) {
+    nl[l].coords.resize(size_t(nb[l]) * 3);
+    nl[l].flags.resize(size_t(nb[l]));
+    if (nb[l]) {
+      ML_CUDA(h, cudaMemcpyAsync(nl[l].coords.data(), nl[l].d_coords, size_t(nb[l]) * 3 * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, st));
+      ML_CUDA(h, cudaMemcpyAsync(nl[l].flags.data(), d_lflags[l], size_t(nb[l]), cudaMemcpyDeviceToHost, st));
+    }
+    if (counts_out != nullptr && has_old) {
+      const size_t ns = size_t(dims_of(h, l).slots());
+      std::vector<uint8_t> hn(ns), ho(ns), sn(ns), so(ns);
+      ML_CUDA(h, cudaMemcpyAsync(hn.data(), nl[l].d_H, ns, cudaMemcpyDeviceToHost, st));
+      ML_CUDA(h, cudaMemcpyAsync(ho.data(), h->lv[l].d_H, ns, cudaMemcpyDeviceToHost, st));
+      ML_CUDA(h, cudaMemcpyAsync(sn.data(), nl[l].d_stored, ns, cudaMemcpyDeviceToHost, st));
+      ML_CUDA(h, cudaMemcpyAsync(so.data(), h->lv[l].d_stored, ns, cudaMemcpyDeviceToHost, st));
+      ML_CUDA(h, cudaStreamSynchronize(st));
+      for (size_t q = 0; q < ns; ++q) {
+        refined += (hn[q] && !ho[q]);
+        coarsened += (!hn[q] && ho[q]);
+        deleted += (so[q] && !sn[q]);
+      }
+    }
+  }
+  ML_CUDA(h, cudaStreamSynchronize(st));
+  int bad = 0;
+  ML_CUDA(h, cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));
+  cleanup();
+  for (auto& X : h->lv) LatticeOps::free_level(X);
+  for (int l = 0; l < L; ++l) {
+    nl[l].cur = 0;
+    h->lv[l] = nl[l];
+  }
+  // the level-0 force field refers to the old block list
+  void* v = h->d_F;
+  LatticeOps::release(v);
+  h->d_F = nullptr;
+  v = h->d_eps;
+  LatticeOps::release(v);
+  h->d_eps = nullptr;
+  h->have_blocks = true;
+  h->device_hierarchy = true;
+  if (counts_out != nullptr) {
+    counts_out[0] = refined;
+    counts_out[1] = coarsened;
+    counts_out[2] = deleted;
+  }
+  ML_TRY(ml_check_status(h));
+  if (bad) return fail(h, HLBM_E_NONFINITE, "%d particle positions are not finite (ignored)", bad);
+  return HLBM_OK;
+}
+
+}  // namespace hlbm

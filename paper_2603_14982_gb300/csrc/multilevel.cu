@@ -1,0 +1,245 @@
+// multilevel.cu -- downward/upward transfers of Algorithm 1 and the moment
+// initialisation of blocks created by a rebuild (Sec. 4.2, Sec. 5.3).
+//
+// All transfer arithmetic is FP64: moments are read from storage, split into
+// (rho, u, S^neq = S - u u), combined with exact power-of-two weights, rescaled
+// and recombined as S = k S^neq + u u with u the combined velocity (S^eq is
+// formed from the interpolated velocity).
+#include "hlbm_internal.h"
+#include "multilevel.cuh"
+
+namespace hlbm {
+namespace {
+
+struct Node64 {
+  double rho, ux, uy, uz, s[6];  // s = S^neq (xx, yy, zz, xy, xz, yz)
+};
+
+template <typename T>
+__device__ __forceinline__ Node64 load64(const void* base, int64_t blk, int cell) {
+  const auto m = load_node<T>(static_cast<const T*>(base), blk, cell, nullptr);
+  Node64 n;
+  n.rho = 1.0 + double(m.drho);
+  n.ux = m.ux;
+  n.uy = m.uy;
+  n.uz = m.uz;
+  n.s[0] = double(m.sxx) - n.ux * n.ux;
+  n.s[1] = double(m.syy) - n.uy * n.uy;
+  n.s[2] = double(m.szz) - n.uz * n.uz;
+  n.s[3] = double(m.sxy) - n.ux * n.uy;
+  n.s[4] = double(m.sxz) - n.ux * n.uz;
+  n.s[5] = double(m.syz) - n.uy * n.uz;
+  return n;
+}
+
+template <typename T>
+__device__ __forceinline__ void store64(void* base, int64_t blk, int cell, const Node64& n, double k) {
+  using R = typename StorageTraits<T>::R;
+  Mom<R> m;
+  m.drho = R(n.rho - 1.0);
+  m.ux = R(n.ux);
+  m.uy = R(n.uy);
+  m.uz = R(n.uz);
+  m.sxx = R(k * n.s[0] + n.ux * n.ux);
+  m.syy = R(k * n.s[1] + n.uy * n.uy);
+  m.szz = R(k * n.s[2] + n.uz * n.uz);
+  m.sxy = R(k * n.s[3] + n.ux * n.uy);
+  m.sxz = R(k * n.s[4] + n.ux * n.uz);
+  m.syz = R(k * n.s[5] + n.uy * n.uz);
+  store_node<T>(static_cast<T*>(base), blk, cell, m, nullptr);
+}
+
+__device__ __forceinline__ void axpy(Node64& acc, double w, const Node64& v) {
+  acc.rho += w * v.rho;
+  acc.ux += w * v.ux;
+  acc.uy += w * v.uy;
+  acc.uz += w * v.uz;
+#pragma unroll
+  for (int r = 0; r < 6; ++r) acc.s[r] += w * v.s[r];
+}
+
+__device__ __forceinline__ Node64 zero64() {
+  Node64 n;
+  n.rho = n.ux = n.uy = n.uz = 0.0;
+#pragma unroll
+  for (int r = 0; r < 6; ++r) n.s[r] = 0.0;
+  return n;
+}
+
+// Block index holding level node (x, y, z) (node coordinates of that level), or -1.
+__device__ __forceinline__ int64_t lookup(const LevelView& v, int x, int y, int z) {
+  const int bx = x >> 3, by = y >> 3, bz = z >> 3;
+  if (bx < 0 || by < 0 || bz < 0 || bx >= v.d.nx || by >= v.d.ny || bz >= v.d.nz) return -1;
+  return v.slot[(int64_t(bz) * v.d.ny + by) * v.d.nx + bx];
+}
+
+__device__ __forceinline__ int cell_of(int x, int y, int z) { return (x & 7) + 8 * (y & 7) + 64 * (z & 7); }
+
+// floor(p/2) and ceil(p/2) on a coarse axis of n nodes: ceil wraps on a
+// periodic axis and is clamped to the last node on a wall axis.
+__device__ __forceinline__ void pair(int p, int n, int periodic, int& lo, int& hi) {
+  lo = p >> 1;
+  hi = (p + 1) >> 1;
+  if (hi >= n) hi = periodic ? hi - n : n - 1;
+}
+
+template <typename T>
+__global__ void k_down(TransferArgs a) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= a.n_nodes) return;
+  const int32_t v = a.nodes[k];
+  const int64_t b = v >> 9;
+  const int cell = v & 511;
+  const int32_t* c = a.fine.coords + 3 * b;
+  const int p[3] = {c[0] * 8 + (cell & 7), c[1] * 8 + ((cell >> 3) & 7), c[2] * 8 + (cell >> 6)};
+  const int n[3] = {a.coarse.d.nx * 8, a.coarse.d.ny * 8, a.coarse.d.nz * 8};
+  int lo[3], hi[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) pair(p[ax], n[ax], a.periodic[ax], lo[ax], hi[ax]);
+  Node64 acc = zero64();
+  for (int q = 0; q < 8; ++q) {
+    const int x = (q & 1) ? hi[0] : lo[0], y = (q & 2) ? hi[1] : lo[1], z = (q & 4) ? hi[2] : lo[2];
+    const int64_t cb = lookup(a.coarse, x, y, z);
+    if (cb < 0) {
+      atomicExch(a.status, 1);
+      return;
+    }
+    const int cc = cell_of(x, y, z);
+    if (a.avg) {
+      // temporal midpoint of the old (other) and new (current) coarse states,
+      // taken per field on rho, u and S^neq
+      const Node64 o = load64<T>(a.coarse.mom_other, cb, cc);
+      const Node64 nw = load64<T>(a.coarse.mom, cb, cc);
+      axpy(acc, 0.0625, o);
+      axpy(acc, 0.0625, nw);
+    } else {
+      axpy(acc, 0.125, load64<T>(a.use_other ? a.coarse.mom_other : a.coarse.mom, cb, cc));
+    }
+  }
+  store64<T>(a.out, b, cell, acc, a.k);
+}
+
+template <typename T>
+__global__ void k_up(TransferArgs a) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= a.n_nodes) return;
+  const int32_t v = a.nodes[k];
+  const int64_t b = v >> 9;
+  const int cell = v & 511;
+  const int32_t* c = a.coarse.coords + 3 * b;
+  const int x = 2 * (c[0] * 8 + (cell & 7)), y = 2 * (c[1] * 8 + ((cell >> 3) & 7)), z = 2 * (c[2] * 8 + (cell >> 6));
+  const int64_t fb = lookup(a.fine, x, y, z);
+  if (fb < 0) {
+    atomicExch(a.status, 1);
+    return;
+  }
+  store64<T>(a.out, b, cell, load64<T>(a.fine.mom, fb, cell_of(x, y, z)), a.k);
+}
+
+// U_l(i): the stored value at level l, else the upward rule applied to U_{l-1}(2i).
+template <typename T>
+__device__ bool resolve_up(const OldHierarchy& o, int l, int x, int y, int z, Node64& out) {
+  for (int m = 0; m <= l; ++m) {
+    const int lev = l - m;
+    const int px = x << m, py = y << m, pz = z << m;
+    const int64_t b = lookup(o.lv[lev], px, py, pz);
+    if (b < 0) continue;
+    out = load64<T>(o.lv[lev].mom, b, cell_of(px, py, pz));
+    for (int k = lev; k < l; ++k)
+#pragma unroll
+      for (int r = 0; r < 6; ++r) out.s[r] *= o.kup[k];
+    return true;
+  }
+  return false;
+}
+
+// D_l(i): U_l(i) if defined, else the downward spatial rule over D_{l+1}.
+template <typename T, int DEPTH>
+__device__ bool resolve(const OldHierarchy& o, int l, int x, int y, int z, Node64& out) {
+  if (resolve_up<T>(o, l, x, y, z, out)) return true;
+  if constexpr (DEPTH == 0) {
+    return false;
+  } else {
+    if (l >= o.L - 1) return false;
+    const int n[3] = {o.ext[0] >> (l + 1), o.ext[1] >> (l + 1), o.ext[2] >> (l + 1)};
+    const int p[3] = {x, y, z};
+    int lo[3], hi[3];
+    for (int ax = 0; ax < 3; ++ax) pair(p[ax], n[ax], o.periodic[ax], lo[ax], hi[ax]);
+    Node64 acc = zero64();
+    for (int q = 0; q < 8; ++q) {
+      Node64 cnode;
+      if (!resolve<T, DEPTH - 1>(o, l + 1, (q & 1) ? hi[0] : lo[0], (q & 2) ? hi[1] : lo[1], (q & 4) ? hi[2] : lo[2],
+                                 cnode))
+        return false;
+      axpy(acc, 0.125, cnode);
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) acc.s[r] *= o.kdown[l];
+    out = acc;
+    return true;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_init_level(OldHierarchy o, int level, const int32_t* __restrict__ coords,
+                                                    void* out, int* status) {
+  const int64_t b = blockIdx.x;
+  const int cell = threadIdx.x;
+  const int x = coords[3 * b] * 8 + (cell & 7), y = coords[3 * b + 1] * 8 + ((cell >> 3) & 7),
+            z = coords[3 * b + 2] * 8 + (cell >> 6);
+  Node64 v;
+  if (!resolve<T, kMaxLevels - 1>(o, level, x, y, z, v)) {
+    atomicExch(status, 2);
+    v = zero64();
+    v.rho = 1.0;
+  }
+  store64<T>(out, b, cell, v, 1.0);
+}
+
+inline unsigned blocks_for(int64_t n) { return unsigned((n + 255) / 256); }
+
+template <typename T>
+cudaError_t down_typed(const TransferArgs& a, cudaStream_t s) {
+  if (a.n_nodes == 0) return cudaSuccess;
+  k_down<T><<<blocks_for(a.n_nodes), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t up_typed(const TransferArgs& a, cudaStream_t s) {
+  if (a.n_nodes == 0) return cudaSuccess;
+  k_up<T><<<blocks_for(a.n_nodes), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t init_typed(const OldHierarchy& o, int level, const int32_t* coords, int64_t nb, void* out, int* status,
+                       cudaStream_t s) {
+  if (nb == 0) return cudaSuccess;
+  k_init_level<T><<<unsigned(nb), 512, 0, s>>>(o, level, coords, out, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define HLBM_ML_DISPATCH(storage, fn, ...)                        \
+  switch (storage) {                                              \
+    case HLBM_STORE_F64: return fn<double>(__VA_ARGS__);          \
+    case HLBM_STORE_F32: return fn<float>(__VA_ARGS__);           \
+    default: return cudaErrorNotSupported;                        \
+  }
+
+cudaError_t transfer_down(int storage, const TransferArgs& a, cudaStream_t s) {
+  HLBM_ML_DISPATCH(storage, down_typed, a, s)
+}
+
+cudaError_t transfer_up(int storage, const TransferArgs& a, cudaStream_t s) {
+  HLBM_ML_DISPATCH(storage, up_typed, a, s)
+}
+
+cudaError_t init_new_level(int storage, const OldHierarchy& old, int level, const int32_t* coords, int64_t nb,
+                           void* out, int* status, cudaStream_t s) {
+  HLBM_ML_DISPATCH(storage, init_typed, old, level, coords, nb, out, status, s)
+}
+
+}  // namespace hlbm

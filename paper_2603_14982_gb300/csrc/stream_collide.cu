@@ -1,4 +1,5 @@
-// stream_collide.cu -- fused pull-stream + moment-space collision of one level.
+// stream_collide.cu -- fused pull-stream + moment-space collision of one level
+// with FP64 storage and arithmetic (one node per thread).
 //
 // One CTA per stored 8^3 block, one thread per node (512 threads).
 //  1. every fluid node of the block reconstructs its 27 post-collision
@@ -256,10 +257,7 @@ cudaError_t launch_typed(const StepArgs& a, cudaStream_t s) {
 cudaError_t launch_stream_collide(int storage, const StepArgs& a, cudaStream_t s) {
   switch (storage) {
     case HLBM_STORE_F64: return launch_typed<double>(a, s);
-    case HLBM_STORE_F32: return launch_typed<float>(a, s);
-    case HLBM_STORE_F16S: return launch_typed<__half>(a, s);
-    case HLBM_STORE_BF16S: return launch_typed<__nv_bfloat16>(a, s);
-    default: return cudaErrorInvalidValue;
+    default: return launch_stream_collide_f2(storage, a, s);
   }
 }
 

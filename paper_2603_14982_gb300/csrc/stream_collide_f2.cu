@@ -1,0 +1,430 @@
+// stream_collide_f2.cu -- FP32-math stream-collide for FP32 and reduced-precision
+// storage: two nodes per thread with packed FP32 arithmetic.
+//
+// One CTA per stored 8^3 block, 256 threads.  Thread (lane, warp) owns the node
+// pair (x, y, z0) and (x, y, z0 + 4) with x = lane & 7, y = (lane >> 3) + 4 (warp & 1),
+// z0 = warp >> 1.  Shared memory holds, per direction j != rest, the pulled
+// population of every node of the block, destination-indexed; a node pair
+// shares one 8-byte slot (node z0 in .x, node z0 + 4 in .y).
+//  A. each thread reconstructs the 26 moving populations of its pair
+//     (Eq. three_order_f) and pushes them to their destinations x + c_j with
+//     wrap-around inside the block: one 64-bit store per direction.  Pushes
+//     that leave the block land, wrapped, exactly in the slots whose true
+//     source is a halo node, so they are overwritten in B.
+//  B. 244 threads each take a pair of halo nodes (read from the 26 neighbour
+//     blocks, mostly L2 hits) and write the 9 directions that enter the block;
+//     nodes whose pull source is a wall or a solid node write their own
+//     opposite population instead (half-way bounce-back).
+//  C. each thread reads the 26 populations of its pair (one 64-bit load per
+//     direction), projects to moments (Eq. rho_u_stress) and collides
+//     (Sec. 3.1; Guo forcing; mixture tau of Sec. 4).  Interface nodes (a
+//     neighbour block not stored) and solid nodes copy their input.
+#include <utility>
+
+#include "hlbm_internal.h"
+#include "lbm_math.cuh"
+#include "v2.cuh"
+
+namespace hlbm {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kHaloPairs = 244;
+
+__host__ __device__ constexpr int slot_of(int j) { return j < 13 ? j : j - 1; }
+
+struct OwnPush {
+  float2* f;
+  int X[3], Y8[3], Z64[3];
+  bool swap[3];
+  V2 g13;
+  template <int J>
+  __device__ __forceinline__ void put(V2 v) {
+    if constexpr (J == 13) {
+      g13 = v;
+    } else {
+      constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
+      const int s = X[cx + 1] + Y8[cy + 1] + Z64[cz + 1];
+      f[slot_of(J) * 256 + s] = swap[cz + 1] ? make_float2(v.v.y, v.v.x) : v.v;
+    }
+  }
+};
+
+constexpr int kTrash = 26 * 512;  // per-lane dummy float slots for masked halo stores
+
+// Halo node pair a = (hx, hy, hz), b = (hx, hy, hz + 4), hz < 4, on an x or y
+// face (inward component SG on axis AX): destinations are addressed like the
+// own pushes (pair slot + half, halves swapped where z wraps); a destination
+// outside the block, or an invalid source, goes to the lane's trash slot.
+template <int AX, int SG>
+struct HaloPushXY {
+  float* f;
+  int X[3], Y8[3], Z64[3];
+  unsigned swp;             // bit (cz+1): node a lands in the high half
+  unsigned vx, vy, vza, vzb;  // bit (c+1): destination coordinate in range
+  bool va, vb;
+  int trash;
+  template <int J>
+  __device__ __forceinline__ void put(V2 v) {
+    constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
+    constexpr int c = AX == 0 ? cx : cy;
+    if constexpr (c == SG) {
+      const int p2 = 2 * (slot_of(J) * 256 + X[cx + 1] + Y8[cy + 1] + Z64[cz + 1]);
+      const bool rng = ((vx >> (cx + 1)) & (vy >> (cy + 1)) & 1u) != 0u;
+      const int ha = (swp >> (cz + 1)) & 1;
+      const bool oka = va && rng && ((vza >> (cz + 1)) & 1u);
+      const bool okb = vb && rng && ((vzb >> (cz + 1)) & 1u);
+      f[oka ? p2 + ha : trash] = v.v.x;
+      f[okb ? p2 + 1 - ha : trash] = v.v.y;
+    }
+  }
+};
+
+// Halo node pair a = (hx, hy, hz), b = (hx, hy + 5, hz) on a z face (hz = -1 or
+// 8; destinations in plane z = 0 or 7, half 0 or 1).
+template <int SG>
+struct HaloPushZ {
+  float* f;
+  int X[3], Y8a[3], Y8b[3];
+  int zoff;                    // 2 * 64 * (z_dest & 3) + (z_dest >> 2)
+  unsigned vx, vya, vyb;
+  bool va, vb;
+  int trash;
+  template <int J>
+  __device__ __forceinline__ void put(V2 v) {
+    constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
+    if constexpr (cz == SG) {
+      const int base = 2 * (slot_of(J) * 256 + X[cx + 1]) + zoff;
+      const unsigned okx = (vx >> (cx + 1)) & 1u;
+      const bool oka = va && (okx & (vya >> (cy + 1)));
+      const bool okb = vb && (okx & (vyb >> (cy + 1)));
+      f[oka ? base + 2 * Y8a[cy + 1] : trash] = v.v.x;
+      f[okb ? base + 2 * Y8b[cy + 1] : trash] = v.v.y;
+    }
+  }
+};
+
+__device__ __forceinline__ unsigned range_mask(int v) {
+  // bit (c+1) set when v + c lies in [0, 8), c in {-1, 0, 1}
+  return ((unsigned)(v - 1) < 8u ? 1u : 0u) | ((unsigned)v < 8u ? 2u : 0u) | ((unsigned)(v + 1) < 8u ? 4u : 0u);
+}
+
+// Half-way bounce-back: bit k of mask = the pull source x - c_k of this node is
+// a wall or a solid node, so slot k of the node receives its own population opp(k).
+struct BouncePush {
+  float* f;
+  int own;  // pair slot
+  unsigned mlo, mhi;
+  template <int J>
+  __device__ __forceinline__ void put(V2 v) {
+    if constexpr (J != 13) {
+      constexpr int K = 26 - J;
+      if ((mlo >> K) & 1u) f[2 * (slot_of(K) * 256 + own)] = v.v.x;
+      if ((mhi >> K) & 1u) f[2 * (slot_of(K) * 256 + own) + 1] = v.v.y;
+    }
+  }
+};
+
+template <int J>
+__device__ __forceinline__ void gather_one(const float2* f, int own, V2 g13, V2 (&g)[27]) {
+  if constexpr (J == 13)
+    g[13] = g13;
+  else
+    g[J] = V2(f[slot_of(J) * 256 + own]);
+}
+
+template <int... Js>
+__device__ __forceinline__ void gather_all(const float2* f, int own, V2 g13, V2 (&g)[27],
+                                           std::integer_sequence<int, Js...>) {
+  (gather_one<Js>(f, own, g13, g), ...);
+}
+
+__device__ __forceinline__ void halo_pair(int t, int& face, int& ax, int& ay, int& az, int& bx, int& by, int& bz) {
+  if (t < 100) {
+    const int q = t < 50 ? t : t - 50;
+    ax = bx = q % 10 - 1;
+    ay = q / 10 - 1;
+    by = ay + 5;
+    az = bz = t < 50 ? -1 : 8;
+    face = t < 50 ? 4 : 5;
+  } else if (t < 180) {
+    const int q = t < 140 ? t - 100 : t - 140;
+    ax = bx = q % 10 - 1;
+    ay = by = t < 140 ? -1 : 8;
+    az = q / 10;
+    bz = az + 4;
+    face = t < 140 ? 2 : 3;
+  } else {
+    const int q = t < 212 ? t - 180 : t - 212;
+    ax = bx = t < 212 ? -1 : 8;
+    ay = by = q % 8;
+    az = q / 8;
+    bz = az + 4;
+    face = t < 212 ? 0 : 1;
+  }
+}
+
+__device__ __forceinline__ int block_dir(int hx, int hy, int hz) {
+  const int dx = hx < 0 ? -1 : (hx > 7 ? 1 : 0);
+  const int dy = hy < 0 ? -1 : (hy > 7 ? 1 : 0);
+  const int dz = hz < 0 ? -1 : (hz > 7 ? 1 : 0);
+  return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+}
+
+__device__ __forceinline__ bool touches_missing(int x, int y, int z, unsigned miss) {
+  const unsigned mx = 2u | (x == 0 ? 1u : 0u) | (x == 7 ? 4u : 0u);
+  const unsigned my = 2u | (y == 0 ? 1u : 0u) | (y == 7 ? 4u : 0u);
+  const unsigned mz = 2u | (z == 0 ? 1u : 0u) | (z == 7 ? 4u : 0u);
+  unsigned touched = 0;
+#pragma unroll
+  for (int iz = 0; iz < 3; ++iz)
+#pragma unroll
+    for (int iy = 0; iy < 3; ++iy)
+      if (((mz >> iz) & 1u) && ((my >> iy) & 1u)) touched |= mx << (3 * iy + 9 * iz);
+  return (touched & miss) != 0u;
+}
+
+__device__ __forceinline__ Mom<V2> pack(const Mom<float>& a, const Mom<float>& b) {
+  Mom<V2> m;
+  m.drho = V2(a.drho, b.drho);
+  m.ux = V2(a.ux, b.ux);
+  m.uy = V2(a.uy, b.uy);
+  m.uz = V2(a.uz, b.uz);
+  m.sxx = V2(a.sxx, b.sxx);
+  m.syy = V2(a.syy, b.syy);
+  m.szz = V2(a.szz, b.szz);
+  m.sxy = V2(a.sxy, b.sxy);
+  m.sxz = V2(a.sxz, b.sxz);
+  m.syz = V2(a.syz, b.syz);
+  return m;
+}
+
+__device__ __forceinline__ Mom<V2> select_halves(const Mom<V2>& a, const Mom<V2>& b, bool lo_b, bool hi_b) {
+  // per half: b where the flag is set, else a
+  auto sel = [&](V2 x, V2 y) { return V2(lo_b ? y.v.x : x.v.x, hi_b ? y.v.y : x.v.y); };
+  Mom<V2> r;
+  r.drho = sel(a.drho, b.drho);
+  r.ux = sel(a.ux, b.ux);
+  r.uy = sel(a.uy, b.uy);
+  r.uz = sel(a.uz, b.uz);
+  r.sxx = sel(a.sxx, b.sxx);
+  r.syy = sel(a.syy, b.syy);
+  r.szz = sel(a.szz, b.szz);
+  r.sxy = sel(a.sxy, b.sxy);
+  r.sxz = sel(a.sxz, b.sxz);
+  r.syz = sel(a.syz, b.syz);
+  return r;
+}
+
+__device__ __forceinline__ Mom<V2> zero_pair() {
+  Mom<V2> m;
+  m.drho = m.ux = m.uy = m.uz = m.sxx = m.syy = m.szz = m.sxy = m.sxz = m.syz = V2(0.f);
+  return m;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
+  extern __shared__ __align__(16) float2 f2buf[];  // [26][256] node pairs + trash
+  float* fbuf = reinterpret_cast<float*>(f2buf);
+  __shared__ int s_nbr[27];
+  __shared__ unsigned s_miss;
+
+  const int64_t blk = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int x = lane & 7, y = (lane >> 3) + ((w & 1) << 2), z0 = w >> 1;
+  const int own = x + 8 * y + 64 * z0;
+  const T* in = static_cast<const T*>(a.in);
+  T* out = static_cast<T*>(a.out);
+  const Scales* sc_in = a.scales_in;
+
+  if (t < 32) {
+    const int v = t < 27 ? a.nbr[blk * 27 + t] : 0;
+    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && v == kMissing);
+    if (t < 27) s_nbr[t] = v;
+    if (t == 0) s_miss = mb;
+  }
+  const uint8_t bf = a.bflags != nullptr ? a.bflags[blk] : 0;
+  const bool solid_any = (bf & kBlockSolidNear) != 0;
+
+  // own node pair: issue the loads early
+  const Mom<V2> m = load_pair<T>(in, blk, own, sc_in);
+  int face = -1, hax = 0, hay = 0, haz = 0, hbx = 0, hby = 0, hbz = 0;
+  if (t < kHaloPairs) halo_pair(t, face, hax, hay, haz, hbx, hby, hbz);
+  __syncthreads();  // s_nbr, s_miss
+
+  bool va = false, vb = false;
+  Mom<V2> hm = zero_pair();
+  if (t < kHaloPairs) {
+    const int na = s_nbr[block_dir(hax, hay, haz)], nb = s_nbr[block_dir(hbx, hby, hbz)];
+    const int sa = (hax & 7) + 8 * (hay & 7) + 64 * (haz & 7), sb = (hbx & 7) + 8 * (hby & 7) + 64 * (hbz & 7);
+    va = na >= 0 && !(solid_any && a.solid[int64_t(na) * kCells + sa]);
+    vb = nb >= 0 && !(solid_any && a.solid[int64_t(nb) * kCells + sb]);
+    if (face < 4) {  // x / y faces: a and b are one stored pair of the same neighbour
+      if (na >= 0) hm = load_pair<T>(in, na, sa, sc_in);
+    } else {
+      Mom<float> la, lb;
+      la.drho = la.ux = la.uy = la.uz = la.sxx = la.syy = la.szz = la.sxy = la.sxz = la.syz = 0.f;
+      lb = la;
+      if (na >= 0) la = load_node<T>(in, na, sa, sc_in);
+      if (nb >= 0) lb = load_node<T>(in, nb, sb, sc_in);
+      hm = pack(la, lb);
+    }
+  }
+
+  // A. push the own pair
+  const V2 kxyz = V2(float(a.kxyz));
+  OwnPush op;
+  op.f = f2buf;
+#pragma unroll
+  for (int c = -1; c <= 1; ++c) {
+    op.X[c + 1] = (x + c) & 7;
+    op.Y8[c + 1] = 8 * ((y + c) & 7);
+    op.Z64[c + 1] = 64 * ((z0 + c) & 3);
+    op.swap[c + 1] = (((z0 + c) & 7) >> 2) != 0;
+  }
+  emit_all(make_coef(m, kxyz), op);
+  __syncthreads();
+
+  // B. halo pairs and bounce-back
+  if (t < kHaloPairs && (va || vb)) {
+    const Coef<V2> c = make_coef(hm, kxyz);
+    const int trash = kTrash + lane;
+    if (face < 4) {
+      int X[3], Y8[3], Z64[3];
+      unsigned swp = 0;
+#pragma unroll
+      for (int k = -1; k <= 1; ++k) {
+        X[k + 1] = (hax + k) & 7;
+        Y8[k + 1] = 8 * ((hay + k) & 7);
+        Z64[k + 1] = 64 * ((haz + k) & 3);
+        swp |= ((((haz + k) & 7) >> 2) & 1u) << (k + 1);
+      }
+      const unsigned vx = range_mask(hax), vy = range_mask(hay), vza = range_mask(haz), vzb = range_mask(hbz);
+      switch (face) {
+        case 0: { HaloPushXY<0, 1> s{fbuf, {X[0], X[1], X[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
+        case 1: { HaloPushXY<0, -1> s{fbuf, {X[0], X[1], X[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
+        case 2: { HaloPushXY<1, 1> s{fbuf, {X[0], X[1], X[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
+        default: { HaloPushXY<1, -1> s{fbuf, {X[0], X[1], X[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
+      }
+    } else {
+      int X[3], Y8a[3], Y8b[3];
+#pragma unroll
+      for (int k = -1; k <= 1; ++k) {
+        X[k + 1] = (hax + k) & 7;
+        Y8a[k + 1] = 8 * ((hay + k) & 7);
+        Y8b[k + 1] = 8 * ((hby + k) & 7);
+      }
+      const unsigned vx = range_mask(hax), vya = range_mask(hay), vyb = range_mask(hby);
+      if (face == 4) {
+        HaloPushZ<1> s{fbuf, {X[0], X[1], X[2]}, {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, 0, vx, vya, vyb, va, vb, trash};
+        emit_all(c, s);
+      } else {
+        HaloPushZ<-1> s{fbuf, {X[0], X[1], X[2]}, {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, 2 * 64 * 3 + 1, vx, vya, vyb, va, vb, trash};
+        emit_all(c, s);
+      }
+    }
+  }
+  if (bf & kBlockBounce) {  // block-uniform
+    const unsigned mlo_b = a.bmask[blk * kCells + own], mhi_b = a.bmask[blk * kCells + own + 256];
+    if ((mlo_b | mhi_b) != 0u) {
+      BouncePush bp{fbuf, own, mlo_b, mhi_b};
+      emit_all(make_coef(load_pair<T>(in, blk, own, sc_in), kxyz), bp);
+    }
+  }
+  __syncthreads();
+
+  // C. gather, project, collide
+  bool copy_lo = false, copy_hi = false;
+  if (solid_any) {
+    copy_lo = a.solid[blk * kCells + own] != 0;
+    copy_hi = a.solid[blk * kCells + own + 256] != 0;
+  }
+  if (s_miss != 0u) {
+    copy_lo = copy_lo || touches_missing(x, y, z0, s_miss);
+    copy_hi = copy_hi || touches_missing(x, y, z0 + 4, s_miss);
+  }
+  Mom<V2> mo;
+  if (copy_lo && copy_hi) {
+    mo = load_pair<T>(in, blk, own, sc_in);
+  } else {
+    V2 g[27];
+    gather_all(f2buf, own, op.g13, g, std::make_integer_sequence<int, 27>{});
+    const PreMom<V2> p = project(g);
+    V2 fx, fy, fz;
+    if (a.F != nullptr) {
+      const float* Fp = a.F + blk * 3 * kCells + own;
+      fx = V2(__ldg(Fp), __ldg(Fp + 256));
+      fy = V2(__ldg(Fp + kCells), __ldg(Fp + kCells + 256));
+      fz = V2(__ldg(Fp + 2 * kCells), __ldg(Fp + 2 * kCells + 256));
+    } else {
+      fx = V2(float(a.fu[0]));
+      fy = V2(float(a.fu[1]));
+      fz = V2(float(a.fu[2]));
+    }
+    V2 tau = V2(float(a.tau));
+    if (a.eps != nullptr) tau = tau * V2(__ldg(a.eps + blk * kCells + own), __ldg(a.eps + blk * kCells + own + 256));
+    mo = collide(p, fx, fy, fz, V2(1) / tau);
+    if (copy_lo || copy_hi) mo = select_halves(mo, load_pair<T>(in, blk, own, sc_in), copy_lo, copy_hi);
+  }
+  store_pair<T>(out, blk, own, mo, a.scales_out);
+}
+
+// Per-node bounce masks: bit k set when the pull source x - c_k of node x is
+// beyond a wall or a solid node.  Sets kBlockBounce on blocks with any bit.
+__global__ void __launch_bounds__(512) k_bounce_masks(const int32_t* __restrict__ nbr,
+                                                      const uint8_t* __restrict__ solid, uint8_t* __restrict__ bflags,
+                                                      uint32_t* __restrict__ bmask) {
+  const int64_t blk = blockIdx.x;
+  const int n = threadIdx.x;
+  const int x = n & 7, y = (n >> 3) & 7, z = n >> 6;
+  const bool solid_any = solid != nullptr && (bflags[blk] & kBlockSolidNear);
+  unsigned m = 0;
+  for (int k = 0; k < 27; ++k) {
+    if (k == 13) continue;
+    const int sx = x - (k % 3 - 1), sy = y - ((k / 3) % 3 - 1), sz = z - (k / 9 - 1);
+    const int dx = sx < 0 ? -1 : (sx > 7 ? 1 : 0), dy = sy < 0 ? -1 : (sy > 7 ? 1 : 0),
+              dz = sz < 0 ? -1 : (sz > 7 ? 1 : 0);
+    const int32_t q = nbr[blk * 27 + (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+    bool hit = q == kWall;
+    if (!hit && solid_any && q >= 0) hit = solid[int64_t(q) * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7)] != 0;
+    if (hit) m |= 1u << k;
+  }
+  bmask[blk * kCells + n] = m;
+  const int any = __syncthreads_or(m != 0u);
+  if (n == 0) bflags[blk] = uint8_t((bflags[blk] & ~kBlockBounce) | (any ? kBlockBounce : 0));
+}
+
+template <typename T>
+cudaError_t launch_f2(const StepArgs& a, cudaStream_t s) {
+  const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t err =
+        cudaFuncSetAttribute(k_stream_collide_f2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    configured = true;
+  }
+  if (a.nb == 0) return cudaSuccess;
+  k_stream_collide_f2<T><<<(unsigned)a.nb, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_stream_collide_f2(int storage, const StepArgs& a, cudaStream_t s) {
+  switch (storage) {
+    case HLBM_STORE_F32: return launch_f2<float>(a, s);
+    case HLBM_STORE_F16S: return launch_f2<__half>(a, s);
+    case HLBM_STORE_BF16S: return launch_f2<__nv_bfloat16>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t compute_bounce_masks(const int32_t* nbr, const uint8_t* solid, uint8_t* bflags, uint32_t* bmask, int64_t nb,
+                                 cudaStream_t s) {
+  if (nb == 0) return cudaSuccess;
+  k_bounce_masks<<<unsigned(nb), 512, 0, s>>>(nbr, solid, bflags, bmask);
+  return cudaGetLastError();
+}
+
+}  // namespace hlbm

@@ -47,6 +47,11 @@ _SIGS = {
     "hlbm_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
     "hlbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hlbm_set_dense": (ctypes.c_int32, [ctypes.c_void_p]),
+    "hlbm_set_fine_blocks": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "hlbm_rebuild_from_particles": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                     ctypes.c_int32, ctypes.c_void_p]),
+    "hlbm_get_interface_nodes": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                                  ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "hlbm_num_blocks": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
     "hlbm_get_blocks": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]),
@@ -159,6 +164,30 @@ class Lattice:
     # ---- blocks
     def set_dense(self):
         self._check(self.lib.hlbm_set_dense(self.h))
+
+    def set_fine_blocks(self, coords):
+        """coords: int32 (n, 3) level-0 block coordinates (bx, by, bz) where Phi = 0."""
+        c = np.ascontiguousarray(np.asarray(coords, dtype=np.int32).reshape(-1, 3))
+        self._check(self.lib.hlbm_set_fine_blocks(self.h, c.ctypes.data if len(c) else None, len(c)))
+
+    def rebuild_from_particles(self, pos):
+        """pos: float32 (n, 3) numpy (host) or torch CUDA tensor; returns (refined, coarsened, deleted)."""
+        counts = np.zeros(3, dtype=np.int64)
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, dtype=np.float32)
+        p, dev = _ptr(pos)
+        n = int(pos.shape[0])
+        self._check(self.lib.hlbm_rebuild_from_particles(self.h, p if n else None, n, dev, counts.ctypes.data))
+        return tuple(int(v) for v in counts)
+
+    def interface_nodes(self, level, which):
+        """int32 array of (block << 9) | node of I^d (which=0) or I^u (which=1)."""
+        n = ctypes.c_int64()
+        self.lib.hlbm_get_interface_nodes(self.h, level, which, None, 0, ctypes.byref(n))
+        out = np.zeros(max(n.value, 1), dtype=np.int32)
+        self._check(self.lib.hlbm_get_interface_nodes(self.h, level, which, out.ctypes.data, n.value,
+                                                      ctypes.byref(n)))
+        return out[:n.value]
 
     def num_blocks(self, level=0):
         n = ctypes.c_int64()

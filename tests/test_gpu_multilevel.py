@@ -1,0 +1,190 @@
+"""Multi-level path on the GPU against the oracle.
+
+* hierarchy maintenance (occupancy -> Phi, sets, flags, compaction, interface
+  node lists) must match the oracle's declarative hierarchy bit-exactly, over a
+  sequence of rebuilds of a falling particle cloud;
+* Algorithm 1 with downward/upward transfers: FP64 storage agrees with the
+  oracle to 1e-11 on every stored node, FP32 within 1e-5 per coarse step;
+* rebuilds carry the moments over (survivors copied, new nodes interpolated)
+  as the oracle does.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hierarchy as hy
+from oracle import multilevel as ml
+from paper_2603_14982_gb300 import homelbm as hl
+from paper_2603_14982_gb300 import workloads as wl
+from tests.helpers import rel_err, row_scales
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_nodes(h, l, which):
+    """(block index << 9) | cell of the oracle's I^d (which=0) / I^u (which=1) nodes."""
+    mask = h.down_nodes(l) if which == 0 else h.up_nodes(l)
+    B = h.B
+    coords = h.blocks(l)
+    index = {tuple(c): i for i, c in enumerate(coords.tolist())}
+    z, y, x = np.nonzero(mask)
+    out = [(index[(xx // B, yy // B, zz // B)] << 9) | ((xx % B) + B * (yy % B) + B * B * (zz % B))
+           for xx, yy, zz in zip(x.tolist(), y.tolist(), z.tolist())]
+    return np.array(sorted(out), dtype=np.int64)
+
+
+def assert_same_hierarchy(lat, h, prev):
+    for l in range(h.L):
+        coords, flags = lat.blocks(l)
+        assert np.array_equal(coords, h.blocks(l)), "level %d block list" % l
+        assert np.array_equal(flags, h.flags(l, prev)), "level %d flags" % l
+        for which in (0, 1):
+            got = np.sort(lat.interface_nodes(l, which).astype(np.int64))
+            assert np.array_equal(got, oracle_nodes(h, l, which)), "level %d interface %d" % (l, which)
+
+
+@pytest.mark.parametrize("ext,L,periodic", [((128, 128, 128), 3, (True, False, True)),
+                                             ((256, 128, 128), 4, (True, False, True)),
+                                             ((128, 128, 128), 2, (False, False, False))])
+def test_hierarchy_bit_exact_over_rebuilds(ext, L, periodic):
+    pos0 = wl.particle_cloud(ext[0], count=20000, seed=9, box=(0.25, 0.4, 0.25), y0_frac=0.2)
+    with hl.Lattice(ext, levels=L, tau=0.9, periodic=periodic, storage="f32") as lat:
+        prev = None
+        for t in range(0, 96, 12):
+            pos = wl.fall(pos0, t)
+            counts = lat.rebuild_from_particles(pos)
+            h = hy.from_particles(pos, ext, 8, L, periodic)
+            assert_same_hierarchy(lat, h, prev)
+            if prev is not None:
+                assert counts == h.counts(prev)
+            prev = h
+
+
+def test_hierarchy_from_device_particles_and_empty_cloud():
+    ext = (128, 128, 128)
+    pos = torch.tensor(wl.particle_cloud(128, count=5000, seed=4), device="cuda")
+    with hl.Lattice(ext, levels=3, tau=0.9, periodic=(True, True, True)) as lat:
+        lat.rebuild_from_particles(pos)
+        assert_same_hierarchy(lat, hy.from_particles(pos.cpu().numpy(), ext, 8, 3, (True,) * 3), None)
+        lat.rebuild_from_particles(np.zeros((0, 3), np.float32))
+        assert lat.num_blocks(0) == 0 and lat.num_blocks(1) == 0 and lat.num_blocks(2) == 4 ** 3
+
+
+def test_nonfinite_particles_are_reported():
+    pos = wl.particle_cloud(64, count=1000, seed=2)
+    pos[5, 1] = np.nan
+    with hl.Lattice((64, 64, 64), levels=2, tau=0.9) as lat:
+        with pytest.raises(hl.HlbmError) as ei:
+            lat.rebuild_from_particles(pos)
+        assert ei.value.code == hl.E_NONFINITE
+        assert lat.num_blocks(0) > 0   # the finite particles still built the hierarchy
+
+
+# ---------------------------------------------------------------- dynamics
+
+def _setup(ext, L, O0, periodic, tau0, fn, storage):
+    h = hy.Hierarchy(O0, ext, 8, L, periodic)
+    m = ml.MultiLevel(h, tau0)
+    for l in range(L):
+        X, Y, Z = m.node_positions(l)
+        m.set_level(l, fn(X, Y, Z))
+    lat = hl.Lattice(ext, levels=L, tau=tau0, periodic=periodic, storage=storage)
+    z, y, x = np.nonzero(O0)
+    lat.set_fine_blocks(np.stack([x, y, z], axis=1))
+    for l in range(L):
+        coords, _ = lat.blocks(l)
+        assert np.array_equal(coords, h.blocks(l))
+        if len(coords):
+            lat.write_moments(hl.dense_to_blocks(m.current(l).numpy(), coords), level=l)
+    # start the oracle from what the GPU holds
+    for l in range(L):
+        coords, _ = lat.blocks(l)
+        if len(coords):
+            got = hl.blocks_to_dense(lat.read_moments(level=l), m.shape[l], coords)
+            m.set_level(l, got)
+    return h, m, lat
+
+
+def _compare(lat, m, tol, u_floor):
+    worst = 0.0
+    for l in range(m.L):
+        coords, _ = lat.blocks(l)
+        if not len(coords):
+            continue
+        got = hl.blocks_to_dense(lat.read_moments(level=l), m.shape[l], coords)
+        ref = m.current(l).numpy()
+        st = m.stored[l].numpy()
+        err = rel_err(got, ref, row_scales(ref, u_floor), mask=st)
+        worst = max(worst, err.max())
+    assert worst < tol, worst
+    return worst
+
+
+def shear(A, n):
+    def fn(X, Y, Z):
+        ux = A * np.sin(2 * np.pi * Y / n)
+        z0 = np.zeros_like(ux)
+        return wl.equilibrium_field(np.ones_like(ux) + 1e-3 * np.cos(2 * np.pi * X / 16), ux, 0.3 * ux, z0)
+    return fn
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-11), ("f32", 2e-5)])
+def test_two_level_shear_wave_matches_oracle(storage, tol):
+    ext = (16, 128, 16)
+    O0 = np.zeros(hy.block_dims(ext, 8, 0), bool)
+    O0[:, 7:9, :] = True
+    h, m, lat = _setup(ext, 2, O0, (True, True, True), 0.8, shear(0.01, 128), storage)
+    with lat:
+        for k in range(3):
+            m.coarse_step()
+            lat.step(2)
+            _compare(lat, m, tol * (k + 1), 0.01)
+
+
+def test_three_level_matches_oracle_fp64():
+    ext = (64, 256, 64)
+    O0 = np.zeros(hy.block_dims(ext, 8, 0), bool)
+    O0[:, 15:17, :] = True
+    h, m, lat = _setup(ext, 3, O0, (True, True, True), 0.9, shear(0.01, 256), "f64")
+    assert all(len(h.blocks(l)) > 0 for l in range(3))
+    with lat:
+        m.coarse_step()
+        lat.step(4)
+        _compare(lat, m, 1e-11, 0.01)
+
+
+def test_three_level_walls_fp32_and_mass_reduction():
+    ext = (64, 128, 64)
+    O0 = np.zeros(hy.block_dims(ext, 8, 0), bool)
+    O0[3:5, 0:2, 3:5] = True            # touching the floor wall
+    per = (True, False, True)
+    h, m, lat = _setup(ext, 3, O0, per, 0.9, shear(0.005, 128), "f32")
+    with lat:
+        m.coarse_step()
+        lat.step(4)
+        _compare(lat, m, 2e-5, 0.005)
+        r = lat.reduce()
+        ro = m.reduce()
+        assert abs(r[0] - ro[0]) / ro[0] < 1e-6
+        assert abs(r[5] - ro[5]) / ro[0] < 1e-6
+
+
+def test_rebuild_moves_moments_like_the_oracle():
+    ext = (32, 128, 32)
+    O0 = np.zeros(hy.block_dims(ext, 8, 0), bool)
+    O0[1, 5:7, 1] = True
+    per = (True, True, True)
+    h, m, lat = _setup(ext, 2, O0, per, 0.8, shear(0.01, 128), "f64")
+    with lat:
+        m.coarse_step()
+        lat.step(2)
+        for shift in (1, 2, 3):
+            O1 = np.zeros_like(O0)
+            O1[1, 5 + shift:7 + shift, (1 + shift) % 4] = True
+            m.rebuild(hy.Hierarchy(O1, ext, 8, 2, per))
+            z, y, x = np.nonzero(O1)
+            lat.set_fine_blocks(np.stack([x, y, z], axis=1))
+            _compare(lat, m, 1e-11, 0.01)
+            m.coarse_step()
+            lat.step(2)
+            _compare(lat, m, 1e-11, 0.01)
