@@ -33,6 +33,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fine-equiv MLUPS and % HBM roofline per step; adjoint/forward time ratio"
 BYTES_PER_NODE_F32 = 80.0
+KERNEL = "k_stream_collide_f2<float>"
+# DRAM bytes (read + write) per launch of KERNEL from one ncu capture of the
+# 192^3 duct, scaled by nodes to 256^3 (profiles/stream_collide_f2_duct192.md);
+# set to None whenever the kernel changes after that capture.
+TRAFFIC_PER_NODE = 532.3e6 / 192 ** 3
 
 
 def measured_peaks():
@@ -199,8 +204,8 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        steps = max(1, min(args.steps, 4))
-        cb = cpu_oracle_sample(64, steps)
+        steps = max(1, min(args.steps, 8))
+        cb = cpu_oracle_sample(128, steps)
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS",
                           "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -235,8 +240,9 @@ def main():
         "data": "synthetic",
         "config": config,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "k_stream_collide<float>", "peak_kind": peak_kind,
+                     "frac": round(achieved / peak, 4),
+                     "traffic": None if TRAFFIC_PER_NODE is None else round(TRAFFIC_PER_NODE * args.n ** 3),
+                     "kernel": KERNEL, "peak_kind": peak_kind,
                      "bytes_per_node": BYTES_PER_NODE_F32},
         "e2e": {"value": round(res["e2e_value"], 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(res["e2e_bytes"] // args.steps),
@@ -245,7 +251,7 @@ def main():
         "clocks": res["clocks"],
     }
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_oracle_sample(64, 12)
+        line["cpu_baseline"] = cpu_oracle_sample(128, 16)
     print(json.dumps(line))
     if world > 1:
         import torch

@@ -468,6 +468,7 @@ int32_t hlbm_step(hlbm_lattice* h, int32_t n_fine_steps) {
   a.fu[1] = h->fu[1];
   a.fu[2] = h->fu[2];
   a.tau = L.tau;
+  a.om = 1.0 / L.tau;
   a.kxyz = h->cfg.xyz_literal ? 13.5 : 27.0;
   a.nb = L.nb;
   for (int32_t s = 0; s < n_fine_steps; ++s) {

@@ -31,6 +31,7 @@ struct StepArgs {
   const Scales* scales_out; // row scales of `out` (device), else null
   double fu[3];             // uniform force when F is null
   double tau;               // level relaxation time
+  double om;                // 1 / tau
   double kxyz;              // third-order xyz weight (27 or 13.5)
   int64_t nb;               // number of blocks
 };

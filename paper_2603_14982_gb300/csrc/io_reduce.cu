@@ -86,9 +86,12 @@ __global__ void __launch_bounds__(512) k_reduce_blocks(const T* __restrict__ src
       fy = Fp[kCells];
       fz = Fp[2 * kCells];
     }
-    const double ux = double(m.ux) - 0.5 * fx / rho;
-    const double uy = double(m.uy) - 0.5 * fy / rho;
-    const double uz = double(m.uz) - 0.5 * fz / rho;
+    // the force shift F / (2 rho) is O(F): a float reciprocal keeps it exact to
+    // far below the FP64 sums' rounding while avoiding FP64 divisions
+    const double hir = 0.5 * double(__frcp_rn(float(rho)));
+    const double ux = double(m.ux) - fx * hir;
+    const double uy = double(m.uy) - fy * hir;
+    const double uz = double(m.uz) - fz * hir;
     v[0] = rho * vol;
     v[1] = rho * ux * vol;
     v[2] = rho * uy * vol;

@@ -23,6 +23,12 @@ struct Dir {
   static constexpr int cz = J / 9 - 1;
 };
 
+// a * b + c and 1 / a for the scalar types (the packed type V2 has its own).
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float inv(float a) { return 1.0f / a; }
+__device__ __forceinline__ double inv(double a) { return 1.0 / a; }
+
 template <typename R>
 struct Mom {
   R drho, ux, uy, uz, sxx, syy, szz, sxy, sxz, syz;
@@ -57,15 +63,17 @@ __device__ __forceinline__ Coef<R> make_coef(const Mom<R>& m, R kxyz) {
   c.Oxz = r9 * m.sxz;
   c.Oyz = r9 * m.syz;
   const R ux = m.ux, uy = m.uy, uz = m.uz;
-  const R two = R(2);
+  const R m2 = R(-2);
   // Gamma_abg = S_ab u_g + S_ag u_b + S_bg u_a - 2 u_a u_b u_g
-  c.Gxxy = r135 * (m.sxx * uy + two * m.sxy * ux - two * ux * ux * uy);
-  c.Gxyy = r135 * (m.syy * ux + two * m.sxy * uy - two * ux * uy * uy);
-  c.Gxxz = r135 * (m.sxx * uz + two * m.sxz * ux - two * ux * ux * uz);
-  c.Gxzz = r135 * (m.szz * ux + two * m.sxz * uz - two * ux * uz * uz);
-  c.Gyzz = r135 * (m.szz * uy + two * m.syz * uz - two * uy * uz * uz);
-  c.Gyyz = r135 * (m.syy * uz + two * m.syz * uy - two * uy * uy * uz);
-  c.Gxyz = kxyz * rho * (m.sxy * uz + m.sxz * uy + m.syz * ux - two * ux * uy * uz);
+  const R sxy2 = m.sxy + m.sxy, sxz2 = m.sxz + m.sxz, syz2 = m.syz + m.syz;
+  const R uxx = m2 * ux * ux, uyy = m2 * uy * uy, uzz = m2 * uz * uz;
+  c.Gxxy = r135 * mad(m.sxx + uxx, uy, sxy2 * ux);  // u_y (S_xx - 2 u_x^2) + 2 S_xy u_x
+  c.Gxyy = r135 * mad(m.syy + uyy, ux, sxy2 * uy);
+  c.Gxxz = r135 * mad(m.sxx + uxx, uz, sxz2 * ux);
+  c.Gxzz = r135 * mad(m.szz + uzz, ux, sxz2 * uz);
+  c.Gyzz = r135 * mad(m.szz + uzz, uy, syz2 * uz);
+  c.Gyyz = r135 * mad(m.syy + uyy, uz, syz2 * uy);
+  c.Gxyz = kxyz * rho * mad(m.sxy, uz, mad(m.sxz, uy, mad(m2 * ux, uy * uz, m.syz * ux)));
   return c;
 }
 
@@ -82,27 +90,27 @@ __device__ __forceinline__ Coef<R> make_coef(const Mom<R>& m, R kxyz) {
 template <typename R, typename Sink>
 __device__ __forceinline__ void emit_all(const Coef<R>& c, Sink& s) {
   const R w0 = R(8.0 / 27.0), wf = R(2.0 / 27.0), we = R(1.0 / 54.0), wc = R(1.0 / 216.0);
-  const R t1 = R(1.0 / 3.0), t2 = R(2.0 / 3.0);
+  const R t2 = R(2.0 / 3.0), mt1 = R(-1.0 / 3.0);
   s.template put<13>(w0 * c.K0);
   {  // faces x
-    const R E = c.K0 + c.Dx, O = c.Ux - t1 * (c.Gxyy + c.Gxzz);
+    const R E = c.K0 + c.Dx, O = mad(mt1, c.Gxyy + c.Gxzz, c.Ux);
     s.template put<14>(wf * (E + O));
     s.template put<12>(wf * (E - O));
   }
   {  // faces y
-    const R E = c.K0 + c.Dy, O = c.Uy - t1 * (c.Gxxy + c.Gyzz);
+    const R E = c.K0 + c.Dy, O = mad(mt1, c.Gxxy + c.Gyzz, c.Uy);
     s.template put<16>(wf * (E + O));
     s.template put<10>(wf * (E - O));
   }
   {  // faces z
-    const R E = c.K0 + c.Dz, O = c.Uz - t1 * (c.Gxxz + c.Gyyz);
+    const R E = c.K0 + c.Dz, O = mad(mt1, c.Gxxz + c.Gyyz, c.Uz);
     s.template put<22>(wf * (E + O));
     s.template put<4>(wf * (E - O));
   }
   {  // edges xy (c_z = 0): j = (sx+1) + 3 (sy+1) + 9
     const R E = c.K0 + c.Dx + c.Dy;
-    const R X = c.Ux + t2 * c.Gxyy - t1 * c.Gxzz;
-    const R Y = c.Uy + t2 * c.Gxxy - t1 * c.Gyzz;
+    const R X = mad(t2, c.Gxyy, mad(mt1, c.Gxzz, c.Ux));
+    const R Y = mad(t2, c.Gxxy, mad(mt1, c.Gyzz, c.Uy));
     const R a = E + c.Oxy, b = E - c.Oxy, p = X + Y, m = X - Y;
     s.template put<17>(we * (a + p));  // (+,+)
     s.template put<9>(we * (a - p));   // (-,-)
@@ -111,8 +119,8 @@ __device__ __forceinline__ void emit_all(const Coef<R>& c, Sink& s) {
   }
   {  // edges xz (c_y = 0): j = (sx+1) + 3 + 9 (sz+1)
     const R E = c.K0 + c.Dx + c.Dz;
-    const R X = c.Ux + t2 * c.Gxzz - t1 * c.Gxyy;
-    const R Z = c.Uz + t2 * c.Gxxz - t1 * c.Gyyz;
+    const R X = mad(t2, c.Gxzz, mad(mt1, c.Gxyy, c.Ux));
+    const R Z = mad(t2, c.Gxxz, mad(mt1, c.Gyyz, c.Uz));
     const R a = E + c.Oxz, b = E - c.Oxz, p = X + Z, m = X - Z;
     s.template put<23>(we * (a + p));  // (+,+)
     s.template put<3>(we * (a - p));   // (-,-)
@@ -121,8 +129,8 @@ __device__ __forceinline__ void emit_all(const Coef<R>& c, Sink& s) {
   }
   {  // edges yz (c_x = 0): j = 1 + 3 (sy+1) + 9 (sz+1)
     const R E = c.K0 + c.Dy + c.Dz;
-    const R Y = c.Uy + t2 * c.Gyzz - t1 * c.Gxxy;
-    const R Z = c.Uz + t2 * c.Gyyz - t1 * c.Gxxz;
+    const R Y = mad(t2, c.Gyzz, mad(mt1, c.Gxxy, c.Uy));
+    const R Z = mad(t2, c.Gyyz, mad(mt1, c.Gxxz, c.Uz));
     const R a = E + c.Oyz, b = E - c.Oyz, p = Y + Z, m = Y - Z;
     s.template put<25>(we * (a + p));  // (+,+)
     s.template put<1>(we * (a - p));   // (-,-)
@@ -131,9 +139,9 @@ __device__ __forceinline__ void emit_all(const Coef<R>& c, Sink& s) {
   }
   {  // corners: value = P(sx,sy) + sz Q(sx,sy)
     const R E = c.K0 + c.Dx + c.Dy + c.Dz;
-    const R X = c.Ux + t2 * (c.Gxyy + c.Gxzz);
-    const R Y = c.Uy + t2 * (c.Gxxy + c.Gyzz);
-    const R Z = c.Uz + t2 * (c.Gxxz + c.Gyyz);
+    const R X = mad(t2, c.Gxyy + c.Gxzz, c.Ux);
+    const R Y = mad(t2, c.Gxxy + c.Gyzz, c.Uy);
+    const R Z = mad(t2, c.Gxxz + c.Gyyz, c.Uz);
     const R pa = E + c.Oxy, pb = E - c.Oxy, pp = X + Y, pm = X - Y;
     const R Ppp = pa + pp, Pmm = pa - pp, Ppm = pb + pm, Pmp = pb - pm;
     const R qa = Z + c.Gxyz, qb = Z - c.Gxyz, qp = c.Oxz + c.Oyz, qm = c.Oxz - c.Oyz;
@@ -202,22 +210,26 @@ __device__ __forceinline__ PreMom<R> project(const R (&g)[27]) {
 template <typename R>
 __device__ __forceinline__ Mom<R> collide(const PreMom<R>& p, R fx, R fy, R fz, R om) {
   const R rho = R(1) + p.drho;
-  const R ir = R(1) / rho;
-  const R ux = (p.jx + R(0.5) * fx) * ir;
-  const R uy = (p.jy + R(0.5) * fy) * ir;
-  const R uz = (p.jz + R(0.5) * fz) * ir;
-  const R a = R(1) - om, b = om * rho, cf = R(1) - R(0.5) * om;
+  const R ir = inv(rho);
+  const R h = R(0.5);
+  const R ux = mad(h, fx, p.jx) * ir;
+  const R uy = mad(h, fy, p.jy) * ir;
+  const R uz = mad(h, fz, p.jz) * ir;
+  const R a = R(1) - om, b = om * rho, cf = R(1) - h * om;
+  const R bux = b * ux, buy = b * uy, buz = b * uz;
+  const R cfx = cf * fx, cfy = cf * fy, cfz = cf * fz;
   Mom<R> m;
   m.drho = p.drho;
-  m.sxx = (a * p.pxx + b * ux * ux + cf * R(2) * ux * fx) * ir;
-  m.syy = (a * p.pyy + b * uy * uy + cf * R(2) * uy * fy) * ir;
-  m.szz = (a * p.pzz + b * uz * uz + cf * R(2) * uz * fz) * ir;
-  m.sxy = (a * p.pxy + b * ux * uy + cf * (ux * fy + fx * uy)) * ir;
-  m.sxz = (a * p.pxz + b * ux * uz + cf * (ux * fz + fx * uz)) * ir;
-  m.syz = (a * p.pyz + b * uy * uz + cf * (uy * fz + fy * uz)) * ir;
-  m.ux = ux + R(0.5) * fx * ir;
-  m.uy = uy + R(0.5) * fy * ir;
-  m.uz = uz + R(0.5) * fz * ir;
+  m.sxx = mad(a, p.pxx, mad(bux, ux, (cfx + cfx) * ux)) * ir;
+  m.syy = mad(a, p.pyy, mad(buy, uy, (cfy + cfy) * uy)) * ir;
+  m.szz = mad(a, p.pzz, mad(buz, uz, (cfz + cfz) * uz)) * ir;
+  m.sxy = mad(a, p.pxy, mad(bux, uy, mad(cfy, ux, cfx * uy))) * ir;
+  m.sxz = mad(a, p.pxz, mad(bux, uz, mad(cfz, ux, cfx * uz))) * ir;
+  m.syz = mad(a, p.pyz, mad(buy, uz, mad(cfz, uy, cfy * uz))) * ir;
+  const R hir = h * ir;
+  m.ux = mad(hir, fx, ux);
+  m.uy = mad(hir, fy, uy);
+  m.uz = mad(hir, fz, uz);
   return m;
 }
 

@@ -109,6 +109,7 @@ int streaming_collision(hlbm_lattice* h, int l) {
   a.bmask = L.d_bmask;
   for (int ax = 0; ax < 3; ++ax) a.fu[ax] = l == 0 ? h->fu[ax] : 0.0;
   a.tau = L.tau;
+  a.om = 1.0 / L.tau;
   a.kxyz = h->cfg.xyz_literal ? 13.5 : 27.0;
   a.nb = L.nb;
   ML_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));

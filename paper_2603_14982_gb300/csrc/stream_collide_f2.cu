@@ -6,6 +6,10 @@
 // z0 = warp >> 1.  Shared memory holds, per direction j != rest, the pulled
 // population of every node of the block, destination-indexed; a node pair
 // shares one 8-byte slot (node z0 in .x, node z0 + 4 in .y).
+// Inside each direction's 256-slot array the pair slot of node (x, y, z & 3)
+// is swizzled, s = (x ^ (y >> 1)) + 8 y + 64 (z & 3), which keeps the 64-bit
+// row accesses conflict-free and spreads the column writes of the x- and
+// y-face halo over more banks.
 //  A. each thread reconstructs the 26 moving populations of its pair
 //     (Eq. three_order_f) and pushes them to their destinations x + c_j with
 //     wrap-around inside the block: one 64-bit store per direction.  Pushes
@@ -35,7 +39,7 @@ __host__ __device__ constexpr int slot_of(int j) { return j < 13 ? j : j - 1; }
 
 struct OwnPush {
   float2* f;
-  int X[3], Y8[3], Z64[3];
+  int XH[9], Y8[3], Z64[3];  // XH[(cx+1) + 3 (cy+1)] = x' ^ (y' >> 1)
   bool swap[3];
   V2 g13;
   template <int J>
@@ -44,7 +48,7 @@ struct OwnPush {
       g13 = v;
     } else {
       constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
-      const int s = X[cx + 1] + Y8[cy + 1] + Z64[cz + 1];
+      const int s = XH[(cx + 1) + 3 * (cy + 1)] + Y8[cy + 1] + Z64[cz + 1];
       f[slot_of(J) * 256 + s] = swap[cz + 1] ? make_float2(v.v.y, v.v.x) : v.v;
     }
   }
@@ -59,7 +63,7 @@ constexpr int kTrash = 26 * 512;  // per-lane dummy float slots for masked halo 
 template <int AX, int SG>
 struct HaloPushXY {
   float* f;
-  int X[3], Y8[3], Z64[3];
+  int X[3], YH[3], Y8[3], Z64[3];
   unsigned swp;             // bit (cz+1): node a lands in the high half
   unsigned vx, vy, vza, vzb;  // bit (c+1): destination coordinate in range
   bool va, vb;
@@ -69,7 +73,7 @@ struct HaloPushXY {
     constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
     constexpr int c = AX == 0 ? cx : cy;
     if constexpr (c == SG) {
-      const int p2 = 2 * (slot_of(J) * 256 + X[cx + 1] + Y8[cy + 1] + Z64[cz + 1]);
+      const int p2 = 2 * (slot_of(J) * 256 + (X[cx + 1] ^ YH[cy + 1]) + Y8[cy + 1] + Z64[cz + 1]);
       const bool rng = ((vx >> (cx + 1)) & (vy >> (cy + 1)) & 1u) != 0u;
       const int ha = (swp >> (cz + 1)) & 1;
       const bool oka = va && rng && ((vza >> (cz + 1)) & 1u);
@@ -85,7 +89,7 @@ struct HaloPushXY {
 template <int SG>
 struct HaloPushZ {
   float* f;
-  int X[3], Y8a[3], Y8b[3];
+  int X[3], YHa[3], YHb[3], Y8a[3], Y8b[3];
   int zoff;                    // 2 * 64 * (z_dest & 3) + (z_dest >> 2)
   unsigned vx, vya, vyb;
   bool va, vb;
@@ -94,12 +98,12 @@ struct HaloPushZ {
   __device__ __forceinline__ void put(V2 v) {
     constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
     if constexpr (cz == SG) {
-      const int base = 2 * (slot_of(J) * 256 + X[cx + 1]) + zoff;
+      const int base = 2 * (slot_of(J) * 256) + zoff;
       const unsigned okx = (vx >> (cx + 1)) & 1u;
       const bool oka = va && (okx & (vya >> (cy + 1)));
       const bool okb = vb && (okx & (vyb >> (cy + 1)));
-      f[oka ? base + 2 * Y8a[cy + 1] : trash] = v.v.x;
-      f[okb ? base + 2 * Y8b[cy + 1] : trash] = v.v.y;
+      f[oka ? base + 2 * ((X[cx + 1] ^ YHa[cy + 1]) + Y8a[cy + 1]) : trash] = v.v.x;
+      f[okb ? base + 2 * ((X[cx + 1] ^ YHb[cy + 1]) + Y8b[cy + 1]) : trash] = v.v.y;
     }
   }
 };
@@ -232,7 +236,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
   const int64_t blk = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int x = lane & 7, y = (lane >> 3) + ((w & 1) << 2), z0 = w >> 1;
-  const int own = x + 8 * y + 64 * z0;
+  const int own = x + 8 * y + 64 * z0;                 // pair slot in global storage
+  const int own_s = (x ^ (y >> 1)) + 8 * y + 64 * z0;  // pair slot in shared memory
   const T* in = static_cast<const T*>(a.in);
   T* out = static_cast<T*>(a.out);
   const Scales* sc_in = a.scales_in;
@@ -277,10 +282,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
   op.f = f2buf;
 #pragma unroll
   for (int c = -1; c <= 1; ++c) {
-    op.X[c + 1] = (x + c) & 7;
     op.Y8[c + 1] = 8 * ((y + c) & 7);
     op.Z64[c + 1] = 64 * ((z0 + c) & 3);
     op.swap[c + 1] = (((z0 + c) & 7) >> 2) != 0;
+#pragma unroll
+    for (int cx = -1; cx <= 1; ++cx) op.XH[(cx + 1) + 3 * (c + 1)] = ((x + cx) & 7) ^ (((y + c) & 7) >> 1);
   }
   emit_all(make_coef(m, kxyz), op);
   __syncthreads();
@@ -290,36 +296,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
     const Coef<V2> c = make_coef(hm, kxyz);
     const int trash = kTrash + lane;
     if (face < 4) {
-      int X[3], Y8[3], Z64[3];
+      int X[3], YH[3], Y8[3], Z64[3];
       unsigned swp = 0;
 #pragma unroll
       for (int k = -1; k <= 1; ++k) {
         X[k + 1] = (hax + k) & 7;
+        YH[k + 1] = ((hay + k) & 7) >> 1;
         Y8[k + 1] = 8 * ((hay + k) & 7);
         Z64[k + 1] = 64 * ((haz + k) & 3);
         swp |= ((((haz + k) & 7) >> 2) & 1u) << (k + 1);
       }
       const unsigned vx = range_mask(hax), vy = range_mask(hay), vza = range_mask(haz), vzb = range_mask(hbz);
       switch (face) {
-        case 0: { HaloPushXY<0, 1> s{fbuf, {X[0], X[1], X[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
-        case 1: { HaloPushXY<0, -1> s{fbuf, {X[0], X[1], X[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
-        case 2: { HaloPushXY<1, 1> s{fbuf, {X[0], X[1], X[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
-        default: { HaloPushXY<1, -1> s{fbuf, {X[0], X[1], X[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
+        case 0: { HaloPushXY<0, 1> s{fbuf, {X[0], X[1], X[2]}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
+        case 1: { HaloPushXY<0, -1> s{fbuf, {X[0], X[1], X[2]}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
+        case 2: { HaloPushXY<1, 1> s{fbuf, {X[0], X[1], X[2]}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
+        default: { HaloPushXY<1, -1> s{fbuf, {X[0], X[1], X[2]}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
       }
     } else {
-      int X[3], Y8a[3], Y8b[3];
+      int X[3], YHa[3], YHb[3], Y8a[3], Y8b[3];
 #pragma unroll
       for (int k = -1; k <= 1; ++k) {
         X[k + 1] = (hax + k) & 7;
+        YHa[k + 1] = ((hay + k) & 7) >> 1;
+        YHb[k + 1] = ((hby + k) & 7) >> 1;
         Y8a[k + 1] = 8 * ((hay + k) & 7);
         Y8b[k + 1] = 8 * ((hby + k) & 7);
       }
       const unsigned vx = range_mask(hax), vya = range_mask(hay), vyb = range_mask(hby);
       if (face == 4) {
-        HaloPushZ<1> s{fbuf, {X[0], X[1], X[2]}, {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, 0, vx, vya, vyb, va, vb, trash};
+        HaloPushZ<1> s{fbuf, {X[0], X[1], X[2]}, {YHa[0], YHa[1], YHa[2]}, {YHb[0], YHb[1], YHb[2]}, {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, 0, vx, vya, vyb, va, vb, trash};
         emit_all(c, s);
       } else {
-        HaloPushZ<-1> s{fbuf, {X[0], X[1], X[2]}, {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, 2 * 64 * 3 + 1, vx, vya, vyb, va, vb, trash};
+        HaloPushZ<-1> s{fbuf, {X[0], X[1], X[2]}, {YHa[0], YHa[1], YHa[2]}, {YHb[0], YHb[1], YHb[2]}, {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, 2 * 64 * 3 + 1, vx, vya, vyb, va, vb, trash};
         emit_all(c, s);
       }
     }
@@ -327,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
   if (bf & kBlockBounce) {  // block-uniform
     const unsigned mlo_b = a.bmask[blk * kCells + own], mhi_b = a.bmask[blk * kCells + own + 256];
     if ((mlo_b | mhi_b) != 0u) {
-      BouncePush bp{fbuf, own, mlo_b, mhi_b};
+      BouncePush bp{fbuf, own_s, mlo_b, mhi_b};
       emit_all(make_coef(load_pair<T>(in, blk, own, sc_in), kxyz), bp);
     }
   }
@@ -348,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
     mo = load_pair<T>(in, blk, own, sc_in);
   } else {
     V2 g[27];
-    gather_all(f2buf, own, op.g13, g, std::make_integer_sequence<int, 27>{});
+    gather_all(f2buf, own_s, op.g13, g, std::make_integer_sequence<int, 27>{});
     const PreMom<V2> p = project(g);
     V2 fx, fy, fz;
     if (a.F != nullptr) {
@@ -361,9 +370,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
       fy = V2(float(a.fu[1]));
       fz = V2(float(a.fu[2]));
     }
-    V2 tau = V2(float(a.tau));
-    if (a.eps != nullptr) tau = tau * V2(__ldg(a.eps + blk * kCells + own), __ldg(a.eps + blk * kCells + own + 256));
-    mo = collide(p, fx, fy, fz, V2(1) / tau);
+    V2 om = V2(float(a.om));
+    if (a.eps != nullptr)
+      om = inv(V2(float(a.tau)) * V2(__ldg(a.eps + blk * kCells + own), __ldg(a.eps + blk * kCells + own + 256)));
+    mo = collide(p, fx, fy, fz, om);
     if (copy_lo || copy_hi) mo = select_halves(mo, load_pair<T>(in, blk, own, sc_in), copy_lo, copy_hi);
   }
   store_pair<T>(out, blk, own, mo, a.scales_out);
