@@ -95,13 +95,43 @@ void LatticeOps::free_level(LevelData& L) {
   release(v);
   L.d_skip = nullptr;
   for (void** q : {(void**)&L.d_coords, (void**)&L.d_slot, (void**)&L.d_H, (void**)&L.d_stored, (void**)&L.d_down,
-                   (void**)&L.d_up}) {
+                   (void**)&L.d_up, (void**)&L.d_scales, (void**)&L.d_amax}) {
     release(*q);
   }
   L.n_down = L.n_up = 0;
   L.nb = 0;
   L.coords.clear();
   L.flags.clear();
+}
+
+static bool reduced(const hlbm_lattice* h) {
+  return h->cfg.storage == HLBM_STORE_F16S || h->cfg.storage == HLBM_STORE_BF16S;
+}
+
+int LatticeOps::init_scales(hlbm_lattice* h, LevelData& L) {
+  if (!reduced(h)) return HLBM_OK;
+  int rc;
+  void* p;
+  if (L.d_scales == nullptr) {
+    if ((rc = alloc(h, &p, 2 * sizeof(Scales)))) return rc;
+    L.d_scales = static_cast<Scales*>(p);
+  }
+  if (L.d_amax == nullptr) {
+    if ((rc = alloc(h, &p, kRows * sizeof(unsigned)))) return rc;
+    L.d_amax = static_cast<unsigned*>(p);
+  }
+  HLBM_CUDA(h, scales_from_public(nullptr, 1, 0, L.d_scales, L.d_amax, h->stream));
+  L.steps_since_rescale = 0;
+  return HLBM_OK;
+}
+
+int LatticeOps::maybe_rescale(hlbm_lattice* h, LevelData& L, bool force) {
+  if (!reduced(h) || L.nb == 0) return HLBM_OK;
+  if (!force && ++L.steps_since_rescale < kRescaleEvery) return HLBM_OK;
+  L.steps_since_rescale = 0;
+  HLBM_CUDA(h, rescale_storage(h->cfg.storage, L.d_mom[L.cur], L.nb, L.d_scales, L.d_scales + 1, L.d_amax,
+                               h->stream));
+  return HLBM_OK;
 }
 
 int LatticeOps::bounce(hlbm_lattice* h, LevelData& L) {
@@ -180,8 +210,6 @@ int32_t hlbm_create(const hlbm_config* cfg, hlbm_lattice** out) {
     return fail(nullptr, HLBM_E_INVALID_ARG, "tau_finest must be finite and > 1/2");
   if (cfg->storage < HLBM_STORE_F64 || cfg->storage > HLBM_STORE_BF16S)
     return fail(nullptr, HLBM_E_INVALID_ARG, "unknown storage %d", cfg->storage);
-  if (cfg->storage == HLBM_STORE_F16S || cfg->storage == HLBM_STORE_BF16S)
-    return fail(nullptr, HLBM_E_UNSUPPORTED, "reduced-precision storage is not built yet");
   if (cfg->rescale_mode < HLBM_RESCALE_POST || cfg->rescale_mode > HLBM_RESCALE_PAPER)
     return fail(nullptr, HLBM_E_INVALID_ARG, "unknown rescale_mode %d", cfg->rescale_mode);
   if (cfg->num_levels > 4) return fail(nullptr, HLBM_E_UNSUPPORTED, "at most 4 levels are supported");
@@ -274,6 +302,7 @@ int32_t hlbm_set_dense(hlbm_lattice* h) {
   // rest state: delta_rho = u = S = 0 is all-zero bits in every storage
   for (int k = 0; k < 2; ++k) HLBM_CUDA(h, cudaMemsetAsync(L.d_mom[k], 0, mom_bytes, h->stream));
   if ((rc = LatticeOps::bounce(h, L))) return rc;
+  if ((rc = LatticeOps::init_scales(h, L))) return rc;
   L.cur = 0;
   HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->have_blocks = true;
@@ -414,7 +443,11 @@ int32_t hlbm_write_moments(hlbm_lattice* h, int32_t level, const void* buf, int3
     HLBM_CUDA(h, cudaMemcpyAsync(h->d_stage, buf, bytes, cudaMemcpyHostToDevice, h->stream));
     src = h->d_stage;
   }
-  HLBM_CUDA(h, import_moments(h->cfg.storage, src, dtype, L.d_mom[L.cur], n, nullptr, h->stream));
+  if (L.d_scales) {
+    HLBM_CUDA(h, scales_from_public(src, dtype, L.nb, L.d_scales, L.d_amax, h->stream));
+    L.steps_since_rescale = 0;
+  }
+  HLBM_CUDA(h, import_moments(h->cfg.storage, src, dtype, L.d_mom[L.cur], n, L.d_scales, h->stream));
   if (!on_device) HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
   return HLBM_OK;
 }
@@ -438,7 +471,7 @@ int32_t hlbm_read_moments(hlbm_lattice* h, int32_t level, void* buf, int32_t dty
     dst = h->d_stage;
   }
   const bool phys = physical_u && level == 0;
-  HLBM_CUDA(h, export_moments(h->cfg.storage, L.d_mom[L.cur], dst, dtype, n, nullptr, phys ? h->d_F : nullptr,
+  HLBM_CUDA(h, export_moments(h->cfg.storage, L.d_mom[L.cur], dst, dtype, n, L.d_scales, phys ? h->d_F : nullptr,
                               h->fu, phys ? 1 : 0, h->stream));
   if (!on_device) {
     HLBM_CUDA(h, cudaMemcpyAsync(buf, h->d_stage, bytes, cudaMemcpyDeviceToHost, h->stream));
@@ -471,11 +504,13 @@ int32_t hlbm_step(hlbm_lattice* h, int32_t n_fine_steps) {
   a.om = 1.0 / L.tau;
   a.kxyz = h->cfg.xyz_literal ? 13.5 : 27.0;
   a.nb = L.nb;
+  a.scales_in = a.scales_out = L.d_scales;
   for (int32_t s = 0; s < n_fine_steps; ++s) {
     a.in = L.d_mom[L.cur];
     a.out = L.d_mom[1 - L.cur];
     HLBM_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
     L.cur = 1 - L.cur;
+    if ((rc = LatticeOps::maybe_rescale(h, L, false))) return rc;
   }
   return HLBM_OK;
 }
@@ -514,7 +549,7 @@ int32_t hlbm_reduce(hlbm_lattice* h, double out[7]) {
     if (L.nb == 0) continue;
     HLBM_CUDA(h, cudaMemsetAsync(d_out, 0, 8 * sizeof(double), h->stream));
     const double vol = std::ldexp(1.0, 3 * l);
-    HLBM_CUDA(h, reduce_level(h->cfg.storage, L.d_mom[L.cur], L.nb, nullptr, L.d_skip, l == 0 ? h->d_F : nullptr,
+    HLBM_CUDA(h, reduce_level(h->cfg.storage, L.d_mom[L.cur], L.nb, L.d_scales, L.d_skip, l == 0 ? h->d_F : nullptr,
                               h->fu, vol, h->d_red, d_out, h->stream));
     double r[8];
     HLBM_CUDA(h, cudaMemcpyAsync(r, d_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

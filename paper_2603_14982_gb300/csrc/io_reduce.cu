@@ -323,3 +323,131 @@ extern "C" int32_t hlbm_reduce_f32_noalloc(const float* mom_dev, int64_t n_block
   }
   return HLBM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Per-row power-of-two scales of the reduced-precision storages.
+// ---------------------------------------------------------------------------
+namespace hlbm {
+namespace {
+
+// |value| maxima of the stored quantities (delta_rho, u, S^neq) per row, as
+// float bits (non-negative floats order like their bit patterns).
+__device__ __forceinline__ void row_values(const Mom<float>& m, float (&v)[kRows]) {
+  v[0] = m.drho;
+  v[1] = m.ux;
+  v[2] = m.uy;
+  v[3] = m.uz;
+  v[4] = m.sxx - m.ux * m.ux;
+  v[5] = m.syy - m.uy * m.uy;
+  v[6] = m.szz - m.uz * m.uz;
+  v[7] = m.sxy - m.ux * m.uy;
+  v[8] = m.sxz - m.ux * m.uz;
+  v[9] = m.syz - m.uy * m.uz;
+}
+
+__device__ __forceinline__ void block_amax(float (&v)[kRows], unsigned* amax) {
+  __shared__ unsigned s[kRows];
+  if (threadIdx.x < kRows) s[threadIdx.x] = 0u;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    float a = fabsf(v[r]);
+    if (!(a <= 3.0e38f)) a = 3.0e38f;  // non-finite values pin the scale to the smallest
+    for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&s[r], __float_as_uint(a));
+  }
+  __syncthreads();
+  if (threadIdx.x < kRows) atomicMax(&amax[threadIdx.x], s[threadIdx.x]);
+}
+
+// amax of a public-layout buffer (rho, u, S), one CTA of 512 threads per block
+template <typename In>
+__global__ void __launch_bounds__(512) k_amax_public(const In* __restrict__ src, unsigned* amax) {
+  const In* p = src + int64_t(blockIdx.x) * kRows * kCells + threadIdx.x;
+  Mom<float> m;
+  m.drho = float(double(p[0]) - 1.0);
+  m.ux = float(p[1 * kCells]);
+  m.uy = float(p[2 * kCells]);
+  m.uz = float(p[3 * kCells]);
+  m.sxx = float(p[4 * kCells]);
+  m.syy = float(p[5 * kCells]);
+  m.szz = float(p[6 * kCells]);
+  m.sxy = float(p[7 * kCells]);
+  m.sxz = float(p[8 * kCells]);
+  m.syz = float(p[9 * kCells]);
+  float v[kRows];
+  row_values(m, v);
+  block_amax(v, amax);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_amax_storage(const T* __restrict__ src, const Scales* sc, unsigned* amax) {
+  float v[kRows];
+  row_values(load_node<T>(src, blockIdx.x, threadIdx.x, sc), v);
+  block_amax(v, amax);
+}
+
+// scale 2^e with amax * 2^e < 2^13 (three binades below the FP16 maximum).
+// The exponent is capped at 20: a row whose amax is (nearly) zero, such as
+// S^neq of an equilibrium initial state, still represents values up to
+// 65504 * 2^-20 = 0.0625 lattice units, while keeping normal FP16 precision
+// down to 6e-11.
+__global__ void k_set_scales(const unsigned* amax, Scales* sc) {
+  const int r = threadIdx.x;
+  if (r >= kRows) return;
+  const float a = __uint_as_float(amax[r]);
+  int e = 20;
+  if (a > 0.f) {
+    int k;
+    frexpf(a, &k);  // a < 2^k
+    e = 13 - k;
+  }
+  e = max(-30, min(20, e));
+  sc->enc[r] = ldexpf(1.f, e);
+  sc->dec[r] = ldexpf(1.f, -e);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_reencode(T* buf, const Scales* from, const Scales* to) {
+  const Mom<float> m = load_node<T>(buf, blockIdx.x, threadIdx.x, from);
+  store_node<T>(buf, blockIdx.x, threadIdx.x, m, to);
+}
+
+template <typename T>
+cudaError_t rescale_typed(void* buf, int64_t nb, Scales* cur, Scales* tmp, unsigned* amax, cudaStream_t s) {
+  if (nb == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(amax, 0, kRows * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  k_amax_storage<T><<<unsigned(nb), 512, 0, s>>>(static_cast<const T*>(buf), cur, amax);
+  k_set_scales<<<1, 32, 0, s>>>(amax, tmp);
+  k_reencode<T><<<unsigned(nb), 512, 0, s>>>(static_cast<T*>(buf), cur, tmp);
+  e = cudaMemcpyAsync(cur, tmp, sizeof(Scales), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t scales_from_public(const void* src, int dtype, int64_t nb, Scales* sc, unsigned* amax, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(amax, 0, kRows * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  if (nb > 0) {
+    if (dtype == 0)
+      k_amax_public<double><<<unsigned(nb), 512, 0, s>>>(static_cast<const double*>(src), amax);
+    else
+      k_amax_public<float><<<unsigned(nb), 512, 0, s>>>(static_cast<const float*>(src), amax);
+  }
+  k_set_scales<<<1, 32, 0, s>>>(amax, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t rescale_storage(int storage, void* buf, int64_t nb, Scales* cur, Scales* tmp, unsigned* amax,
+                            cudaStream_t s) {
+  switch (storage) {
+    case HLBM_STORE_F16S: return rescale_typed<__half>(buf, nb, cur, tmp, amax, s);
+    case HLBM_STORE_BF16S: return rescale_typed<__nv_bfloat16>(buf, nb, cur, tmp, amax, s);
+    default: return cudaSuccess;
+  }
+}
+
+}  // namespace hlbm

@@ -21,4 +21,12 @@ cudaError_t export_moments(int storage, const void* src, void* dst, int dtype, i
 cudaError_t reduce_level(int storage, const void* src, int64_t nb, const Scales* sc, const uint8_t* skip,
                          const float* F, const double* fu, double vol, double* part, double* out, cudaStream_t s);
 
+// Scales (reduced-precision storages) from the amax of a public-layout buffer
+// (dtype 0 = f64, 1 = f32, device).  amax: scratch of 10 unsigned.
+cudaError_t scales_from_public(const void* src, int dtype, int64_t nb, Scales* sc, unsigned* amax, cudaStream_t s);
+// Recompute the scales of a stored buffer from its amax and re-encode it in
+// place (no-op for FP32 / FP64 storage).  tmp: a second Scales in device memory.
+cudaError_t rescale_storage(int storage, void* buf, int64_t nb, Scales* cur, Scales* tmp, unsigned* amax,
+                            cudaStream_t s);
+
 }  // namespace hlbm

@@ -10,6 +10,8 @@
 
 namespace hlbm {
 
+constexpr int kRescaleEvery = 32;  // steps between scale refreshes of FP16/BF16 storage
+
 struct LevelData {
   int64_t nb = 0;                  // stored blocks
   std::vector<int32_t> coords;     // host copy [nb][3] (bx, by, bz), ascending slot id
@@ -30,6 +32,11 @@ struct LevelData {
   int64_t n_down = 0, n_up = 0;    // interface node counts (I^d, I^u)
   int32_t* d_down = nullptr;       // [n_down] (block << 9) | cell
   int32_t* d_up = nullptr;         // [n_up]
+  // reduced-precision storage: row scales shared by both buffers, a spare
+  // Scales for re-encoding, and the amax scratch
+  Scales* d_scales = nullptr;      // [2]
+  unsigned* d_amax = nullptr;      // [kRows]
+  int steps_since_rescale = 0;
 };
 
 }  // namespace hlbm
@@ -75,6 +82,10 @@ struct LatticeOps {
   static int alloc(hlbm_lattice* h, void** p, size_t bytes);
   static void release(void*& p);
   static void free_level(LevelData& L);
+  // Allocate the scale state of a reduced-precision level (scales for amax 0).
+  static int init_scales(hlbm_lattice* h, LevelData& L);
+  // Re-derive a reduced-precision level's scales every kRescaleEvery steps.
+  static int maybe_rescale(hlbm_lattice* h, LevelData& L, bool force);
   // (Re)compute d_bflags / d_bmask of a level from its neighbour table and solids.
   static int bounce(hlbm_lattice* h, LevelData& L);
   static void build_nbr(const hlbm_lattice* h, int level, const std::vector<int32_t>& coords,

@@ -51,6 +51,7 @@ LevelView view_of(const LevelData& L, GridDims d) {
   v.mom = L.d_mom[L.cur];
   v.mom_other = L.d_mom[1 - L.cur];
   v.nb = L.nb;
+  v.sc = L.d_scales;
   return v;
 }
 
@@ -64,6 +65,7 @@ int downward(hlbm_lattice* h, int l, int s, bool refresh) {
   a.fine = view_of(F, dims_of(h, l));
   a.coarse = view_of(C, dims_of(h, l + 1));
   a.out = F.d_mom[F.cur];
+  a.out_sc = F.d_scales;
   a.nodes = F.d_down;
   a.n_nodes = F.n_down;
   a.avg = (!refresh && s == 2) ? 1 : 0;
@@ -83,6 +85,7 @@ int upward(hlbm_lattice* h, int l) {
   a.fine = view_of(F, dims_of(h, l));
   a.coarse = view_of(C, dims_of(h, l + 1));
   a.out = C.d_mom[C.cur];
+  a.out_sc = C.d_scales;
   a.nodes = C.d_up;
   a.n_nodes = C.n_up;
   a.k = h->kup[l];
@@ -112,9 +115,10 @@ int streaming_collision(hlbm_lattice* h, int l) {
   a.om = 1.0 / L.tau;
   a.kxyz = h->cfg.xyz_literal ? 13.5 : 27.0;
   a.nb = L.nb;
+  a.scales_in = a.scales_out = L.d_scales;
   ML_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
   L.cur = 1 - L.cur;
-  return HLBM_OK;
+  return LatticeOps::maybe_rescale(h, L, false);
 }
 
 // AdvanceLBM(l, s) of Algorithm 1.
@@ -306,6 +310,18 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     cleanup();
     return rc;
   }
+  for (int l = 0; l < L && rc == HLBM_OK; ++l) {
+    rc = LatticeOps::init_scales(h, nl[l]);
+    // moments carried over from every old level: start from the widest range
+    // of the old level and refit below
+    if (rc == HLBM_OK && has_old && nl[l].d_scales != nullptr && h->lv[l].d_scales != nullptr)
+      ML_CUDA(h, cudaMemcpyAsync(nl[l].d_scales, h->lv[l].d_scales, sizeof(Scales), cudaMemcpyDeviceToDevice, st));
+  }
+  if (rc) {
+    free_new();
+    cleanup();
+    return rc;
+  }
   if (has_old) {
     OldHierarchy o{};
     o.L = L;
@@ -319,15 +335,19 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     o.ext[1] = h->cfg.ny;
     o.ext[2] = h->cfg.nz;
     for (int l = 0; l < L; ++l)
-      ML_CUDA(h, init_new_level(h->cfg.storage, o, l, nl[l].d_coords, nb[l], nl[l].d_mom[0], h->d_status, st));
+      ML_CUDA(h, init_new_level(h->cfg.storage, o, l, nl[l].d_coords, nb[l], nl[l].d_mom[0], nl[l].d_scales,
+                                h->d_status, st));
   } else {
     for (int l = 0; l < L; ++l)
       if (nb[l]) ML_CUDA(h, cudaMemsetAsync(nl[l].d_mom[0], 0, size_t(nb[l]) * kCells * node_bytes, st));
   }
-  for (int l = 0; l < L; ++l)
+  for (int l = 0; l < L; ++l) {
+    nl[l].cur = 0;
+    ML_TRY(LatticeOps::maybe_rescale(h, nl[l], true));
     if (nb[l])
       ML_CUDA(h, cudaMemcpyAsync(nl[l].d_mom[1], nl[l].d_mom[0], size_t(nb[l]) * kCells * node_bytes,
                                  cudaMemcpyDeviceToDevice, st));
+  }
 
   // 7. host copies of the lists; counts of refined / coarsened / deleted blocks
   int64_t refined = 0, coarsened = 0, deleted = 0;

@@ -16,8 +16,8 @@ struct Node64 {
 };
 
 template <typename T>
-__device__ __forceinline__ Node64 load64(const void* base, int64_t blk, int cell) {
-  const auto m = load_node<T>(static_cast<const T*>(base), blk, cell, nullptr);
+__device__ __forceinline__ Node64 load64(const void* base, int64_t blk, int cell, const Scales* sc) {
+  const auto m = load_node<T>(static_cast<const T*>(base), blk, cell, sc);
   Node64 n;
   n.rho = 1.0 + double(m.drho);
   n.ux = m.ux;
@@ -33,7 +33,8 @@ __device__ __forceinline__ Node64 load64(const void* base, int64_t blk, int cell
 }
 
 template <typename T>
-__device__ __forceinline__ void store64(void* base, int64_t blk, int cell, const Node64& n, double k) {
+__device__ __forceinline__ void store64(void* base, int64_t blk, int cell, const Node64& n, double k,
+                                        const Scales* sc) {
   using R = typename StorageTraits<T>::R;
   Mom<R> m;
   m.drho = R(n.rho - 1.0);
@@ -46,7 +47,7 @@ __device__ __forceinline__ void store64(void* base, int64_t blk, int cell, const
   m.sxy = R(k * n.s[3] + n.ux * n.uy);
   m.sxz = R(k * n.s[4] + n.ux * n.uz);
   m.syz = R(k * n.s[5] + n.uy * n.uz);
-  store_node<T>(static_cast<T*>(base), blk, cell, m, nullptr);
+  store_node<T>(static_cast<T*>(base), blk, cell, m, sc);
 }
 
 __device__ __forceinline__ void axpy(Node64& acc, double w, const Node64& v) {
@@ -108,15 +109,15 @@ __global__ void k_down(TransferArgs a) {
     if (a.avg) {
       // temporal midpoint of the old (other) and new (current) coarse states,
       // taken per field on rho, u and S^neq
-      const Node64 o = load64<T>(a.coarse.mom_other, cb, cc);
-      const Node64 nw = load64<T>(a.coarse.mom, cb, cc);
+      const Node64 o = load64<T>(a.coarse.mom_other, cb, cc, a.coarse.sc);
+      const Node64 nw = load64<T>(a.coarse.mom, cb, cc, a.coarse.sc);
       axpy(acc, 0.0625, o);
       axpy(acc, 0.0625, nw);
     } else {
-      axpy(acc, 0.125, load64<T>(a.use_other ? a.coarse.mom_other : a.coarse.mom, cb, cc));
+      axpy(acc, 0.125, load64<T>(a.use_other ? a.coarse.mom_other : a.coarse.mom, cb, cc, a.coarse.sc));
     }
   }
-  store64<T>(a.out, b, cell, acc, a.k);
+  store64<T>(a.out, b, cell, acc, a.k, a.out_sc);
 }
 
 template <typename T>
@@ -133,7 +134,7 @@ __global__ void k_up(TransferArgs a) {
     atomicExch(a.status, 1);
     return;
   }
-  store64<T>(a.out, b, cell, load64<T>(a.fine.mom, fb, cell_of(x, y, z)), a.k);
+  store64<T>(a.out, b, cell, load64<T>(a.fine.mom, fb, cell_of(x, y, z), a.fine.sc), a.k, a.out_sc);
 }
 
 // U_l(i): the stored value at level l, else the upward rule applied to U_{l-1}(2i).
@@ -144,7 +145,7 @@ __device__ bool resolve_up(const OldHierarchy& o, int l, int x, int y, int z, No
     const int px = x << m, py = y << m, pz = z << m;
     const int64_t b = lookup(o.lv[lev], px, py, pz);
     if (b < 0) continue;
-    out = load64<T>(o.lv[lev].mom, b, cell_of(px, py, pz));
+    out = load64<T>(o.lv[lev].mom, b, cell_of(px, py, pz), o.lv[lev].sc);
     for (int k = lev; k < l; ++k)
 #pragma unroll
       for (int r = 0; r < 6; ++r) out.s[r] *= o.kup[k];
@@ -182,7 +183,7 @@ __device__ bool resolve(const OldHierarchy& o, int l, int x, int y, int z, Node6
 
 template <typename T>
 __global__ void __launch_bounds__(512) k_init_level(OldHierarchy o, int level, const int32_t* __restrict__ coords,
-                                                    void* out, int* status) {
+                                                    void* out, const Scales* out_sc, int* status) {
   const int64_t b = blockIdx.x;
   const int cell = threadIdx.x;
   const int x = coords[3 * b] * 8 + (cell & 7), y = coords[3 * b + 1] * 8 + ((cell >> 3) & 7),
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(512) k_init_level(OldHierarchy o, int level, c
     v = zero64();
     v.rho = 1.0;
   }
-  store64<T>(out, b, cell, v, 1.0);
+  store64<T>(out, b, cell, v, 1.0, out_sc);
 }
 
 inline unsigned blocks_for(int64_t n) { return unsigned((n + 255) / 256); }
@@ -213,10 +214,10 @@ cudaError_t up_typed(const TransferArgs& a, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t init_typed(const OldHierarchy& o, int level, const int32_t* coords, int64_t nb, void* out, int* status,
-                       cudaStream_t s) {
+cudaError_t init_typed(const OldHierarchy& o, int level, const int32_t* coords, int64_t nb, void* out,
+                       const Scales* out_sc, int* status, cudaStream_t s) {
   if (nb == 0) return cudaSuccess;
-  k_init_level<T><<<unsigned(nb), 512, 0, s>>>(o, level, coords, out, status);
+  k_init_level<T><<<unsigned(nb), 512, 0, s>>>(o, level, coords, out, out_sc, status);
   return cudaGetLastError();
 }
 
@@ -226,6 +227,8 @@ cudaError_t init_typed(const OldHierarchy& o, int level, const int32_t* coords, 
   switch (storage) {                                              \
     case HLBM_STORE_F64: return fn<double>(__VA_ARGS__);          \
     case HLBM_STORE_F32: return fn<float>(__VA_ARGS__);           \
+    case HLBM_STORE_F16S: return fn<__half>(__VA_ARGS__);         \
+    case HLBM_STORE_BF16S: return fn<__nv_bfloat16>(__VA_ARGS__); \
     default: return cudaErrorNotSupported;                        \
   }
 
@@ -238,8 +241,8 @@ cudaError_t transfer_up(int storage, const TransferArgs& a, cudaStream_t s) {
 }
 
 cudaError_t init_new_level(int storage, const OldHierarchy& old, int level, const int32_t* coords, int64_t nb,
-                           void* out, int* status, cudaStream_t s) {
-  HLBM_ML_DISPATCH(storage, init_typed, old, level, coords, nb, out, status, s)
+                           void* out, const Scales* out_sc, int* status, cudaStream_t s) {
+  HLBM_ML_DISPATCH(storage, init_typed, old, level, coords, nb, out, out_sc, status, s)
 }
 
 }  // namespace hlbm

@@ -19,11 +19,13 @@ struct LevelView {
   const void* mom;            // current buffer
   const void* mom_other;      // the other ping-pong buffer
   int64_t nb;
+  const Scales* sc;           // row scales (reduced-precision storage) or null
 };
 
 struct TransferArgs {
   LevelView fine, coarse;
   void* out;                  // buffer written (fine for down, coarse for up)
+  const Scales* out_sc;       // its row scales or null
   const int32_t* nodes;       // (block << 9) | cell of the written level
   int64_t n_nodes;
   int avg;                    // down: 1 = temporal midpoint of coarse mom_other (old) and mom (new)
@@ -53,6 +55,6 @@ struct OldHierarchy {
 // holds the coincident node, else the downward spatial rule from old coarser
 // levels (recursively).  status is set to 1 if a node has no source.
 cudaError_t init_new_level(int storage, const OldHierarchy& old, int level, const int32_t* coords, int64_t nb,
-                           void* out, int* status, cudaStream_t s);
+                           void* out, const Scales* out_sc, int* status, cudaStream_t s);
 
 }  // namespace hlbm

@@ -188,3 +188,18 @@ def test_rebuild_moves_moments_like_the_oracle():
             m.coarse_step()
             lat.step(2)
             _compare(lat, m, 1e-11, 0.01)
+
+
+@pytest.mark.parametrize("storage,tol", [("f16s", 3e-2), ("bf16s", 0.2)])
+def test_two_level_reduced_precision(storage, tol):
+    """Two-level shear wave with FP16/BF16-scaled storage stays within the
+    stated error of the FP64 oracle over 3 coarse steps (error reported)."""
+    ext = (16, 128, 16)
+    O0 = np.zeros(hy.block_dims(ext, 8, 0), bool)
+    O0[:, 7:9, :] = True
+    h, m, lat = _setup(ext, 2, O0, (True, True, True), 0.8, shear(0.01, 128), storage)
+    with lat:
+        for k in range(3):
+            m.coarse_step()
+            lat.step(2)
+        _compare(lat, m, tol, 0.01)

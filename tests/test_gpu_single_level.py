@@ -150,3 +150,51 @@ def test_duct_256_sampled_nodes_one_step():
     assert err.max() < 1e-5, err
     # exact mass conservation with walls, to FP32 rounding of the stored density deviation
     assert abs(r1[0] - r0[0]) / r0[0] < 1e-9
+
+
+# ------------------------------------------------------------ reduced-precision storage
+# Codes of delta_rho, u and S^neq are scaled so each row's amax sits below 2^13:
+# one rounding costs at most 2^-11 (fp16) / 2^-8 (bf16) of the row amax times
+# the headroom factor 8.  The tolerances below are per step, against the
+# FP64 oracle started from the decoded GPU state.
+RP_TOL = {"f16s": 8 * 2.0 ** -11, "bf16s": 8 * 2.0 ** -8}
+
+
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+def test_reduced_precision_roundtrip(storage):
+    M0 = wl.random_field((16, 16, 16), 71)
+    with hl.Lattice((16, 16, 16), storage=storage) as lat:
+        lat.set_dense()
+        lat.write_moments(hl.dense_to_blocks(M0))
+        got = hl.blocks_to_dense(lat.read_moments(), (16, 16, 16))
+    # compare the stored quantities: delta_rho, u, S^neq
+    def q(M):
+        Q = M.copy()
+        Q[0] -= 1.0
+        for r, (a, b) in zip(range(4, 10), [(1, 1), (2, 2), (3, 3), (1, 2), (1, 3), (2, 3)]):
+            Q[r] = M[r] - M[a] * M[b]
+        return Q
+    err = rel_err(q(got), q(M0), np.abs(q(M0)).reshape(10, -1).max(axis=1))
+    assert err.max() < RP_TOL[storage] / 8 * 1.01, err
+
+
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+def test_reduced_precision_step_vs_oracle(storage):
+    M0 = wl.random_field((24, 16, 32), 72)
+    start, got = run_gpu(M0, (32, 16, 24), 1, 0.7, storage, periodic=(True, False, True), force=(1e-5, 0.0, 0.0))
+    ref = oracle(start, 1, 0.7, periodic=(True, False, True), force=(1e-5, 0.0, 0.0))
+    err = rel_err(got, ref, row_scales(ref, 0.02))
+    assert err.max() < RP_TOL[storage], err
+
+
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+def test_reduced_precision_taylor_green_across_rescale(storage):
+    """40 steps (the scales are refit after 32) of the 32^3 TGV; the error
+    against the FP64 oracle grows at most linearly in the step count."""
+    M0 = wl.taylor_green_3d(32, 0.05)
+    start, got = run_gpu(M0, (32, 32, 32), 40, 0.6, storage)
+    ref = oracle(start, 40, 0.6)
+    err = rel_err(got, ref, row_scales(ref, 0.05))
+    assert err[:4].max() < 40 * RP_TOL[storage] / 4, err
+    ke = lambda M: float((0.5 * M[0] * (M[1] ** 2 + M[2] ** 2 + M[3] ** 2)).sum())
+    assert abs(ke(got) / ke(ref) - 1) < (0.01 if storage == "f16s" else 0.05)
