@@ -176,6 +176,20 @@ int32_t hlbm_synchronize(hlbm_lattice *h);
    Synchronous.  Returns HLBM_E_NONFINITE if the mass is not finite. */
 int32_t hlbm_reduce(hlbm_lattice *h, double out[7]);
 
+/* Reverse mode of the single-level step (the paper has no adjoint; this
+   differentiates Sec. 3.1 with the Guo force and eps*tau of Sec. 4 with
+   respect to the level-0 force field).
+   hlbm_forward_record advances n_steps steps like hlbm_step and keeps the
+   state every ckpt_every steps (device memory, one moment buffer each).
+   hlbm_adjoint then takes dL/dM of the final stored moments (float32 device
+   buffer, public layout [nb][10][512], rho row = d/d rho) and writes dL/dF
+   (float32 device [nb][3][512], the layout of hlbm_set_force) by recomputing
+   each checkpoint segment and stepping backwards; the force sums are FP64.
+   Single-level lattices with FP32 or FP64 storage; force, eps and solids must
+   not change between the two calls.  Synchronous. */
+int32_t hlbm_forward_record(hlbm_lattice *h, int32_t n_steps, int32_t ckpt_every);
+int32_t hlbm_adjoint(hlbm_lattice *h, const float *dL_dM_dev, float *dL_dF_dev);
+
 /* Allocation-free FP64 reduction of a moment buffer the caller already holds.
  * The paper has no counterpart; this entry point exists for callers that must
  * not allocate device memory: code embedded in a host application that owns

@@ -15,9 +15,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libhomelbm.so")
 SOURCES = ["api.cu", "stream_collide.cu", "stream_collide_f2.cu", "io_reduce.cu", "hierarchy.cu", "multilevel.cu",
-           "ml_host.cu"]
+           "ml_host.cu", "adjoint.cu"]
 HEADERS = ["hlbm_internal.h", "lbm_math.cuh", "storage.cuh", "io_reduce.h", "lattice_state.h", "hierarchy.cuh",
-           "multilevel.cuh", "v2.cuh"]
+           "multilevel.cuh", "v2.cuh", "adjoint_math.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

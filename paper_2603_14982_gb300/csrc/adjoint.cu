@@ -1,0 +1,408 @@
+// adjoint.cu -- reverse-mode step of the single-level stream-collide and the
+// checkpointed driver behind hlbm_forward_record / hlbm_adjoint.  The paper
+// has no adjoint; the forward it reverses is Sec. 3.1 with the Guo force and
+// the mixture relaxation time of Sec. 4.
+//
+// Per reverse step (lambda = dL/dM of the step's output):
+//   k_adj_pull: every node recomputes its pulled pre-collision moments p from
+//     the step's input M (the same pull as the forward), applies the transposed
+//     collision Jacobian to lambda, writes lambda_p and adds dL/dF (FP64).
+//   k_adj_push: every node x forms gbar_i(x) = P_i^T lambda_p(x) and hands it to
+//     its pull source x - c_i through a shared buffer indexed by the destination
+//     (wall and solid slots mirror the bounce-back); every source y gathers what
+//     it fed, takes the weighted moments that transpose its 17 Hermite
+//     coefficients and applies (dA/dM)^T at M(y): lambda of the step's input.
+// Both kernels gather; no atomics, so the result is deterministic.
+#include <cuda_runtime.h>
+
+#include <utility>
+#include <vector>
+
+#include "adjoint_math.cuh"
+#include "hlbm_internal.h"
+#include "lattice_state.h"
+
+namespace hlbm {
+namespace {
+
+constexpr int kExt = 10;
+constexpr int kExtCells = 1000;
+constexpr int kHaloCells = 488;
+
+__host__ __device__ constexpr int slot_of(int j) { return j < 13 ? j : j - 1; }
+template <int J>
+__host__ __device__ constexpr int ext_off() {
+  return Dir<J>::cx + kExt * (Dir<J>::cy + kExt * Dir<J>::cz);
+}
+__device__ __forceinline__ int ext_index(int x, int y, int z) { return (x + 1) + kExt * ((y + 1) + kExt * (z + 1)); }
+
+// Halo node t of 488: coordinates (-1 or 8 on the face axis) and face 0..5
+// (x-, x+, y-, y+, z-, z+); z faces own the 10x10 planes, y faces the 10x8
+// remainder, x faces the 8x8 remainder.
+__device__ __forceinline__ void halo_cell(int t, int& hx, int& hy, int& hz, int& face) {
+  if (t < 200) {
+    const int u = t < 100 ? t : t - 100;
+    hz = t < 100 ? -1 : 8;
+    hx = u % 10 - 1;
+    hy = u / 10 - 1;
+    face = t < 100 ? 4 : 5;
+  } else if (t < 360) {
+    const int u = t < 280 ? t - 200 : t - 280;
+    hy = t < 280 ? -1 : 8;
+    hx = u % 10 - 1;
+    hz = u / 10;
+    face = t < 280 ? 2 : 3;
+  } else {
+    const int u = t < 424 ? t - 360 : t - 424;
+    hx = t < 424 ? -1 : 8;
+    hy = u % 8;
+    hz = u / 8;
+    face = t < 424 ? 0 : 1;
+  }
+}
+
+__device__ __forceinline__ int block_dir(int hx, int hy, int hz) {
+  const int dx = hx < 0 ? -1 : (hx > 7 ? 1 : 0);
+  const int dy = hy < 0 ? -1 : (hy > 7 ? 1 : 0);
+  const int dz = hz < 0 ? -1 : (hz > 7 ? 1 : 0);
+  return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+}
+
+// Sink writing value J to slot J of ext index e (all J), or only those J whose
+// component on axis AX equals SG (AX < 0: all).
+template <typename R, int AX, int SG>
+struct ExtSink {
+  R* f;
+  int e;
+  R g13;
+  template <int J>
+  __device__ __forceinline__ void put(R v) {
+    if constexpr (J == 13) {
+      g13 = v;
+    } else {
+      constexpr int c = AX == 0 ? Dir<J>::cx : (AX == 1 ? Dir<J>::cy : (AX == 2 ? Dir<J>::cz : SG));
+      if constexpr (c == SG) f[slot_of(J) * kExtCells + e] = v;
+    }
+  }
+};
+
+template <typename R, int AX, int SG, typename Emit>
+__device__ __forceinline__ void emit_face(int face, Emit&& emit, R* f, int e) {
+  (void)face;
+  ExtSink<R, AX, SG> s{f, e, R(0)};
+  emit(s);
+}
+
+// Dispatch a sink for halo face `face` with component sign `inward` (+1: the
+// directions entering the block, -1: the directions leaving it).
+template <typename R, typename Emit>
+__device__ __forceinline__ void emit_halo(int face, bool entering, Emit&& emit, R* f, int e) {
+  switch (face * 2 + (entering ? 0 : 1)) {
+    case 0: emit_face<R, 0, 1>(face, emit, f, e); break;
+    case 1: emit_face<R, 0, -1>(face, emit, f, e); break;
+    case 2: emit_face<R, 0, -1>(face, emit, f, e); break;
+    case 3: emit_face<R, 0, 1>(face, emit, f, e); break;
+    case 4: emit_face<R, 1, 1>(face, emit, f, e); break;
+    case 5: emit_face<R, 1, -1>(face, emit, f, e); break;
+    case 6: emit_face<R, 1, -1>(face, emit, f, e); break;
+    case 7: emit_face<R, 1, 1>(face, emit, f, e); break;
+    case 8: emit_face<R, 2, 1>(face, emit, f, e); break;
+    case 9: emit_face<R, 2, -1>(face, emit, f, e); break;
+    case 10: emit_face<R, 2, -1>(face, emit, f, e); break;
+    default: emit_face<R, 2, 1>(face, emit, f, e); break;
+  }
+}
+
+// Source-indexed pull gather (forward order): g[J] = f[J][e - c_J].
+template <typename R, int J>
+__device__ __forceinline__ void pull_one(const R* f, int e, R g13, R (&g)[27]) {
+  if constexpr (J == 13)
+    g[13] = g13;
+  else
+    g[J] = f[slot_of(J) * kExtCells + e - ext_off<J>()];
+}
+// Destination-indexed push gather (reverse order): g[J] = f[J][e + c_J].
+template <typename R, int J>
+__device__ __forceinline__ void push_one(const R* f, int e, R g13, R (&g)[27]) {
+  if constexpr (J == 13)
+    g[13] = g13;
+  else
+    g[J] = f[slot_of(J) * kExtCells + e + ext_off<J>()];
+}
+template <typename R, bool PULL, int... Js>
+__device__ __forceinline__ void gather27(const R* f, int e, R g13, R (&g)[27], std::integer_sequence<int, Js...>) {
+  if constexpr (PULL)
+    (pull_one<R, Js>(f, e, g13, g), ...);
+  else
+    (push_one<R, Js>(f, e, g13, g), ...);
+}
+
+// Bounce-back fill at a wall / solid position w (block-local hx, hy, hz):
+// forward (PULL): f[J][w] = f[opp J][w + c_J]  (the node w + c_J pulls its own opposite)
+// reverse:        f[J][w] = f[opp J][w - c_J]  (the source w - c_J fed itself)
+template <typename R, bool PULL, int J>
+__device__ __forceinline__ void mirror_one(R* f, int eh, int hx, int hy, int hz, bool solid_any,
+                                           const uint8_t* s_solid) {
+  if constexpr (J != 13) {
+    constexpr int sg = PULL ? 1 : -1;
+    const int x = hx + sg * Dir<J>::cx, y = hy + sg * Dir<J>::cy, z = hz + sg * Dir<J>::cz;
+    if ((unsigned)x < 8u && (unsigned)y < 8u && (unsigned)z < 8u) {
+      const int ed = eh + sg * ext_off<J>();
+      if (!(solid_any && s_solid[ed])) f[slot_of(J) * kExtCells + eh] = f[slot_of(26 - J) * kExtCells + ed];
+    }
+  }
+}
+template <typename R, bool PULL, int... Js>
+__device__ __forceinline__ void mirror27(R* f, int eh, int hx, int hy, int hz, bool solid_any, const uint8_t* s_solid,
+                                         std::integer_sequence<int, Js...>) {
+  (mirror_one<R, PULL, Js>(f, eh, hx, hy, hz, solid_any, s_solid), ...);
+}
+
+template <typename R>
+__device__ __forceinline__ PreMom<R> load_pm(const float* p, int64_t blk, int cell) {
+  const float* q = p + blk * (kRows * kCells) + cell;
+  PreMom<R> l;
+  l.drho = R(q[0]);
+  l.jx = R(q[1 * kCells]);
+  l.jy = R(q[2 * kCells]);
+  l.jz = R(q[3 * kCells]);
+  l.pxx = R(q[4 * kCells]);
+  l.pyy = R(q[5 * kCells]);
+  l.pzz = R(q[6 * kCells]);
+  l.pxy = R(q[7 * kCells]);
+  l.pxz = R(q[8 * kCells]);
+  l.pyz = R(q[9 * kCells]);
+  return l;
+}
+
+template <typename R>
+__device__ __forceinline__ Mom<R> load_lam(const float* p, int64_t blk, int cell) {
+  const float* q = p + blk * (kRows * kCells) + cell;
+  Mom<R> l;
+  l.drho = R(q[0]);
+  l.ux = R(q[1 * kCells]);
+  l.uy = R(q[2 * kCells]);
+  l.uz = R(q[3 * kCells]);
+  l.sxx = R(q[4 * kCells]);
+  l.syy = R(q[5 * kCells]);
+  l.szz = R(q[6 * kCells]);
+  l.sxy = R(q[7 * kCells]);
+  l.sxz = R(q[8 * kCells]);
+  l.syz = R(q[9 * kCells]);
+  return l;
+}
+
+template <typename R>
+__device__ __forceinline__ void store10(float* p, int64_t blk, int cell, R a0, R a1, R a2, R a3, R a4, R a5, R a6, R a7,
+                                        R a8, R a9) {
+  float* q = p + blk * (kRows * kCells) + cell;
+  q[0] = float(a0);
+  q[1 * kCells] = float(a1);
+  q[2 * kCells] = float(a2);
+  q[3 * kCells] = float(a3);
+  q[4 * kCells] = float(a4);
+  q[5 * kCells] = float(a5);
+  q[6 * kCells] = float(a6);
+  q[7 * kCells] = float(a7);
+  q[8 * kCells] = float(a8);
+  q[9 * kCells] = float(a9);
+}
+
+// Emits gbar_J for all J of one node's lambda_p to a sink.
+template <typename R>
+struct GbEmit {
+  PreMom<R> l;
+  template <typename S>
+  __device__ __forceinline__ void run(S& s) const {
+    run_seq(s, std::make_integer_sequence<int, 27>{});
+  }
+  template <typename S, int... Js>
+  __device__ __forceinline__ void run_seq(S& s, std::integer_sequence<int, Js...>) const {
+    (s.template put<Js>(gbar<Js>(l)), ...);
+  }
+};
+
+struct AdjArgs {
+  const float* lam;   // dL/dM of the step's output [nb][10][512]
+  float* lamp;        // dL/dp of the pre-collision moments [nb][10][512]
+  double* dF;         // accumulated dL/dF [nb][3][512]
+  float* lam_out;     // dL/dM of the step's input [nb][10][512]
+};
+
+// Shared part: the block's ext buffer filled with the forward pull (PULL) or
+// the reverse push; returns after the mirror barrier.
+template <typename T, bool PULL>
+__device__ __forceinline__ void fill_ext(const StepArgs& a, const AdjArgs& d, int64_t blk, int t, int* s_nbr,
+                                         unsigned& s_wall, uint8_t* s_solid, typename StorageTraits<T>::R* fbuf,
+                                         typename StorageTraits<T>::R& g13, bool& solid_any) {
+  using R = typename StorageTraits<T>::R;
+  const T* in = static_cast<const T*>(a.in);
+  if (t < 32) {
+    const int v = t < 27 ? a.nbr[blk * 27 + t] : 0;
+    const unsigned wb = __ballot_sync(0xffffffffu, t < 27 && v == kWall);
+    if (t < 27) s_nbr[t] = v;
+    if (t == 0) s_wall = wb;
+  }
+  solid_any = a.bflags != nullptr && (a.bflags[blk] & kBlockSolidNear);
+  const int x = t & 7, y = (t >> 3) & 7, z = t >> 6;
+  const int e = ext_index(x, y, z);
+  int hx = 0, hy = 0, hz = 0, face = 0, eh = 0, hnb = kMissing, hsrc = 0;
+  if (t < kHaloCells) {
+    halo_cell(t, hx, hy, hz, face);
+    eh = ext_index(hx, hy, hz);
+    hsrc = (hx & 7) + 8 * (hy & 7) + 64 * (hz & 7);
+  }
+  __syncthreads();
+  if (t < kHaloCells) hnb = s_nbr[block_dir(hx, hy, hz)];
+  if (solid_any) {
+    s_solid[e] = a.solid[blk * kCells + t];
+    if (t < kHaloCells) s_solid[eh] = hnb >= 0 ? a.solid[int64_t(hnb) * kCells + hsrc] : 0;
+    __syncthreads();
+  }
+  const bool own_solid = solid_any && s_solid[e];
+  const R kxyz = R(a.kxyz);
+  if constexpr (PULL) {
+    ExtSink<R, -1, 0> own{fbuf, e, R(0)};
+    if (!own_solid) emit_all(make_coef(load_node<T>(in, blk, t, a.scales_in), kxyz), own);
+    g13 = own.g13;
+    if (t < kHaloCells && hnb >= 0 && !(solid_any && s_solid[eh])) {
+      const Coef<R> c = make_coef(load_node<T>(in, hnb, hsrc, a.scales_in), kxyz);
+      emit_halo<R>(face, true, [&](auto& s) { emit_all(c, s); }, fbuf, eh);
+    }
+  } else {
+    // gbar of the own node and of the halo nodes whose pull source is inside
+    ExtSink<R, -1, 0> own{fbuf, e, R(0)};
+    if (!own_solid) GbEmit<R>{load_pm<R>(d.lamp, blk, t)}.run(own);
+    g13 = own.g13;
+    if (t < kHaloCells && hnb >= 0 && !(solid_any && s_solid[eh])) {
+      const GbEmit<R> gb{load_pm<R>(d.lamp, hnb, hsrc)};
+      emit_halo<R>(face, false, [&](auto& s) { gb.run(s); }, fbuf, eh);
+    }
+  }
+  __syncthreads();
+  if (s_wall != 0u || solid_any) {
+    if (own_solid) mirror27<R, PULL>(fbuf, e, x, y, z, solid_any, s_solid, std::make_integer_sequence<int, 27>{});
+    if (t < kHaloCells && (hnb == kWall || (hnb >= 0 && solid_any && s_solid[eh])))
+      mirror27<R, PULL>(fbuf, eh, hx, hy, hz, solid_any, s_solid, std::make_integer_sequence<int, 27>{});
+    __syncthreads();
+  }
+}
+
+// Reverse step, part 1: lambda_p and dL/dF.
+template <typename T>
+__global__ void __launch_bounds__(512, 1) k_adj_pull(StepArgs a, AdjArgs d) {
+  using R = typename StorageTraits<T>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* fbuf = reinterpret_cast<R*>(smem_raw);
+  __shared__ int s_nbr[27];
+  __shared__ unsigned s_wall;
+  __shared__ uint8_t s_solid[kExtCells];
+  const int64_t blk = blockIdx.x;
+  const int t = threadIdx.x;
+  R g13;
+  bool solid_any;
+  fill_ext<T, true>(a, d, blk, t, s_nbr, s_wall, s_solid, fbuf, g13, solid_any);
+  const int e = ext_index(t & 7, (t >> 3) & 7, t >> 6);
+  const bool frozen = solid_any && s_solid[e];
+  if (frozen) {  // a solid node copies its input: no dependence on the pulls or on F
+    store10<R>(d.lamp, blk, t, R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0));
+    return;
+  }
+  R g[27];
+  gather27<R, true>(fbuf, e, g13, g, std::make_integer_sequence<int, 27>{});
+  const PreMom<R> p = project(g);
+  R fx, fy, fz;
+  if (a.F != nullptr) {
+    const float* Fp = a.F + blk * 3 * kCells + t;
+    fx = R(Fp[0]);
+    fy = R(Fp[kCells]);
+    fz = R(Fp[2 * kCells]);
+  } else {
+    fx = R(a.fu[0]);
+    fy = R(a.fu[1]);
+    fz = R(a.fu[2]);
+  }
+  R om = R(a.om);
+  if (a.eps != nullptr) om = R(1) / (R(a.tau) * R(a.eps[blk * kCells + t]));
+  PreMom<R> lp;
+  R lfx, lfy, lfz;
+  collide_vjp(p, fx, fy, fz, om, load_lam<R>(d.lam, blk, t), lp, lfx, lfy, lfz);
+  store10<R>(d.lamp, blk, t, lp.drho, lp.jx, lp.jy, lp.jz, lp.pxx, lp.pyy, lp.pzz, lp.pxy, lp.pxz, lp.pyz);
+  double* dF = d.dF + blk * 3 * kCells + t;
+  dF[0] += double(lfx);
+  dF[kCells] += double(lfy);
+  dF[2 * kCells] += double(lfz);
+}
+
+// Reverse step, part 2: lambda of the step's input moments.
+template <typename T>
+__global__ void __launch_bounds__(512, 1) k_adj_push(StepArgs a, AdjArgs d) {
+  using R = typename StorageTraits<T>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* fbuf = reinterpret_cast<R*>(smem_raw);
+  __shared__ int s_nbr[27];
+  __shared__ unsigned s_wall;
+  __shared__ uint8_t s_solid[kExtCells];
+  const int64_t blk = blockIdx.x;
+  const int t = threadIdx.x;
+  R g13;
+  bool solid_any;
+  fill_ext<T, false>(a, d, blk, t, s_nbr, s_wall, s_solid, fbuf, g13, solid_any);
+  const int e = ext_index(t & 7, (t >> 3) & 7, t >> 6);
+  const bool frozen = solid_any && s_solid[e];
+  const Mom<R> lam = load_lam<R>(d.lam, blk, t);
+  if (frozen) {  // M'(y) = M(y)
+    store10<R>(d.lam_out, blk, t, lam.drho, lam.ux, lam.uy, lam.uz, lam.sxx, lam.syy, lam.szz, lam.sxy, lam.sxz,
+               lam.syz);
+    return;
+  }
+  R gb[27];
+  gather27<R, false>(fbuf, e, g13, gb, std::make_integer_sequence<int, 27>{});
+  const Coef<R> gh = adjoint_moments(gb);
+  // the coefficient Jacobian already carries the weights w_i: ghat includes them
+  const Mom<R> lm = coef_vjp(load_node<T>(static_cast<const T*>(a.in), blk, t, a.scales_in), gh, R(a.kxyz));
+  store10<R>(d.lam_out, blk, t, lm.drho, lm.ux, lm.uy, lm.uz, lm.sxx, lm.syy, lm.szz, lm.sxy, lm.sxz, lm.syz);
+}
+
+template <typename T>
+cudaError_t launch_adj(const StepArgs& a, const AdjArgs& d, cudaStream_t s) {
+  using R = typename StorageTraits<T>::R;
+  const size_t smem = size_t(26) * kExtCells * sizeof(R);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_adj_pull<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_adj_push<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (a.nb == 0) return cudaSuccess;
+  k_adj_pull<T><<<unsigned(a.nb), 512, smem, s>>>(a, d);
+  k_adj_push<T><<<unsigned(a.nb), 512, smem, s>>>(a, d);
+  return cudaGetLastError();
+}
+
+__global__ void k_dF_out(const double* __restrict__ dF, float* __restrict__ out, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = float(dF[i]);
+}
+
+}  // namespace
+
+cudaError_t adjoint_step(int storage, const StepArgs& a, const float* lam, float* lamp, double* dF, float* lam_out,
+                         cudaStream_t s) {
+  const AdjArgs d{lam, lamp, dF, lam_out};
+  switch (storage) {
+    case HLBM_STORE_F64: return launch_adj<double>(a, d, s);
+    case HLBM_STORE_F32: return launch_adj<float>(a, d, s);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+cudaError_t adjoint_dF_to_float(const double* dF, float* out, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_dF_out<<<unsigned((n + 255) / 256), 256, 0, s>>>(dF, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace hlbm

@@ -258,6 +258,7 @@ int32_t hlbm_destroy(hlbm_lattice* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& L : h->lv) LatticeOps::free_level(L);
   LatticeOps::release(h->d_stage);
+  for (void*& c : h->ckpt) LatticeOps::release(c);
   void* v = h->d_status;
   LatticeOps::release(v);
   v = h->d_red;
@@ -564,6 +565,116 @@ int32_t hlbm_reduce(hlbm_lattice* h, double out[7]) {
   rc = ml_check_status(h);
   if (rc) return rc;
   if (!std::isfinite(total[0])) return fail(h, HLBM_E_NONFINITE, "mass is not finite");
+  return HLBM_OK;
+}
+
+static StepArgs level0_args(hlbm_lattice* h) {
+  LevelData& L = h->lv[0];
+  StepArgs a{};
+  a.nbr = L.d_nbr;
+  a.F = h->d_F;
+  a.eps = h->d_eps;
+  a.solid = L.d_solid;
+  a.bflags = L.d_bflags;
+  a.bmask = L.d_bmask;
+  for (int k = 0; k < 3; ++k) a.fu[k] = h->fu[k];
+  a.tau = L.tau;
+  a.om = 1.0 / L.tau;
+  a.kxyz = h->cfg.xyz_literal ? 13.5 : 27.0;
+  a.nb = L.nb;
+  a.scales_in = a.scales_out = L.d_scales;
+  return a;
+}
+
+int32_t hlbm_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (h->cfg.num_levels != 1) return fail(h, HLBM_E_UNSUPPORTED, "the adjoint needs a single-level lattice");
+  if (h->cfg.storage != HLBM_STORE_F32 && h->cfg.storage != HLBM_STORE_F64)
+    return fail(h, HLBM_E_UNSUPPORTED, "the adjoint needs FP32 or FP64 storage");
+  if (!h->have_blocks) return fail(h, HLBM_E_BAD_STATE, "no blocks are stored");
+  if (n_steps <= 0 || ckpt_every <= 0) return fail(h, HLBM_E_INVALID_ARG, "n_steps and ckpt_every must be positive");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  for (void*& c : h->ckpt) LatticeOps::release(c);
+  h->ckpt.clear();
+  h->rec_steps = h->rec_every = 0;
+  LevelData& L = h->lv[0];
+  const size_t bytes = size_t(L.nb) * kRows * kCells * (h->cfg.storage == HLBM_STORE_F64 ? 8 : 4);
+  const int n_ck = (n_steps + ckpt_every - 1) / ckpt_every;
+  for (int c = 0; c < n_ck; ++c) {
+    void* p;
+    if ((rc = LatticeOps::alloc(h, &p, bytes))) return rc;
+    h->ckpt.push_back(p);
+  }
+  for (int32_t t = 0; t < n_steps; ++t) {
+    if (t % ckpt_every == 0)
+      HLBM_CUDA(h, cudaMemcpyAsync(h->ckpt[t / ckpt_every], L.d_mom[L.cur], bytes, cudaMemcpyDeviceToDevice,
+                                   h->stream));
+    if ((rc = hlbm_step(h, 1))) return rc;
+  }
+  h->rec_steps = n_steps;
+  h->rec_every = ckpt_every;
+  return HLBM_OK;
+}
+
+int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (h->rec_steps <= 0) return fail(h, HLBM_E_BAD_STATE, "call hlbm_forward_record first");
+  if (dL_dM_dev == nullptr || dL_dF_dev == nullptr) return fail(h, HLBM_E_INVALID_ARG, "NULL buffer");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  LevelData& L = h->lv[0];
+  const int64_t nb = L.nb;
+  const size_t bytes = size_t(nb) * kRows * kCells * (h->cfg.storage == HLBM_STORE_F64 ? 8 : 4);
+  const size_t lam_elems = size_t(nb) * kRows * kCells;
+  const int K = h->rec_every, n = h->rec_steps;
+  std::vector<void*> tmp;
+  auto release_all = [&]() {
+    for (void*& p : tmp) LatticeOps::release(p);
+  };
+  auto get = [&](size_t b, void** out) -> int {
+    int r = LatticeOps::alloc(h, out, b);
+    if (r == HLBM_OK) tmp.push_back(*out);
+    return r;
+  };
+  void *lam0, *lam1, *lamp, *dF;
+  std::vector<void*> seg(size_t(K), nullptr);
+  if ((rc = get(lam_elems * 4, &lam0)) || (rc = get(lam_elems * 4, &lam1)) || (rc = get(lam_elems * 4, &lamp)) ||
+      (rc = get(size_t(nb) * 3 * kCells * sizeof(double), &dF))) {
+    release_all();
+    return rc;
+  }
+  for (int i = 1; i < K; ++i)
+    if ((rc = get(bytes, &seg[i]))) {
+      release_all();
+      return rc;
+    }
+  float* lam[2] = {static_cast<float*>(lam0), static_cast<float*>(lam1)};
+  int c = 0;
+  cudaError_t e = cudaMemcpyAsync(lam[0], dL_dM_dev, lam_elems * 4, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dF, 0, size_t(nb) * 3 * kCells * sizeof(double), h->stream);
+  StepArgs a = level0_args(h);
+  const int n_seg = (n + K - 1) / K;
+  for (int s = n_seg - 1; s >= 0 && e == cudaSuccess; --s) {
+    const int t0 = s * K, ns = (n - t0) < K ? (n - t0) : K;
+    seg[0] = h->ckpt[s];
+    for (int i = 1; i < ns && e == cudaSuccess; ++i) {  // recompute the segment's states
+      a.in = seg[i - 1];
+      a.out = seg[i];
+      e = launch_stream_collide(h->cfg.storage, a, h->stream);
+    }
+    for (int i = ns - 1; i >= 0 && e == cudaSuccess; --i) {
+      a.in = seg[i];
+      e = adjoint_step(h->cfg.storage, a, lam[c], static_cast<float*>(lamp), static_cast<double*>(dF), lam[1 - c],
+                       h->stream);
+      c = 1 - c;
+    }
+  }
+  if (e == cudaSuccess) e = adjoint_dF_to_float(static_cast<double*>(dF), dL_dF_dev, nb * 3 * kCells, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  seg[0] = nullptr;
+  release_all();
+  if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
   return HLBM_OK;
 }
 

@@ -40,6 +40,13 @@ struct StepArgs {
 // packed-FP32 node-pair kernel (stream_collide_f2.cu).
 cudaError_t launch_stream_collide(int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_stream_collide_f2(int storage, const StepArgs& a, cudaStream_t s);
+// One reverse step of the single-level stream-collide (adjoint.cu): lam = dL/dM
+// of the step's output, lam_out = dL/dM of its input (a.in), dF += dL/dF.
+// lamp is scratch [nb][10][512]; all lambda arrays are natural node order.
+cudaError_t adjoint_step(int storage, const StepArgs& a, const float* lam, float* lamp, double* dF, float* lam_out,
+                         cudaStream_t s);
+cudaError_t adjoint_dF_to_float(const double* dF, float* out, int64_t n, cudaStream_t s);
+
 // Per-node bounce masks and the kBlockBounce flag from a neighbour table and
 // an optional solid mask (bflags must hold kBlockSolidNear where solids are near).
 cudaError_t compute_bounce_masks(const int32_t* nbr, const uint8_t* solid, uint8_t* bflags, uint32_t* bmask,

@@ -56,6 +56,9 @@ struct hlbm_lattice {
   bool device_hierarchy = false;  // levels were built by the device rebuild pipeline
   double kup[8] = {0}, kdown[8] = {0};  // S^neq factors between level l and l+1
   int* d_status = nullptr;    // device status word of the transfer kernels (0 = ok)
+  // forward run recorded for the adjoint: states at steps 0, K, 2K, ...
+  std::vector<void*> ckpt;
+  int32_t rec_steps = 0, rec_every = 0;
   std::string err;
 
   void block_dims(int level, int dims[3]) const {

@@ -65,6 +65,8 @@ _SIGS = {
     "hlbm_step": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     "hlbm_synchronize": (ctypes.c_int32, [ctypes.c_void_p]),
     "hlbm_reduce": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "hlbm_forward_record": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
+    "hlbm_adjoint": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "hlbm_reduce_f32_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -238,6 +240,14 @@ class Lattice:
     def step(self, n_fine_steps=1):
         self._check(self.lib.hlbm_step(self.h, int(n_fine_steps)))
 
+    def forward_record(self, n_steps, ckpt_every):
+        self._check(self.lib.hlbm_forward_record(self.h, int(n_steps), int(ckpt_every)))
+
+    def adjoint(self, dL_dM, dL_dF):
+        """dL_dM: torch CUDA float32 [n][10][512]; dL_dF: torch CUDA float32 [n][3][512] (written)."""
+        self._check(self.lib.hlbm_adjoint(self.h, _ptr(dL_dM)[0], _ptr(dL_dF)[0]))
+        return dL_dF
+
     def synchronize(self):
         self._check(self.lib.hlbm_synchronize(self.h))
 
@@ -275,3 +285,30 @@ def blocks_to_dense(Mb, shape, coords=None, fill=np.nan):
         t[c[:, 2], c[:, 1], c[:, 0]] = Mb
     t = t.reshape(nz // 8, ny // 8, nx // 8, R, 8, 8, 8).transpose(3, 0, 4, 1, 5, 2, 6)
     return np.ascontiguousarray(t.reshape(R, nz, ny, nx))
+
+
+def make_force_autograd(lattice, n_steps, ckpt_every):
+    """A torch.autograd.Function mapping the level-0 force field F ([n][3][512]
+    float32 CUDA) to the stored moments after ``n_steps`` steps from the
+    lattice's current state ([n][10][512] float32 CUDA, public layout).  The
+    backward pass runs the library's checkpointed adjoint."""
+    import torch
+
+    class ForceToMoments(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, F):
+            Fc = F.detach().contiguous()
+            lattice.set_force(Fc)
+            lattice.forward_record(n_steps, ckpt_every)
+            out = torch.empty((lattice.num_blocks(0), 10, 512), dtype=torch.float32, device=F.device)
+            lattice.read_moments(out)
+            lattice.synchronize()
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            dF = torch.empty((lattice.num_blocks(0), 3, 512), dtype=torch.float32, device=grad_out.device)
+            lattice.adjoint(grad_out.contiguous().float(), dF)
+            return dF
+
+    return ForceToMoments.apply
