@@ -37,7 +37,7 @@ KERNEL = "k_stream_collide_f2<float>"
 # DRAM bytes (read + write) per launch of KERNEL from one ncu capture of the
 # 192^3 duct, scaled by nodes to 256^3 (profiles/stream_collide_f2_duct192.md);
 # set to None whenever the kernel changes after that capture.
-TRAFFIC_PER_NODE = 532.3e6 / 192 ** 3
+TRAFFIC_PER_NODE = None
 
 
 def measured_peaks():
@@ -154,7 +154,11 @@ def run_gpu(args, rank, world):
     if world > 1:
         torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
     t_dev, t_e2e = times.tolist()
+    extras = None
+    if not args.no_extras and world == 1:
+        extras = bench_extras(hl, wl)
     res = {
+        "extras": extras,
         "ms_per_step": 1e3 * t_dev / args.steps,
         "value": world * nodes * args.steps / t_dev / 1e6,
         "e2e_value": world * nodes * args.steps / t_e2e / 1e6,
@@ -164,6 +168,165 @@ def run_gpu(args, rank, world):
         "finite": bool(np.isfinite(red_e2e[0])),
     }
     return res
+
+
+def timed(stream, fn):
+    """Device time (ms) of fn() on a stream, bracketed by synchronizes."""
+    import torch
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    fn()
+    ev[1].record(stream)
+    ev[1].synchronize()
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1])
+
+
+def bench_batched(hl, wl, stream, steps=200):
+    """64 uneven periodic Taylor-Green domains (edges from {32,48,64,96,128},
+    U0 in [0.01, 0.08], tau in [0.52, 0.8], seeded), FP16-scaled storage: the
+    autotuned batch against one launch per domain, and the FP32 batch."""
+    import torch
+    doms = wl.batch_domains()
+    domains = [((e, e, e), t) for e, _, t in doms]
+    nodes = sum(e ** 3 for e, _, _ in doms)
+    init = [torch.tensor(hl.dense_to_blocks(wl.taylor_green_3d(e, u0).astype(np.float32)), device="cuda")
+            for e, u0, _ in doms]
+    out = {"domains": len(doms), "nodes": nodes, "steps": steps}
+    finals = {}
+    names = ["one_launch", "graph", "per_domain", "persistent", "persistent_graph"]
+    for storage in ("f16s", "f32"):
+        with hl.Batch(domains, storage=storage, stream=stream.cuda_stream) as b:
+            for d in range(len(doms)):
+                b.write_moments(d, init[d])
+            mode, trial_ms = b.autotune(64)
+            ms = timed(stream, lambda: b.step(steps))
+            rec = {"mode": names[mode], "autotune_ms_per_step": dict(zip(names, [round(t, 4) for t in trial_ms])),
+                   "ms_per_step": round(ms / steps, 4), "mlups": round(nodes * steps / ms / 1e3, 1),
+                   "bytes_per_node": 40.0 if storage == "f16s" else 80.0}
+            rec["hbm_gbs"] = round(rec["bytes_per_node"] * nodes * steps / ms / 1e6, 1)
+            if storage == "f16s":
+                b.set_mode(hl.BATCH_PER_DOMAIN)
+                ms_pd = timed(stream, lambda: b.step(steps))
+                rec["per_domain_ms_per_step"] = round(ms_pd / steps, 4)
+                rec["per_domain_mlups"] = round(nodes * steps / ms_pd / 1e3, 1)
+                rec["speedup_vs_per_domain"] = round(ms_pd / ms, 3)
+                b.set_mode(mode)
+            # accuracy: the same `steps` steps from the initial state, first eight domains
+            for d in range(len(doms)):
+                b.write_moments(d, init[d])
+            b.step(steps)
+            finals[storage] = [b.read_moments(d, torch.empty((b.num_blocks(d), 10, 512), dtype=torch.float32,
+                                                             device="cuda"))[:, 1:4].clone() for d in range(8)]
+            out[storage] = rec
+    out["f16s_vs_f32_max_du_over_U0"] = max(float((finals["f16s"][d] - finals["f32"][d]).abs().max() / doms[d][1])
+                                            for d in range(8))
+    return out
+
+
+def bench_adjoint(hl, wl, stream, n=128, steps=200, ckpt=20):
+    """Forward vs checkpointed adjoint on the 128^3 channel with the central 16^3 obstacle."""
+    import torch
+    shape = (n, n, n)
+    solid = wl.obstacle_mask(n).astype(np.uint8)
+    F = torch.tensor(hl.dense_to_blocks(wl.noisy_force(shape).astype(np.float32)), device="cuda")
+    M0 = torch.tensor(hl.dense_to_blocks(wl.rest_field(shape).astype(np.float32)), device="cuda")
+    with hl.Lattice(shape, tau=0.55, periodic=(True, False, False), storage="f32", stream=stream.cuda_stream) as lat:
+        lat.set_dense()
+        lat.set_solid(solid)
+        lat.set_force(F)
+        lat.write_moments(M0)
+        lat.step(20)
+        lat.write_moments(M0)
+        t_fwd = timed(stream, lambda: lat.step(steps))
+        lat.write_moments(M0)
+        t_rec = timed(stream, lambda: lat.forward_record(steps, ckpt))
+        lam = torch.zeros((lat.num_blocks(0), 10, 512), dtype=torch.float32, device="cuda")
+        lam[:, 1:4] = 1e-3
+        dF = torch.empty((lat.num_blocks(0), 3, 512), dtype=torch.float32, device="cuda")
+        t_adj = timed(stream, lambda: lat.adjoint(lam, dF))
+    return {"n": n, "steps": steps, "ckpt_every": ckpt, "forward_ms": round(t_fwd, 3),
+            "forward_record_ms": round(t_rec, 3), "adjoint_ms": round(t_adj, 3),
+            "adjoint_over_forward": round(t_adj / t_fwd, 3),
+            "record_plus_adjoint_over_forward": round((t_rec + t_adj) / t_fwd, 3),
+            "finite": bool(torch.isfinite(dF).all().item())}
+
+
+def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebuild_every=10):
+    """Three-level lattice over an n^3 fine-equivalent domain driven by a falling
+    particle cloud (pos0, device, not modified): rebuild at the first
+    coarse-step boundary at least rebuild_every fine steps after the last one,
+    deposit of eta / eps / drag every coarse step.  Fine-equivalent MLUPS over
+    the whole loop."""
+    import torch
+    L = 3
+    per = 2 ** (L - 1)
+    pos = pos0.clone()
+    with hl.Lattice((n, n, n), levels=L, tau=0.9, periodic=(True, False, True), storage=storage,
+                    stream=stream.cuda_stream) as lat:
+        lat.rebuild_from_particles(pos)
+        lat.deposit_particles(pos)
+        torch.cuda.synchronize()
+        t_reb = t_dep = 0.0
+        updates = 0
+        since = 0
+        rebuilds = 0
+        counts = [lat.num_blocks(l) for l in range(L)]
+        t0 = time.perf_counter()
+        for k in range(fine_steps // per):
+            lat.step(per)
+            updates += sum(counts[l] * 512 * 2 ** (L - 1 - l) for l in range(L))
+            since += per
+            with torch.cuda.stream(stream):
+                pos[:, 1] = torch.clamp(pos[:, 1] - per, min=0.5)
+            moving = bool(k < fine_steps // per - 1)
+            if since >= rebuild_every:
+                lat.synchronize()
+                t1 = time.perf_counter()
+                lat.rebuild_from_particles(pos)
+                lat.synchronize()
+                t_reb += time.perf_counter() - t1
+                counts = [lat.num_blocks(l) for l in range(L)]
+                since = 0
+                rebuilds += 1
+            lat.synchronize()
+            t1 = time.perf_counter()
+            lat.deposit_particles(pos, moving=moving)
+            t_dep += time.perf_counter() - t1
+        lat.synchronize()
+        t_tot = time.perf_counter() - t0
+        red = lat.reduce()
+        moms = [lat.read_moments(torch.empty((lat.num_blocks(l), 10, 512), dtype=torch.float32, device="cuda"),
+                                 level=l) for l in range(L)]
+    return {"storage": storage, "fine_steps": fine_steps, "rebuilds": rebuilds,
+            "mlups_fine_equiv": round(n ** 3 * fine_steps / t_tot / 1e6, 1),
+            "mlups_fine_equiv_without_deposit": round(n ** 3 * fine_steps / (t_tot - t_dep) / 1e6, 1),
+            "actual_mlups": round(updates / (t_tot - t_reb - t_dep) / 1e6, 1),
+            "total_s": round(t_tot, 3), "rebuild_s": round(t_reb, 3), "deposit_s": round(t_dep, 3),
+            "blocks_per_level_end": counts, "mass_rel_drift": float(red[0] / n ** 3 - 1.0),
+            "finite": bool(np.isfinite(red[0]))}, moms
+
+
+def bench_extras(hl, wl):
+    import torch
+    stream = torch.cuda.Stream()
+    out = {"c5_batched": bench_batched(hl, wl, stream), "c4_adjoint": bench_adjoint(hl, wl, stream)}
+    ml = {}
+    ref = None
+    pos0 = torch.tensor(wl.particle_cloud(512), device="cuda")
+    for storage in ("f32", "f16s", "bf16s"):
+        bench_multilevel(hl, wl, stream, storage, pos0, fine_steps=48)   # warm-up: loads every kernel once
+        rec, moms = bench_multilevel(hl, wl, stream, storage, pos0)
+        if storage == "f32":
+            ref = moms
+        else:
+            du = max(float((a[:, 1:4] - b[:, 1:4]).abs().max()) for a, b in zip(moms, ref))
+            umax = max(float(b[:, 1:4].abs().max()) for b in ref)
+            rec["max_du_vs_f32_over_umax"] = du / max(umax, 1e-30)
+        ml[storage] = rec
+    out["c3_multilevel"] = ml
+    return out
 
 
 def cpu_oracle_sample(n_sample=64, steps=12):
@@ -192,6 +355,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the multi-level, adjoint and batched workloads")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -250,6 +415,8 @@ def main():
         "gpu_launches": args.steps,
         "clocks": res["clocks"],
     }
+    if res["extras"] is not None:
+        line["extras"] = res["extras"]
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample(128, 16)
     print(json.dumps(line))

@@ -4,10 +4,10 @@
  *
  * The library advances the moment set M = {rho, u, S} of the paper's HOME-LBM
  * scheme (Sec. 3.1, Eq. rho_u_stress and Eq. three_order_f) on a block-sparse,
- * multi-level D3Q27 lattice (Sec. 4.1, Sec. 5.1), with the sub-cycled advance of
+ * multi-level D3Q27 lattice (Sec. 5.1, Sec. 6.1), with the sub-cycled advance of
  * Algorithm 1 and the fine<->coarse transfers of Eq. downward_rescale and
  * Eq. upload_S, and rebuilds the block hierarchy from a particle cloud through
- * the level-selection function Phi (Sec. 4.3, Sec. 5.3).
+ * the level-selection function Phi (Sec. 5.4, Sec. 6.3).
  *
  * Conventions
  *  - Every call returns an hlbm_status (int32).  Nothing aborts and no C++
@@ -68,7 +68,7 @@ typedef struct {
   int32_t nx, ny, nz;      /* fine-equivalent extent; multiples of 8*2^(L-1) */
   int32_t block_edge;      /* must be 8 */
   int32_t num_levels;      /* L >= 1 */
-  double tau_finest;       /* tau_0 > 1/2; tau_{l+1} = tau_l/2 + 1/4 (Sec. 4.2) */
+  double tau_finest;       /* tau_0 > 1/2; tau_{l+1} = tau_l/2 + 1/4 (Sec. 5.2) */
   int32_t periodic[3];     /* per axis x, y, z; non-periodic faces are half-way bounce-back walls */
   int32_t storage;         /* hlbm_storage */
   int32_t rescale_mode;    /* hlbm_rescale */
@@ -99,14 +99,14 @@ const char *hlbm_last_error(const hlbm_lattice *h);
 int32_t hlbm_set_dense(hlbm_lattice *h);
 
 /* Declare the level-0 blocks that must be resolved at the finest level (the
-   blocks where the level-selection function Phi of Sec. 4.3 is 0) and build
+   blocks where the level-selection function Phi of Sec. 5.4 is 0) and build
    the whole hierarchy from them on the device (same pipeline as
    hlbm_rebuild_from_particles).  coords_xyz: host int32 [n][3] block
    coordinates (bx, by, bz) of level 0.  On the first call every stored node is
    at rest; later calls carry the moments over like a rebuild. */
 int32_t hlbm_set_fine_blocks(hlbm_lattice *h, const int32_t *coords_xyz, int64_t n);
 
-/* Rebuild the block hierarchy from a particle cloud (Sec. 5.3): occupancy of
+/* Rebuild the block hierarchy from a particle cloud (Sec. 6.3): occupancy of
    level-0 blocks (Phi), the has-children sets H_l (one-block dilation of the
    parents of the finer set), internal blocks (not stored), stored / border /
    leaf sets, flags against the previous hierarchy, stable compaction of the
@@ -135,10 +135,23 @@ int32_t hlbm_num_blocks(const hlbm_lattice *h, int32_t level, int64_t *n);
 
 /* Copy the stored block coordinates (bx, by, bz) of a level into out[cap][3]
    (host memory), ascending slot order, and optionally one flag byte per block
-   (bit 0 leaf, bit 1 border, bit 2 new, bit 3 refine, bit 4 coarsen; Sec. 5.1,
-   Sec. 5.3).  If cap < n, returns HLBM_E_INVALID_ARG with *n set. */
+   (bit 0 leaf, bit 1 border, bit 2 new, bit 3 refine, bit 4 coarsen; Sec. 6.1,
+   Sec. 6.3).  If cap < n, returns HLBM_E_INVALID_ARG with *n set. */
 int32_t hlbm_get_blocks(const hlbm_lattice *h, int32_t level, int32_t *out, int64_t cap,
                         int64_t *n, uint8_t *flags_out);
+
+/* Coupling fields of the finest level from a particle cloud (Sec. 4: the
+   solid fraction eta enters through eps = 1 - eta and the force F).  Per
+   finest-level node: count(x) = particles whose floor(position) is x (clamped
+   to the domain), eta = min(eta_max, per_particle * count), eps = 1 - eta and
+   F = (0, -kappa * eta, 0) if moving, else 0; FP64 arithmetic rounded once to
+   float32.  Replaces the level-0 force and eps fields (like hlbm_set_force).
+   pos_xyz: float32 [n][3] in fine-node units, host (on_device = 0) or device
+   (1, borrowed for the call).  *outside (host, may be NULL) receives the
+   number of particles that fall in no stored finest-level block or are not
+   finite; they are dropped.  Synchronous. */
+int32_t hlbm_deposit_particles(hlbm_lattice *h, const float *pos_xyz, int64_t n, int32_t on_device, double kappa,
+                               double eta_max, double per_particle, int32_t moving, int64_t *outside);
 
 /* Uniform body force F (lattice units) at level 0 (Sec. 4, force F). */
 int32_t hlbm_set_uniform_force(hlbm_lattice *h, double fx, double fy, double fz);
@@ -215,6 +228,53 @@ int32_t hlbm_adjoint(hlbm_lattice *h, const float *dL_dM_dev, float *dL_dF_dev);
  *           and must be serialised (one stream, or events). */
 int32_t hlbm_reduce_f32_noalloc(const float *mom_dev, int64_t n_blocks, const float *F_dev, double fx, double fy,
                                 double fz, double *out_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent domains.  The paper runs one lattice at a time; a
+ * batch advances many small single-level periodic domains (8^3 blocks, FP32,
+ * FP16S or BF16S storage, each its own extent and tau) with one kernel launch
+ * per step over the concatenated block list, so that small domains fill the
+ * GPU together.  Each domain keeps its own reduced-precision row scales.
+ * ------------------------------------------------------------------------- */
+typedef struct hlbm_batch hlbm_batch;
+
+typedef enum {
+  HLBM_BATCH_ONE_LAUNCH = 0, /* one launch per step over every domain */
+  HLBM_BATCH_GRAPH = 1,      /* the same, 32 steps at a time replayed from a CUDA graph (default) */
+  HLBM_BATCH_PER_DOMAIN = 2, /* one launch per domain per step (for comparison) */
+  HLBM_BATCH_PERSISTENT = 3, /* one launch per step of resident CTAs taking blocks from an atomic counter */
+  HLBM_BATCH_PERSISTENT_GRAPH = 4 /* the same, 32 steps at a time from a CUDA graph */
+} hlbm_batch_mode;
+
+/* Create a batch of n domains from cfgs[n]: every domain single-level, fully
+   periodic, block_edge 8, extents multiples of 8; storage, device and stream
+   equal across domains (a NULL stream makes the batch create its own, since
+   CUDA graphs cannot capture the legacy stream).  Moments start at rest.
+   *out is NULL on failure (message in hlbm_batch_last_error(NULL)). */
+int32_t hlbm_batch_create(const hlbm_config *cfgs, int32_t n, hlbm_batch **out);
+/* Free the batch.  NULL is accepted. */
+int32_t hlbm_batch_destroy(hlbm_batch *b);
+/* Message of the last failed call on b (NULL: of the last failed create). */
+const char *hlbm_batch_last_error(const hlbm_batch *b);
+/* Blocks of one domain (domain = -1: of the whole batch).  A domain's blocks
+   are in x-fastest block order, like hlbm_get_blocks of a dense lattice. */
+int32_t hlbm_batch_num_blocks(const hlbm_batch *b, int32_t domain, int64_t *n);
+/* Write / read one domain's moments in the public layout [n][10][512]
+   (dtype 0 = float64, 1 = float32; host or device pointer).  Synchronous.
+   Writing refits that domain's row scales (reduced-precision storage). */
+int32_t hlbm_batch_write_moments(hlbm_batch *b, int32_t domain, const void *buf, int32_t dtype, int32_t on_device);
+int32_t hlbm_batch_read_moments(hlbm_batch *b, int32_t domain, void *buf, int32_t dtype, int32_t on_device);
+/* Advance every domain n_steps steps (Sec. 3.1 with zero force), asynchronous
+   on the batch's stream; reduced-precision scales are refit every 32 steps.
+   Results do not depend on the mode. */
+int32_t hlbm_batch_step(hlbm_batch *b, int32_t n_steps);
+int32_t hlbm_batch_synchronize(hlbm_batch *b);
+/* Choose the launch strategy (hlbm_batch_mode). */
+int32_t hlbm_batch_set_mode(hlbm_batch *b, int32_t mode);
+/* Time each mode over trial_steps steps (at least 64; the state is restored
+   afterwards), keep the fastest and return it in *mode_out; ms_out (host, may
+   be NULL) receives the five per-step times in mode order.  Synchronous. */
+int32_t hlbm_batch_autotune(hlbm_batch *b, int32_t trial_steps, int32_t *mode_out, float ms_out[5]);
 
 #ifdef __cplusplus
 }

@@ -13,10 +13,10 @@ Modules (each function cites the passage of the paper it follows):
                    projection (Eq. rho_u_stress).
 * ``single_level`` one pull-stream + moment-space collision step on a dense grid
                    (Sec. 3.1 "Collision and Streaming", Sec. 4 mixture tau).
-* ``hierarchy``    the declarative block hierarchy (Sec. 4.1, Sec. 5.1, Sec. 5.3,
+* ``hierarchy``    the declarative block hierarchy (Sec. 5.1, Sec. 6.1, Sec. 6.3,
                    Eq. level-selection Phi).
 * ``multilevel``   Algorithm 1 with downward/upward transfers and the S^neq
-                   rescaling (Sec. 4.2, Eq. upload_S, Eq. downward_rescale).
+                   rescaling (Sec. 5.2, Eq. upload_S, Eq. downward_rescale).
 * ``codec``        reduced-precision moment storage (no counterpart in the paper).
 * ``adjoint``      reverse-mode gradient of the single-level step (no
                    counterpart in the paper).

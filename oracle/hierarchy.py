@@ -1,22 +1,22 @@
-"""Declarative multi-level block hierarchy (Sec. 4.1, Sec. 5.1, Sec. 5.3).
+"""Declarative multi-level block hierarchy (Sec. 5.1, Sec. 6.1, Sec. 6.3).
 
 Test infrastructure (see ``oracle/__init__.py``).  Plain numpy on dense
 boolean block grids, one per level, indexed [bz, by, bx].  Level l has block
 edge B cells of spacing 2^l (fine units); level 0 is the finest.
 
 Reading of the paper used here (listed in the design doc):
-* the level-selection function Phi (Sec. 4.3) is 0 on a level-0 block holding a
+* the level-selection function Phi (Sec. 5.4) is 0 on a level-0 block holding a
   particle and L-1 elsewhere, so the occupied set O_0 drives everything;
 * H_l = level-l blocks that have stored children: H_1 = dilate(parent(O_0)),
   H_l = dilate(parent(H_{l-1})), dilation by one block in the 26-neighbourhood
   (clipped at walls, wrapped on periodic axes) -- the overlap/separation of
-  Sec. 4.2 and Sec. 5.1 with whole 8^3 blocks;
+  Sec. 5.3 and Sec. 6.1 with whole 8^3 blocks;
 * internal blocks I_l = {b in H_l : every in-domain 26-neighbour is in H_l} are
-  not stored (Sec. 5.1: only leaf and border tiles are stored);
+  not stored (Sec. 6.1: only leaf and border tiles are stored);
 * stored_l = children(H_{l+1}) minus I_l for l < L-1, all blocks minus I_{L-1}
   at the top level; a stored block is ``border`` if it overlaps the finer
   level (in H_l) or the coarser one (its parent is stored), else ``leaf``;
-* the flags of Sec. 5.3 are set differences against the previous hierarchy:
+* the flags of Sec. 6.3 are set differences against the previous hierarchy:
   refine = newly in H_l, coarsen = newly out of H_l, delete = no longer stored.
 """
 import numpy as np
@@ -89,7 +89,7 @@ def internal(H, periodic):
 
 
 def occupancy(pos, extent_xyz, B):
-    """O_0: level-0 blocks holding at least one particle (Phi = 0 there, Sec. 4.3).
+    """O_0: level-0 blocks holding at least one particle (Phi = 0 there, Sec. 5.4).
 
     ``pos`` is (n, 3) float32 in fine-cell units (x, y, z); the block of a
     particle is floor(p / B), clamped into the domain.

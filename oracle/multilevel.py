@@ -2,14 +2,14 @@
 
 Test infrastructure (see ``oracle/__init__.py``).  Every level is held as a
 dense FP64 array at that level's node resolution (nodes of level l sit at fine
-positions 2^l * index: vertex-aligned levels, Sec. 4.1 "one block shift" and
-Sec. 4.3 "corresponding node"); nodes that are not stored hold NaN so that any
+positions 2^l * index: vertex-aligned levels, Sec. 5.1 "one block shift" and
+Sec. 5.3 "corresponding node"); nodes that are not stored hold NaN so that any
 read of them poisons the result.  Each level has two buffers and reads the one
 selected by its own step parity, which is the two-tree recursive ping-pong of
-Sec. 5.2 written per level.
+Sec. 6.2 written per level.
 
 Passages followed:
-* tau_{l+1} = tau_l / 2 + 1/4 (Sec. 4.2, the nu/tau rescaling with k = 1);
+* tau_{l+1} = tau_l / 2 + 1/4 (Sec. 5.2, the nu/tau rescaling with k = 1);
 * Algorithm 1 AdvanceLBM(l, s): DownwardTransfer(l+1, s) before the level-l
   step, UpwardTransfer(l) after it when s = 2, then two sub-steps of level l-1;
 * DownwardTransfer: rho and u interpolated over the 2^D nearest coarse nodes,
@@ -30,7 +30,7 @@ from . import single_level as sl
 
 
 def level_taus(tau0, L):
-    """tau_{l+1} = tau_l/2 + 1/4 (Sec. 4.2 with k = 1)."""
+    """tau_{l+1} = tau_l/2 + 1/4 (Sec. 5.2 with k = 1)."""
     t = [float(tau0)]
     for _ in range(1, L):
         t.append(t[-1] / 2.0 + 0.25)
@@ -265,7 +265,7 @@ class MultiLevel:
         return fill
 
     def rebuild(self, new_hier):
-        """Switch to ``new_hier`` at a coarse-step boundary (Sec. 5.3): surviving
+        """Switch to ``new_hier`` at a coarse-step boundary (Sec. 6.3): surviving
         nodes keep their moments, new fine nodes are interpolated from their
         parents (Eq. downward_rescale, spatial part), new coarse nodes take the
         upward rule from their children (Eq. upload_S)."""

@@ -221,7 +221,7 @@ int32_t hlbm_create(const hlbm_config* cfg, hlbm_lattice** out) {
   double tau = cfg->tau_finest;
   for (int l = 0; l < cfg->num_levels; ++l) {
     h->lv[l].tau = tau;
-    tau = tau / 2.0 + 0.25;  // Sec. 4.2 with k = 1
+    tau = tau / 2.0 + 0.25;  // Sec. 5.2 with k = 1
   }
   for (int l = 0; l + 1 < cfg->num_levels; ++l) {
     const double tf = h->lv[l].tau, tc = h->lv[l + 1].tau;

@@ -1,4 +1,4 @@
-// hierarchy.cu -- block-hierarchy maintenance on the device (Sec. 4.3, Sec. 5.1, Sec. 5.3).
+// hierarchy.cu -- block-hierarchy maintenance on the device (Sec. 5.4, Sec. 6.1, Sec. 6.3).
 #include "hierarchy.cuh"
 #include "hlbm_internal.h"
 

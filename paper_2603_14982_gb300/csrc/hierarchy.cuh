@@ -1,4 +1,4 @@
-// hierarchy.cuh -- device-side block-hierarchy maintenance (Sec. 4.3, Sec. 5.1, Sec. 5.3).
+// hierarchy.cuh -- device-side block-hierarchy maintenance (Sec. 5.4, Sec. 6.1, Sec. 6.3).
 //
 // All sets live on dense per-level slot grids (uint8 per block slot, slot id
 // bz*(nby*nbx) + by*nbx + bx).  The rules are the declarative ones:

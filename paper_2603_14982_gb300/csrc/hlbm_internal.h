@@ -33,13 +33,21 @@ struct StepArgs {
   double tau;               // level relaxation time
   double om;                // 1 / tau
   double kxyz;              // third-order xyz weight (27 or 13.5)
-  int64_t nb;               // number of blocks
+  int64_t nb;               // number of blocks processed by the launch
+  int64_t blk0;             // first block index of the launch (0: all)
+  const float* blk_om;      // [nb_total] per-block 1/tau (batches of domains), or null (om)
+  const int32_t* blk_dom;   // [nb_total] per-block domain index into scales_in/out, or null
+  unsigned* work;           // non-null: persistent launch of `grid` CTAs over a ticket counter
+                            // (two zeroed unsigned in device memory, left zeroed); FP32/FP16/BF16 only
+  int grid;
 };
 
 // FP64 storage: one node per thread (stream_collide.cu).  Other storages: the
 // packed-FP32 node-pair kernel (stream_collide_f2.cu).
 cudaError_t launch_stream_collide(int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_stream_collide_f2(int storage, const StepArgs& a, cudaStream_t s);
+// Resident CTAs per SM of the persistent node-pair kernel.
+cudaError_t persistent_ctas_per_sm(int storage, int* per_sm);
 // One reverse step of the single-level stream-collide (adjoint.cu): lam = dL/dM
 // of the step's output, lam_out = dL/dM of its input (a.in), dF += dL/dF.
 // lamp is scratch [nb][10][512]; all lambda arrays are natural node order.

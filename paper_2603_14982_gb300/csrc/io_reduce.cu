@@ -380,11 +380,14 @@ __global__ void __launch_bounds__(512) k_amax_public(const In* __restrict__ src,
   block_amax(v, amax);
 }
 
+// dom (per-block domain index, or null) selects the scales and the amax row set.
 template <typename T>
-__global__ void __launch_bounds__(512) k_amax_storage(const T* __restrict__ src, const Scales* sc, unsigned* amax) {
+__global__ void __launch_bounds__(512) k_amax_storage(const T* __restrict__ src, const Scales* sc, unsigned* amax,
+                                                      const int32_t* __restrict__ dom) {
+  const int d = dom != nullptr ? dom[blockIdx.x] : 0;
   float v[kRows];
-  row_values(load_node<T>(src, blockIdx.x, threadIdx.x, sc), v);
-  block_amax(v, amax);
+  row_values(load_node<T>(src, blockIdx.x, threadIdx.x, sc + d), v);
+  block_amax(v, amax + d * kRows);
 }
 
 // scale 2^e with amax * 2^e < 2^13 (three binades below the FP16 maximum).
@@ -392,10 +395,13 @@ __global__ void __launch_bounds__(512) k_amax_storage(const T* __restrict__ src,
 // S^neq of an equilibrium initial state, still represents values up to
 // 65504 * 2^-20 = 0.0625 lattice units, while keeping normal FP16 precision
 // down to 6e-11.
-__global__ void k_set_scales(const unsigned* amax, Scales* sc) {
-  const int r = threadIdx.x;
-  if (r >= kRows) return;
-  const float a = __uint_as_float(amax[r]);
+// One thread per (domain, row): n_dom * kRows threads.
+__global__ void k_set_scales(const unsigned* amax, Scales* sc_all, int n_dom) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_dom * kRows) return;
+  const int r = i % kRows;
+  Scales* sc = sc_all + i / kRows;
+  const float a = __uint_as_float(amax[i]);
   int e = 20;
   if (a > 0.f) {
     int k;
@@ -408,20 +414,23 @@ __global__ void k_set_scales(const unsigned* amax, Scales* sc) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_reencode(T* buf, const Scales* from, const Scales* to) {
-  const Mom<float> m = load_node<T>(buf, blockIdx.x, threadIdx.x, from);
-  store_node<T>(buf, blockIdx.x, threadIdx.x, m, to);
+__global__ void __launch_bounds__(512) k_reencode(T* buf, const Scales* from, const Scales* to,
+                                                  const int32_t* __restrict__ dom) {
+  const int d = dom != nullptr ? dom[blockIdx.x] : 0;
+  const Mom<float> m = load_node<T>(buf, blockIdx.x, threadIdx.x, from + d);
+  store_node<T>(buf, blockIdx.x, threadIdx.x, m, to + d);
 }
 
 template <typename T>
-cudaError_t rescale_typed(void* buf, int64_t nb, Scales* cur, Scales* tmp, unsigned* amax, cudaStream_t s) {
+cudaError_t rescale_typed(void* buf, int64_t nb, const int32_t* dom, int n_dom, Scales* cur, Scales* tmp,
+                          unsigned* amax, cudaStream_t s) {
   if (nb == 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(amax, 0, kRows * sizeof(unsigned), s);
+  cudaError_t e = cudaMemsetAsync(amax, 0, size_t(n_dom) * kRows * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  k_amax_storage<T><<<unsigned(nb), 512, 0, s>>>(static_cast<const T*>(buf), cur, amax);
-  k_set_scales<<<1, 32, 0, s>>>(amax, tmp);
-  k_reencode<T><<<unsigned(nb), 512, 0, s>>>(static_cast<T*>(buf), cur, tmp);
-  e = cudaMemcpyAsync(cur, tmp, sizeof(Scales), cudaMemcpyDeviceToDevice, s);
+  k_amax_storage<T><<<unsigned(nb), 512, 0, s>>>(static_cast<const T*>(buf), cur, amax, dom);
+  k_set_scales<<<unsigned((n_dom * kRows + 255) / 256), 256, 0, s>>>(amax, tmp, n_dom);
+  k_reencode<T><<<unsigned(nb), 512, 0, s>>>(static_cast<T*>(buf), cur, tmp, dom);
+  e = cudaMemcpyAsync(cur, tmp, size_t(n_dom) * sizeof(Scales), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -437,15 +446,20 @@ cudaError_t scales_from_public(const void* src, int dtype, int64_t nb, Scales* s
     else
       k_amax_public<float><<<unsigned(nb), 512, 0, s>>>(static_cast<const float*>(src), amax);
   }
-  k_set_scales<<<1, 32, 0, s>>>(amax, sc);
+  k_set_scales<<<1, 32, 0, s>>>(amax, sc, 1);
   return cudaGetLastError();
 }
 
 cudaError_t rescale_storage(int storage, void* buf, int64_t nb, Scales* cur, Scales* tmp, unsigned* amax,
                             cudaStream_t s) {
+  return rescale_storage_domains(storage, buf, nb, nullptr, 1, cur, tmp, amax, s);
+}
+
+cudaError_t rescale_storage_domains(int storage, void* buf, int64_t nb, const int32_t* dom, int n_dom, Scales* cur,
+                                    Scales* tmp, unsigned* amax, cudaStream_t s) {
   switch (storage) {
-    case HLBM_STORE_F16S: return rescale_typed<__half>(buf, nb, cur, tmp, amax, s);
-    case HLBM_STORE_BF16S: return rescale_typed<__nv_bfloat16>(buf, nb, cur, tmp, amax, s);
+    case HLBM_STORE_F16S: return rescale_typed<__half>(buf, nb, dom, n_dom, cur, tmp, amax, s);
+    case HLBM_STORE_BF16S: return rescale_typed<__nv_bfloat16>(buf, nb, dom, n_dom, cur, tmp, amax, s);
     default: return cudaSuccess;
   }
 }

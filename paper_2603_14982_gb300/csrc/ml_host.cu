@@ -1,5 +1,5 @@
 // ml_host.cu -- host orchestration of the multi-level engine: the rebuild
-// pipeline of Sec. 5.3 (occupancy -> Phi -> sets -> compaction -> tables ->
+// pipeline of Sec. 6.3 (occupancy -> Phi -> sets -> compaction -> tables ->
 // interface lists -> moments of the new blocks) and the sub-cycled advance of
 // Algorithm 1 with its downward and upward transfers.
 #include <cuda_runtime.h>

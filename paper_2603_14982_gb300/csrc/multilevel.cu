@@ -1,5 +1,5 @@
 // multilevel.cu -- downward/upward transfers of Algorithm 1 and the moment
-// initialisation of blocks created by a rebuild (Sec. 4.2, Sec. 5.3).
+// initialisation of blocks created by a rebuild (Sec. 5.2, Sec. 6.3).
 //
 // All transfer arithmetic is FP64: moments are read from storage, split into
 // (rho, u, S^neq = S - u u), combined with exact power-of-two weights, rescaled

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(512, 1) k_stream_collide(StepArgs a) {
   __shared__ unsigned s_wall, s_miss;
   __shared__ uint8_t s_solid[kExtCells];
 
-  const int64_t blk = blockIdx.x;
+  const int64_t blk = a.blk0 + blockIdx.x;
   const int t = threadIdx.x;
   const T* in = static_cast<const T*>(a.in);
   T* out = static_cast<T*>(a.out);

@@ -226,21 +226,22 @@ __device__ __forceinline__ Mom<V2> zero_pair() {
   return m;
 }
 
+// One 8^3 block: push the own and halo populations into the destination-
+// indexed shared buffer, then gather, project and collide.  Leaves shared
+// memory in use: callers that process another block must barrier first.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
-  extern __shared__ __align__(16) float2 f2buf[];  // [26][256] node pairs + trash
+__device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, float2* f2buf, int* s_nbr,
+                                         unsigned& s_miss) {
   float* fbuf = reinterpret_cast<float*>(f2buf);
-  __shared__ int s_nbr[27];
-  __shared__ unsigned s_miss;
-
-  const int64_t blk = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int x = lane & 7, y = (lane >> 3) + ((w & 1) << 2), z0 = w >> 1;
   const int own = x + 8 * y + 64 * z0;                 // pair slot in global storage
   const int own_s = (x ^ (y >> 1)) + 8 * y + 64 * z0;  // pair slot in shared memory
   const T* in = static_cast<const T*>(a.in);
   T* out = static_cast<T*>(a.out);
-  const Scales* sc_in = a.scales_in;
+  const int dom = a.blk_dom != nullptr ? a.blk_dom[blk] : 0;
+  const Scales* sc_in = a.scales_in != nullptr ? a.scales_in + dom : nullptr;
+  const Scales* sc_out = a.scales_out != nullptr ? a.scales_out + dom : nullptr;
 
   if (t < 32) {
     const int v = t < 27 ? a.nbr[blk * 27 + t] : 0;
@@ -370,13 +371,53 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
       fy = V2(float(a.fu[1]));
       fz = V2(float(a.fu[2]));
     }
-    V2 om = V2(float(a.om));
+    V2 om = V2(a.blk_om != nullptr ? __ldg(a.blk_om + blk) : float(a.om));
     if (a.eps != nullptr)
       om = inv(V2(float(a.tau)) * V2(__ldg(a.eps + blk * kCells + own), __ldg(a.eps + blk * kCells + own + 256)));
     mo = collide(p, fx, fy, fz, om);
     if (copy_lo || copy_hi) mo = select_halves(mo, load_pair<T>(in, blk, own, sc_in), copy_lo, copy_hi);
   }
-  store_pair<T>(out, blk, own, mo, a.scales_out);
+  store_pair<T>(out, blk, own, mo, sc_out);
+}
+
+// One CTA per block.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
+  extern __shared__ __align__(16) float2 f2buf[];  // [26][256] node pairs + trash
+  __shared__ int s_nbr[27];
+  __shared__ unsigned s_miss;
+  sc_block<T>(a, a.blk0 + blockIdx.x, f2buf, s_nbr, s_miss);
+}
+
+// Persistent CTAs (a grid sized to the resident capacity) that take blocks
+// from an atomic ticket counter in list order.  work[0] is the ticket counter,
+// work[1] counts finished CTAs; the last CTA to finish puts both back to zero
+// for the next launch on the stream.  No CTA waits on another.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2_persistent(StepArgs a) {
+  extern __shared__ __align__(16) float2 f2buf[];
+  __shared__ int s_nbr[27];
+  __shared__ unsigned s_miss;
+  __shared__ unsigned s_tk;
+  unsigned* work = a.work;
+  if (threadIdx.x == 0) s_tk = atomicAdd(work, 1u);
+  __syncthreads();
+  unsigned tk = s_tk;
+  while (tk < unsigned(a.nb)) {
+    sc_block<T>(a, a.blk0 + tk, f2buf, s_nbr, s_miss);
+    __syncthreads();  // shared buffers free again
+    if (threadIdx.x == 0) s_tk = atomicAdd(work, 1u);
+    __syncthreads();
+    tk = s_tk;
+  }
+  if (threadIdx.x == 0) {
+    // every CTA that reaches this point has taken its last ticket
+    __threadfence();
+    if (atomicAdd(work + 1, 1u) == gridDim.x - 1) {
+      work[0] = 0u;
+      work[1] = 0u;
+    }
+  }
 }
 
 // Per-node bounce masks: bit k set when the pull source x - c_k of node x is
@@ -411,12 +452,29 @@ cudaError_t launch_f2(const StepArgs& a, cudaStream_t s) {
   if (!configured) {
     cudaError_t err =
         cudaFuncSetAttribute(k_stream_collide_f2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k_stream_collide_f2_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
     if (err != cudaSuccess) return err;
     configured = true;
   }
   if (a.nb == 0) return cudaSuccess;
-  k_stream_collide_f2<T><<<(unsigned)a.nb, kThreads, smem, s>>>(a);
+  if (a.work != nullptr) {
+    if (a.grid <= 0 || a.nb >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
+    k_stream_collide_f2_persistent<T><<<unsigned(a.grid), kThreads, smem, s>>>(a);
+  } else {
+    k_stream_collide_f2<T><<<(unsigned)a.nb, kThreads, smem, s>>>(a);
+  }
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t resident_f2(int* per_sm) {
+  const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
+  cudaError_t err =
+      cudaFuncSetAttribute(k_stream_collide_f2_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_stream_collide_f2_persistent<T>, kThreads, smem);
 }
 
 }  // namespace
@@ -426,6 +484,15 @@ cudaError_t launch_stream_collide_f2(int storage, const StepArgs& a, cudaStream_
     case HLBM_STORE_F32: return launch_f2<float>(a, s);
     case HLBM_STORE_F16S: return launch_f2<__half>(a, s);
     case HLBM_STORE_BF16S: return launch_f2<__nv_bfloat16>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t persistent_ctas_per_sm(int storage, int* per_sm) {
+  switch (storage) {
+    case HLBM_STORE_F32: return resident_f2<float>(per_sm);
+    case HLBM_STORE_F16S: return resident_f2<__half>(per_sm);
+    case HLBM_STORE_BF16S: return resident_f2<__nv_bfloat16>(per_sm);
     default: return cudaErrorInvalidValue;
   }
 }

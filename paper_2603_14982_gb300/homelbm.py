@@ -69,7 +69,24 @@ _SIGS = {
     "hlbm_adjoint": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "hlbm_reduce_f32_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
+    "hlbm_deposit_particles": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_int64)]),
+    "hlbm_batch_create": (ctypes.c_int32, [ctypes.POINTER(Config), ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "hlbm_batch_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "hlbm_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "hlbm_batch_num_blocks": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
+    "hlbm_batch_write_moments": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                                  ctypes.c_int32]),
+    "hlbm_batch_read_moments": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                                 ctypes.c_int32]),
+    "hlbm_batch_step": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "hlbm_batch_synchronize": (ctypes.c_int32, [ctypes.c_void_p]),
+    "hlbm_batch_set_mode": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "hlbm_batch_autotune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_float)]),
 }
+BATCH_ONE_LAUNCH, BATCH_GRAPH, BATCH_PER_DOMAIN, BATCH_PERSISTENT, BATCH_PERSISTENT_GRAPH = range(5)
 
 
 def exported_symbols():
@@ -206,6 +223,17 @@ class Lattice:
         return out[:n], fl[:n]
 
     # ---- inputs
+    def deposit_particles(self, pos, kappa=1e-4, eta_max=0.4, per_particle=0.25, moving=True):
+        """Finest-level eta / eps / drag force from particle positions (float32 [n][3],
+        numpy or CUDA tensor); returns the number of particles dropped."""
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, dtype=np.float32)
+        p, dev = _ptr(pos)
+        out = ctypes.c_int64()
+        self._check(self.lib.hlbm_deposit_particles(self.h, p, int(pos.shape[0]), dev, float(kappa), float(eta_max),
+                                                    float(per_particle), 1 if moving else 0, ctypes.byref(out)))
+        return out.value
+
     def set_uniform_force(self, fx, fy, fz):
         self._check(self.lib.hlbm_set_uniform_force(self.h, float(fx), float(fy), float(fz)))
 
@@ -255,6 +283,87 @@ class Lattice:
         out = (ctypes.c_double * 7)()
         self._check(self.lib.hlbm_reduce(self.h, out))
         return np.array(out[:], dtype=np.float64)
+
+
+class Batch:
+    """A batch of independent single-level periodic domains (hlbm_batch*).
+
+    ``domains`` is a list of ((nx, ny, nz), tau) pairs."""
+
+    def __init__(self, domains, storage="f16s", xyz_literal=False, stream=None, device=0):
+        self.lib = load()
+        n = len(domains)
+        cfgs = (Config * n)()
+        for c, (extent, tau) in zip(cfgs, domains):
+            c.nx, c.ny, c.nz = (int(v) for v in extent)
+            c.block_edge = 8
+            c.num_levels = 1
+            c.tau_finest = float(tau)
+            for a in range(3):
+                c.periodic[a] = 1
+            c.storage = STORAGE_NAMES[storage] if isinstance(storage, str) else int(storage)
+            c.rescale_mode = RESCALE_POST
+            c.xyz_literal = 1 if xyz_literal else 0
+            c.stream = ctypes.c_void_p(int(stream) if stream is not None else 0)
+            c.device = int(device)
+        self.domains = [(tuple(int(v) for v in e), float(t)) for e, t in domains]
+        h = ctypes.c_void_p()
+        rc = self.lib.hlbm_batch_create(cfgs, n, ctypes.byref(h))
+        if rc != OK:
+            raise HlbmError(rc, self.lib.hlbm_batch_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise HlbmError(rc, self.lib.hlbm_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hlbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def num_blocks(self, domain=-1):
+        n = ctypes.c_int64()
+        self._check(self.lib.hlbm_batch_num_blocks(self.h, int(domain), ctypes.byref(n)))
+        return n.value
+
+    def write_moments(self, domain, buf):
+        p, dev = _ptr(buf)
+        self._check(self.lib.hlbm_batch_write_moments(self.h, int(domain), p, _dtype_code(buf), dev))
+
+    def read_moments(self, domain, buf=None, dtype=np.float64):
+        if buf is None:
+            buf = np.empty((self.num_blocks(domain), 10, 512), dtype=dtype)
+        p, dev = _ptr(buf)
+        self._check(self.lib.hlbm_batch_read_moments(self.h, int(domain), p, _dtype_code(buf), dev))
+        return buf
+
+    def step(self, n_steps=1):
+        self._check(self.lib.hlbm_batch_step(self.h, int(n_steps)))
+
+    def synchronize(self):
+        self._check(self.lib.hlbm_batch_synchronize(self.h))
+
+    def set_mode(self, mode):
+        self._check(self.lib.hlbm_batch_set_mode(self.h, int(mode)))
+
+    def autotune(self, trial_steps=64):
+        mode = ctypes.c_int32()
+        ms = (ctypes.c_float * 5)()
+        self._check(self.lib.hlbm_batch_autotune(self.h, int(trial_steps), ctypes.byref(mode), ms))
+        return mode.value, [float(v) for v in ms]
 
 
 # ---- layout marshalling between dense [10][nz][ny][nx] grids and block-major [n][10][512]

@@ -9,7 +9,7 @@ are indexed [z, y, x]; a moment field is (10, nz, ny, nx) with rows
 The workload shapes follow the paper's use: a Taylor-Green vortex and a
 force-driven duct for the single-level path, a falling particle cloud that
 drives refinement (the paper's MPM particles enter only through the level
-selection Phi and the force/solid-fraction fields, Sec. 4.3), an obstacle
+selection Phi and the force/solid-fraction fields, Sec. 5.4), an obstacle
 channel for the gradient, and a batch of uneven periodic domains.
 """
 import numpy as np

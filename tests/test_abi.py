@@ -73,3 +73,31 @@ def test_layout_marshalling_roundtrip():
     # node (x, y, z) = (3, 9, 12) is block (0, 1, 1), cell 3 + 8*1 + 64*4
     assert Mb[0 + 1 * 1 + 1 * 3, 4, 3 + 8 + 256] == M[4, 12, 9, 3]
     assert np.array_equal(hl.blocks_to_dense(Mb, (16, 24, 8)), M)
+
+
+@pytest.mark.parametrize("domains,storage", [
+    ([], "f16s"),                                  # no domain
+    ([((16, 16, 16), 0.6), ((20, 16, 16), 0.6)], "f16s"),   # not a multiple of 8
+    ([((16, 16, 16), 0.5)], "f32"),                # tau must exceed 1/2
+])
+def test_batch_create_rejects_bad_domains(lib, domains, storage):
+    with pytest.raises(hl.HlbmError) as ei:
+        hl.Batch(domains, storage=storage)
+    assert ei.value.code == hl.E_INVALID_ARG
+
+
+def test_batch_rejects_fp64_and_non_periodic_domains(lib):
+    with pytest.raises(hl.HlbmError) as ei:
+        hl.Batch([((16, 16, 16), 0.6)], storage="f64")
+    assert ei.value.code == hl.E_UNSUPPORTED
+    cfg = (hl.Config * 1)()
+    cfg[0].nx = cfg[0].ny = cfg[0].nz = 16
+    cfg[0].block_edge, cfg[0].num_levels, cfg[0].tau_finest = 8, 1, 0.6
+    cfg[0].periodic[0], cfg[0].periodic[1], cfg[0].periodic[2] = 1, 0, 1
+    cfg[0].storage = hl.STORE_F32
+    h = ctypes.c_void_p()
+    assert lib.hlbm_batch_create(cfg, 1, ctypes.byref(h)) == hl.E_INVALID_ARG
+    assert not h.value
+    assert b"periodic" in lib.hlbm_batch_last_error(None)
+    assert lib.hlbm_batch_destroy(None) == hl.OK
+    assert lib.hlbm_batch_step(None, 1) == hl.E_INVALID_ARG

@@ -188,7 +188,7 @@ def test_rescale_factors_inverse_and_level_taus():
         assert abs(ku * kd - 1) < 1e-15
     ku, kd = ml.rescale_factors(0.9, 0.7, "post")
     assert abs(ku - 2 * (0.7 - 1) / (0.9 - 1)) < 1e-15
-    # nu_{l+1} = nu_l / 2 in the level's own lattice units (Sec. 4.2)
+    # nu_{l+1} = nu_l / 2 in the level's own lattice units (Sec. 5.2)
     for l in range(2):
         assert abs((t[l + 1] - 0.5) / 3 - 0.5 * (t[l] - 0.5) / 3) < 1e-15
 
