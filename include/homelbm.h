@@ -74,7 +74,10 @@ typedef struct {
   int32_t rescale_mode;    /* hlbm_rescale */
   int32_t xyz_literal;     /* 0: third-order xyz weight 1/c_s^6 (Hermite series);
                               1: 1/(2 c_s^6) as printed after Eq. three_order_f */
-  void *stream;            /* cudaStream_t, borrowed */
+  void *stream;            /* cudaStream_t, borrowed: every kernel, copy and device
+                              allocation of the handle is ordered on it (device
+                              buffers come from the stream-ordered pool), so it
+                              must stay valid until hlbm_destroy returns */
   int32_t device;          /* CUDA device ordinal */
 } hlbm_config;
 
@@ -147,9 +150,10 @@ int32_t hlbm_get_blocks(const hlbm_lattice *h, int32_t level, int32_t *out, int6
    F = (0, -kappa * eta, 0) if moving, else 0; FP64 arithmetic rounded once to
    float32.  Replaces the level-0 force and eps fields (like hlbm_set_force).
    pos_xyz: float32 [n][3] in fine-node units, host (on_device = 0) or device
-   (1, borrowed for the call).  *outside (host, may be NULL) receives the
-   number of particles that fall in no stored finest-level block or are not
-   finite; they are dropped.  Synchronous. */
+   (1, borrowed until the call's work on the stream has run).  Particles that
+   fall in no stored finest-level block or are not finite are dropped; with
+   outside != NULL the call waits for the stream and stores their number in
+   *outside (host), with outside == NULL it returns without waiting. */
 int32_t hlbm_deposit_particles(hlbm_lattice *h, const float *pos_xyz, int64_t n, int32_t on_device, double kappa,
                                double eta_max, double per_particle, int32_t moving, int64_t *outside);
 

@@ -25,6 +25,19 @@
 namespace hlbm {
 namespace {
 
+// Kernel parameters in the arithmetic type: the float copies for FP32 math
+// (a double-to-float conversion in the kernel would run on the FP64 pipe).
+template <typename R>
+__device__ __forceinline__ R pick(double d, float f);
+template <>
+__device__ __forceinline__ float pick<float>(double, float f) {
+  return f;
+}
+template <>
+__device__ __forceinline__ double pick<double>(double d, float) {
+  return d;
+}
+
 constexpr int kExt = 10;
 constexpr int kExtCells = 1000;
 constexpr int kHaloCells = 488;
@@ -260,7 +273,7 @@ __device__ __forceinline__ void fill_ext(const StepArgs& a, const AdjArgs& d, in
     __syncthreads();
   }
   const bool own_solid = solid_any && s_solid[e];
-  const R kxyz = R(a.kxyz);
+  const R kxyz = pick<R>(a.kxyz, a.kxyzf);
   if constexpr (PULL) {
     ExtSink<R, -1, 0> own{fbuf, e, R(0)};
     if (!own_solid) emit_all(make_coef(load_node<T>(in, blk, t, a.scales_in), kxyz), own);
@@ -318,12 +331,12 @@ __global__ void __launch_bounds__(512, 1) k_adj_pull(StepArgs a, AdjArgs d) {
     fy = R(Fp[kCells]);
     fz = R(Fp[2 * kCells]);
   } else {
-    fx = R(a.fu[0]);
-    fy = R(a.fu[1]);
-    fz = R(a.fu[2]);
+    fx = pick<R>(a.fu[0], a.fuf[0]);
+    fy = pick<R>(a.fu[1], a.fuf[1]);
+    fz = pick<R>(a.fu[2], a.fuf[2]);
   }
-  R om = R(a.om);
-  if (a.eps != nullptr) om = R(1) / (R(a.tau) * R(a.eps[blk * kCells + t]));
+  R om = pick<R>(a.om, a.omf);
+  if (a.eps != nullptr) om = R(1) / (pick<R>(a.tau, a.tauf) * R(a.eps[blk * kCells + t]));
   PreMom<R> lp;
   R lfx, lfy, lfz;
   collide_vjp(p, fx, fy, fz, om, load_lam<R>(d.lam, blk, t), lp, lfx, lfy, lfz);
@@ -360,12 +373,17 @@ __global__ void __launch_bounds__(512, 1) k_adj_push(StepArgs a, AdjArgs d) {
   gather27<R, false>(fbuf, e, g13, gb, std::make_integer_sequence<int, 27>{});
   const Coef<R> gh = adjoint_moments(gb);
   // the coefficient Jacobian already carries the weights w_i: ghat includes them
-  const Mom<R> lm = coef_vjp(load_node<T>(static_cast<const T*>(a.in), blk, t, a.scales_in), gh, R(a.kxyz));
+  const Mom<R> lm = coef_vjp(load_node<T>(static_cast<const T*>(a.in), blk, t, a.scales_in), gh, pick<R>(a.kxyz, a.kxyzf));
   store10<R>(d.lam_out, blk, t, lm.drho, lm.ux, lm.uy, lm.uz, lm.sxx, lm.syy, lm.szz, lm.sxy, lm.sxz, lm.syz);
 }
 
 template <typename T>
-cudaError_t launch_adj(const StepArgs& a, const AdjArgs& d, cudaStream_t s) {
+cudaError_t launch_adj(const StepArgs& a_in, const AdjArgs& d, cudaStream_t s) {
+  StepArgs a = a_in;
+  for (int k = 0; k < 3; ++k) a.fuf[k] = float(a.fu[k]);
+  a.tauf = float(a.tau);
+  a.omf = float(a.om);
+  a.kxyzf = float(a.kxyz);
   using R = typename StorageTraits<T>::R;
   const size_t smem = size_t(26) * kExtCells * sizeof(R);
   static bool configured = false;

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of libhomelbm.so (declared in include/homelbm.h).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -56,47 +57,59 @@ namespace hlbm {
 
 int LatticeOps::set_device(hlbm_lattice* h) {
   HLBM_CUDA(h, cudaSetDevice(h->cfg.device));
+  // Device buffers come from the device's stream-ordered pool.  Freed memory
+  // stays cached in the pool (no release threshold), so that the allocations
+  // of a hierarchy rebuild neither map new memory nor synchronise the device.
+  static std::atomic<bool> pool_ready[64];
+  const int dev = h->cfg.device;
+  if (dev >= 0 && dev < 64 && !pool_ready[dev].load()) {
+    cudaMemPool_t pool;
+    HLBM_CUDA(h, cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t threshold = UINT64_MAX;
+    HLBM_CUDA(h, cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold));
+    pool_ready[dev].store(true);
+  }
   return HLBM_OK;
 }
 
 int LatticeOps::alloc(hlbm_lattice* h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return HLBM_OK;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocAsync(p, bytes, h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
-    return fail(h, HLBM_E_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return fail(h, HLBM_E_OOM, "cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
   }
   return HLBM_OK;
 }
 
-void LatticeOps::release(void*& p) {
-  if (p) cudaFree(p);
+void LatticeOps::release(hlbm_lattice* h, void*& p) {
+  if (p) cudaFreeAsync(p, h->stream);
   p = nullptr;
 }
 
-void LatticeOps::free_level(LevelData& L) {
-  release(L.d_mom[0]);
-  release(L.d_mom[1]);
+void LatticeOps::free_level(hlbm_lattice* h, LevelData& L) {
+  release(h, L.d_mom[0]);
+  release(h, L.d_mom[1]);
   void* v = L.d_nbr;
-  release(v);
+  release(h, v);
   L.d_nbr = nullptr;
   v = L.d_bflags;
-  release(v);
+  release(h, v);
   L.d_bflags = nullptr;
   v = L.d_bmask;
-  release(v);
+  release(h, v);
   L.d_bmask = nullptr;
   v = L.d_solid;
-  release(v);
+  release(h, v);
   L.d_solid = nullptr;
   v = L.d_skip;
-  release(v);
+  release(h, v);
   L.d_skip = nullptr;
   for (void** q : {(void**)&L.d_coords, (void**)&L.d_slot, (void**)&L.d_H, (void**)&L.d_stored, (void**)&L.d_down,
                    (void**)&L.d_up, (void**)&L.d_scales, (void**)&L.d_amax}) {
-    release(*q);
+    release(h, *q);
   }
   L.n_down = L.n_up = 0;
   L.nb = 0;
@@ -256,17 +269,20 @@ int32_t hlbm_destroy(hlbm_lattice* h) {
   if (h == nullptr) return HLBM_OK;
   cudaSetDevice(h->cfg.device);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (auto& L : h->lv) LatticeOps::free_level(L);
-  LatticeOps::release(h->d_stage);
-  for (void*& c : h->ckpt) LatticeOps::release(c);
+  for (auto& L : h->lv) LatticeOps::free_level(h, L);
+  LatticeOps::release(h, h->d_stage);
+  for (void*& c : h->ckpt) LatticeOps::release(h, c);
   void* v = h->d_status;
-  LatticeOps::release(v);
+  LatticeOps::release(h, v);
   v = h->d_red;
-  LatticeOps::release(v);
+  LatticeOps::release(h, v);
   v = h->d_F;
-  LatticeOps::release(v);
+  LatticeOps::release(h, v);
   v = h->d_eps;
-  LatticeOps::release(v);
+  LatticeOps::release(h, v);
+  v = h->d_count;
+  LatticeOps::release(h, v);
+  if (h->stream) cudaStreamSynchronize(h->stream);  // the frees are ordered on the stream
   delete h;
   return HLBM_OK;
 }
@@ -277,7 +293,7 @@ int32_t hlbm_set_dense(hlbm_lattice* h) {
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
   LevelData& L = h->lv[0];
-  LatticeOps::free_level(L);
+  LatticeOps::free_level(h, L);
   int dims[3];
   h->block_dims(0, dims);
   const int64_t nb = int64_t(dims[0]) * dims[1] * dims[2];
@@ -349,10 +365,10 @@ int32_t hlbm_set_force(hlbm_lattice* h, const float* F_dev, const float* eps_dev
   if (rc) return rc;
   const int64_t n = h->lv[0].nb * kCells;
   void* v = h->d_F;
-  LatticeOps::release(v);
+  LatticeOps::release(h, v);
   h->d_F = nullptr;
   v = h->d_eps;
-  LatticeOps::release(v);
+  LatticeOps::release(h, v);
   h->d_eps = nullptr;
   if (F_dev) {
     void* p;
@@ -378,10 +394,10 @@ int32_t hlbm_set_solid(hlbm_lattice* h, const uint8_t* mask) {
   if (rc) return rc;
   LevelData& L = h->lv[0];
   void* v = L.d_solid;
-  LatticeOps::release(v);
+  LatticeOps::release(h, v);
   L.d_solid = nullptr;
   v = L.d_bflags;
-  LatticeOps::release(v);
+  LatticeOps::release(h, v);
   L.d_bflags = nullptr;
   if (mask == nullptr) return LatticeOps::bounce(h, L);
   int dims[3];
@@ -418,7 +434,7 @@ int32_t hlbm_set_solid(hlbm_lattice* h, const uint8_t* mask) {
 
 static int stage(hlbm_lattice* h, size_t bytes) {
   if (h->stage_bytes >= bytes) return HLBM_OK;
-  LatticeOps::release(h->d_stage);
+  LatticeOps::release(h, h->d_stage);
   h->stage_bytes = 0;
   int rc = LatticeOps::alloc(h, &h->d_stage, bytes);
   if (rc) return rc;
@@ -535,7 +551,7 @@ int32_t hlbm_reduce(hlbm_lattice* h, double out[7]) {
   const size_t need = size_t(nbmax) * 7 + 2 * 8;
   if (h->red_n < need) {
     void* v = h->d_red;
-    LatticeOps::release(v);
+    LatticeOps::release(h, v);
     h->d_red = nullptr;
     h->red_n = 0;
     void* p;
@@ -595,7 +611,7 @@ int32_t hlbm_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every
   if (n_steps <= 0 || ckpt_every <= 0) return fail(h, HLBM_E_INVALID_ARG, "n_steps and ckpt_every must be positive");
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
-  for (void*& c : h->ckpt) LatticeOps::release(c);
+  for (void*& c : h->ckpt) LatticeOps::release(h, c);
   h->ckpt.clear();
   h->rec_steps = h->rec_every = 0;
   LevelData& L = h->lv[0];
@@ -630,7 +646,7 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
   const int K = h->rec_every, n = h->rec_steps;
   std::vector<void*> tmp;
   auto release_all = [&]() {
-    for (void*& p : tmp) LatticeOps::release(p);
+    for (void*& p : tmp) LatticeOps::release(h, p);
   };
   auto get = [&](size_t b, void** out) -> int {
     int r = LatticeOps::alloc(h, out, b);

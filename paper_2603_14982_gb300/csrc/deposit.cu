@@ -79,27 +79,26 @@ extern "C" int32_t hlbm_deposit_particles(hlbm_lattice* h, const float* pos_xyz,
     if ((rc = LatticeOps::alloc(h, &p, size_t(n_nodes) * sizeof(float)))) return rc;
     h->d_eps = static_cast<float*>(p);
   }
-  if ((rc = LatticeOps::alloc(h, &p, sizeof(unsigned long long)))) return rc;
-  unsigned long long* d_out = static_cast<unsigned long long*>(p);
+  if (h->d_count == nullptr) {
+    if ((rc = LatticeOps::alloc(h, &p, sizeof(unsigned long long)))) return rc;
+    h->d_count = static_cast<unsigned long long*>(p);
+  }
   const float* d_pos = pos_xyz;
   void* staged = nullptr;
   cudaError_t e = cudaSuccess;
   if (!on_device && n > 0) {
-    if ((rc = LatticeOps::alloc(h, &staged, size_t(n) * 3 * sizeof(float)))) {
-      cudaFree(d_out);
-      return rc;
-    }
+    if ((rc = LatticeOps::alloc(h, &staged, size_t(n) * 3 * sizeof(float)))) return rc;
     e = cudaMemcpyAsync(staged, pos_xyz, size_t(n) * 3 * sizeof(float), cudaMemcpyHostToDevice, h->stream);
     d_pos = static_cast<const float*>(staged);
   }
   int dims[3];
   h->block_dims(0, dims);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_out, 0, sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_eps, 0, size_t(n_nodes) * sizeof(float), h->stream);
   if (e == cudaSuccess && n > 0) {
     k_count_particles<<<unsigned((n + 255) / 256), 256, 0, h->stream>>>(
         d_pos, n, h->cfg.nx, h->cfg.ny, h->cfg.nz, dims[0], dims[1], h->device_hierarchy ? L.d_slot : nullptr,
-        reinterpret_cast<unsigned*>(h->d_eps), d_out);
+        reinterpret_cast<unsigned*>(h->d_eps), h->d_count);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && n_nodes > 0) {
@@ -108,10 +107,11 @@ extern "C" int32_t hlbm_deposit_particles(hlbm_lattice* h, const float* pos_xyz,
     e = cudaGetLastError();
   }
   unsigned long long out_h = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&out_h, d_out, sizeof(out_h), cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(d_out);
-  if (staged) cudaFree(staged);
+  if (e == cudaSuccess && outside != nullptr) {
+    e = cudaMemcpyAsync(&out_h, h->d_count, sizeof(out_h), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (staged) LatticeOps::release(h, staged);
   if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "particle deposit: %s", cudaGetErrorString(e));
   if (outside) *outside = int64_t(out_h);
   return HLBM_OK;

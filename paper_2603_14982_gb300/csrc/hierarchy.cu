@@ -285,6 +285,21 @@ __global__ void __launch_bounds__(512) k_iface_scatter(const int32_t* __restrict
     down[k] = v;
 }
 
+__global__ void k_count_changes(const uint8_t* __restrict__ hn, const uint8_t* __restrict__ ho,
+                                const uint8_t* __restrict__ sn, const uint8_t* __restrict__ so, int64_t n,
+                                unsigned long long* out) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool in = i < n;
+  const unsigned r = __ballot_sync(0xffffffffu, in && hn[i] && !ho[i]);
+  const unsigned c = __ballot_sync(0xffffffffu, in && !hn[i] && ho[i]);
+  const unsigned d = __ballot_sync(0xffffffffu, in && so[i] && !sn[i]);
+  if ((threadIdx.x & 31) == 0) {
+    if (r) atomicAdd(out + 0, (unsigned long long)__popc(r));
+    if (c) atomicAdd(out + 1, (unsigned long long)__popc(c));
+    if (d) atomicAdd(out + 2, (unsigned long long)__popc(d));
+  }
+}
+
 inline unsigned grid_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
 
 }  // namespace
@@ -358,6 +373,13 @@ cudaError_t interface_scatter(const int32_t* nbr, const uint8_t* skip, int64_t n
                               int32_t* down, int32_t* up, cudaStream_t s) {
   if (nb == 0) return cudaSuccess;
   k_iface_scatter<<<unsigned(nb), 512, 0, s>>>(nbr, skip, nb, scratch, down, up);
+  return cudaGetLastError();
+}
+
+cudaError_t count_changes(const uint8_t* H_new, const uint8_t* H_old, const uint8_t* stored_new,
+                          const uint8_t* stored_old, int64_t slots, unsigned long long* counts_dev, cudaStream_t s) {
+  if (slots == 0) return cudaSuccess;
+  k_count_changes<<<grid_for(slots, 256), 256, 0, s>>>(H_new, H_old, stored_new, stored_old, slots, counts_dev);
   return cudaGetLastError();
 }
 

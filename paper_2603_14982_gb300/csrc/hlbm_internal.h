@@ -40,6 +40,9 @@ struct StepArgs {
   unsigned* work;           // non-null: persistent launch of `grid` CTAs over a ticket counter
                             // (two zeroed unsigned in device memory, left zeroed); FP32/FP16/BF16 only
   int grid;
+  // float copies of fu, tau, om, kxyz for the FP32-math kernel (set by its launcher:
+  // FP64 conversions run on the slow FP64 pipe, so the kernel takes floats)
+  float fuf[3], tauf, omf, kxyzf;
 };
 
 // FP64 storage: one node per thread (stream_collide.cu).  Other storages: the

@@ -56,6 +56,7 @@ struct hlbm_lattice {
   bool device_hierarchy = false;  // levels were built by the device rebuild pipeline
   double kup[8] = {0}, kdown[8] = {0};  // S^neq factors between level l and l+1
   int* d_status = nullptr;    // device status word of the transfer kernels (0 = ok)
+  unsigned long long* d_count = nullptr;  // scratch counter (particles dropped by a deposit)
   // forward run recorded for the adjoint: states at steps 0, K, 2K, ...
   std::vector<void*> ckpt;
   int32_t rec_steps = 0, rec_every = 0;
@@ -83,8 +84,8 @@ int ml_check_status(hlbm_lattice* h);
 struct LatticeOps {
   static int set_device(hlbm_lattice* h);
   static int alloc(hlbm_lattice* h, void** p, size_t bytes);
-  static void release(void*& p);
-  static void free_level(LevelData& L);
+  static void release(hlbm_lattice* h, void*& p);
+  static void free_level(hlbm_lattice* h, LevelData& L);
   // Allocate the scale state of a reduced-precision level (scales for amax 0).
   static int init_scales(hlbm_lattice* h, LevelData& L);
   // Re-derive a reduced-precision level's scales every kRescaleEvery steps.

@@ -174,7 +174,7 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
   ML_TRY(alloc_t(h, &d_occ, size_t(d0.slots())));
   std::vector<void*> tmp = {d_occ};
   auto cleanup = [&]() {
-    for (void*& p : tmp) LatticeOps::release(p);
+    for (void*& p : tmp) LatticeOps::release(h, p);
   };
   ML_CUDA(h, cudaMemsetAsync(d_bad, 0, sizeof(int), st));
   if (blocks != nullptr) {
@@ -201,7 +201,7 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
   std::vector<LevelData> nl(L);
   for (int l = 0; l < L; ++l) nl[l].tau = h->lv[l].tau;
   auto free_new = [&]() {
-    for (auto& X : nl) LatticeOps::free_level(X);
+    for (auto& X : nl) LatticeOps::free_level(h, X);
   };
   int rc = HLBM_OK;
   std::vector<uint8_t*> d_I(L, nullptr), d_fl(L, nullptr);
@@ -350,7 +350,15 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
   }
 
   // 7. host copies of the lists; counts of refined / coarsened / deleted blocks
-  int64_t refined = 0, coarsened = 0, deleted = 0;
+  unsigned long long changes[3] = {0, 0, 0};
+  unsigned long long* d_changes = reinterpret_cast<unsigned long long*>(d_tot + 3 * L);
+  if (counts_out != nullptr && has_old) {
+    ML_CUDA(h, cudaMemsetAsync(d_changes, 0, 3 * sizeof(unsigned long long), st));
+    for (int l = 0; l < L; ++l)
+      ML_CUDA(h, count_changes(nl[l].d_H, h->lv[l].d_H, nl[l].d_stored, h->lv[l].d_stored, dims_of(h, l).slots(),
+                               d_changes, st));
+    ML_CUDA(h, cudaMemcpyAsync(changes, d_changes, sizeof(changes), cudaMemcpyDeviceToHost, st));
+  }
   for (int l = 0; l < L; ++l) {
     nl[l].coords.resize(size_t(nb[l]) * 3);
     nl[l].flags.resize(size_t(nb[l]));
@@ -359,36 +367,23 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
                                  cudaMemcpyDeviceToHost, st));
       ML_CUDA(h, cudaMemcpyAsync(nl[l].flags.data(), d_lflags[l], size_t(nb[l]), cudaMemcpyDeviceToHost, st));
     }
-    if (counts_out != nullptr && has_old) {
-      const size_t ns = size_t(dims_of(h, l).slots());
-      std::vector<uint8_t> hn(ns), ho(ns), sn(ns), so(ns);
-      ML_CUDA(h, cudaMemcpyAsync(hn.data(), nl[l].d_H, ns, cudaMemcpyDeviceToHost, st));
-      ML_CUDA(h, cudaMemcpyAsync(ho.data(), h->lv[l].d_H, ns, cudaMemcpyDeviceToHost, st));
-      ML_CUDA(h, cudaMemcpyAsync(sn.data(), nl[l].d_stored, ns, cudaMemcpyDeviceToHost, st));
-      ML_CUDA(h, cudaMemcpyAsync(so.data(), h->lv[l].d_stored, ns, cudaMemcpyDeviceToHost, st));
-      ML_CUDA(h, cudaStreamSynchronize(st));
-      for (size_t q = 0; q < ns; ++q) {
-        refined += (hn[q] && !ho[q]);
-        coarsened += (!hn[q] && ho[q]);
-        deleted += (so[q] && !sn[q]);
-      }
-    }
   }
   ML_CUDA(h, cudaStreamSynchronize(st));
+  const int64_t refined = int64_t(changes[0]), coarsened = int64_t(changes[1]), deleted = int64_t(changes[2]);
   int bad = 0;
   ML_CUDA(h, cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));
   cleanup();
-  for (auto& X : h->lv) LatticeOps::free_level(X);
+  for (auto& X : h->lv) LatticeOps::free_level(h, X);
   for (int l = 0; l < L; ++l) {
     nl[l].cur = 0;
     h->lv[l] = nl[l];
   }
   // the level-0 force field refers to the old block list
   void* v = h->d_F;
-  LatticeOps::release(v);
+  LatticeOps::release(h, v);
   h->d_F = nullptr;
   v = h->d_eps;
-  LatticeOps::release(v);
+  LatticeOps::release(h, v);
   h->d_eps = nullptr;
   h->have_blocks = true;
   h->device_hierarchy = true;

@@ -16,7 +16,8 @@
 //     that leave the block land, wrapped, exactly in the slots whose true
 //     source is a halo node, so they are overwritten in B.
 //  B. 244 threads each take a pair of halo nodes (read from the 26 neighbour
-//     blocks, mostly L2 hits) and write the 9 directions that enter the block;
+//     blocks, mostly L2 hits) and write the 9 directions that enter the block
+//     (one code path per face axis: upper faces are reflected onto lower ones);
 //     nodes whose pull source is a wall or a solid node write their own
 //     opposite population instead (half-way bounce-back).
 //  C. each thread reads the 26 populations of its pair (one 64-bit load per
@@ -56,54 +57,55 @@ struct OwnPush {
 
 constexpr int kTrash = 26 * 512;  // per-lane dummy float slots for masked halo stores
 
-// Halo node pair a = (hx, hy, hz), b = (hx, hy, hz + 4), hz < 4, on an x or y
-// face (inward component SG on axis AX): destinations are addressed like the
-// own pushes (pair slot + half, halves swapped where z wraps); a destination
-// outside the block, or an invalid source, goes to the lane's trash slot.
-template <int AX, int SG>
-struct HaloPushXY {
+// Halo pushes in a canonical orientation: the halo node lies just below the
+// block on the face axis and pushes the 9 directions whose component on that
+// axis is +1.  Threads on the upper face reflect their moments along the face
+// axis first (Eq. three_order_f is covariant under reflections), so canonical
+// direction J carries the population of its mirror image; d0 / d1 shift the
+// store to the mirror direction's slot (d1 for the mirrors that lie on the
+// other side of the rest index).  oka / okb: bit J set when the .x / .y value
+// of canonical direction J has a destination inside the block and a valid
+// source; other values go to the lane's trash slot.
+
+// x faces (AX = 0) and y faces (AX = 1): node pair a = (hx, hy, hz), b = hz + 4,
+// one stored pair of the same neighbour.  X / YH / Y8 / Z64 hold the actual
+// destination coordinates (swizzle parts) for canonical component c at [c+1];
+// ha[c+1]: node a lands in the high half of its pair slot.
+template <int AX>
+struct HaloXY {
   float* f;
-  int X[3], YH[3], Y8[3], Z64[3];
-  unsigned swp;             // bit (cz+1): node a lands in the high half
-  unsigned vx, vy, vza, vzb;  // bit (c+1): destination coordinate in range
-  bool va, vb;
-  int trash;
+  int X[3], YH[3], Y8[3], Z64[3], ha[3];
+  unsigned oka, okb;
+  int d0, d1, trash;
   template <int J>
   __device__ __forceinline__ void put(V2 v) {
     constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
     constexpr int c = AX == 0 ? cx : cy;
-    if constexpr (c == SG) {
-      const int p2 = 2 * (slot_of(J) * 256 + (X[cx + 1] ^ YH[cy + 1]) + Y8[cy + 1] + Z64[cz + 1]);
-      const bool rng = ((vx >> (cx + 1)) & (vy >> (cy + 1)) & 1u) != 0u;
-      const int ha = (swp >> (cz + 1)) & 1;
-      const bool oka = va && rng && ((vza >> (cz + 1)) & 1u);
-      const bool okb = vb && rng && ((vzb >> (cz + 1)) & 1u);
-      f[oka ? p2 + ha : trash] = v.v.x;
-      f[okb ? p2 + 1 - ha : trash] = v.v.y;
+    if constexpr (c == 1) {
+      constexpr bool cross = AX == 0 ? (cy == 0 && cz == 0) : (cz == 0);
+      const int p2 = 2 * (slot_of(J) * 256 + (X[cx + 1] ^ YH[cy + 1]) + Y8[cy + 1] + Z64[cz + 1]) + (cross ? d1 : d0);
+      const int h = ha[cz + 1];
+      f[((oka >> J) & 1u) ? p2 + h : trash] = v.v.x;
+      f[((okb >> J) & 1u) ? p2 + 1 - h : trash] = v.v.y;
     }
   }
 };
 
-// Halo node pair a = (hx, hy, hz), b = (hx, hy + 5, hz) on a z face (hz = -1 or
-// 8; destinations in plane z = 0 or 7, half 0 or 1).
-template <int SG>
-struct HaloPushZ {
+// z faces: node pair a = (hx, hy, hz), b = (hx, hy + 5, hz); zoff addresses the
+// destination plane (z = 0: pair slot 0, low half; z = 7: pair slot 3, high half).
+struct HaloZ {
   float* f;
   int X[3], YHa[3], YHb[3], Y8a[3], Y8b[3];
-  int zoff;                    // 2 * 64 * (z_dest & 3) + (z_dest >> 2)
-  unsigned vx, vya, vyb;
-  bool va, vb;
-  int trash;
+  int zoff;
+  unsigned oka, okb;
+  int d, trash;
   template <int J>
   __device__ __forceinline__ void put(V2 v) {
     constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
-    if constexpr (cz == SG) {
-      const int base = 2 * (slot_of(J) * 256) + zoff;
-      const unsigned okx = (vx >> (cx + 1)) & 1u;
-      const bool oka = va && (okx & (vya >> (cy + 1)));
-      const bool okb = vb && (okx & (vyb >> (cy + 1)));
-      f[oka ? base + 2 * ((X[cx + 1] ^ YHa[cy + 1]) + Y8a[cy + 1]) : trash] = v.v.x;
-      f[okb ? base + 2 * ((X[cx + 1] ^ YHb[cy + 1]) + Y8b[cy + 1]) : trash] = v.v.y;
+    if constexpr (cz == 1) {
+      const int base = 2 * (slot_of(J) * 256) + zoff + d;
+      f[((oka >> J) & 1u) ? base + 2 * ((X[cx + 1] ^ YHa[cy + 1]) + Y8a[cy + 1]) : trash] = v.v.x;
+      f[((okb >> J) & 1u) ? base + 2 * ((X[cx + 1] ^ YHb[cy + 1]) + Y8b[cy + 1]) : trash] = v.v.y;
     }
   }
 };
@@ -111,6 +113,15 @@ struct HaloPushZ {
 __device__ __forceinline__ unsigned range_mask(int v) {
   // bit (c+1) set when v + c lies in [0, 8), c in {-1, 0, 1}
   return ((unsigned)(v - 1) < 8u ? 1u : 0u) | ((unsigned)v < 8u ? 2u : 0u) | ((unsigned)(v + 1) < 8u ? 4u : 0u);
+}
+
+// Bit j = (cx+1) + 3 (cy+1) + 9 (cz+1) set when bit cx+1 of vx, bit cy+1 of vy
+// and bit cz+1 of vz are all set (per-axis masks as from range_mask).
+__device__ __forceinline__ unsigned dir_mask(unsigned vx, unsigned vy, unsigned vz) {
+  const unsigned mx = vx * 0x1249249u;  // vx in every 3-bit group
+  const unsigned my = ((vy & 1u) * 0x7u | ((vy >> 1) & 1u) * 0x38u | ((vy >> 2) & 1u) * 0x1C0u) * 0x40201u;
+  const unsigned mz = (vz & 1u) * 0x1FFu | ((vz >> 1) & 1u) * 0x3FE00u | ((vz >> 2) & 1u) * 0x7FC0000u;
+  return mx & my & mz;
 }
 
 // Half-way bounce-back: bit k of mask = the pull source x - c_k of this node is
@@ -143,28 +154,35 @@ __device__ __forceinline__ void gather_all(const float2* f, int own, V2 g13, V2 
   (gather_one<Js>(f, own, g13, g), ...);
 }
 
-__device__ __forceinline__ void halo_pair(int t, int& face, int& ax, int& ay, int& az, int& bx, int& by, int& bz) {
-  if (t < 100) {
-    const int q = t < 50 ? t : t - 50;
+// Halo work of thread t < kHaloPairs: cls 0 = x faces (threads 0-63), 1 = y
+// faces (64-143), 2 = z faces (144-243), so that only one warp mixes two
+// classes; mir = upper face.  Node pair a = (ax, ay, az), b = (bx, by, bz).
+__device__ __forceinline__ void halo_pair(int t, int& cls, bool& mir, int& ax, int& ay, int& az, int& bx, int& by,
+                                          int& bz) {
+  if (t < 64) {
+    const int q = t & 31;
+    cls = 0;
+    mir = t >= 32;
+    ax = bx = mir ? 8 : -1;
+    ay = by = q & 7;
+    az = q >> 3;
+    bz = az + 4;
+  } else if (t < 144) {
+    const int q = t < 104 ? t - 64 : t - 104;
+    cls = 1;
+    mir = t >= 104;
+    ax = bx = q % 10 - 1;
+    ay = by = mir ? 8 : -1;
+    az = q / 10;
+    bz = az + 4;
+  } else {
+    const int q = t < 194 ? t - 144 : t - 194;
+    cls = 2;
+    mir = t >= 194;
     ax = bx = q % 10 - 1;
     ay = q / 10 - 1;
     by = ay + 5;
-    az = bz = t < 50 ? -1 : 8;
-    face = t < 50 ? 4 : 5;
-  } else if (t < 180) {
-    const int q = t < 140 ? t - 100 : t - 140;
-    ax = bx = q % 10 - 1;
-    ay = by = t < 140 ? -1 : 8;
-    az = q / 10;
-    bz = az + 4;
-    face = t < 140 ? 2 : 3;
-  } else {
-    const int q = t < 212 ? t - 180 : t - 212;
-    ax = bx = t < 212 ? -1 : 8;
-    ay = by = q % 8;
-    az = q / 8;
-    bz = az + 4;
-    face = t < 212 ? 0 : 1;
+    az = bz = mir ? 8 : -1;
   }
 }
 
@@ -254,8 +272,9 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
 
   // own node pair: issue the loads early
   const Mom<V2> m = load_pair<T>(in, blk, own, sc_in);
-  int face = -1, hax = 0, hay = 0, haz = 0, hbx = 0, hby = 0, hbz = 0;
-  if (t < kHaloPairs) halo_pair(t, face, hax, hay, haz, hbx, hby, hbz);
+  int cls = -1, hax = 0, hay = 0, haz = 0, hbx = 0, hby = 0, hbz = 0;
+  bool mir = false;
+  if (t < kHaloPairs) halo_pair(t, cls, mir, hax, hay, haz, hbx, hby, hbz);
   __syncthreads();  // s_nbr, s_miss
 
   bool va = false, vb = false;
@@ -265,7 +284,7 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
     const int sa = (hax & 7) + 8 * (hay & 7) + 64 * (haz & 7), sb = (hbx & 7) + 8 * (hby & 7) + 64 * (hbz & 7);
     va = na >= 0 && !(solid_any && a.solid[int64_t(na) * kCells + sa]);
     vb = nb >= 0 && !(solid_any && a.solid[int64_t(nb) * kCells + sb]);
-    if (face < 4) {  // x / y faces: a and b are one stored pair of the same neighbour
+    if (cls < 2) {  // x / y faces: a and b are one stored pair of the same neighbour
       if (na >= 0) hm = load_pair<T>(in, na, sa, sc_in);
     } else {
       Mom<float> la, lb;
@@ -278,7 +297,7 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
   }
 
   // A. push the own pair
-  const V2 kxyz = V2(float(a.kxyz));
+  const V2 kxyz = V2(a.kxyzf);
   OwnPush op;
   op.f = f2buf;
 #pragma unroll
@@ -294,25 +313,55 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
 
   // B. halo pairs and bounce-back
   if (t < kHaloPairs && (va || vb)) {
+    // reflect the upper-face pairs along the face axis (u and S components with
+    // an odd count of that axis change sign)
+    const V2 sg = V2(mir ? -1.f : 1.f);
+    if (cls == 0) {
+      hm.ux = hm.ux * sg;
+      hm.sxy = hm.sxy * sg;
+      hm.sxz = hm.sxz * sg;
+    } else if (cls == 1) {
+      hm.uy = hm.uy * sg;
+      hm.sxy = hm.sxy * sg;
+      hm.syz = hm.syz * sg;
+    } else {
+      hm.uz = hm.uz * sg;
+      hm.sxz = hm.sxz * sg;
+      hm.syz = hm.syz * sg;
+    }
     const Coef<V2> c = make_coef(hm, kxyz);
     const int trash = kTrash + lane;
-    if (face < 4) {
-      int X[3], YH[3], Y8[3], Z64[3];
-      unsigned swp = 0;
+    const unsigned ma = va ? ~0u : 0u, mb = vb ? ~0u : 0u;
+    if (cls < 2) {
+      int Zc[3], HA[3];
 #pragma unroll
       for (int k = -1; k <= 1; ++k) {
-        X[k + 1] = (hax + k) & 7;
-        YH[k + 1] = ((hay + k) & 7) >> 1;
-        Y8[k + 1] = 8 * ((hay + k) & 7);
-        Z64[k + 1] = 64 * ((haz + k) & 3);
-        swp |= ((((haz + k) & 7) >> 2) & 1u) << (k + 1);
+        Zc[k + 1] = 64 * ((haz + k) & 3);
+        HA[k + 1] = ((haz + k) & 7) >> 2;
       }
-      const unsigned vx = range_mask(hax), vy = range_mask(hay), vza = range_mask(haz), vzb = range_mask(hbz);
-      switch (face) {
-        case 0: { HaloPushXY<0, 1> s{fbuf, {X[0], X[1], X[2]}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
-        case 1: { HaloPushXY<0, -1> s{fbuf, {X[0], X[1], X[2]}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
-        case 2: { HaloPushXY<1, 1> s{fbuf, {X[0], X[1], X[2]}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
-        default: { HaloPushXY<1, -1> s{fbuf, {X[0], X[1], X[2]}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Z64[0], Z64[1], Z64[2]}, swp, vx, vy, vza, vzb, va, vb, trash}; emit_all(c, s); } break;
+      const unsigned vza = range_mask(haz), vzb = range_mask(hbz);
+      const int face_dst = mir ? 7 : 0;  // destination coordinate on the face axis
+      if (cls == 0) {
+        int YH[3], Y8[3];
+#pragma unroll
+        for (int k = -1; k <= 1; ++k) {
+          YH[k + 1] = ((hay + k) & 7) >> 1;
+          Y8[k + 1] = 8 * ((hay + k) & 7);
+        }
+        const unsigned vy = range_mask(hay);
+        HaloXY<0> s{fbuf, {0, 0, face_dst}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Zc[0], Zc[1], Zc[2]},
+                    {HA[0], HA[1], HA[2]}, dir_mask(7u, vy, vza) & ma, dir_mask(7u, vy, vzb) & mb,
+                    mir ? -1024 : 0, mir ? -512 : 0, trash};
+        emit_all(c, s);
+      } else {
+        int X[3];
+#pragma unroll
+        for (int k = -1; k <= 1; ++k) X[k + 1] = (hax + k) & 7;
+        const unsigned vx = range_mask(hax);
+        HaloXY<1> s{fbuf, {X[0], X[1], X[2]}, {0, 0, face_dst >> 1}, {0, 0, 8 * face_dst}, {Zc[0], Zc[1], Zc[2]},
+                    {HA[0], HA[1], HA[2]}, dir_mask(vx, 7u, vza) & ma, dir_mask(vx, 7u, vzb) & mb,
+                    mir ? -3072 : 0, mir ? -2560 : 0, trash};
+        emit_all(c, s);
       }
     } else {
       int X[3], YHa[3], YHb[3], Y8a[3], Y8b[3];
@@ -324,14 +373,12 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
         Y8a[k + 1] = 8 * ((hay + k) & 7);
         Y8b[k + 1] = 8 * ((hby + k) & 7);
       }
-      const unsigned vx = range_mask(hax), vya = range_mask(hay), vyb = range_mask(hby);
-      if (face == 4) {
-        HaloPushZ<1> s{fbuf, {X[0], X[1], X[2]}, {YHa[0], YHa[1], YHa[2]}, {YHb[0], YHb[1], YHb[2]}, {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, 0, vx, vya, vyb, va, vb, trash};
-        emit_all(c, s);
-      } else {
-        HaloPushZ<-1> s{fbuf, {X[0], X[1], X[2]}, {YHa[0], YHa[1], YHa[2]}, {YHb[0], YHb[1], YHb[2]}, {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, 2 * 64 * 3 + 1, vx, vya, vyb, va, vb, trash};
-        emit_all(c, s);
-      }
+      const unsigned vx = range_mask(hax);
+      HaloZ s{fbuf, {X[0], X[1], X[2]}, {YHa[0], YHa[1], YHa[2]}, {YHb[0], YHb[1], YHb[2]},
+              {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, mir ? 2 * 64 * 3 + 1 : 0,
+              dir_mask(vx, range_mask(hay), 7u) & ma, dir_mask(vx, range_mask(hby), 7u) & mb, mir ? -17 * 512 : 0,
+              trash};
+      emit_all(c, s);
     }
   }
   if (bf & kBlockBounce) {  // block-uniform
@@ -367,13 +414,13 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
       fy = V2(__ldg(Fp + kCells), __ldg(Fp + kCells + 256));
       fz = V2(__ldg(Fp + 2 * kCells), __ldg(Fp + 2 * kCells + 256));
     } else {
-      fx = V2(float(a.fu[0]));
-      fy = V2(float(a.fu[1]));
-      fz = V2(float(a.fu[2]));
+      fx = V2(a.fuf[0]);
+      fy = V2(a.fuf[1]);
+      fz = V2(a.fuf[2]);
     }
-    V2 om = V2(a.blk_om != nullptr ? __ldg(a.blk_om + blk) : float(a.om));
+    V2 om = V2(a.blk_om != nullptr ? __ldg(a.blk_om + blk) : a.omf);
     if (a.eps != nullptr)
-      om = inv(V2(float(a.tau)) * V2(__ldg(a.eps + blk * kCells + own), __ldg(a.eps + blk * kCells + own + 256)));
+      om = inv(V2(a.tauf) * V2(__ldg(a.eps + blk * kCells + own), __ldg(a.eps + blk * kCells + own + 256)));
     mo = collide(p, fx, fy, fz, om);
     if (copy_lo || copy_hi) mo = select_halves(mo, load_pair<T>(in, blk, own, sc_in), copy_lo, copy_hi);
   }
@@ -446,7 +493,12 @@ __global__ void __launch_bounds__(512) k_bounce_masks(const int32_t* __restrict_
 }
 
 template <typename T>
-cudaError_t launch_f2(const StepArgs& a, cudaStream_t s) {
+cudaError_t launch_f2(const StepArgs& a_in, cudaStream_t s) {
+  StepArgs a = a_in;
+  for (int k = 0; k < 3; ++k) a.fuf[k] = float(a.fu[k]);
+  a.tauf = float(a.tau);
+  a.omf = float(a.om);
+  a.kxyzf = float(a.kxyz);
   const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
   static bool configured = false;
   if (!configured) {

@@ -223,16 +223,18 @@ class Lattice:
         return out[:n], fl[:n]
 
     # ---- inputs
-    def deposit_particles(self, pos, kappa=1e-4, eta_max=0.4, per_particle=0.25, moving=True):
+    def deposit_particles(self, pos, kappa=1e-4, eta_max=0.4, per_particle=0.25, moving=True, wait=True):
         """Finest-level eta / eps / drag force from particle positions (float32 [n][3],
-        numpy or CUDA tensor); returns the number of particles dropped."""
+        numpy or CUDA tensor).  wait=True returns the number of particles dropped;
+        wait=False returns None without waiting for the stream."""
         if isinstance(pos, np.ndarray):
             pos = np.ascontiguousarray(pos, dtype=np.float32)
         p, dev = _ptr(pos)
         out = ctypes.c_int64()
         self._check(self.lib.hlbm_deposit_particles(self.h, p, int(pos.shape[0]), dev, float(kappa), float(eta_max),
-                                                    float(per_particle), 1 if moving else 0, ctypes.byref(out)))
-        return out.value
+                                                    float(per_particle), 1 if moving else 0,
+                                                    ctypes.byref(out) if wait else None))
+        return out.value if wait else None
 
     def set_uniform_force(self, fx, fy, fz):
         self._check(self.lib.hlbm_set_uniform_force(self.h, float(fx), float(fy), float(fz)))
