@@ -37,7 +37,7 @@ KERNEL = "k_stream_collide_f2<float>"
 # DRAM bytes (read + write) per launch of KERNEL from one ncu capture of the
 # 192^3 duct, scaled by nodes to 256^3 (profiles/stream_collide_f2_duct192.md);
 # set to None whenever the kernel changes after that capture.
-TRAFFIC_PER_NODE = None
+TRAFFIC_PER_NODE = 531.7e6 / 192 ** 3
 
 
 def measured_peaks():
@@ -355,7 +355,28 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the multi-level, adjoint and batched workloads")
+    ap.add_argument("--only", choices=["multilevel", "adjoint", "batched"],
+                    help="run one secondary workload alone and print its JSON (profiling runs)")
+    ap.add_argument("--adj-steps", type=int, default=200)
+    ap.add_argument("--adj-ckpt", type=int, default=20)
     args = ap.parse_args()
+    if args.only:
+        import torch
+        from paper_2603_14982_gb300 import build as B
+        from paper_2603_14982_gb300 import homelbm as hl
+        from paper_2603_14982_gb300 import workloads as wl
+        B.build()
+        stream = torch.cuda.Stream()
+        if args.only == "adjoint":
+            res = bench_adjoint(hl, wl, stream, steps=args.adj_steps, ckpt=args.adj_ckpt)
+        elif args.only == "batched":
+            res = bench_batched(hl, wl, stream)
+        else:
+            pos0 = torch.tensor(wl.particle_cloud(512), device="cuda")
+            bench_multilevel(hl, wl, stream, "f32", pos0, fine_steps=48)
+            res = bench_multilevel(hl, wl, stream, "f32", pos0)[0]
+        print(json.dumps({"only": args.only, "result": res}))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.warmup < 3:
