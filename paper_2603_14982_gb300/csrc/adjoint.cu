@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "adjoint_math.cuh"
+#include "f2_common.cuh"
 #include "hlbm_internal.h"
 #include "lattice_state.h"
 
@@ -377,6 +378,251 @@ __global__ void __launch_bounds__(512, 1) k_adj_push(StepArgs a, AdjArgs d) {
   store10<R>(d.lam_out, blk, t, lm.drho, lm.ux, lm.uy, lm.uz, lm.sxx, lm.syy, lm.szz, lm.sxy, lm.sxz, lm.syz);
 }
 
+// ---------------------------------------------------------------- node-pair reverse step
+// FP32 storage: the reverse step on node pairs with packed FP32 arithmetic,
+// streaming through the same destination-indexed shared buffer as the forward
+// kernel (f2_common.cuh).
+
+// Node values of the reverse stream: lambda_p (float32, natural node order)
+// and its transposed projection.  A node hands gbar_J back to its pull source
+// x - c_J, i.e. along -c_J: the value it emits for direction K is gbar_{26-K},
+// and the gather then holds ghat_{26-J} in slot J.  Bounce-back slots take the
+// node's own value the same way.
+struct LamSource {
+  using Node = PreMom<V2>;
+  const float* lp;
+  __device__ __forceinline__ Node pair(int64_t b, int cell) const {
+    const float* q = lp + b * (kRows * kCells) + cell;
+    Node n;
+    n.drho = V2(q[0], q[256]);
+    n.jx = V2(q[kCells], q[kCells + 256]);
+    n.jy = V2(q[2 * kCells], q[2 * kCells + 256]);
+    n.jz = V2(q[3 * kCells], q[3 * kCells + 256]);
+    n.pxx = V2(q[4 * kCells], q[4 * kCells + 256]);
+    n.pyy = V2(q[5 * kCells], q[5 * kCells + 256]);
+    n.pzz = V2(q[6 * kCells], q[6 * kCells + 256]);
+    n.pxy = V2(q[7 * kCells], q[7 * kCells + 256]);
+    n.pxz = V2(q[8 * kCells], q[8 * kCells + 256]);
+    n.pyz = V2(q[9 * kCells], q[9 * kCells + 256]);
+    return n;
+  }
+  __device__ __forceinline__ Node own(int64_t b, int cell) const { return pair(b, cell); }
+  __device__ __forceinline__ Node two(int ba, int ca, int bb, int cb) const {
+    float va[kRows], vb[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      va[r] = ba >= 0 ? lp[int64_t(ba) * (kRows * kCells) + r * kCells + ca] : 0.f;
+      vb[r] = bb >= 0 ? lp[int64_t(bb) * (kRows * kCells) + r * kCells + cb] : 0.f;
+    }
+    Node n;
+    n.drho = V2(va[0], vb[0]);
+    n.jx = V2(va[1], vb[1]);
+    n.jy = V2(va[2], vb[2]);
+    n.jz = V2(va[3], vb[3]);
+    n.pxx = V2(va[4], vb[4]);
+    n.pyy = V2(va[5], vb[5]);
+    n.pzz = V2(va[6], vb[6]);
+    n.pxy = V2(va[7], vb[7]);
+    n.pxz = V2(va[8], vb[8]);
+    n.pyz = V2(va[9], vb[9]);
+    return n;
+  }
+  __device__ __forceinline__ static Node zero() {
+    Node n;
+    n.drho = n.jx = n.jy = n.jz = n.pxx = n.pyy = n.pzz = n.pxy = n.pxz = n.pyz = V2(0.f);
+    return n;
+  }
+  // reflection along axis cls: j and Pi components with an odd count of that axis change sign
+  __device__ __forceinline__ static void mirror(Node& n, int cls, V2 sg) {
+    if (cls == 0) {
+      n.jx = n.jx * sg;
+      n.pxy = n.pxy * sg;
+      n.pxz = n.pxz * sg;
+    } else if (cls == 1) {
+      n.jy = n.jy * sg;
+      n.pxy = n.pxy * sg;
+      n.pyz = n.pyz * sg;
+    } else {
+      n.jz = n.jz * sg;
+      n.pxz = n.pxz * sg;
+      n.pyz = n.pyz * sg;
+    }
+  }
+  template <typename S, int... Ks>
+  __device__ __forceinline__ static void emit_seq(const Node& n, S& s, std::integer_sequence<int, Ks...>) {
+    (s.template put<Ks>(gbar<26 - Ks>(n)), ...);
+  }
+  template <typename S>
+  __device__ __forceinline__ void emit(const Node& n, S& s) const {
+    emit_seq(n, s, std::make_integer_sequence<int, 27>{});
+  }
+};
+
+__device__ __forceinline__ void store_pair10(float* p, int64_t blk, int cell, const V2 (&v)[kRows], bool zlo,
+                                             bool zhi) {
+  float* q = p + blk * (kRows * kCells) + cell;
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    q[r * kCells] = zlo ? 0.f : v[r].v.x;
+    q[r * kCells + 256] = zhi ? 0.f : v[r].v.y;
+  }
+}
+
+// Reverse step, part 1 (node pairs): recomputed pull and projection, then
+// lambda_p = (dC/dp)^T lambda' and dL/dF += (dC/dF)^T lambda' (FP64 sums).
+template <typename T>
+__global__ void __launch_bounds__(f2::kThreads, 2) k_adj_pull2(StepArgs a, AdjArgs d) {
+  extern __shared__ __align__(16) float2 f2buf[];
+  __shared__ int s_nbr[27];
+  __shared__ unsigned s_miss;
+  const int64_t blk = blockIdx.x;
+  f2::PairCtx cx = f2::pair_ctx();
+  const f2::MomSource<T> src{static_cast<const T*>(a.in), a.scales_in, V2(a.kxyzf)};
+  f2::stream_pairs(src, a, blk, f2buf, s_nbr, s_miss, cx);
+  const int own = cx.own;
+  bool fz_lo = false, fz_hi = false;  // solid nodes copy their input: no dependence on the pulls or on F
+  if (cx.solid_any) {
+    fz_lo = a.solid[blk * kCells + own] != 0;
+    fz_hi = a.solid[blk * kCells + own + 256] != 0;
+  }
+  V2 out[kRows];
+  if (fz_lo && fz_hi) {
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) out[r] = V2(0.f);
+    store_pair10(d.lamp, blk, own, out, true, true);
+    return;
+  }
+  V2 g[27];
+  f2::gather_all(f2buf, cx.own_s, cx.g13, g, std::make_integer_sequence<int, 27>{});
+  const PreMom<V2> p = project(g);
+  V2 fx, fy, fz;
+  if (a.F != nullptr) {
+    const float* Fp = a.F + blk * 3 * kCells + own;
+    fx = V2(__ldg(Fp), __ldg(Fp + 256));
+    fy = V2(__ldg(Fp + kCells), __ldg(Fp + kCells + 256));
+    fz = V2(__ldg(Fp + 2 * kCells), __ldg(Fp + 2 * kCells + 256));
+  } else {
+    fx = V2(a.fuf[0]);
+    fy = V2(a.fuf[1]);
+    fz = V2(a.fuf[2]);
+  }
+  V2 om = V2(a.omf);
+  if (a.eps != nullptr)
+    om = inv(V2(a.tauf) * V2(__ldg(a.eps + blk * kCells + own), __ldg(a.eps + blk * kCells + own + 256)));
+  const Mom<V2> lo = [&] {
+    const LamSource ls{d.lam};
+    const PreMom<V2> q = ls.pair(blk, own);  // same 10-row layout, read as moments
+    Mom<V2> m;
+    m.drho = q.drho;
+    m.ux = q.jx;
+    m.uy = q.jy;
+    m.uz = q.jz;
+    m.sxx = q.pxx;
+    m.syy = q.pyy;
+    m.szz = q.pzz;
+    m.sxy = q.pxy;
+    m.sxz = q.pxz;
+    m.syz = q.pyz;
+    return m;
+  }();
+  PreMom<V2> lp;
+  V2 lfx, lfy, lfz;
+  collide_vjp(p, fx, fy, fz, om, lo, lp, lfx, lfy, lfz);
+  out[0] = lp.drho;
+  out[1] = lp.jx;
+  out[2] = lp.jy;
+  out[3] = lp.jz;
+  out[4] = lp.pxx;
+  out[5] = lp.pyy;
+  out[6] = lp.pzz;
+  out[7] = lp.pxy;
+  out[8] = lp.pxz;
+  out[9] = lp.pyz;
+  store_pair10(d.lamp, blk, own, out, fz_lo, fz_hi);
+  double* dF = d.dF + blk * 3 * kCells + own;
+  if (!fz_lo) {
+    dF[0] += double(lfx.v.x);
+    dF[kCells] += double(lfy.v.x);
+    dF[2 * kCells] += double(lfz.v.x);
+  }
+  if (!fz_hi) {
+    dF[256] += double(lfx.v.y);
+    dF[kCells + 256] += double(lfy.v.y);
+    dF[2 * kCells + 256] += double(lfz.v.y);
+  }
+}
+
+// Reverse step, part 2 (node pairs): gbar streamed back to the pull sources,
+// weighted moments transposing the 17 Hermite coefficients, (dA/dM)^T at the
+// step's input moments.
+template <typename T>
+__global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjArgs d) {
+  extern __shared__ __align__(16) float2 f2buf[];
+  __shared__ int s_nbr[27];
+  __shared__ unsigned s_miss;
+  const int64_t blk = blockIdx.x;
+  f2::PairCtx cx = f2::pair_ctx();
+  const LamSource src{d.lamp};
+  f2::stream_pairs(src, a, blk, f2buf, s_nbr, s_miss, cx);
+  const int own = cx.own;
+  bool fz_lo = false, fz_hi = false;  // solid nodes: M'(y) = M(y)
+  if (cx.solid_any) {
+    fz_lo = a.solid[blk * kCells + own] != 0;
+    fz_hi = a.solid[blk * kCells + own + 256] != 0;
+  }
+  V2 out[kRows];
+  if (!(fz_lo && fz_hi)) {
+    V2 g[27];
+    f2::gather_all(f2buf, cx.own_s, cx.g13, g, std::make_integer_sequence<int, 27>{});
+    V2 gh_in[27];
+#pragma unroll
+    for (int j = 0; j < 27; ++j) gh_in[j] = g[26 - j];
+    const Coef<V2> gh = adjoint_moments(gh_in);
+    const Mom<V2> lm = coef_vjp(load_pair<T>(static_cast<const T*>(a.in), blk, own, a.scales_in), gh, V2(a.kxyzf));
+    out[0] = lm.drho;
+    out[1] = lm.ux;
+    out[2] = lm.uy;
+    out[3] = lm.uz;
+    out[4] = lm.sxx;
+    out[5] = lm.syy;
+    out[6] = lm.szz;
+    out[7] = lm.sxy;
+    out[8] = lm.sxz;
+    out[9] = lm.syz;
+  }
+  if (fz_lo || fz_hi) {
+    const LamSource ls{d.lam};
+    const PreMom<V2> q = ls.pair(blk, own);
+    const V2 lam[kRows] = {q.drho, q.jx, q.jy, q.jz, q.pxx, q.pyy, q.pzz, q.pxy, q.pxz, q.pyz};
+#pragma unroll
+    for (int r = 0; r < kRows; ++r)
+      out[r] = V2(fz_lo ? lam[r].v.x : out[r].v.x, fz_hi ? lam[r].v.y : out[r].v.y);
+  }
+  store_pair10(d.lam_out, blk, own, out, false, false);
+}
+
+template <typename T>
+cudaError_t launch_adj2(const StepArgs& a_in, const AdjArgs& d, cudaStream_t s) {
+  StepArgs a = a_in;
+  for (int k = 0; k < 3; ++k) a.fuf[k] = float(a.fu[k]);
+  a.tauf = float(a.tau);
+  a.omf = float(a.om);
+  a.kxyzf = float(a.kxyz);
+  const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_adj_pull2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_adj_push2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (a.nb == 0) return cudaSuccess;
+  k_adj_pull2<T><<<unsigned(a.nb), f2::kThreads, smem, s>>>(a, d);
+  k_adj_push2<T><<<unsigned(a.nb), f2::kThreads, smem, s>>>(a, d);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_adj(const StepArgs& a_in, const AdjArgs& d, cudaStream_t s) {
   StepArgs a = a_in;
@@ -412,7 +658,7 @@ cudaError_t adjoint_step(int storage, const StepArgs& a, const float* lam, float
   const AdjArgs d{lam, lamp, dF, lam_out};
   switch (storage) {
     case HLBM_STORE_F64: return launch_adj<double>(a, d, s);
-    case HLBM_STORE_F32: return launch_adj<float>(a, d, s);
+    case HLBM_STORE_F32: return launch_adj2<float>(a, d, s);
     default: return cudaErrorNotSupported;
   }
 }

@@ -26,6 +26,7 @@
 //     neighbour block not stored) and solid nodes copy their input.
 #include <utility>
 
+#include "f2_common.cuh"
 #include "hlbm_internal.h"
 #include "lbm_math.cuh"
 #include "v2.cuh"
@@ -33,362 +34,24 @@
 namespace hlbm {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kHaloPairs = 244;
+using namespace f2;
 
-__host__ __device__ constexpr int slot_of(int j) { return j < 13 ? j : j - 1; }
-
-struct OwnPush {
-  float2* f;
-  int XH[9], Y8[3], Z64[3];  // XH[(cx+1) + 3 (cy+1)] = x' ^ (y' >> 1)
-  bool swap[3];
-  V2 g13;
-  template <int J>
-  __device__ __forceinline__ void put(V2 v) {
-    if constexpr (J == 13) {
-      g13 = v;
-    } else {
-      constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
-      const int s = XH[(cx + 1) + 3 * (cy + 1)] + Y8[cy + 1] + Z64[cz + 1];
-      f[slot_of(J) * 256 + s] = swap[cz + 1] ? make_float2(v.v.y, v.v.x) : v.v;
-    }
-  }
-};
-
-constexpr int kTrash = 26 * 512;  // per-lane dummy float slots for masked halo stores
-
-// Halo pushes in a canonical orientation: the halo node lies just below the
-// block on the face axis and pushes the 9 directions whose component on that
-// axis is +1.  Threads on the upper face reflect their moments along the face
-// axis first (Eq. three_order_f is covariant under reflections), so canonical
-// direction J carries the population of its mirror image; d0 / d1 shift the
-// store to the mirror direction's slot (d1 for the mirrors that lie on the
-// other side of the rest index).  oka / okb: bit J set when the .x / .y value
-// of canonical direction J has a destination inside the block and a valid
-// source; other values go to the lane's trash slot.
-
-// x faces (AX = 0) and y faces (AX = 1): node pair a = (hx, hy, hz), b = hz + 4,
-// one stored pair of the same neighbour.  X / YH / Y8 / Z64 hold the actual
-// destination coordinates (swizzle parts) for canonical component c at [c+1];
-// ha[c+1]: node a lands in the high half of its pair slot.
-template <int AX>
-struct HaloXY {
-  float* f;
-  int X[3], YH[3], Y8[3], Z64[3], ha[3];
-  unsigned oka, okb;
-  int d0, d1, trash;
-  template <int J>
-  __device__ __forceinline__ void put(V2 v) {
-    constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
-    constexpr int c = AX == 0 ? cx : cy;
-    if constexpr (c == 1) {
-      constexpr bool cross = AX == 0 ? (cy == 0 && cz == 0) : (cz == 0);
-      const int p2 = 2 * (slot_of(J) * 256 + (X[cx + 1] ^ YH[cy + 1]) + Y8[cy + 1] + Z64[cz + 1]) + (cross ? d1 : d0);
-      const int h = ha[cz + 1];
-      f[((oka >> J) & 1u) ? p2 + h : trash] = v.v.x;
-      f[((okb >> J) & 1u) ? p2 + 1 - h : trash] = v.v.y;
-    }
-  }
-};
-
-// z faces: node pair a = (hx, hy, hz), b = (hx, hy + 5, hz); zoff addresses the
-// destination plane (z = 0: pair slot 0, low half; z = 7: pair slot 3, high half).
-struct HaloZ {
-  float* f;
-  int X[3], YHa[3], YHb[3], Y8a[3], Y8b[3];
-  int zoff;
-  unsigned oka, okb;
-  int d, trash;
-  template <int J>
-  __device__ __forceinline__ void put(V2 v) {
-    constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
-    if constexpr (cz == 1) {
-      const int base = 2 * (slot_of(J) * 256) + zoff + d;
-      f[((oka >> J) & 1u) ? base + 2 * ((X[cx + 1] ^ YHa[cy + 1]) + Y8a[cy + 1]) : trash] = v.v.x;
-      f[((okb >> J) & 1u) ? base + 2 * ((X[cx + 1] ^ YHb[cy + 1]) + Y8b[cy + 1]) : trash] = v.v.y;
-    }
-  }
-};
-
-__device__ __forceinline__ unsigned range_mask(int v) {
-  // bit (c+1) set when v + c lies in [0, 8), c in {-1, 0, 1}
-  return ((unsigned)(v - 1) < 8u ? 1u : 0u) | ((unsigned)v < 8u ? 2u : 0u) | ((unsigned)(v + 1) < 8u ? 4u : 0u);
-}
-
-// Bit j = (cx+1) + 3 (cy+1) + 9 (cz+1) set when bit cx+1 of vx, bit cy+1 of vy
-// and bit cz+1 of vz are all set (per-axis masks as from range_mask).
-__device__ __forceinline__ unsigned dir_mask(unsigned vx, unsigned vy, unsigned vz) {
-  const unsigned mx = vx * 0x1249249u;  // vx in every 3-bit group
-  const unsigned my = ((vy & 1u) * 0x7u | ((vy >> 1) & 1u) * 0x38u | ((vy >> 2) & 1u) * 0x1C0u) * 0x40201u;
-  const unsigned mz = (vz & 1u) * 0x1FFu | ((vz >> 1) & 1u) * 0x3FE00u | ((vz >> 2) & 1u) * 0x7FC0000u;
-  return mx & my & mz;
-}
-
-// Half-way bounce-back: bit k of mask = the pull source x - c_k of this node is
-// a wall or a solid node, so slot k of the node receives its own population opp(k).
-struct BouncePush {
-  float* f;
-  int own;  // pair slot
-  unsigned mlo, mhi;
-  template <int J>
-  __device__ __forceinline__ void put(V2 v) {
-    if constexpr (J != 13) {
-      constexpr int K = 26 - J;
-      if ((mlo >> K) & 1u) f[2 * (slot_of(K) * 256 + own)] = v.v.x;
-      if ((mhi >> K) & 1u) f[2 * (slot_of(K) * 256 + own) + 1] = v.v.y;
-    }
-  }
-};
-
-template <int J>
-__device__ __forceinline__ void gather_one(const float2* f, int own, V2 g13, V2 (&g)[27]) {
-  if constexpr (J == 13)
-    g[13] = g13;
-  else
-    g[J] = V2(f[slot_of(J) * 256 + own]);
-}
-
-template <int... Js>
-__device__ __forceinline__ void gather_all(const float2* f, int own, V2 g13, V2 (&g)[27],
-                                           std::integer_sequence<int, Js...>) {
-  (gather_one<Js>(f, own, g13, g), ...);
-}
-
-// Halo work of thread t < kHaloPairs: cls 0 = x faces (threads 0-63), 1 = y
-// faces (64-143), 2 = z faces (144-243), so that only one warp mixes two
-// classes; mir = upper face.  Node pair a = (ax, ay, az), b = (bx, by, bz).
-__device__ __forceinline__ void halo_pair(int t, int& cls, bool& mir, int& ax, int& ay, int& az, int& bx, int& by,
-                                          int& bz) {
-  if (t < 64) {
-    const int q = t & 31;
-    cls = 0;
-    mir = t >= 32;
-    ax = bx = mir ? 8 : -1;
-    ay = by = q & 7;
-    az = q >> 3;
-    bz = az + 4;
-  } else if (t < 144) {
-    const int q = t < 104 ? t - 64 : t - 104;
-    cls = 1;
-    mir = t >= 104;
-    ax = bx = q % 10 - 1;
-    ay = by = mir ? 8 : -1;
-    az = q / 10;
-    bz = az + 4;
-  } else {
-    const int q = t < 194 ? t - 144 : t - 194;
-    cls = 2;
-    mir = t >= 194;
-    ax = bx = q % 10 - 1;
-    ay = q / 10 - 1;
-    by = ay + 5;
-    az = bz = mir ? 8 : -1;
-  }
-}
-
-__device__ __forceinline__ int block_dir(int hx, int hy, int hz) {
-  const int dx = hx < 0 ? -1 : (hx > 7 ? 1 : 0);
-  const int dy = hy < 0 ? -1 : (hy > 7 ? 1 : 0);
-  const int dz = hz < 0 ? -1 : (hz > 7 ? 1 : 0);
-  return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-}
-
-__device__ __forceinline__ bool touches_missing(int x, int y, int z, unsigned miss) {
-  const unsigned mx = 2u | (x == 0 ? 1u : 0u) | (x == 7 ? 4u : 0u);
-  const unsigned my = 2u | (y == 0 ? 1u : 0u) | (y == 7 ? 4u : 0u);
-  const unsigned mz = 2u | (z == 0 ? 1u : 0u) | (z == 7 ? 4u : 0u);
-  unsigned touched = 0;
-#pragma unroll
-  for (int iz = 0; iz < 3; ++iz)
-#pragma unroll
-    for (int iy = 0; iy < 3; ++iy)
-      if (((mz >> iz) & 1u) && ((my >> iy) & 1u)) touched |= mx << (3 * iy + 9 * iz);
-  return (touched & miss) != 0u;
-}
-
-__device__ __forceinline__ Mom<V2> pack(const Mom<float>& a, const Mom<float>& b) {
-  Mom<V2> m;
-  m.drho = V2(a.drho, b.drho);
-  m.ux = V2(a.ux, b.ux);
-  m.uy = V2(a.uy, b.uy);
-  m.uz = V2(a.uz, b.uz);
-  m.sxx = V2(a.sxx, b.sxx);
-  m.syy = V2(a.syy, b.syy);
-  m.szz = V2(a.szz, b.szz);
-  m.sxy = V2(a.sxy, b.sxy);
-  m.sxz = V2(a.sxz, b.sxz);
-  m.syz = V2(a.syz, b.syz);
-  return m;
-}
-
-__device__ __forceinline__ Mom<V2> select_halves(const Mom<V2>& a, const Mom<V2>& b, bool lo_b, bool hi_b) {
-  // per half: b where the flag is set, else a
-  auto sel = [&](V2 x, V2 y) { return V2(lo_b ? y.v.x : x.v.x, hi_b ? y.v.y : x.v.y); };
-  Mom<V2> r;
-  r.drho = sel(a.drho, b.drho);
-  r.ux = sel(a.ux, b.ux);
-  r.uy = sel(a.uy, b.uy);
-  r.uz = sel(a.uz, b.uz);
-  r.sxx = sel(a.sxx, b.sxx);
-  r.syy = sel(a.syy, b.syy);
-  r.szz = sel(a.szz, b.szz);
-  r.sxy = sel(a.sxy, b.sxy);
-  r.sxz = sel(a.sxz, b.sxz);
-  r.syz = sel(a.syz, b.syz);
-  return r;
-}
-
-__device__ __forceinline__ Mom<V2> zero_pair() {
-  Mom<V2> m;
-  m.drho = m.ux = m.uy = m.uz = m.sxx = m.syy = m.szz = m.sxy = m.sxz = m.syz = V2(0.f);
-  return m;
-}
-
-// One 8^3 block: push the own and halo populations into the destination-
-// indexed shared buffer, then gather, project and collide.  Leaves shared
-// memory in use: callers that process another block must barrier first.
+// One 8^3 block of the forward step: stream the populations through shared
+// memory, then gather, project and collide.  Leaves shared memory in use:
+// callers that process another block must barrier first.
 template <typename T>
 __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, float2* f2buf, int* s_nbr,
                                          unsigned& s_miss) {
-  float* fbuf = reinterpret_cast<float*>(f2buf);
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int x = lane & 7, y = (lane >> 3) + ((w & 1) << 2), z0 = w >> 1;
-  const int own = x + 8 * y + 64 * z0;                 // pair slot in global storage
-  const int own_s = (x ^ (y >> 1)) + 8 * y + 64 * z0;  // pair slot in shared memory
+  PairCtx cx = pair_ctx();
+  const int x = cx.x, y = cx.y, z0 = cx.z0, own = cx.own, own_s = cx.own_s;
   const T* in = static_cast<const T*>(a.in);
   T* out = static_cast<T*>(a.out);
   const int dom = a.blk_dom != nullptr ? a.blk_dom[blk] : 0;
   const Scales* sc_in = a.scales_in != nullptr ? a.scales_in + dom : nullptr;
   const Scales* sc_out = a.scales_out != nullptr ? a.scales_out + dom : nullptr;
-
-  if (t < 32) {
-    const int v = t < 27 ? a.nbr[blk * 27 + t] : 0;
-    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && v == kMissing);
-    if (t < 27) s_nbr[t] = v;
-    if (t == 0) s_miss = mb;
-  }
-  const uint8_t bf = a.bflags != nullptr ? a.bflags[blk] : 0;
-  const bool solid_any = (bf & kBlockSolidNear) != 0;
-
-  // own node pair: issue the loads early
-  const Mom<V2> m = load_pair<T>(in, blk, own, sc_in);
-  int cls = -1, hax = 0, hay = 0, haz = 0, hbx = 0, hby = 0, hbz = 0;
-  bool mir = false;
-  if (t < kHaloPairs) halo_pair(t, cls, mir, hax, hay, haz, hbx, hby, hbz);
-  __syncthreads();  // s_nbr, s_miss
-
-  bool va = false, vb = false;
-  Mom<V2> hm = zero_pair();
-  if (t < kHaloPairs) {
-    const int na = s_nbr[block_dir(hax, hay, haz)], nb = s_nbr[block_dir(hbx, hby, hbz)];
-    const int sa = (hax & 7) + 8 * (hay & 7) + 64 * (haz & 7), sb = (hbx & 7) + 8 * (hby & 7) + 64 * (hbz & 7);
-    va = na >= 0 && !(solid_any && a.solid[int64_t(na) * kCells + sa]);
-    vb = nb >= 0 && !(solid_any && a.solid[int64_t(nb) * kCells + sb]);
-    if (cls < 2) {  // x / y faces: a and b are one stored pair of the same neighbour
-      if (na >= 0) hm = load_pair<T>(in, na, sa, sc_in);
-    } else {
-      Mom<float> la, lb;
-      la.drho = la.ux = la.uy = la.uz = la.sxx = la.syy = la.szz = la.sxy = la.sxz = la.syz = 0.f;
-      lb = la;
-      if (na >= 0) la = load_node<T>(in, na, sa, sc_in);
-      if (nb >= 0) lb = load_node<T>(in, nb, sb, sc_in);
-      hm = pack(la, lb);
-    }
-  }
-
-  // A. push the own pair
-  const V2 kxyz = V2(a.kxyzf);
-  OwnPush op;
-  op.f = f2buf;
-#pragma unroll
-  for (int c = -1; c <= 1; ++c) {
-    op.Y8[c + 1] = 8 * ((y + c) & 7);
-    op.Z64[c + 1] = 64 * ((z0 + c) & 3);
-    op.swap[c + 1] = (((z0 + c) & 7) >> 2) != 0;
-#pragma unroll
-    for (int cx = -1; cx <= 1; ++cx) op.XH[(cx + 1) + 3 * (c + 1)] = ((x + cx) & 7) ^ (((y + c) & 7) >> 1);
-  }
-  emit_all(make_coef(m, kxyz), op);
-  __syncthreads();
-
-  // B. halo pairs and bounce-back
-  if (t < kHaloPairs && (va || vb)) {
-    // reflect the upper-face pairs along the face axis (u and S components with
-    // an odd count of that axis change sign)
-    const V2 sg = V2(mir ? -1.f : 1.f);
-    if (cls == 0) {
-      hm.ux = hm.ux * sg;
-      hm.sxy = hm.sxy * sg;
-      hm.sxz = hm.sxz * sg;
-    } else if (cls == 1) {
-      hm.uy = hm.uy * sg;
-      hm.sxy = hm.sxy * sg;
-      hm.syz = hm.syz * sg;
-    } else {
-      hm.uz = hm.uz * sg;
-      hm.sxz = hm.sxz * sg;
-      hm.syz = hm.syz * sg;
-    }
-    const Coef<V2> c = make_coef(hm, kxyz);
-    const int trash = kTrash + lane;
-    const unsigned ma = va ? ~0u : 0u, mb = vb ? ~0u : 0u;
-    if (cls < 2) {
-      int Zc[3], HA[3];
-#pragma unroll
-      for (int k = -1; k <= 1; ++k) {
-        Zc[k + 1] = 64 * ((haz + k) & 3);
-        HA[k + 1] = ((haz + k) & 7) >> 2;
-      }
-      const unsigned vza = range_mask(haz), vzb = range_mask(hbz);
-      const int face_dst = mir ? 7 : 0;  // destination coordinate on the face axis
-      if (cls == 0) {
-        int YH[3], Y8[3];
-#pragma unroll
-        for (int k = -1; k <= 1; ++k) {
-          YH[k + 1] = ((hay + k) & 7) >> 1;
-          Y8[k + 1] = 8 * ((hay + k) & 7);
-        }
-        const unsigned vy = range_mask(hay);
-        HaloXY<0> s{fbuf, {0, 0, face_dst}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Zc[0], Zc[1], Zc[2]},
-                    {HA[0], HA[1], HA[2]}, dir_mask(7u, vy, vza) & ma, dir_mask(7u, vy, vzb) & mb,
-                    mir ? -1024 : 0, mir ? -512 : 0, trash};
-        emit_all(c, s);
-      } else {
-        int X[3];
-#pragma unroll
-        for (int k = -1; k <= 1; ++k) X[k + 1] = (hax + k) & 7;
-        const unsigned vx = range_mask(hax);
-        HaloXY<1> s{fbuf, {X[0], X[1], X[2]}, {0, 0, face_dst >> 1}, {0, 0, 8 * face_dst}, {Zc[0], Zc[1], Zc[2]},
-                    {HA[0], HA[1], HA[2]}, dir_mask(vx, 7u, vza) & ma, dir_mask(vx, 7u, vzb) & mb,
-                    mir ? -3072 : 0, mir ? -2560 : 0, trash};
-        emit_all(c, s);
-      }
-    } else {
-      int X[3], YHa[3], YHb[3], Y8a[3], Y8b[3];
-#pragma unroll
-      for (int k = -1; k <= 1; ++k) {
-        X[k + 1] = (hax + k) & 7;
-        YHa[k + 1] = ((hay + k) & 7) >> 1;
-        YHb[k + 1] = ((hby + k) & 7) >> 1;
-        Y8a[k + 1] = 8 * ((hay + k) & 7);
-        Y8b[k + 1] = 8 * ((hby + k) & 7);
-      }
-      const unsigned vx = range_mask(hax);
-      HaloZ s{fbuf, {X[0], X[1], X[2]}, {YHa[0], YHa[1], YHa[2]}, {YHb[0], YHb[1], YHb[2]},
-              {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, mir ? 2 * 64 * 3 + 1 : 0,
-              dir_mask(vx, range_mask(hay), 7u) & ma, dir_mask(vx, range_mask(hby), 7u) & mb, mir ? -17 * 512 : 0,
-              trash};
-      emit_all(c, s);
-    }
-  }
-  if (bf & kBlockBounce) {  // block-uniform
-    const unsigned mlo_b = a.bmask[blk * kCells + own], mhi_b = a.bmask[blk * kCells + own + 256];
-    if ((mlo_b | mhi_b) != 0u) {
-      BouncePush bp{fbuf, own_s, mlo_b, mhi_b};
-      emit_all(make_coef(load_pair<T>(in, blk, own, sc_in), kxyz), bp);
-    }
-  }
-  __syncthreads();
+  const MomSource<T> src{in, sc_in, V2(a.kxyzf)};
+  stream_pairs(src, a, blk, f2buf, s_nbr, s_miss, cx);
+  const bool solid_any = cx.solid_any;
 
   // C. gather, project, collide
   bool copy_lo = false, copy_hi = false;
@@ -405,7 +68,7 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
     mo = load_pair<T>(in, blk, own, sc_in);
   } else {
     V2 g[27];
-    gather_all(f2buf, own_s, op.g13, g, std::make_integer_sequence<int, 27>{});
+    gather_all(f2buf, own_s, cx.g13, g, std::make_integer_sequence<int, 27>{});
     const PreMom<V2> p = project(g);
     V2 fx, fy, fz;
     if (a.F != nullptr) {

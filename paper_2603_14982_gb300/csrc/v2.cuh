@@ -26,5 +26,6 @@ __device__ __forceinline__ V2 mad(V2 a, V2 b, V2 c) { return V2(__ffma2_rn(a.v, 
 // correctly rounded reciprocal of each lane (equal to 1.0f / x)
 __device__ __forceinline__ V2 inv(V2 a) { return V2(__frcp_rn(a.v.x), __frcp_rn(a.v.y)); }
 __device__ __forceinline__ V2& operator+=(V2& a, V2 b) { return a = a + b; }
+__device__ __forceinline__ V2& operator-=(V2& a, V2 b) { return a = a - b; }
 
 }  // namespace hlbm
