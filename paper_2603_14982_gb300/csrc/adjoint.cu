@@ -3,16 +3,19 @@
 // has no adjoint; the forward it reverses is Sec. 3.1 with the Guo force and
 // the mixture relaxation time of Sec. 4.
 //
-// Per reverse step (lambda = dL/dM of the step's output):
-//   k_adj_pull: every node recomputes its pulled pre-collision moments p from
-//     the step's input M (the same pull as the forward), applies the transposed
-//     collision Jacobian to lambda, writes lambda_p and adds dL/dF (FP64).
-//   k_adj_push: every node x forms gbar_i(x) = P_i^T lambda_p(x) and hands it to
-//     its pull source x - c_i through a shared buffer indexed by the destination
-//     (wall and solid slots mirror the bounce-back); every source y gathers what
-//     it fed, takes the weighted moments that transpose its 17 Hermite
-//     coefficients and applies (dA/dM)^T at M(y): lambda of the step's input.
-// Both kernels gather; no atomics, so the result is deterministic.
+// Per reverse step (lambda = dL/dM of the step's output), FP32 storage:
+//   the recomputed forward step has recorded its pre-collision moments p;
+//   k_adj_collide (elementwise) applies the transposed collision Jacobian to
+//     lambda: lambda_p, and adds dL/dF (FP64 sums);
+//   k_adj_push2 (node pairs): every node x forms gbar_i(x) = P_i^T lambda_p(x)
+//     and hands it back to its pull source x - c_i through the destination-
+//     indexed shared buffer of the forward kernel (bounce-back slots take the
+//     node's own value); every source y gathers what it fed, takes the weighted
+//     moments that transpose its 17 Hermite coefficients and applies
+//     (dA/dM)^T at M(y): lambda of the step's input.
+// FP64 storage: one node per thread; k_adj_pull recomputes the pull itself,
+// k_adj_push is the same reverse stream on a source-indexed buffer.
+// All kernels gather; no atomics, so the result is deterministic.
 #include <cuda_runtime.h>
 
 #include <utility>
@@ -237,10 +240,12 @@ struct GbEmit {
 };
 
 struct AdjArgs {
-  const float* lam;   // dL/dM of the step's output [nb][10][512]
-  float* lamp;        // dL/dp of the pre-collision moments [nb][10][512]
-  double* dF;         // accumulated dL/dF [nb][3][512]
-  float* lam_out;     // dL/dM of the step's input [nb][10][512]
+  const float* lam;       // dL/dM of the step's output [nb][10][512] (node-pair push: copied at solid nodes)
+  float* lamp;            // dL/dp of the pre-collision moments [nb][10][512]
+  double* dF;             // accumulated dL/dF [nb][3][512]
+  float* lam_out;         // dL/dM of the step's input [nb][10][512]
+  const float* pre_prev;  // fused push: recorded p of the previous step
+  float* lamp_out;        // fused push: dL/dp of the previous step
 };
 
 // Shared part: the block's ext buffer filled with the forward pull (PULL) or
@@ -468,36 +473,16 @@ __device__ __forceinline__ void store_pair10(float* p, int64_t blk, int cell, co
   }
 }
 
-// Reverse step, part 1 (node pairs): recomputed pull and projection, then
-// lambda_p = (dC/dp)^T lambda' and dL/dF += (dC/dF)^T lambda' (FP64 sums).
-template <typename T>
-__global__ void __launch_bounds__(f2::kThreads, 2) k_adj_pull2(StepArgs a, AdjArgs d) {
-  extern __shared__ __align__(16) float2 f2buf[];
-  __shared__ int s_nbr[27];
-  __shared__ unsigned s_miss;
-  const int64_t blk = blockIdx.x;
-  f2::PairCtx cx = f2::pair_ctx();
-  const f2::MomSource<T> src{static_cast<const T*>(a.in), a.scales_in, V2(a.kxyzf)};
-  f2::stream_pairs(src, a, blk, f2buf, s_nbr, s_miss, cx);
-  const int own = cx.own;
-  bool fz_lo = false, fz_hi = false;  // solid nodes copy their input: no dependence on the pulls or on F
-  if (cx.solid_any) {
-    fz_lo = a.solid[blk * kCells + own] != 0;
-    fz_hi = a.solid[blk * kCells + own + 256] != 0;
-  }
-  V2 out[kRows];
-  if (fz_lo && fz_hi) {
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) out[r] = V2(0.f);
-    store_pair10(d.lamp, blk, own, out, true, true);
-    return;
-  }
-  V2 g[27];
-  f2::gather_all(f2buf, cx.own_s, cx.g13, g, std::make_integer_sequence<int, 27>{});
-  const PreMom<V2> p = project(g);
+// Transposed collision of a node pair (cells c and c + 256 of block blk) from
+// its recorded pre-collision moments p and lambda' = dL/dM of the step's
+// output: stores lambda_p = (dC/dp)^T lambda' and adds (dC/dF)^T lambda' to dF
+// (FP64).  Solid halves (fz_lo / fz_hi) get lambda_p = 0 and no force term.
+__device__ __forceinline__ void collide_adj_pair(const StepArgs& a, int64_t blk, int c, const PreMom<V2>& p,
+                                                 const Mom<V2>& lo, bool fz_lo, bool fz_hi, float* lamp,
+                                                 double* dF_all) {
   V2 fx, fy, fz;
   if (a.F != nullptr) {
-    const float* Fp = a.F + blk * 3 * kCells + own;
+    const float* Fp = a.F + blk * 3 * kCells + c;
     fx = V2(__ldg(Fp), __ldg(Fp + 256));
     fy = V2(__ldg(Fp + kCells), __ldg(Fp + kCells + 256));
     fz = V2(__ldg(Fp + 2 * kCells), __ldg(Fp + 2 * kCells + 256));
@@ -508,38 +493,13 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_pull2(StepArgs a, AdjAr
   }
   V2 om = V2(a.omf);
   if (a.eps != nullptr)
-    om = inv(V2(a.tauf) * V2(__ldg(a.eps + blk * kCells + own), __ldg(a.eps + blk * kCells + own + 256)));
-  const Mom<V2> lo = [&] {
-    const LamSource ls{d.lam};
-    const PreMom<V2> q = ls.pair(blk, own);  // same 10-row layout, read as moments
-    Mom<V2> m;
-    m.drho = q.drho;
-    m.ux = q.jx;
-    m.uy = q.jy;
-    m.uz = q.jz;
-    m.sxx = q.pxx;
-    m.syy = q.pyy;
-    m.szz = q.pzz;
-    m.sxy = q.pxy;
-    m.sxz = q.pxz;
-    m.syz = q.pyz;
-    return m;
-  }();
+    om = inv(V2(a.tauf) * V2(__ldg(a.eps + blk * kCells + c), __ldg(a.eps + blk * kCells + c + 256)));
   PreMom<V2> lp;
   V2 lfx, lfy, lfz;
   collide_vjp(p, fx, fy, fz, om, lo, lp, lfx, lfy, lfz);
-  out[0] = lp.drho;
-  out[1] = lp.jx;
-  out[2] = lp.jy;
-  out[3] = lp.jz;
-  out[4] = lp.pxx;
-  out[5] = lp.pyy;
-  out[6] = lp.pzz;
-  out[7] = lp.pxy;
-  out[8] = lp.pxz;
-  out[9] = lp.pyz;
-  store_pair10(d.lamp, blk, own, out, fz_lo, fz_hi);
-  double* dF = d.dF + blk * 3 * kCells + own;
+  const V2 out[kRows] = {lp.drho, lp.jx, lp.jy, lp.jz, lp.pxx, lp.pyy, lp.pzz, lp.pxy, lp.pxz, lp.pyz};
+  store_pair10(lamp, blk, c, out, fz_lo, fz_hi);
+  double* dF = dF_all + blk * 3 * kCells + c;
   if (!fz_lo) {
     dF[0] += double(lfx.v.x);
     dF[kCells] += double(lfy.v.x);
@@ -552,10 +512,29 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_pull2(StepArgs a, AdjAr
   }
 }
 
+__device__ __forceinline__ Mom<V2> as_mom(const PreMom<V2>& q) {
+  Mom<V2> m;
+  m.drho = q.drho;
+  m.ux = q.jx;
+  m.uy = q.jy;
+  m.uz = q.jz;
+  m.sxx = q.pxx;
+  m.syy = q.pyy;
+  m.szz = q.pzz;
+  m.sxy = q.pxy;
+  m.sxz = q.pxz;
+  m.syz = q.pyz;
+  return m;
+}
+
 // Reverse step, part 2 (node pairs): gbar streamed back to the pull sources,
 // weighted moments transposing the 17 Hermite coefficients, (dA/dM)^T at the
-// step's input moments.
-template <typename T>
+// step's input moments: lambda of the step's input.  kFuse: instead of storing
+// it, go on with part 1 of the previous step at the same node (its transposed
+// collision needs only this node's lambda and recorded p), writing that step's
+// lambda_p to d.lamp_out and its force term to d.dF.  Solid nodes keep
+// lambda = d.lam (nothing streams into them).
+template <typename T, bool kFuse>
 __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjArgs d) {
   extern __shared__ __align__(16) float2 f2buf[];
   __shared__ int s_nbr[27];
@@ -570,7 +549,7 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
     fz_lo = a.solid[blk * kCells + own] != 0;
     fz_hi = a.solid[blk * kCells + own + 256] != 0;
   }
-  V2 out[kRows];
+  Mom<V2> lm;
   if (!(fz_lo && fz_hi)) {
     V2 g[27];
     f2::gather_all(f2buf, cx.own_s, cx.g13, g, std::make_integer_sequence<int, 27>{});
@@ -578,49 +557,58 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
 #pragma unroll
     for (int j = 0; j < 27; ++j) gh_in[j] = g[26 - j];
     const Coef<V2> gh = adjoint_moments(gh_in);
-    const Mom<V2> lm = coef_vjp(load_pair<T>(static_cast<const T*>(a.in), blk, own, a.scales_in), gh, V2(a.kxyzf));
-    out[0] = lm.drho;
-    out[1] = lm.ux;
-    out[2] = lm.uy;
-    out[3] = lm.uz;
-    out[4] = lm.sxx;
-    out[5] = lm.syy;
-    out[6] = lm.szz;
-    out[7] = lm.sxy;
-    out[8] = lm.sxz;
-    out[9] = lm.syz;
+    lm = coef_vjp(load_pair<T>(static_cast<const T*>(a.in), blk, own, a.scales_in), gh, V2(a.kxyzf));
   }
-  if (fz_lo || fz_hi) {
-    const LamSource ls{d.lam};
-    const PreMom<V2> q = ls.pair(blk, own);
-    const V2 lam[kRows] = {q.drho, q.jx, q.jy, q.jz, q.pxx, q.pyy, q.pzz, q.pxy, q.pxz, q.pyz};
+  if constexpr (kFuse) {
+    if (fz_lo && fz_hi) {
+      V2 z[kRows];
 #pragma unroll
-    for (int r = 0; r < kRows; ++r)
-      out[r] = V2(fz_lo ? lam[r].v.x : out[r].v.x, fz_hi ? lam[r].v.y : out[r].v.y);
+      for (int r = 0; r < kRows; ++r) z[r] = V2(0.f);
+      store_pair10(d.lamp_out, blk, own, z, true, true);
+      return;
+    }
+    collide_adj_pair(a, blk, own, LamSource{d.pre_prev}.pair(blk, own), lm, fz_lo, fz_hi, d.lamp_out, d.dF);
+  } else {
+    V2 out[kRows] = {lm.drho, lm.ux, lm.uy, lm.uz, lm.sxx, lm.syy, lm.szz, lm.sxy, lm.sxz, lm.syz};
+    if (fz_lo || fz_hi) {
+      const PreMom<V2> q = LamSource{d.lam}.pair(blk, own);
+      const V2 lam[kRows] = {q.drho, q.jx, q.jy, q.jz, q.pxx, q.pyy, q.pzz, q.pxy, q.pxz, q.pyz};
+#pragma unroll
+      for (int r = 0; r < kRows; ++r)
+        out[r] = V2(fz_lo ? lam[r].v.x : out[r].v.x, fz_hi ? lam[r].v.y : out[r].v.y);
+    }
+    store_pair10(d.lam_out, blk, own, out, false, false);
   }
-  store_pair10(d.lam_out, blk, own, out, false, false);
 }
 
-template <typename T>
-cudaError_t launch_adj2(const StepArgs& a_in, const AdjArgs& d, cudaStream_t s) {
+// Reverse step, part 1 from recorded pre-collision moments p (elementwise,
+// one thread per node pair: cells t and t + 256).
+__global__ void __launch_bounds__(256) k_adj_collide(StepArgs a, const float* __restrict__ pre, AdjArgs d) {
+  const int64_t blk = blockIdx.x;
+  const int t = threadIdx.x;
+  bool fz_lo = false, fz_hi = false;
+  if (a.bflags != nullptr && (a.bflags[blk] & kBlockSolidNear)) {
+    fz_lo = a.solid[blk * kCells + t] != 0;
+    fz_hi = a.solid[blk * kCells + t + 256] != 0;
+  }
+  if (fz_lo && fz_hi) {
+    V2 z[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) z[r] = V2(0.f);
+    store_pair10(d.lamp, blk, t, z, true, true);
+    return;
+  }
+  collide_adj_pair(a, blk, t, LamSource{pre}.pair(blk, t), as_mom(LamSource{d.lam}.pair(blk, t)), fz_lo, fz_hi,
+                   d.lamp, d.dF);
+}
+
+StepArgs with_floats(const StepArgs& a_in) {
   StepArgs a = a_in;
   for (int k = 0; k < 3; ++k) a.fuf[k] = float(a.fu[k]);
   a.tauf = float(a.tau);
   a.omf = float(a.om);
   a.kxyzf = float(a.kxyz);
-  const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_adj_pull2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_adj_push2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  if (a.nb == 0) return cudaSuccess;
-  k_adj_pull2<T><<<unsigned(a.nb), f2::kThreads, smem, s>>>(a, d);
-  k_adj_push2<T><<<unsigned(a.nb), f2::kThreads, smem, s>>>(a, d);
-  return cudaGetLastError();
+  return a;
 }
 
 template <typename T>
@@ -658,9 +646,51 @@ cudaError_t adjoint_step(int storage, const StepArgs& a, const float* lam, float
   const AdjArgs d{lam, lamp, dF, lam_out};
   switch (storage) {
     case HLBM_STORE_F64: return launch_adj<double>(a, d, s);
-    case HLBM_STORE_F32: return launch_adj2<float>(a, d, s);
     default: return cudaErrorNotSupported;
   }
+}
+
+cudaError_t adjoint_collide(const StepArgs& a_in, const float* pre, const float* lam, float* lamp, double* dF,
+                            cudaStream_t s) {
+  if (a_in.nb == 0) return cudaSuccess;
+  const StepArgs a = with_floats(a_in);
+  const AdjArgs d{lam, lamp, dF, nullptr};
+  k_adj_collide<<<unsigned(a.nb), 256, 0, s>>>(a, pre, d);
+  return cudaGetLastError();
+}
+
+template <bool kFuse>
+cudaError_t launch_push2(const StepArgs& a_in, const AdjArgs& d, cudaStream_t s) {
+  const StepArgs a = with_floats(a_in);
+  const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_adj_push2<float, kFuse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (a.nb == 0) return cudaSuccess;
+  k_adj_push2<float, kFuse><<<unsigned(a.nb), f2::kThreads, smem, s>>>(a, d);
+  return cudaGetLastError();
+}
+
+cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp, float* lam_out, cudaStream_t s) {
+  AdjArgs d{};
+  d.lam = lam;
+  d.lamp = const_cast<float*>(lamp);
+  d.lam_out = lam_out;
+  return launch_push2<false>(a, d, s);
+}
+
+cudaError_t adjoint_push_collide(const StepArgs& a, const float* lamp, const float* pre_prev, float* lamp_out,
+                                 double* dF, cudaStream_t s) {
+  AdjArgs d{};
+  d.lamp = const_cast<float*>(lamp);
+  d.pre_prev = pre_prev;
+  d.lamp_out = lamp_out;
+  d.dF = dF;
+  return launch_push2<true>(a, d, s);
 }
 
 cudaError_t adjoint_dF_to_float(const double* dF, float* out, int64_t n, cudaStream_t s) {

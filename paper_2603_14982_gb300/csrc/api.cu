@@ -653,15 +653,24 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
     if (r == HLBM_OK) tmp.push_back(*out);
     return r;
   };
-  void *lam0, *lam1, *lamp, *dF;
-  std::vector<void*> seg(size_t(K), nullptr);
+  // FP32 storage records the pre-collision moments of every recomputed step
+  // (one float32 buffer per step of a segment), so the reverse step needs no
+  // second streaming pass; FP64 storage recomputes the pull in its reverse step.
+  const bool record = h->cfg.storage == HLBM_STORE_F32;
+  void *lam0, *lam1, *lamp, *lamp2, *dF;
+  std::vector<void*> seg(size_t(K) + 1, nullptr), pre(record ? size_t(K) : 0, nullptr);
   if ((rc = get(lam_elems * 4, &lam0)) || (rc = get(lam_elems * 4, &lam1)) || (rc = get(lam_elems * 4, &lamp)) ||
-      (rc = get(size_t(nb) * 3 * kCells * sizeof(double), &dF))) {
+      (rc = get(lam_elems * 4, &lamp2)) || (rc = get(size_t(nb) * 3 * kCells * sizeof(double), &dF))) {
     release_all();
     return rc;
   }
-  for (int i = 1; i < K; ++i)
+  for (int i = 1; i <= (record ? K : K - 1); ++i)
     if ((rc = get(bytes, &seg[i]))) {
+      release_all();
+      return rc;
+    }
+  for (int i = 0; i < int(pre.size()); ++i)
+    if ((rc = get(lam_elems * 4, &pre[i]))) {
       release_all();
       return rc;
     }
@@ -674,6 +683,38 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
   for (int s = n_seg - 1; s >= 0 && e == cudaSuccess; --s) {
     const int t0 = s * K, ns = (n - t0) < K ? (n - t0) : K;
     seg[0] = h->ckpt[s];
+    if (record) {
+      // lam[0]: dL/dM of the final state (kept: solid nodes keep it for all
+      // steps); lam[1]: dL/dM at the segment boundary.  Per segment: the
+      // transposed collision of its last step, then for every step i > 0 its
+      // reverse stream fused with the transposed collision of step i - 1, then
+      // the reverse stream of the first step (not needed for the first segment:
+      // only dL/dF is returned).
+      float* lp[2] = {static_cast<float*>(lamp), static_cast<float*>(lamp2)};
+      int q = 0;
+      for (int i = 0; i < ns && e == cudaSuccess; ++i) {  // recompute the segment, keeping states and p
+        a.in = seg[i];
+        a.out = seg[i + 1];
+        a.pre_out = static_cast<float*>(pre[i]);
+        e = launch_stream_collide_record(a, h->stream);
+      }
+      a.pre_out = nullptr;
+      a.in = seg[ns - 1];
+      if (e == cudaSuccess)
+        e = adjoint_collide(a, static_cast<const float*>(pre[ns - 1]), s == n_seg - 1 ? lam[0] : lam[1], lp[q],
+                            static_cast<double*>(dF), h->stream);
+      for (int i = ns - 1; i >= 1 && e == cudaSuccess; --i) {
+        a.in = seg[i];
+        e = adjoint_push_collide(a, lp[q], static_cast<const float*>(pre[i - 1]), lp[1 - q], static_cast<double*>(dF),
+                                 h->stream);
+        q = 1 - q;
+      }
+      if (s > 0 && e == cudaSuccess) {
+        a.in = seg[0];
+        e = adjoint_push(a, lam[0], lp[q], lam[1], h->stream);
+      }
+      continue;
+    }
     for (int i = 1; i < ns && e == cudaSuccess; ++i) {  // recompute the segment's states
       a.in = seg[i - 1];
       a.out = seg[i];

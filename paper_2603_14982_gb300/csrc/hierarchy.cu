@@ -237,18 +237,59 @@ __global__ void __launch_bounds__(512) k_iface_count(const int32_t* __restrict__
   }
 }
 
-__global__ void k_iface_scan(int64_t* __restrict__ counts, int64_t nb, int64_t* __restrict__ totals) {
-  if (threadIdx.x != 0) return;
-  int64_t rd = 0, ru = 0;
-  for (int64_t b = 0; b < nb; ++b) {
+// Exclusive scan of the (down, up) counts of nb blocks in place, totals to
+// totals[0..1]: one CTA, each thread scans a contiguous run of blocks.
+__global__ void __launch_bounds__(1024) k_iface_scan(int64_t* __restrict__ counts, int64_t nb,
+                                                     int64_t* __restrict__ totals) {
+  __shared__ int64_t s_d[32], s_u[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+  const int64_t per = (nb + blockDim.x - 1) / blockDim.x;
+  const int64_t b0 = min(nb, int64_t(t) * per), b1 = min(nb, b0 + per);
+  int64_t sd = 0, su = 0;
+  for (int64_t b = b0; b < b1; ++b) {
+    sd += counts[2 * b];
+    su += counts[2 * b + 1];
+  }
+  int64_t id = sd, iu = su;  // inclusive warp scan
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t vd = __shfl_up_sync(0xffffffffu, id, o), vu = __shfl_up_sync(0xffffffffu, iu, o);
+    if (lane >= o) {
+      id += vd;
+      iu += vu;
+    }
+  }
+  if (lane == 31) {
+    s_d[w] = id;
+    s_u[w] = iu;
+  }
+  __syncthreads();
+  if (w == 0) {
+    int64_t xd = lane < nw ? s_d[lane] : 0, xu = lane < nw ? s_u[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t vd = __shfl_up_sync(0xffffffffu, xd, o), vu = __shfl_up_sync(0xffffffffu, xu, o);
+      if (lane >= o) {
+        xd += vd;
+        xu += vu;
+      }
+    }
+    s_d[lane] = xd;  // inclusive over warps
+    s_u[lane] = xu;
+  }
+  __syncthreads();
+  int64_t rd = (w > 0 ? s_d[w - 1] : 0) + id - sd, ru = (w > 0 ? s_u[w - 1] : 0) + iu - su;
+  for (int64_t b = b0; b < b1; ++b) {
     const int64_t cd = counts[2 * b], cu = counts[2 * b + 1];
     counts[2 * b] = rd;
     counts[2 * b + 1] = ru;
     rd += cd;
     ru += cu;
   }
-  totals[0] = rd;
-  totals[1] = ru;
+  if (t == 0) {
+    totals[0] = s_d[nw - 1];
+    totals[1] = s_u[nw - 1];
+  }
 }
 
 __global__ void __launch_bounds__(512) k_iface_scatter(const int32_t* __restrict__ nbr,
@@ -365,7 +406,7 @@ cudaError_t interface_count(const int32_t* nbr, const uint8_t* skip, int64_t nb,
                             int64_t* counts_dev, cudaStream_t s) {
   if (nb == 0) return cudaMemsetAsync(counts_dev, 0, 2 * sizeof(int64_t), s);
   k_iface_count<<<unsigned(nb), 512, 0, s>>>(nbr, skip, nb, scratch);
-  k_iface_scan<<<1, 32, 0, s>>>(scratch, nb, counts_dev);
+  k_iface_scan<<<1, 1024, 0, s>>>(scratch, nb, counts_dev);
   return cudaGetLastError();
 }
 

@@ -43,20 +43,35 @@ struct StepArgs {
   // float copies of fu, tau, om, kxyz for the FP32-math kernel (set by its launcher:
   // FP64 conversions run on the slow FP64 pipe, so the kernel takes floats)
   float fuf[3], tauf, omf, kxyzf;
+  float* pre_out;           // [nb][10][512] float32 natural order: pre-collision moments (recording launch)
 };
 
 // FP64 storage: one node per thread (stream_collide.cu).  Other storages: the
 // packed-FP32 node-pair kernel (stream_collide_f2.cu).
 cudaError_t launch_stream_collide(int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_stream_collide_f2(int storage, const StepArgs& a, cudaStream_t s);
+// FP32 storage: the step that also writes the pre-collision moments p to
+// a.pre_out (forward steps recomputed by the adjoint).
+cudaError_t launch_stream_collide_record(const StepArgs& a, cudaStream_t s);
 // Resident CTAs per SM of the persistent node-pair kernel.
 cudaError_t persistent_ctas_per_sm(int storage, int* per_sm);
-// One reverse step of the single-level stream-collide (adjoint.cu): lam = dL/dM
+// One reverse step of the single-level stream-collide, FP64 storage (adjoint.cu): lam = dL/dM
 // of the step's output, lam_out = dL/dM of its input (a.in), dF += dL/dF.
 // lamp is scratch [nb][10][512]; all lambda arrays are natural node order.
 cudaError_t adjoint_step(int storage, const StepArgs& a, const float* lam, float* lamp, double* dF, float* lam_out,
                          cudaStream_t s);
 cudaError_t adjoint_dF_to_float(const double* dF, float* out, int64_t n, cudaStream_t s);
+// FP32 storage, reverse step from recorded pre-collision moments: adjoint_collide
+// (elementwise: lamp = (dC/dp)^T lam, dF += (dC/dF)^T lam) then adjoint_push
+// (lam_out = dL/dM of the step's input a.in; solid nodes copy lam).
+cudaError_t adjoint_collide(const StepArgs& a, const float* pre, const float* lam, float* lamp, double* dF,
+                            cudaStream_t s);
+cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp, float* lam_out, cudaStream_t s);
+// adjoint_push of a step fused with adjoint_collide of the step before it
+// (recorded p = pre_prev): writes that step's lamp to lamp_out, adds to dF.
+// The step's own lam_out is not stored.
+cudaError_t adjoint_push_collide(const StepArgs& a, const float* lamp, const float* pre_prev, float* lamp_out,
+                                 double* dF, cudaStream_t s);
 
 // Per-node bounce masks and the kBlockBounce flag from a neighbour table and
 // an optional solid mask (bflags must hold kBlockSolidNear where solids are near).

@@ -97,26 +97,32 @@ __global__ void k_down(TransferArgs a) {
   int lo[3], hi[3];
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) pair(p[ax], n[ax], a.periodic[ax], lo[ax], hi[ax]);
+  // distinct stencil nodes only: an even fine index has one coarse node (weight
+  // 1), an odd one two (weight 1/2 each); the weights are exact in FP64
+  const int nx = hi[0] != lo[0] ? 2 : 1, ny = hi[1] != lo[1] ? 2 : 1, nz = hi[2] != lo[2] ? 2 : 1;
+  const double w = 1.0 / double(nx * ny * nz);
   Node64 acc = zero64();
-  for (int q = 0; q < 8; ++q) {
-    const int x = (q & 1) ? hi[0] : lo[0], y = (q & 2) ? hi[1] : lo[1], z = (q & 4) ? hi[2] : lo[2];
-    const int64_t cb = lookup(a.coarse, x, y, z);
-    if (cb < 0) {
-      atomicExch(a.status, 1);
-      return;
-    }
-    const int cc = cell_of(x, y, z);
-    if (a.avg) {
-      // temporal midpoint of the old (other) and new (current) coarse states,
-      // taken per field on rho, u and S^neq
-      const Node64 o = load64<T>(a.coarse.mom_other, cb, cc, a.coarse.sc);
-      const Node64 nw = load64<T>(a.coarse.mom, cb, cc, a.coarse.sc);
-      axpy(acc, 0.0625, o);
-      axpy(acc, 0.0625, nw);
-    } else {
-      axpy(acc, 0.125, load64<T>(a.use_other ? a.coarse.mom_other : a.coarse.mom, cb, cc, a.coarse.sc));
-    }
-  }
+  for (int qz = 0; qz < nz; ++qz)
+    for (int qy = 0; qy < ny; ++qy)
+      for (int qx = 0; qx < nx; ++qx) {
+        const int x = qx ? hi[0] : lo[0], y = qy ? hi[1] : lo[1], z = qz ? hi[2] : lo[2];
+        const int64_t cb = lookup(a.coarse, x, y, z);
+        if (cb < 0) {
+          atomicExch(a.status, 1);
+          return;
+        }
+        const int cc = cell_of(x, y, z);
+        if (a.avg) {
+          // temporal midpoint of the old (other) and new (current) coarse states,
+          // taken per field on rho, u and S^neq
+          const Node64 o = load64<T>(a.coarse.mom_other, cb, cc, a.coarse.sc);
+          const Node64 nw = load64<T>(a.coarse.mom, cb, cc, a.coarse.sc);
+          axpy(acc, 0.5 * w, o);
+          axpy(acc, 0.5 * w, nw);
+        } else {
+          axpy(acc, w, load64<T>(a.use_other ? a.coarse.mom_other : a.coarse.mom, cb, cc, a.coarse.sc));
+        }
+      }
   store64<T>(a.out, b, cell, acc, a.k, a.out_sc);
 }
 
@@ -188,6 +194,17 @@ __global__ void __launch_bounds__(512) k_init_level(OldHierarchy o, int level, c
   const int cell = threadIdx.x;
   const int x = coords[3 * b] * 8 + (cell & 7), y = coords[3 * b + 1] * 8 + ((cell >> 3) & 7),
             z = coords[3 * b + 2] * 8 + (cell >> 6);
+  // a node stored at this level before the rebuild keeps its stored codes
+  // (the new level starts from the old level's scales)
+  const int64_t ob = lookup(o.lv[level], x, y, z);
+  if (ob >= 0) {
+    const int off = node_offset<T>(cell);
+    const T* src = static_cast<const T*>(o.lv[level].mom) + ob * (kRows * kCells) + off;
+    T* dst = static_cast<T*>(out) + b * (kRows * kCells) + off;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) dst[r * kCells] = src[r * kCells];
+    return;
+  }
   Node64 v;
   if (!resolve<T, kMaxLevels - 1>(o, level, x, y, z, v)) {
     atomicExch(status, 2);

@@ -39,7 +39,7 @@ using namespace f2;
 // One 8^3 block of the forward step: stream the populations through shared
 // memory, then gather, project and collide.  Leaves shared memory in use:
 // callers that process another block must barrier first.
-template <typename T>
+template <typename T, bool kRecord = false>
 __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, float2* f2buf, int* s_nbr,
                                          unsigned& s_miss) {
   PairCtx cx = pair_ctx();
@@ -70,6 +70,15 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
     V2 g[27];
     gather_all(f2buf, own_s, cx.g13, g, std::make_integer_sequence<int, 27>{});
     const PreMom<V2> p = project(g);
+    if constexpr (kRecord) {  // pre-collision moments for the reverse step (natural order, float32)
+      float* q = a.pre_out + blk * (kRows * kCells) + own;
+      const V2 r[kRows] = {p.drho, p.jx, p.jy, p.jz, p.pxx, p.pyy, p.pzz, p.pxy, p.pxz, p.pyz};
+#pragma unroll
+      for (int k = 0; k < kRows; ++k) {
+        q[k * kCells] = r[k].v.x;
+        q[k * kCells + 256] = r[k].v.y;
+      }
+    }
     V2 fx, fy, fz;
     if (a.F != nullptr) {
       const float* Fp = a.F + blk * 3 * kCells + own;
@@ -97,6 +106,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
   __shared__ int s_nbr[27];
   __shared__ unsigned s_miss;
   sc_block<T>(a, a.blk0 + blockIdx.x, f2buf, s_nbr, s_miss);
+}
+
+// The same step, also writing the pre-collision moments to a.pre_out (the
+// recomputed forward steps of the adjoint).
+__global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2_record(StepArgs a) {
+  extern __shared__ __align__(16) float2 f2buf[];
+  __shared__ int s_nbr[27];
+  __shared__ unsigned s_miss;
+  sc_block<float, true>(a, a.blk0 + blockIdx.x, f2buf, s_nbr, s_miss);
 }
 
 // Persistent CTAs (a grid sized to the resident capacity) that take blocks
@@ -139,6 +157,17 @@ __global__ void __launch_bounds__(512) k_bounce_masks(const int32_t* __restrict_
   const int n = threadIdx.x;
   const int x = n & 7, y = (n >> 3) & 7, z = n >> 6;
   const bool solid_any = solid != nullptr && (bflags[blk] & kBlockSolidNear);
+  // no wall among the 26 neighbours and no solid nearby: no bounce-back (the
+  // masks of such blocks are never read)
+  __shared__ int s_wall;
+  if (n == 0) s_wall = 0;
+  __syncthreads();
+  if (n < 27 && nbr[blk * 27 + n] == kWall) s_wall = 1;
+  __syncthreads();
+  if (!s_wall && !solid_any) {
+    if (n == 0) bflags[blk] = uint8_t(bflags[blk] & ~kBlockBounce);
+    return;
+  }
   unsigned m = 0;
   for (int k = 0; k < 27; ++k) {
     if (k == 13) continue;
@@ -201,6 +230,26 @@ cudaError_t launch_stream_collide_f2(int storage, const StepArgs& a, cudaStream_
     case HLBM_STORE_BF16S: return launch_f2<__nv_bfloat16>(a, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_stream_collide_record(const StepArgs& a_in, cudaStream_t s) {
+  StepArgs a = a_in;
+  for (int k = 0; k < 3; ++k) a.fuf[k] = float(a.fu[k]);
+  a.tauf = float(a.tau);
+  a.omf = float(a.om);
+  a.kxyzf = float(a.kxyz);
+  const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t err =
+        cudaFuncSetAttribute(k_stream_collide_f2_record, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    configured = true;
+  }
+  if (a.nb == 0) return cudaSuccess;
+  if (a.pre_out == nullptr) return cudaErrorInvalidValue;
+  k_stream_collide_f2_record<<<(unsigned)a.nb, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t persistent_ctas_per_sm(int storage, int* per_sm) {
