@@ -8,7 +8,9 @@
   bit, in FP32 and FP16-scaled storage (its scales are its own);
 * FP16-scaled TGV domains of very different amplitudes against the oracle
   across a refit: per-domain scales keep each domain's relative error;
-* the autotuner returns a valid mode and restores the state.
+* the autotuner returns a valid mode and restores the state;
+* the full 64-domain batch of the bench, one step, sampled nodes against
+  single-node oracle updates.
 """
 import numpy as np
 import pytest
@@ -127,3 +129,32 @@ def test_autotune_restores_state():
     fresh = batch_result(domains, fields, "f16s", hl.BATCH_ONE_LAUNCH, 38)
     for d in range(len(domains)):
         assert np.array_equal(cont[d], fresh[d])
+
+
+def test_full_batch_sampled_nodes_one_step():
+    """The 64-domain FP16-scaled batch of the bench (edges 32..128): one step,
+    sampled nodes of four domains against single-node oracle updates from the
+    decoded start state."""
+    from tests.helpers import oracle_node_update
+    doms = wl.batch_domains()
+    domains = [((e, e, e), t) for e, _, t in doms]
+    pick = [0, 21, 42, 63]
+    with hl.Batch(domains, storage="f16s") as b:
+        starts = {}
+        for d, (e, u0, _) in enumerate(doms):
+            M = wl.taylor_green_3d(e, u0).astype(np.float32)
+            b.write_moments(d, torch.tensor(hl.dense_to_blocks(M), device="cuda"))
+        for d in pick:
+            e = doms[d][0]
+            starts[d] = hl.blocks_to_dense(b.read_moments(d), (e, e, e))
+        b.set_mode(hl.BATCH_GRAPH)
+        b.step(1)
+        got = {d: hl.blocks_to_dense(b.read_moments(d), (doms[d][0],) * 3) for d in pick}
+    rng = np.random.default_rng(17)
+    for d in pick:
+        e, u0, tau = doms[d]
+        nodes = [tuple(int(v) for v in rng.integers(0, e, 3)) for _ in range(6)] + [(0, 0, 0), (e - 1, e - 1, e - 1)]
+        ref = oracle_node_update(starts[d], nodes, tau, (True, True, True))
+        g = np.stack([got[d][:, z, y, x] for (x, y, z) in nodes], axis=1)
+        err = rel_err(g, ref, row_scales(ref, u0))
+        assert err.max() < RP_TOL["f16s"], (d, err)

@@ -6,7 +6,9 @@
 * Algorithm 1 with downward/upward transfers: FP64 storage agrees with the
   oracle to 1e-11 on every stored node, FP32 within 1e-5 per coarse step;
 * rebuilds carry the moments over (survivors copied, new nodes interpolated)
-  as the oracle does.
+  as the oracle does;
+* at full size (512^3, three levels, the 2M-particle falling cloud) the
+  hierarchy stays bit-exact.
 """
 import numpy as np
 import pytest
@@ -203,3 +205,22 @@ def test_two_level_reduced_precision(storage, tol):
             m.coarse_step()
             lat.step(2)
         _compare(lat, m, tol, 0.01)
+
+
+def test_full_size_falling_cloud_hierarchy_bit_exact():
+    """The 512^3 three-level domain with the 2M-particle cloud (bench workload):
+    block lists, flags, interface nodes and change counts equal the oracle's at
+    rebuilds spread over the fall (first, mid-fall, landed)."""
+    ext = (512, 512, 512)
+    per = (True, False, True)
+    pos0 = wl.particle_cloud(512)
+    with hl.Lattice(ext, levels=3, tau=0.9, periodic=per, storage="f32") as lat:
+        prev = None
+        for t in (0, 12, 240, 480):
+            pos = wl.fall(pos0, t)
+            counts = lat.rebuild_from_particles(torch.tensor(pos, device="cuda"))
+            h = hy.from_particles(pos, ext, 8, 3, per)
+            assert_same_hierarchy(lat, h, prev)
+            if prev is not None:
+                assert counts == h.counts(prev)
+            prev = h
