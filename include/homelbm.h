@@ -202,6 +202,10 @@ int32_t hlbm_reduce(hlbm_lattice *h, double out[7]);
    buffer, public layout [nb][10][512], rho row = d/d rho) and writes dL/dF
    (float32 device [nb][3][512], the layout of hlbm_set_force) by recomputing
    each checkpoint segment and stepping backwards; the force sums are FP64.
+   Device memory during the call: with FP32 storage, the K = ckpt_every states
+   and pre-collision moment fields of one segment (2 K x 40 B per node) plus
+   four float32 moment-sized buffers and the FP64 dL/dF sum (24 B per node);
+   with FP64 storage, K - 1 states (80 B per node each) and the same buffers.
    Single-level lattices with FP32 or FP64 storage; force, eps and solids must
    not change between the two calls.  Synchronous. */
 int32_t hlbm_forward_record(hlbm_lattice *h, int32_t n_steps, int32_t ckpt_every);

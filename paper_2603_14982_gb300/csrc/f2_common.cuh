@@ -253,9 +253,12 @@ __device__ __forceinline__ PairCtx pair_ctx() {
 // every node pair emits 27 values (Src::emit) that land at the node the
 // value streams to; halo pairs of the 26 neighbour blocks supply the values
 // entering the block; bounce-back slots take the node's own value of the
-// opposite direction.  Src supplies the node values: the stored moments and
-// their populations (forward step) or lambda_p and its transposed
-// projection (reverse step).  Ends with a barrier; the caller gathers.
+// opposite direction.  Src supplies the node values: lambda_p and its
+// transposed projection for the reverse step of the adjoint (the forward
+// kernel writes the same phases out for the stored moments).  Ends with a
+// barrier; the caller gathers.  Src provides Node, own(blk, slot),
+// pair(blk, slot), two(ba, ca, bb, cb), zero(), mirror(node, axis, sign) and
+// emit(node, sink).
 template <typename Src>
 __device__ __forceinline__ void stream_pairs(const Src& src, const StepArgs& a, const int64_t blk, float2* f2buf,
                                              int* s_nbr, unsigned& s_miss, PairCtx& cx) {
@@ -373,48 +376,6 @@ __device__ __forceinline__ void stream_pairs(const Src& src, const StepArgs& a, 
   }
   __syncthreads();
 }
-
-// Node values of the forward step: the stored moments (storage type T) and
-// their populations (Eq. three_order_f).
-template <typename T>
-struct MomSource {
-  using Node = Mom<V2>;
-  const T* in;
-  const Scales* sc;
-  V2 kxyz;
-  __device__ __forceinline__ Node own(int64_t blk, int slot) const { return load_pair<T>(in, blk, slot, sc); }
-  __device__ __forceinline__ Node pair(int64_t b, int slot) const { return load_pair<T>(in, b, slot, sc); }
-  // two single nodes (block, cell); a negative block gives zeros
-  __device__ __forceinline__ Node two(int ba, int ca, int bb, int cb) const {
-    Mom<float> la, lb;
-    la.drho = la.ux = la.uy = la.uz = la.sxx = la.syy = la.szz = la.sxy = la.sxz = la.syz = 0.f;
-    lb = la;
-    if (ba >= 0) la = load_node<T>(in, ba, ca, sc);
-    if (bb >= 0) lb = load_node<T>(in, bb, cb, sc);
-    return pack(la, lb);
-  }
-  __device__ __forceinline__ static Node zero() { return zero_pair(); }
-  // reflection along axis cls: u and S components with an odd count of that axis change sign
-  __device__ __forceinline__ static void mirror(Node& n, int cls, V2 sg) {
-    if (cls == 0) {
-      n.ux = n.ux * sg;
-      n.sxy = n.sxy * sg;
-      n.sxz = n.sxz * sg;
-    } else if (cls == 1) {
-      n.uy = n.uy * sg;
-      n.sxy = n.sxy * sg;
-      n.syz = n.syz * sg;
-    } else {
-      n.uz = n.uz * sg;
-      n.sxz = n.sxz * sg;
-      n.syz = n.syz * sg;
-    }
-  }
-  template <typename S>
-  __device__ __forceinline__ void emit(const Node& n, S& s) const {
-    emit_all(make_coef(n, kxyz), s);
-  }
-};
 
 }  // namespace f2
 }  // namespace hlbm

@@ -187,8 +187,11 @@ __device__ bool resolve(const OldHierarchy& o, int l, int x, int y, int z, Node6
   }
 }
 
+// 2 CTAs of 512 threads per SM (at most 64 registers): the copy of surviving
+// nodes is the common path; the recursive resolution of new nodes is rare and
+// may spill.
 template <typename T>
-__global__ void __launch_bounds__(512) k_init_level(OldHierarchy o, int level, const int32_t* __restrict__ coords,
+__global__ void __launch_bounds__(512, 2) k_init_level(OldHierarchy o, int level, const int32_t* __restrict__ coords,
                                                     void* out, const Scales* out_sc, int* status) {
   const int64_t b = blockIdx.x;
   const int cell = threadIdx.x;
