@@ -37,7 +37,7 @@ KERNEL = "k_stream_collide_f2<float>"
 # DRAM bytes (read + write) per launch of KERNEL from one ncu capture of the
 # 192^3 duct, scaled by nodes to 256^3 (profiles/stream_collide_f2_duct192.md);
 # set to None whenever the kernel changes after that capture.
-TRAFFIC_PER_NODE = None
+TRAFFIC_PER_NODE = 531.8e6 / 192 ** 3
 
 
 def measured_peaks():
@@ -88,6 +88,23 @@ class ClockSampler:
         os.unlink(self.f.name)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(values, world, device):
+    """Element-wise maximum of per-rank timings (seconds) over all ranks."""
+    if world <= 1:
+        return list(values)
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_mlups(nodes, steps, world, seconds):
+    """Whole-job throughput of independent replicas: every rank advances its own
+    copy of the workload, so the job updates world * nodes * steps nodes in the
+    slowest rank's time."""
+    return world * nodes * steps / seconds / 1e6
 
 
 def duct_lattice(hl, n, stream):
@@ -150,18 +167,15 @@ def run_gpu(args, rank, world):
     red_e2e = lat.reduce()
     t_e2e = time.perf_counter() - t0
     lat.close()
-    times = torch.tensor([ms / 1e3, t_e2e], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    t_dev, t_e2e = times.tolist()
+    t_dev, t_e2e = max_over_ranks([ms / 1e3, t_e2e], world, "cuda")
     extras = None
     if not args.no_extras and world == 1:
         extras = bench_extras(hl, wl)
     res = {
         "extras": extras,
         "ms_per_step": 1e3 * t_dev / args.steps,
-        "value": world * nodes * args.steps / t_dev / 1e6,
-        "e2e_value": world * nodes * args.steps / t_e2e / 1e6,
+        "value": job_mlups(nodes, args.steps, world, t_dev),
+        "e2e_value": job_mlups(nodes, args.steps, world, t_e2e),
         "clocks": clk,
         "mass": red[0],
         "e2e_bytes": M0.nbytes,

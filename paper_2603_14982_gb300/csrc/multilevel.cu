@@ -1,10 +1,13 @@
 // multilevel.cu -- downward/upward transfers of Algorithm 1 and the moment
 // initialisation of blocks created by a rebuild (Sec. 5.2, Sec. 6.3).
 //
-// All transfer arithmetic is FP64: moments are read from storage, split into
-// (rho, u, S^neq = S - u u), combined with exact power-of-two weights, rescaled
-// and recombined as S = k S^neq + u u with u the combined velocity (S^eq is
-// formed from the interpolated velocity).
+// Each stencil node's moments are read from storage and split into
+// (rho, u, S^neq = S - u u) in FP32 (one fused multiply-add per S^neq entry,
+// rounded once); the weighted sums over the stencil and the temporal midpoint
+// are accumulated in FP64 with exact power-of-two weights; the result is
+// rescaled and recombined as S = k S^neq + u u (S^eq formed from the
+// interpolated velocity) in FP32.  FP64 work is kept to the accumulation: on
+// GB300 the FP64 pipe runs at a small fraction of the FP32 rate.
 #include "hlbm_internal.h"
 #include "multilevel.cuh"
 
@@ -23,12 +26,12 @@ __device__ __forceinline__ Node64 load64(const void* base, int64_t blk, int cell
   n.ux = m.ux;
   n.uy = m.uy;
   n.uz = m.uz;
-  n.s[0] = double(m.sxx) - n.ux * n.ux;
-  n.s[1] = double(m.syy) - n.uy * n.uy;
-  n.s[2] = double(m.szz) - n.uz * n.uz;
-  n.s[3] = double(m.sxy) - n.ux * n.uy;
-  n.s[4] = double(m.sxz) - n.ux * n.uz;
-  n.s[5] = double(m.syz) - n.uy * n.uz;
+  n.s[0] = double(mad(-m.ux, m.ux, m.sxx));
+  n.s[1] = double(mad(-m.uy, m.uy, m.syy));
+  n.s[2] = double(mad(-m.uz, m.uz, m.szz));
+  n.s[3] = double(mad(-m.ux, m.uy, m.sxy));
+  n.s[4] = double(mad(-m.ux, m.uz, m.sxz));
+  n.s[5] = double(mad(-m.uy, m.uz, m.syz));
   return n;
 }
 
@@ -37,16 +40,17 @@ __device__ __forceinline__ void store64(void* base, int64_t blk, int cell, const
                                         const Scales* sc) {
   using R = typename StorageTraits<T>::R;
   Mom<R> m;
+  const R ux = R(n.ux), uy = R(n.uy), uz = R(n.uz), kk = R(k);
   m.drho = R(n.rho - 1.0);
-  m.ux = R(n.ux);
-  m.uy = R(n.uy);
-  m.uz = R(n.uz);
-  m.sxx = R(k * n.s[0] + n.ux * n.ux);
-  m.syy = R(k * n.s[1] + n.uy * n.uy);
-  m.szz = R(k * n.s[2] + n.uz * n.uz);
-  m.sxy = R(k * n.s[3] + n.ux * n.uy);
-  m.sxz = R(k * n.s[4] + n.ux * n.uz);
-  m.syz = R(k * n.s[5] + n.uy * n.uz);
+  m.ux = ux;
+  m.uy = uy;
+  m.uz = uz;
+  m.sxx = mad(kk, R(n.s[0]), ux * ux);
+  m.syy = mad(kk, R(n.s[1]), uy * uy);
+  m.szz = mad(kk, R(n.s[2]), uz * uz);
+  m.sxy = mad(kk, R(n.s[3]), ux * uy);
+  m.sxz = mad(kk, R(n.s[4]), ux * uz);
+  m.syz = mad(kk, R(n.s[5]), uy * uz);
   store_node<T>(static_cast<T*>(base), blk, cell, m, sc);
 }
 
