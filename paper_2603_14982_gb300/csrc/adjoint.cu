@@ -537,12 +537,11 @@ __device__ __forceinline__ Mom<V2> as_mom(const PreMom<V2>& q) {
 template <typename T, bool kFuse>
 __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjArgs d) {
   extern __shared__ __align__(16) float2 f2buf[];
-  __shared__ int s_nbr[27];
   __shared__ unsigned s_miss;
   const int64_t blk = blockIdx.x;
   f2::PairCtx cx = f2::pair_ctx();
   const LamSource src{d.lamp};
-  f2::stream_pairs(src, a, blk, f2buf, s_nbr, s_miss, cx);
+  f2::stream_pairs(src, a, blk, f2buf, s_miss, cx);
   const int own = cx.own;
   bool fz_lo = false, fz_hi = false;  // solid nodes: M'(y) = M(y)
   if (cx.solid_any) {

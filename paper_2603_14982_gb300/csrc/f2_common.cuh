@@ -261,14 +261,13 @@ __device__ __forceinline__ PairCtx pair_ctx() {
 // emit(node, sink).
 template <typename Src>
 __device__ __forceinline__ void stream_pairs(const Src& src, const StepArgs& a, const int64_t blk, float2* f2buf,
-                                             int* s_nbr, unsigned& s_miss, PairCtx& cx) {
+                                             unsigned& s_miss, PairCtx& cx) {
   float* fbuf = reinterpret_cast<float*>(f2buf);
   const int t = cx.t, lane = cx.lane, x = cx.x, y = cx.y, z0 = cx.z0, own = cx.own, own_s = cx.own_s;
 
   if (t < 32) {
     const int v = t < 27 ? a.nbr[blk * 27 + t] : 0;
     const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && v == kMissing);
-    if (t < 27) s_nbr[t] = v;
     if (t == 0) s_miss = mb;
   }
   const uint8_t bf = a.bflags != nullptr ? a.bflags[blk] : 0;
@@ -281,12 +280,12 @@ __device__ __forceinline__ void stream_pairs(const Src& src, const StepArgs& a, 
   int cls = -1, hax = 0, hay = 0, haz = 0, hbx = 0, hby = 0, hbz = 0;
   bool mir = false;
   if (t < kHaloPairs) halo_pair(t, cls, mir, hax, hay, haz, hbx, hby, hbz);
-  __syncthreads();  // s_nbr, s_miss
 
   bool va = false, vb = false;
   typename Src::Node hm = Src::zero();
   if (t < kHaloPairs) {
-    const int na = s_nbr[block_dir(hax, hay, haz)], nb = s_nbr[block_dir(hbx, hby, hbz)];
+    const int na = __ldg(a.nbr + blk * 27 + block_dir(hax, hay, haz));
+    const int nb = __ldg(a.nbr + blk * 27 + block_dir(hbx, hby, hbz));
     const int sa = (hax & 7) + 8 * (hay & 7) + 64 * (haz & 7), sb = (hbx & 7) + 8 * (hby & 7) + 64 * (hbz & 7);
     va = na >= 0 && !(solid_any && a.solid[int64_t(na) * kCells + sa]);
     vb = nb >= 0 && !(solid_any && a.solid[int64_t(nb) * kCells + sb]);
