@@ -37,7 +37,7 @@ KERNEL = "k_stream_collide_f2<float>"
 # DRAM bytes (read + write) per launch of KERNEL from one ncu capture of the
 # 192^3 duct, scaled by nodes to 256^3 (profiles/stream_collide_f2_duct192.md);
 # set to None whenever the kernel changes after that capture.
-TRAFFIC_PER_NODE = None
+TRAFFIC_PER_NODE = 531.9e6 / 192 ** 3
 
 
 def measured_peaks():
