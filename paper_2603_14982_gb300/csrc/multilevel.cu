@@ -104,29 +104,56 @@ __global__ void k_down(TransferArgs a) {
   // distinct stencil nodes only: an even fine index has one coarse node (weight
   // 1), an odd one two (weight 1/2 each); the weights are exact in FP64
   const int nx = hi[0] != lo[0] ? 2 : 1, ny = hi[1] != lo[1] ? 2 : 1, nz = hi[2] != lo[2] ? 2 : 1;
-  const double w = 1.0 / double(nx * ny * nz);
+  const int nq = nx * ny * nz;
+  const double w = 1.0 / double(nq);
+  // all stencil lookups first (independent loads), then the node loads two
+  // corners at a time so that their latencies overlap
+  int64_t cb[8];
+  int cc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int qx = q % nx, qy = (q / nx) % ny, qz = q / (nx * ny);
+    const int x = qx ? hi[0] : lo[0], y = qy ? hi[1] : lo[1], z = qz ? hi[2] : lo[2];
+    cb[q] = q < nq ? lookup(a.coarse, x, y, z) : 0;
+    cc[q] = cell_of(x, y, z);
+  }
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) ok = ok && cb[q] >= 0;
+  if (!ok) {
+    atomicExch(a.status, 1);
+    return;
+  }
   Node64 acc = zero64();
-  for (int qz = 0; qz < nz; ++qz)
-    for (int qy = 0; qy < ny; ++qy)
-      for (int qx = 0; qx < nx; ++qx) {
-        const int x = qx ? hi[0] : lo[0], y = qy ? hi[1] : lo[1], z = qz ? hi[2] : lo[2];
-        const int64_t cb = lookup(a.coarse, x, y, z);
-        if (cb < 0) {
-          atomicExch(a.status, 1);
-          return;
-        }
-        const int cc = cell_of(x, y, z);
-        if (a.avg) {
-          // temporal midpoint of the old (other) and new (current) coarse states,
-          // taken per field on rho, u and S^neq
-          const Node64 o = load64<T>(a.coarse.mom_other, cb, cc, a.coarse.sc);
-          const Node64 nw = load64<T>(a.coarse.mom, cb, cc, a.coarse.sc);
-          axpy(acc, 0.5 * w, o);
-          axpy(acc, 0.5 * w, nw);
-        } else {
-          axpy(acc, w, load64<T>(a.use_other ? a.coarse.mom_other : a.coarse.mom, cb, cc, a.coarse.sc));
-        }
+  const void* cur = a.use_other ? a.coarse.mom_other : a.coarse.mom;
+#pragma unroll
+  for (int q = 0; q < 8; q += 2) {
+    if (q >= nq) break;
+    const bool two = q + 1 < nq;
+    if (a.avg) {
+      // temporal midpoint of the old (other) and new (current) coarse states,
+      // taken per field on rho, u and S^neq
+      const Node64 o0 = load64<T>(a.coarse.mom_other, cb[q], cc[q], a.coarse.sc);
+      const Node64 n0 = load64<T>(a.coarse.mom, cb[q], cc[q], a.coarse.sc);
+      Node64 o1 = zero64(), n1 = zero64();
+      if (two) {
+        o1 = load64<T>(a.coarse.mom_other, cb[q + 1], cc[q + 1], a.coarse.sc);
+        n1 = load64<T>(a.coarse.mom, cb[q + 1], cc[q + 1], a.coarse.sc);
       }
+      axpy(acc, 0.5 * w, o0);
+      axpy(acc, 0.5 * w, n0);
+      if (two) {
+        axpy(acc, 0.5 * w, o1);
+        axpy(acc, 0.5 * w, n1);
+      }
+    } else {
+      const Node64 v0 = load64<T>(cur, cb[q], cc[q], a.coarse.sc);
+      Node64 v1 = zero64();
+      if (two) v1 = load64<T>(cur, cb[q + 1], cc[q + 1], a.coarse.sc);
+      axpy(acc, w, v0);
+      if (two) axpy(acc, w, v1);
+    }
+  }
   store64<T>(a.out, b, cell, acc, a.k, a.out_sc);
 }
 
