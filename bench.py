@@ -38,6 +38,11 @@ KERNEL = "k_stream_collide_f2<float>"
 # 192^3 duct, scaled by nodes to 256^3 (profiles/stream_collide_f2_duct192.md);
 # set to None whenever the kernel changes after that capture.
 TRAFFIC_PER_NODE = 531.9e6 / 192 ** 3
+# FP32 operations per node update of KERNEL (ncu thread-level counts of FADD,
+# FMUL, FFMA and their packed forms on the 192^3 duct, profiles/
+# stream_collide_f2_duct192.md; FMA = 2); None when not measured for the
+# current kernel.
+FLOP_PER_NODE = 544.9
 
 
 def measured_peaks():
@@ -88,6 +93,29 @@ class ClockSampler:
         os.unlink(self.f.name)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def fp32_sgemm_tflops(n=8192, reps=10):
+    """FP32 CUDA-core rate of this GPU: cuBLAS SGEMM with TF32 off (2 n^3 flop each)."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        for _ in range(3):
+            c = a @ b
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(reps):
+            c = a @ b
+        ev[1].record()
+        ev[1].synchronize()
+        del a, b, c
+        return 2.0 * n ** 3 * reps / (ev[0].elapsed_time(ev[1]) / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 def max_over_ranks(values, world, device):
@@ -285,6 +313,7 @@ def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebui
         torch.cuda.synchronize()
         t_reb = 0.0
         updates = 0
+        updates0 = 0   # finest-level updates (they also read the force and fluid-fraction fields)
         since = 0
         rebuilds = 0
         counts = [lat.num_blocks(l) for l in range(L)]
@@ -292,6 +321,7 @@ def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebui
         for k in range(fine_steps // per):
             lat.step(per)
             updates += sum(counts[l] * 512 * 2 ** (L - 1 - l) for l in range(L))
+            updates0 += counts[0] * 512 * 2 ** (L - 1)
             since += per
             with torch.cuda.stream(stream):
                 pos[:, 1] = torch.clamp(pos[:, 1] - per, min=0.5)
@@ -311,7 +341,11 @@ def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebui
         red = lat.reduce()
         moms = [lat.read_moments(torch.empty((lat.num_blocks(l), 10, 512), dtype=torch.float32, device="cuda"),
                                  level=l) for l in range(L)]
+    bpn = 80.0 if storage == "f32" else 40.0
+    actual_gbs = (updates * bpn + updates0 * 16.0) / t_tot / 1e9
+    peak, _ = measured_peaks()
     return {"storage": storage, "fine_steps": fine_steps, "rebuilds": rebuilds,
+            "actual_gbs": round(actual_gbs, 1), "actual_gbs_over_peak": round(actual_gbs / peak, 4),
             "mlups_fine_equiv": round(n ** 3 * fine_steps / t_tot / 1e6, 1),
             "actual_updates_per_s_M": round(updates / t_tot / 1e6, 1),
             "total_s": round(t_tot, 4), "rebuild_s": round(t_reb, 4), "rebuild_ms_each": round(1e3 * t_reb / rebuilds, 3),
@@ -323,7 +357,8 @@ def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebui
 def bench_extras(hl, wl):
     import torch
     stream = torch.cuda.Stream()
-    out = {"c5_batched": bench_batched(hl, wl, stream), "c4_adjoint": bench_adjoint(hl, wl, stream)}
+    out = {"c5_batched": bench_batched(hl, wl, stream), "c4_adjoint": bench_adjoint(hl, wl, stream),
+           "fp32_sgemm_tflops": round(fp32_sgemm_tflops(), 1)}
     ml = {}
     ref = None
     pos0 = torch.tensor(wl.particle_cloud(512), device="cuda")
@@ -450,6 +485,14 @@ def main():
     }
     if res["extras"] is not None:
         line["extras"] = res["extras"]
+        if FLOP_PER_NODE is not None:
+            # the same kernel against the FP32 CUDA-core rate (it is issue-bound)
+            tf = args.n ** 3 * FLOP_PER_NODE / (res["ms_per_step"] / 1e3) / 1e12
+            pk = res["extras"].get("fp32_sgemm_tflops")
+            line["extras"]["alu_roofline"] = {
+                "kernel": KERNEL, "flop_per_node": FLOP_PER_NODE, "achieved_tflops": round(tf, 2),
+                "peak_tflops": pk, "peak_kind": "cuBLAS SGEMM 8192^3, TF32 off, measured in this run",
+                "frac": round(tf / pk, 4) if pk else None}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample(128, 16)
     print(json.dumps(line))

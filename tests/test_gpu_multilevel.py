@@ -8,7 +8,10 @@
 * rebuilds carry the moments over (survivors copied, new nodes interpolated)
   as the oracle does;
 * at full size (512^3, three levels, the 2M-particle falling cloud) the
-  hierarchy stays bit-exact.
+  hierarchy stays bit-exact;
+* the 128^3 downscale of that workload (cloud, deposited drag and fluid
+  fraction) agrees with the FP64 oracle in FP32, FP16- and BF16-scaled
+  storage within the per-step bounds accumulated over 16 fine steps.
 """
 import numpy as np
 import pytest
@@ -224,3 +227,55 @@ def test_full_size_falling_cloud_hierarchy_bit_exact():
             if prev is not None:
                 assert counts == h.counts(prev)
             prev = h
+
+
+CLOUD128_COARSE_STEPS = 4
+
+
+@pytest.fixture(scope="module")
+def cloud128_oracle():
+    """FP64 oracle of the three-level cloud workload downscaled to 128^3
+    fine-equivalent (31,250 particles in the same box), from rest, with the
+    float32-rounded drag force and fluid fraction on the finest level."""
+    ext = (128, 128, 128)
+    per = (True, False, True)
+    pos = wl.particle_cloud(128, count=2_000_000 // 64)
+    F, eps = wl.cloud_force_fields(pos, (128, 128, 128))
+    h = hy.from_particles(pos, ext, 8, 3, per)
+    m = ml.MultiLevel(h, 0.9, force=torch.tensor(F.astype(np.float32).astype(np.float64)),
+                      eps=torch.tensor(eps.astype(np.float32).astype(np.float64)))
+    for l in range(3):
+        n = 128 >> l
+        m.set_level(l, wl.rest_field((n, n, n)))
+    for _ in range(CLOUD128_COARSE_STEPS):
+        m.coarse_step()
+    return pos, m
+
+
+# per-step bounds (FP32: 1e-5 of the row scale; reduced precision: one rounding
+# of the row code, 2^-11 / 2^-8 of the amax times the headroom factor 8),
+# accumulated linearly over the 16 fine steps
+@pytest.mark.parametrize("storage,tol", [("f32", 16 * 1e-5), ("f16s", 16 * 8 * 2.0 ** -11),
+                                         ("bf16s", 16 * 8 * 2.0 ** -8)])
+def test_cloud_downscale_128_against_fp64_oracle(cloud128_oracle, storage, tol):
+    """The 128^3 downscale of the cloud workload: hierarchy from the cloud, drag
+    force and fluid fraction deposited on the finest level, 16 fine steps from
+    rest; every stored node of every level against the FP64 oracle, relative to
+    each row's largest value (velocity floor 1e-4).  The errors are printed."""
+    pos, m = cloud128_oracle
+    with hl.Lattice((128, 128, 128), levels=3, tau=0.9, periodic=(True, False, True), storage=storage) as lat:
+        lat.rebuild_from_particles(pos)
+        assert lat.deposit_particles(pos) == 0
+        lat.step(4 * CLOUD128_COARSE_STEPS)
+        worst = 0.0
+        for l in range(3):
+            coords, _ = lat.blocks(l)
+            if not len(coords):
+                continue
+            got = hl.blocks_to_dense(lat.read_moments(level=l), m.shape[l], coords)
+            ref = m.current(l).numpy()
+            err = rel_err(got, ref, row_scales(ref, 1e-4), mask=m.stored[l].numpy())
+            worst = max(worst, float(err.max()))
+    print("cloud 128^3, %s, %d fine steps: max error / row scale = %.3e"
+          % (storage, 4 * CLOUD128_COARSE_STEPS, worst))
+    assert worst < tol, worst
