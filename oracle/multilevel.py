@@ -152,11 +152,18 @@ class MultiLevel:
         s = float(1 << l)
         return x * s, y * s, z * s
 
-    def set_level(self, l, M):
-        """Set both buffers of level l from a dense (10, nz_l, ny_l, nx_l) array;
-        nodes that are not stored become NaN."""
-        M = torch.as_tensor(M, dtype=torch.float64).clone()
-        M[:, ~self.stored[l]] = float("nan")
+    def set_level(self, l, M, fill=None, dtype=torch.float64):
+        """Set both buffers of level l from a dense (10, nz_l, ny_l, nx_l) array.
+
+        Nodes that are not stored become NaN, so that any read of them poisons
+        the result; ``fill`` (10 values) puts a finite state there instead,
+        for reverse-mode differentiation, where 0 * NaN in the chain rule
+        would poison gradients that do not depend on those nodes."""
+        M = torch.as_tensor(M).to(dtype).clone()
+        if fill is None:
+            M[:, ~self.stored[l]] = float("nan")
+        else:
+            M[:, ~self.stored[l]] = torch.as_tensor(fill, dtype=dtype).unsqueeze(1)
         self.buf[l] = [M.clone(), M.clone()]
         self.cur[l] = 0
 
@@ -196,8 +203,15 @@ class MultiLevel:
                   [0.5 * (old[2][r] + new[2][r]) for r in range(6)])
         _, k_down = self.k_updown(l)
         vals = interpolate_down(Mc, nodes, self.periodic, k_down)
-        M = self.current(l)
+        self._assign(l, nodes, vals)
+
+    def _assign(self, l, nodes, vals):
+        """Overwrite ``nodes`` of level l's read buffer.  The buffer is replaced
+        by an updated copy rather than written in place, so that reverse-mode
+        differentiation can still use the values earlier operations read."""
+        M = self.current(l).clone()
         M[:, nodes[0], nodes[1], nodes[2]] = vals
+        self.buf[l][self.cur[l]] = M
 
     def upward_transfer(self, l):
         """UpwardTransfer(l): I^u_{l+1} nodes copy their coincident level-l node (Eq. upload_S)."""
@@ -208,7 +222,7 @@ class MultiLevel:
         Mf = self.current(l)
         fz, fy, fx = (2 * nodes[0], 2 * nodes[1], 2 * nodes[2])
         rho, u, sneq = split_neq(Mf[:, fz, fy, fx])
-        self.current(l + 1)[:, nodes[0], nodes[1], nodes[2]] = join_neq(rho, u, sneq, k_up)
+        self._assign(l + 1, nodes, join_neq(rho, u, sneq, k_up))
 
     def advance(self, l, s):
         """AdvanceLBM(l, s) of Algorithm 1."""

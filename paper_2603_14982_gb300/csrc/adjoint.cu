@@ -246,6 +246,7 @@ struct AdjArgs {
   float* lam_out;         // dL/dM of the step's input [nb][10][512]
   const float* pre_prev;  // fused push: recorded p of the previous step
   float* lamp_out;        // fused push: dL/dp of the previous step
+  const float* lam_add;   // plain push: added to lam_out at every node, or null
 };
 
 // Shared part: the block's ext buffer filled with the forward pull (PULL) or
@@ -476,7 +477,9 @@ __device__ __forceinline__ void store_pair10(float* p, int64_t blk, int cell, co
 // Transposed collision of a node pair (cells c and c + 256 of block blk) from
 // its recorded pre-collision moments p and lambda' = dL/dM of the step's
 // output: stores lambda_p = (dC/dp)^T lambda' and adds (dC/dF)^T lambda' to dF
-// (FP64).  Solid halves (fz_lo / fz_hi) get lambda_p = 0 and no force term.
+// (FP64; skipped when dF_all is null).  Frozen halves (fz_lo / fz_hi: solid
+// or interface nodes, which copy their input) get lambda_p = 0 and no force
+// term.
 __device__ __forceinline__ void collide_adj_pair(const StepArgs& a, int64_t blk, int c, const PreMom<V2>& p,
                                                  const Mom<V2>& lo, bool fz_lo, bool fz_hi, float* lamp,
                                                  double* dF_all) {
@@ -499,6 +502,7 @@ __device__ __forceinline__ void collide_adj_pair(const StepArgs& a, int64_t blk,
   collide_vjp(p, fx, fy, fz, om, lo, lp, lfx, lfy, lfz);
   const V2 out[kRows] = {lp.drho, lp.jx, lp.jy, lp.jz, lp.pxx, lp.pyy, lp.pzz, lp.pxy, lp.pxz, lp.pyz};
   store_pair10(lamp, blk, c, out, fz_lo, fz_hi);
+  if (dF_all == nullptr) return;
   double* dF = dF_all + blk * 3 * kCells + c;
   if (!fz_lo) {
     dF[0] += double(lfx.v.x);
@@ -533,7 +537,11 @@ __device__ __forceinline__ Mom<V2> as_mom(const PreMom<V2>& q) {
 // it, go on with part 1 of the previous step at the same node (its transposed
 // collision needs only this node's lambda and recorded p), writing that step's
 // lambda_p to d.lamp_out and its force term to d.dF.  Solid nodes keep
-// lambda = d.lam (nothing streams into them).
+// lambda = d.lam (nothing streams into them).  The plain form also serves the
+// multi-level adjoint: interface nodes (a neighbour block not stored) copy
+// their input in the forward step, so d.lam passes through and adds to what
+// streams back from the nodes that pull from them; d.lam_add, if set, is
+// added everywhere.  The fused form is for lattices without interface nodes.
 template <typename T, bool kFuse>
 __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjArgs d) {
   extern __shared__ __align__(16) float2 f2buf[];
@@ -548,10 +556,26 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
     fz_lo = a.solid[blk * kCells + own] != 0;
     fz_hi = a.solid[blk * kCells + own + 256] != 0;
   }
+  bool cp_lo = false, cp_hi = false;  // interface nodes
+  if (!kFuse && s_miss != 0u) {
+    cp_lo = !fz_lo && f2::touches_missing(cx.x, cx.y, cx.z0, s_miss);
+    cp_hi = !fz_hi && f2::touches_missing(cx.x, cx.y, cx.z0 + 4, s_miss);
+  }
   Mom<V2> lm;
   if (!(fz_lo && fz_hi)) {
     V2 g[27];
     f2::gather_all(f2buf, cx.own_s, cx.g13, g, std::make_integer_sequence<int, 27>{});
+    if (cp_lo || cp_hi) {
+      // an interface node's slots fed from a block that is not stored hold
+      // wrapped own pushes, not adjoints: nothing streams back from there
+      const unsigned mlo = cp_lo ? f2::missing_sources(cx.x, cx.y, cx.z0, s_miss) : 0u;
+      const unsigned mhi = cp_hi ? f2::missing_sources(cx.x, cx.y, cx.z0 + 4, s_miss) : 0u;
+#pragma unroll
+      for (int K = 0; K < 27; ++K) {
+        if ((mlo >> K) & 1u) g[K].v.x = 0.f;
+        if ((mhi >> K) & 1u) g[K].v.y = 0.f;
+      }
+    }
     V2 gh_in[27];
 #pragma unroll
     for (int j = 0; j < 27; ++j) gh_in[j] = g[26 - j];
@@ -569,12 +593,21 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
     collide_adj_pair(a, blk, own, LamSource{d.pre_prev}.pair(blk, own), lm, fz_lo, fz_hi, d.lamp_out, d.dF);
   } else {
     V2 out[kRows] = {lm.drho, lm.ux, lm.uy, lm.uz, lm.sxx, lm.syy, lm.szz, lm.sxy, lm.sxz, lm.syz};
-    if (fz_lo || fz_hi) {
+    if (fz_lo || fz_hi || cp_lo || cp_hi) {
       const PreMom<V2> q = LamSource{d.lam}.pair(blk, own);
       const V2 lam[kRows] = {q.drho, q.jx, q.jy, q.jz, q.pxx, q.pyy, q.pzz, q.pxy, q.pxz, q.pyz};
 #pragma unroll
-      for (int r = 0; r < kRows; ++r)
-        out[r] = V2(fz_lo ? lam[r].v.x : out[r].v.x, fz_hi ? lam[r].v.y : out[r].v.y);
+      for (int r = 0; r < kRows; ++r) {
+        const float lo = fz_lo ? lam[r].v.x : (cp_lo ? out[r].v.x + lam[r].v.x : out[r].v.x);
+        const float hi = fz_hi ? lam[r].v.y : (cp_hi ? out[r].v.y + lam[r].v.y : out[r].v.y);
+        out[r] = V2(lo, hi);
+      }
+    }
+    if (d.lam_add != nullptr) {
+      const PreMom<V2> q = LamSource{d.lam_add}.pair(blk, own);
+      const V2 add[kRows] = {q.drho, q.jx, q.jy, q.jz, q.pxx, q.pyy, q.pzz, q.pxy, q.pxz, q.pyz};
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) out[r] = out[r] + add[r];
     }
     store_pair10(d.lam_out, blk, own, out, false, false);
   }
@@ -583,12 +616,24 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
 // Reverse step, part 1 from recorded pre-collision moments p (elementwise,
 // one thread per node pair: cells t and t + 256).
 __global__ void __launch_bounds__(256) k_adj_collide(StepArgs a, const float* __restrict__ pre, AdjArgs d) {
+  __shared__ unsigned s_miss;
   const int64_t blk = blockIdx.x;
   const int t = threadIdx.x;
+  if (t < 32) {
+    const int v = t < 27 ? a.nbr[blk * 27 + t] : 0;
+    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && v == kMissing);
+    if (t == 0) s_miss = mb;
+  }
+  __syncthreads();
   bool fz_lo = false, fz_hi = false;
   if (a.bflags != nullptr && (a.bflags[blk] & kBlockSolidNear)) {
     fz_lo = a.solid[blk * kCells + t] != 0;
     fz_hi = a.solid[blk * kCells + t + 256] != 0;
+  }
+  if (s_miss != 0u) {  // interface nodes copy their input: no collision to transpose
+    const int x = t & 7, y = (t >> 3) & 7, z = t >> 6;
+    fz_lo = fz_lo || f2::touches_missing(x, y, z, s_miss);
+    fz_hi = fz_hi || f2::touches_missing(x, y, z + 4, s_miss);
   }
   if (fz_lo && fz_hi) {
     V2 z[kRows];
@@ -674,11 +719,13 @@ cudaError_t launch_push2(const StepArgs& a_in, const AdjArgs& d, cudaStream_t s)
   return cudaGetLastError();
 }
 
-cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp, float* lam_out, cudaStream_t s) {
+cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp, float* lam_out, cudaStream_t s,
+                         const float* lam_add) {
   AdjArgs d{};
   d.lam = lam;
   d.lamp = const_cast<float*>(lamp);
   d.lam_out = lam_out;
+  d.lam_add = lam_add;
   return launch_push2<false>(a, d, s);
 }
 

@@ -1,0 +1,528 @@
+// adjoint_ml.cu -- reverse mode of the multi-level advance (Algorithm 1) with
+// FP32 storage: the transposed downward and upward transfers (Sec. 5.2 and
+// 5.3, with their S^neq rescaling) and the checkpointed driver behind
+// hlbm_forward_record / hlbm_adjoint for lattices with a device hierarchy.
+//
+// One coarse step of Algorithm 1 is a fixed sequence of operations on the
+// per-level states A_l (read buffer) and P_l (the state before the level's
+// last step, read by the downward transfer of the next finer level):
+//   SC(l)      P_l <- A_l, A_l <- step(A_l)          (interface nodes copy)
+//   DOWN(l, s) A_l[I^d_l] <- D(P_{l+1}) (s = 1) or D((P_{l+1} + A_{l+1}) / 2)
+//   UP(l)      A_{l+1}[I^u_{l+1}] <- U(A_l)
+// The reverse pass walks that sequence backwards with the adjoints lambda_A,
+// lambda_P of every level:
+//   SC^T    lambda_A <- (d step / d A)^T lambda_A + lambda_P, lambda_P <- 0
+//   DOWN^T  lambda_P_{l+1} (and lambda_A_{l+1} at s = 2) += (dD)^T lambda_A_l[I^d],
+//           lambda_A_l[I^d] <- 0
+//   UP^T    lambda_A_l += (dU)^T lambda_A_{l+1}[I^u], lambda_A_{l+1}[I^u] <- 0
+// Each checkpoint segment is recomputed first: every SC writes a fresh output
+// buffer and its pre-collision moments; the transfers write in place and keep
+// the values they overwrite (an undo log), which the reverse pass puts back,
+// so that every operation sees its inputs as they were in the forward run.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "hierarchy.cuh"
+#include "hlbm_internal.h"
+#include "lattice_state.h"
+#include "multilevel.cuh"
+
+namespace hlbm {
+namespace {
+
+constexpr int64_t kBlockVals = int64_t(kRows) * kCells;
+
+__device__ __forceinline__ int64_t find_block(const LevelView& v, int x, int y, int z) {
+  const int bx = x >> 3, by = y >> 3, bz = z >> 3;
+  if (bx < 0 || by < 0 || bz < 0 || bx >= v.d.nx || by >= v.d.ny || bz >= v.d.nz) return -1;
+  return v.slot[(int64_t(bz) * v.d.ny + by) * v.d.nx + bx];
+}
+
+__device__ __forceinline__ int node_cell(int x, int y, int z) { return (x & 7) + 8 * (y & 7) + 64 * (z & 7); }
+
+// Coarse stencil indices along one axis, as the downward transfer takes them.
+__device__ __forceinline__ void stencil_axis(int p, int n, int periodic, int& lo, int& hi) {
+  lo = p >> 1;
+  hi = (p + 1) >> 1;
+  if (hi >= n) hi = periodic ? hi - n : n - 1;
+}
+
+// Moments (delta_rho, u, S) of a node of an FP32 level (paired node order).
+__device__ __forceinline__ void load_f32(const void* base, int64_t blk, int cell, float (&m)[kRows]) {
+  const float* p = static_cast<const float*>(base) + blk * kBlockVals + node_offset<float>(cell);
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) m[r] = p[r * kCells];
+}
+
+// Adds to the adjoint of stored moments m (delta_rho, u, S) the contribution
+// of a weighted S^neq = S - u u split: lam_rho, lam_u (before the split) and
+// lam_sn, all times w.
+__device__ __forceinline__ void add_split_adjoint(float* lam, const float (&m)[kRows], float w, float lrho,
+                                                  const float (&lu)[3], const float (&lsn)[6], bool atomic) {
+  const float ux = m[1], uy = m[2], uz = m[3];
+  float v[kRows];
+  v[0] = w * lrho;
+  v[1] = w * (lu[0] - (2.f * ux * lsn[0] + uy * lsn[3] + uz * lsn[4]));
+  v[2] = w * (lu[1] - (2.f * uy * lsn[1] + ux * lsn[3] + uz * lsn[5]));
+  v[3] = w * (lu[2] - (2.f * uz * lsn[2] + ux * lsn[4] + uy * lsn[5]));
+#pragma unroll
+  for (int r = 0; r < 6; ++r) v[4 + r] = w * lsn[r];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    if (atomic)
+      atomicAdd(lam + r * kCells, v[r]);
+    else
+      lam[r * kCells] += v[r];
+  }
+}
+
+struct DownAdjArgs {
+  LevelView fine, coarse;  // coarse.mom = A_{l+1} (new), coarse.mom_other = P_{l+1} (old)
+  const int32_t* nodes;    // I^d_l: (block << 9) | cell
+  int64_t n_nodes;
+  int avg;                 // 1: s = 2 (temporal midpoint), 0: s = 1 (old state only)
+  float k;                 // S^neq factor of the transfer
+  int periodic[3];
+  float* lam_fine;         // lambda_A_l, natural order: read at I^d, then zeroed
+  float* lam_new;          // lambda_A_{l+1} (s = 2)
+  float* lam_old;          // lambda_P_{l+1}
+};
+
+// Transposed downward transfer.  The forward value at fine node n is
+//   rho = sum_j w_j rho_j, u = sum_j w_j u_j, sn = sum_j w_j (S_j - u_j u_j),
+//   stored (rho - 1, u, k sn + u u)
+// over the distinct coarse stencil nodes j (and over the old and new states
+// with weight 1/2 each at s = 2).  Coarse nodes are shared between fine
+// nodes, so their adjoints are accumulated with atomics.
+__global__ void k_down_adj(DownAdjArgs a) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= a.n_nodes) return;
+  const int32_t v = a.nodes[k];
+  const int64_t b = v >> 9;
+  const int cell = v & 511;
+  const int32_t* c = a.fine.coords + 3 * b;
+  const int p[3] = {c[0] * 8 + (cell & 7), c[1] * 8 + ((cell >> 3) & 7), c[2] * 8 + (cell >> 6)};
+  const int n[3] = {a.coarse.d.nx * 8, a.coarse.d.ny * 8, a.coarse.d.nz * 8};
+  int lo[3], hi[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) stencil_axis(p[ax], n[ax], a.periodic[ax], lo[ax], hi[ax]);
+  const int nx = hi[0] != lo[0] ? 2 : 1, ny = hi[1] != lo[1] ? 2 : 1, nz = hi[2] != lo[2] ? 2 : 1;
+  const int nq = nx * ny * nz;
+  const float w = 1.f / float(nq);
+  int64_t cb[8];
+  int cc[8];
+  for (int q = 0; q < nq; ++q) {
+    const int qx = q % nx, qy = (q / nx) % ny, qz = q / (nx * ny);
+    const int x = qx ? hi[0] : lo[0], y = qy ? hi[1] : lo[1], z = qz ? hi[2] : lo[2];
+    cb[q] = find_block(a.coarse, x, y, z);
+    cc[q] = node_cell(x, y, z);
+    if (cb[q] < 0) return;  // the forward transfer reported this already
+  }
+  // lambda at the fine node; the transfer overwrote the node, so its own
+  // adjoint ends here
+  float* lf = a.lam_fine + b * kBlockVals + cell;
+  float L[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    L[r] = lf[r * kCells];
+    lf[r * kCells] = 0.f;
+  }
+  // the interpolated velocity (FP64 sums as in the forward transfer)
+  double su[3] = {0.0, 0.0, 0.0};
+  for (int q = 0; q < nq; ++q) {
+    float m[kRows];
+    if (a.avg) {
+      float o[kRows];
+      load_f32(a.coarse.mom_other, cb[q], cc[q], o);
+      load_f32(a.coarse.mom, cb[q], cc[q], m);
+      for (int ax = 0; ax < 3; ++ax) su[ax] += 0.5 * double(w) * (double(o[1 + ax]) + double(m[1 + ax]));
+    } else {
+      load_f32(a.coarse.mom_other, cb[q], cc[q], m);
+      for (int ax = 0; ax < 3; ++ax) su[ax] += double(w) * double(m[1 + ax]);
+    }
+  }
+  const float ux = float(su[0]), uy = float(su[1]), uz = float(su[2]);
+  // adjoint of stored S = k sn + u u and of u
+  float lu[3];
+  lu[0] = L[1] + 2.f * ux * L[4] + uy * L[7] + uz * L[8];
+  lu[1] = L[2] + 2.f * uy * L[5] + ux * L[7] + uz * L[9];
+  lu[2] = L[3] + 2.f * uz * L[6] + ux * L[8] + uy * L[9];
+  float lsn[6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) lsn[r] = a.k * L[4 + r];
+  for (int q = 0; q < nq; ++q) {
+    float m[kRows];
+    load_f32(a.coarse.mom_other, cb[q], cc[q], m);
+    add_split_adjoint(a.lam_old + cb[q] * kBlockVals + cc[q], m, a.avg ? 0.5f * w : w, L[0], lu, lsn, true);
+    if (a.avg) {
+      load_f32(a.coarse.mom, cb[q], cc[q], m);
+      add_split_adjoint(a.lam_new + cb[q] * kBlockVals + cc[q], m, 0.5f * w, L[0], lu, lsn, true);
+    }
+  }
+}
+
+struct UpAdjArgs {
+  LevelView fine, coarse;  // fine.mom = A_l as the upward transfer read it
+  const int32_t* nodes;    // I^u_{l+1}: (block << 9) | cell of the coarse level
+  int64_t n_nodes;
+  float k;                 // S^neq factor of the transfer
+  float* lam_fine;         // lambda_A_l
+  float* lam_coarse;       // lambda_A_{l+1}: read at I^u, then zeroed
+};
+
+// Transposed upward transfer: the coarse node stores (rho_f - 1, u_f,
+// k S_f + (1 - k) u_f u_f) of its coincident fine node, which no other coarse
+// node reads, so the fine adjoint is updated without atomics.
+__global__ void k_up_adj(UpAdjArgs a) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= a.n_nodes) return;
+  const int32_t v = a.nodes[k];
+  const int64_t b = v >> 9;
+  const int cell = v & 511;
+  const int32_t* c = a.coarse.coords + 3 * b;
+  const int x = 2 * (c[0] * 8 + (cell & 7)), y = 2 * (c[1] * 8 + ((cell >> 3) & 7)), z = 2 * (c[2] * 8 + (cell >> 6));
+  const int64_t fb = find_block(a.fine, x, y, z);
+  if (fb < 0) return;
+  float* lc = a.lam_coarse + b * kBlockVals + cell;
+  float L[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    L[r] = lc[r * kCells];
+    lc[r * kCells] = 0.f;
+  }
+  const int fc = node_cell(x, y, z);
+  float m[kRows];
+  load_f32(a.fine.mom, fb, fc, m);
+  const float ux = m[1], uy = m[2], uz = m[3], e = 1.f - a.k;
+  float* lf = a.lam_fine + fb * kBlockVals + fc;
+  lf[0] += L[0];
+  lf[kCells] += L[1] + e * (2.f * ux * L[4] + uy * L[7] + uz * L[8]);
+  lf[2 * kCells] += L[2] + e * (2.f * uy * L[5] + ux * L[7] + uz * L[9]);
+  lf[3 * kCells] += L[3] + e * (2.f * uz * L[6] + ux * L[8] + uy * L[9]);
+#pragma unroll
+  for (int r = 4; r < kRows; ++r) lf[r * kCells] += a.k * L[r];
+}
+
+// Undo log of the transfers: the 10 stored values of each listed node.
+__global__ void k_gather_nodes(const float* __restrict__ buf, const int32_t* __restrict__ nodes, int64_t n,
+                               float* __restrict__ log) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int32_t v = nodes[k];
+  const float* p = buf + int64_t(v >> 9) * kBlockVals + node_offset<float>(v & 511);
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) log[k * kRows + r] = p[r * kCells];
+}
+
+__global__ void k_scatter_nodes(float* __restrict__ buf, const int32_t* __restrict__ nodes, int64_t n,
+                                const float* __restrict__ log) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int32_t v = nodes[k];
+  float* p = buf + int64_t(v >> 9) * kBlockVals + node_offset<float>(v & 511);
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) p[r * kCells] = log[k * kRows + r];
+}
+
+inline unsigned grid_for(int64_t n) { return unsigned((n + 255) / 256); }
+
+// ---------------------------------------------------------------- host driver
+
+enum OpKind { kSC, kDown, kUp };
+
+struct Op {
+  OpKind kind;
+  int l, s;
+  // pointers as the forward recomputation used them
+  void* in = nullptr;       // SC: input state; DOWN: fine state written; UP: coarse state written
+  void* out = nullptr;      // SC: output state
+  float* pre = nullptr;     // SC: pre-collision moments
+  void* c_old = nullptr;    // DOWN: P_{l+1}
+  void* c_new = nullptr;    // DOWN: A_{l+1}; UP: the fine state read (A_l)
+  float* undo = nullptr;    // DOWN / UP: overwritten values
+};
+
+// The operations of one coarse step, in the order of AdvanceLBM (Algorithm 1).
+void coarse_step_ops(int L, int l, int s, std::vector<Op>& ops) {
+  if (l < L - 1) ops.push_back(Op{kDown, l, s});
+  ops.push_back(Op{kSC, l, 0});
+  if (l < L - 1 && s == 2) ops.push_back(Op{kUp, l, 0});
+  if (l > 0) {
+    coarse_step_ops(L, l - 1, 1, ops);
+    coarse_step_ops(L, l - 1, 2, ops);
+  }
+}
+
+GridDims level_dims(const hlbm_lattice* h, int l) {
+  int d[3];
+  h->block_dims(l, d);
+  return GridDims{d[0], d[1], d[2]};
+}
+
+LevelView level_view(const hlbm_lattice* h, int l, const void* mom, const void* other) {
+  const LevelData& L = h->lv[l];
+  LevelView v{};
+  v.d = level_dims(h, l);
+  v.slot = L.d_slot;
+  v.coords = L.d_coords;
+  v.mom = mom;
+  v.mom_other = other;
+  v.nb = L.nb;
+  v.sc = nullptr;
+  return v;
+}
+
+StepArgs level_args(const hlbm_lattice* h, int l) {
+  const LevelData& L = h->lv[l];
+  StepArgs a{};
+  a.nbr = L.d_nbr;
+  a.F = l == 0 ? h->d_F : nullptr;
+  a.eps = l == 0 ? h->d_eps : nullptr;
+  a.solid = L.d_solid;
+  a.bflags = L.d_bflags;
+  a.bmask = L.d_bmask;
+  for (int ax = 0; ax < 3; ++ax) a.fu[ax] = l == 0 ? h->fu[ax] : 0.0;
+  a.tau = L.tau;
+  a.om = 1.0 / L.tau;
+  a.kxyz = h->cfg.xyz_literal ? 13.5 : 27.0;
+  a.nb = L.nb;
+  return a;
+}
+
+}  // namespace
+
+int ml_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every) {
+  const int L = h->cfg.num_levels;
+  const int32_t per = 1 << (L - 1);
+  if (h->cfg.storage != HLBM_STORE_F32)
+    return fail(h, HLBM_E_UNSUPPORTED, "the adjoint of a multi-level or sparse lattice needs FP32 storage");
+  if (n_steps % per != 0 || ckpt_every % per != 0)
+    return fail(h, HLBM_E_INVALID_ARG, "n_steps and ckpt_every must be multiples of %d fine steps", per);
+  const int32_t n_coarse = n_steps / per, k_coarse = ckpt_every / per;
+  const int n_ck = (n_coarse + k_coarse - 1) / k_coarse;
+  int rc;
+  for (int c = 0; c < n_ck; ++c)
+    for (int l = 0; l < L; ++l) {
+      void* p = nullptr;
+      if ((rc = LatticeOps::alloc(h, &p, size_t(h->lv[l].nb) * kBlockVals * sizeof(float)))) return rc;
+      h->ckpt.push_back(p);
+    }
+  for (int32_t t = 0; t < n_coarse; ++t) {
+    if (t % k_coarse == 0)
+      for (int l = 0; l < L; ++l) {
+        const LevelData& Lv = h->lv[l];
+        if (Lv.nb == 0) continue;
+        const cudaError_t e = cudaMemcpyAsync(h->ckpt[size_t(t / k_coarse) * L + l], Lv.d_mom[Lv.cur],
+                                              size_t(Lv.nb) * kBlockVals * sizeof(float), cudaMemcpyDeviceToDevice,
+                                              h->stream);
+        if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "checkpoint copy: %s", cudaGetErrorString(e));
+      }
+    if ((rc = ml_advance_coarse(h, 1))) return rc;
+  }
+  h->rec_steps = n_steps;
+  h->rec_every = ckpt_every;
+  return ml_check_status(h);
+}
+
+int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
+  const int L = h->cfg.num_levels;
+  const int32_t per = 1 << (L - 1);
+  const int32_t n_coarse = h->rec_steps / per, k_coarse = h->rec_every / per;
+  const int n_seg = (n_coarse + k_coarse - 1) / k_coarse;
+  std::vector<size_t> vals(L);
+  size_t vmax = 0;
+  for (int l = 0; l < L; ++l) {
+    vals[l] = size_t(h->lv[l].nb) * kBlockVals;
+    if (vals[l] > vmax) vmax = vals[l];
+  }
+  std::vector<void*> tmp;
+  auto release_all = [&]() {
+    for (void*& p : tmp) LatticeOps::release(h, p);
+  };
+  int rc = HLBM_OK;
+  auto get = [&](size_t bytes, void** out) -> int {
+    *out = nullptr;
+    if (rc != HLBM_OK) return rc;
+    rc = LatticeOps::alloc(h, out, bytes);
+    if (rc == HLBM_OK && *out != nullptr) tmp.push_back(*out);
+    return rc;
+  };
+  // one coarse step's operations; the segment repeats them
+  std::vector<Op> step_ops;
+  coarse_step_ops(L, L - 1, 1, step_ops);
+  // adjoints (each sized for the largest level, so that buffers can swap)
+  std::vector<float*> lamA(L), lamP(L);
+  float *spare = nullptr, *lamp = nullptr;
+  double* dF = nullptr;
+  for (int l = 0; l < L; ++l) {
+    void* p;
+    get(vmax * sizeof(float), &p);
+    lamA[l] = static_cast<float*>(p);
+    get(vmax * sizeof(float), &p);
+    lamP[l] = static_cast<float*>(p);
+  }
+  {
+    void* p;
+    get(vmax * sizeof(float), &p);
+    spare = static_cast<float*>(p);
+    get(vmax * sizeof(float), &p);
+    lamp = static_cast<float*>(p);
+    get(size_t(h->lv[0].nb) * 3 * kCells * sizeof(double), &p);
+    dF = static_cast<double*>(p);
+  }
+  // segment buffers: working copies of the checkpoint, one output and one
+  // pre-collision buffer per SC operation, undo logs per transfer
+  std::vector<void*> work(L, nullptr);
+  for (int l = 0; l < L; ++l) get(vals[l] * sizeof(float), &work[l]);
+  std::vector<Op> seg_ops;
+  for (int c = 0; c < k_coarse; ++c) seg_ops.insert(seg_ops.end(), step_ops.begin(), step_ops.end());
+  for (Op& op : seg_ops) {
+    void* p;
+    if (op.kind == kSC) {
+      get(vals[op.l] * sizeof(float), &op.out);
+      get(vals[op.l] * sizeof(float), &p);
+      op.pre = static_cast<float*>(p);
+    } else {
+      const int64_t n = op.kind == kDown ? h->lv[op.l].n_down : h->lv[op.l + 1].n_up;
+      get(size_t(n) * kRows * sizeof(float), &p);
+      op.undo = static_cast<float*>(p);
+    }
+  }
+  if (rc != HLBM_OK) {
+    release_all();
+    return rc;
+  }
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  size_t off = 0;
+  for (int l = 0; l < L && e == cudaSuccess; ++l) {
+    if (vals[l]) e = cudaMemcpyAsync(lamA[l], dL_dM + off, vals[l] * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && vals[l]) e = cudaMemsetAsync(lamP[l], 0, vals[l] * sizeof(float), st);
+    off += vals[l];
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(dF, 0, size_t(h->lv[0].nb) * 3 * kCells * sizeof(double), st);
+
+  for (int sgi = n_seg - 1; sgi >= 0 && e == cudaSuccess; --sgi) {
+    const int nc = (n_coarse - sgi * k_coarse) < k_coarse ? (n_coarse - sgi * k_coarse) : k_coarse;
+    const size_t n_ops = size_t(nc) * step_ops.size();
+    // 1. recompute the segment from its checkpoint, logging what every operation read
+    std::vector<void*> cur(L), prev(L, nullptr);
+    for (int l = 0; l < L && e == cudaSuccess; ++l) {
+      if (vals[l])
+        e = cudaMemcpyAsync(work[l], h->ckpt[size_t(sgi) * L + l], vals[l] * sizeof(float),
+                            cudaMemcpyDeviceToDevice, st);
+      cur[l] = work[l];
+    }
+    for (size_t i = 0; i < n_ops && e == cudaSuccess; ++i) {
+      Op& op = seg_ops[i];
+      const int l = op.l;
+      if (op.kind == kSC) {
+        if (h->lv[l].nb == 0) {
+          prev[l] = cur[l];
+          continue;
+        }
+        StepArgs a = level_args(h, l);
+        a.in = cur[l];
+        a.out = op.out;
+        a.pre_out = op.pre;
+        e = launch_stream_collide_record(a, st);
+        op.in = cur[l];
+        prev[l] = cur[l];
+        cur[l] = op.out;
+      } else if (op.kind == kDown) {
+        const LevelData& F = h->lv[l];
+        op.in = cur[l];
+        op.c_old = prev[l + 1];
+        op.c_new = cur[l + 1];
+        if (F.n_down == 0) continue;
+        k_gather_nodes<<<grid_for(F.n_down), 256, 0, st>>>(static_cast<const float*>(cur[l]), F.d_down, F.n_down,
+                                                           op.undo);
+        TransferArgs t{};
+        t.fine = level_view(h, l, cur[l], nullptr);
+        t.coarse = level_view(h, l + 1, cur[l + 1], prev[l + 1]);
+        t.out = cur[l];
+        t.nodes = F.d_down;
+        t.n_nodes = F.n_down;
+        t.avg = op.s == 2 ? 1 : 0;
+        t.use_other = op.s == 1 ? 1 : 0;
+        t.k = h->kdown[l];
+        for (int ax = 0; ax < 3; ++ax) t.periodic[ax] = h->cfg.periodic[ax];
+        t.status = h->d_status;
+        e = transfer_down(HLBM_STORE_F32, t, st);
+      } else {
+        const LevelData& C = h->lv[l + 1];
+        op.in = cur[l + 1];
+        op.c_new = cur[l];
+        if (C.n_up == 0) continue;
+        k_gather_nodes<<<grid_for(C.n_up), 256, 0, st>>>(static_cast<const float*>(cur[l + 1]), C.d_up, C.n_up,
+                                                         op.undo);
+        TransferArgs t{};
+        t.fine = level_view(h, l, cur[l], nullptr);
+        t.coarse = level_view(h, l + 1, cur[l + 1], nullptr);
+        t.out = cur[l + 1];
+        t.nodes = C.d_up;
+        t.n_nodes = C.n_up;
+        t.k = h->kup[l];
+        for (int ax = 0; ax < 3; ++ax) t.periodic[ax] = h->cfg.periodic[ax];
+        t.status = h->d_status;
+        e = transfer_up(HLBM_STORE_F32, t, st);
+      }
+      if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    // 2. walk the operations backwards
+    for (size_t i = n_ops; i-- > 0 && e == cudaSuccess;) {
+      const Op& op = seg_ops[i];
+      const int l = op.l;
+      if (op.kind == kSC) {
+        if (h->lv[l].nb == 0) continue;
+        StepArgs a = level_args(h, l);
+        a.in = op.in;
+        e = adjoint_collide(a, op.pre, lamA[l], lamp, l == 0 ? dF : nullptr, st);
+        if (e == cudaSuccess) e = adjoint_push(a, lamA[l], lamp, spare, st, lamP[l]);
+        if (e == cudaSuccess) e = cudaMemsetAsync(lamP[l], 0, vals[l] * sizeof(float), st);
+        std::swap(lamA[l], spare);
+      } else if (op.kind == kDown) {
+        const LevelData& F = h->lv[l];
+        if (F.n_down == 0) continue;
+        DownAdjArgs d{};
+        d.fine = level_view(h, l, op.in, nullptr);
+        d.coarse = level_view(h, l + 1, op.c_new, op.c_old);
+        d.nodes = F.d_down;
+        d.n_nodes = F.n_down;
+        d.avg = op.s == 2 ? 1 : 0;
+        d.k = float(h->kdown[l]);
+        for (int ax = 0; ax < 3; ++ax) d.periodic[ax] = h->cfg.periodic[ax];
+        d.lam_fine = lamA[l];
+        d.lam_new = lamA[l + 1];
+        d.lam_old = lamP[l + 1];
+        k_down_adj<<<grid_for(F.n_down), 256, 0, st>>>(d);
+        k_scatter_nodes<<<grid_for(F.n_down), 256, 0, st>>>(static_cast<float*>(op.in), F.d_down, F.n_down,
+                                                            op.undo);
+      } else {
+        const LevelData& C = h->lv[l + 1];
+        if (C.n_up == 0) continue;
+        UpAdjArgs u{};
+        u.fine = level_view(h, l, op.c_new, nullptr);
+        u.coarse = level_view(h, l + 1, op.in, nullptr);
+        u.nodes = C.d_up;
+        u.n_nodes = C.n_up;
+        u.k = float(h->kup[l]);
+        u.lam_fine = lamA[l];
+        u.lam_coarse = lamA[l + 1];
+        k_up_adj<<<grid_for(C.n_up), 256, 0, st>>>(u);
+        k_scatter_nodes<<<grid_for(C.n_up), 256, 0, st>>>(static_cast<float*>(op.in), C.d_up, C.n_up, op.undo);
+      }
+      if (e == cudaSuccess) e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess)
+    e = adjoint_dF_to_float(dF, dL_dF, h->lv[0].nb * 3 * kCells, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  release_all();
+  if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
+  return ml_check_status(h);
+}
+
+}  // namespace hlbm

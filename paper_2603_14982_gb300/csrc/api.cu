@@ -323,6 +323,7 @@ int32_t hlbm_set_dense(hlbm_lattice* h) {
   L.cur = 0;
   HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->have_blocks = true;
+  ++h->hier_gen;
   return HLBM_OK;
 }
 
@@ -604,7 +605,6 @@ static StepArgs level0_args(hlbm_lattice* h) {
 
 int32_t hlbm_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every) {
   if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
-  if (h->cfg.num_levels != 1) return fail(h, HLBM_E_UNSUPPORTED, "the adjoint needs a single-level lattice");
   if (h->cfg.storage != HLBM_STORE_F32 && h->cfg.storage != HLBM_STORE_F64)
     return fail(h, HLBM_E_UNSUPPORTED, "the adjoint needs FP32 or FP64 storage");
   if (!h->have_blocks) return fail(h, HLBM_E_BAD_STATE, "no blocks are stored");
@@ -614,6 +614,12 @@ int32_t hlbm_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every
   for (void*& c : h->ckpt) LatticeOps::release(h, c);
   h->ckpt.clear();
   h->rec_steps = h->rec_every = 0;
+  h->rec_gen = -1;
+  if (h->device_hierarchy) {  // block layout from the rebuild pipeline: the multi-level engine
+    if ((rc = ml_forward_record(h, n_steps, ckpt_every))) return rc;
+    h->rec_gen = h->hier_gen;
+    return HLBM_OK;
+  }
   LevelData& L = h->lv[0];
   const size_t bytes = size_t(L.nb) * kRows * kCells * (h->cfg.storage == HLBM_STORE_F64 ? 8 : 4);
   const int n_ck = (n_steps + ckpt_every - 1) / ckpt_every;
@@ -630,6 +636,7 @@ int32_t hlbm_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every
   }
   h->rec_steps = n_steps;
   h->rec_every = ckpt_every;
+  h->rec_gen = h->hier_gen;
   return HLBM_OK;
 }
 
@@ -637,8 +644,10 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
   if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
   if (h->rec_steps <= 0) return fail(h, HLBM_E_BAD_STATE, "call hlbm_forward_record first");
   if (dL_dM_dev == nullptr || dL_dF_dev == nullptr) return fail(h, HLBM_E_INVALID_ARG, "NULL buffer");
+  if (h->rec_gen != h->hier_gen) return fail(h, HLBM_E_BAD_STATE, "the block layout changed after hlbm_forward_record");
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
+  if (h->device_hierarchy) return ml_adjoint(h, dL_dM_dev, dL_dF_dev);
   LevelData& L = h->lv[0];
   const int64_t nb = L.nb;
   const size_t bytes = size_t(nb) * kRows * kCells * (h->cfg.storage == HLBM_STORE_F64 ? 8 : 4);

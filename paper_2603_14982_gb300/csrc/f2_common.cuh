@@ -175,6 +175,19 @@ __device__ __forceinline__ int block_dir(int hx, int hy, int hz) {
   return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
 }
 
+// Bit K set when x - c_K of block-local node (x, y, z) lies in a neighbour
+// block whose bit is set in miss (bit (dx+1) + 3 (dy+1) + 9 (dz+1)).  Slot K
+// of such a node receives no halo push: it still holds a wrapped own push.
+__device__ __forceinline__ unsigned missing_sources(int x, int y, int z, unsigned miss) {
+  unsigned m = 0;
+#pragma unroll
+  for (int K = 0; K < 27; ++K) {
+    const int cx = K % 3 - 1, cy = (K / 3) % 3 - 1, cz = K / 9 - 1;
+    if ((miss >> block_dir(x - cx, y - cy, z - cz)) & 1u) m |= 1u << K;
+  }
+  return m;
+}
+
 __device__ __forceinline__ bool touches_missing(int x, int y, int z, unsigned miss) {
   const unsigned mx = 2u | (x == 0 ? 1u : 0u) | (x == 7 ? 4u : 0u);
   const unsigned my = 2u | (y == 0 ? 1u : 0u) | (y == 7 ? 4u : 0u);

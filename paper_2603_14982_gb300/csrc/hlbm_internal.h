@@ -62,11 +62,14 @@ cudaError_t adjoint_step(int storage, const StepArgs& a, const float* lam, float
                          cudaStream_t s);
 cudaError_t adjoint_dF_to_float(const double* dF, float* out, int64_t n, cudaStream_t s);
 // FP32 storage, reverse step from recorded pre-collision moments: adjoint_collide
-// (elementwise: lamp = (dC/dp)^T lam, dF += (dC/dF)^T lam) then adjoint_push
-// (lam_out = dL/dM of the step's input a.in; solid nodes copy lam).
+// (elementwise: lamp = (dC/dp)^T lam, dF += (dC/dF)^T lam unless dF is null;
+// solid and interface nodes get lamp = 0) then adjoint_push (lam_out = dL/dM
+// of the step's input a.in; solid nodes copy lam, interface nodes add it to
+// what streams back; lam_add, if set, is added at every node).
 cudaError_t adjoint_collide(const StepArgs& a, const float* pre, const float* lam, float* lamp, double* dF,
                             cudaStream_t s);
-cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp, float* lam_out, cudaStream_t s);
+cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp, float* lam_out, cudaStream_t s,
+                         const float* lam_add = nullptr);
 // adjoint_push of a step fused with adjoint_collide of the step before it
 // (recorded p = pre_prev): writes that step's lamp to lamp_out, adds to dF.
 // The step's own lam_out is not stored.

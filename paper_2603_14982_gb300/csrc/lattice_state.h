@@ -58,8 +58,11 @@ struct hlbm_lattice {
   int* d_status = nullptr;    // device status word of the transfer kernels (0 = ok)
   unsigned long long* d_count = nullptr;  // scratch counter (particles dropped by a deposit)
   // forward run recorded for the adjoint: states at steps 0, K, 2K, ...
+  // (multi-level: one buffer per level and checkpoint, [c * L + l])
   std::vector<void*> ckpt;
   int32_t rec_steps = 0, rec_every = 0;
+  int64_t hier_gen = 0;  // bumped whenever the block layout changes
+  int64_t rec_gen = -1;  // hier_gen of the recorded run
   std::string err;
 
   void block_dims(int level, int dims[3]) const {
@@ -80,6 +83,12 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
                int64_t n_blocks, int64_t counts_out[3]);
 int ml_advance_coarse(hlbm_lattice* h, int64_t n_coarse);
 int ml_check_status(hlbm_lattice* h);
+// Reverse mode of the multi-level advance, FP32 storage (adjoint_ml.cu):
+// record n_steps fine steps with a checkpoint of every level each ckpt_every
+// fine steps (both multiples of 2^(L-1)), then the adjoint from dL/dM of the
+// final state (levels concatenated) to dL/dF of the level-0 force.
+int ml_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every);
+int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF);
 
 struct LatticeOps {
   static int set_device(hlbm_lattice* h);

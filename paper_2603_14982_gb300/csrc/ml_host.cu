@@ -387,6 +387,7 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
   h->d_eps = nullptr;
   h->have_blocks = true;
   h->device_hierarchy = true;
+  ++h->hier_gen;
   if (counts_out != nullptr) {
     counts_out[0] = refined;
     counts_out[1] = coarsened;

@@ -274,7 +274,9 @@ class Lattice:
         self._check(self.lib.hlbm_forward_record(self.h, int(n_steps), int(ckpt_every)))
 
     def adjoint(self, dL_dM, dL_dF):
-        """dL_dM: torch CUDA float32 [n][10][512]; dL_dF: torch CUDA float32 [n][3][512] (written)."""
+        """dL_dM: torch CUDA float32 [n][10][512] of the final state (multi-level
+        lattices: every level's blocks, level 0 first); dL_dF: torch CUDA
+        float32 [n0][3][512] (written)."""
         self._check(self.lib.hlbm_adjoint(self.h, _ptr(dL_dM)[0], _ptr(dL_dF)[0]))
         return dL_dF
 
@@ -399,10 +401,11 @@ def blocks_to_dense(Mb, shape, coords=None, fill=np.nan):
 
 
 def make_force_autograd(lattice, n_steps, ckpt_every):
-    """A torch.autograd.Function mapping the level-0 force field F ([n][3][512]
-    float32 CUDA) to the stored moments after ``n_steps`` steps from the
-    lattice's current state ([n][10][512] float32 CUDA, public layout).  The
-    backward pass runs the library's checkpointed adjoint."""
+    """A torch.autograd.Function mapping the level-0 force field F ([n0][3][512]
+    float32 CUDA) to the stored moments after ``n_steps`` fine steps from the
+    lattice's current state ([n][10][512] float32 CUDA, public layout; every
+    level's blocks, level 0 first).  The backward pass runs the library's
+    checkpointed adjoint."""
     import torch
 
     class ForceToMoments(torch.autograd.Function):
@@ -411,8 +414,13 @@ def make_force_autograd(lattice, n_steps, ckpt_every):
             Fc = F.detach().contiguous()
             lattice.set_force(Fc)
             lattice.forward_record(n_steps, ckpt_every)
-            out = torch.empty((lattice.num_blocks(0), 10, 512), dtype=torch.float32, device=F.device)
-            lattice.read_moments(out)
+            counts = [lattice.num_blocks(l) for l in range(lattice.levels)]
+            out = torch.empty((sum(counts), 10, 512), dtype=torch.float32, device=F.device)
+            o = 0
+            for l, n in enumerate(counts):
+                if n:
+                    lattice.read_moments(out[o:o + n], level=l)
+                o += n
             lattice.synchronize()
             return out
 

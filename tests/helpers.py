@@ -58,3 +58,39 @@ def oracle_node_update(M, nodes, tau, periodic, force=None, eps=None, solid=None
         Mn = sl.step(P, tau, force=Fp, eps=ep, periodic=(True, True, True), solid=sp, mode=mode, blocked=blocked)
         out.append(Mn[:, 1, 1, 1].numpy())
     return np.stack(out, axis=1)
+
+
+# Multi-level adjoint cases: a hierarchy, per-level dense initial fields (a
+# shear wave), a seeded level-0 force field and loss weights W_l (zero where
+# level l stores no node) for L = sum_l <W_l, M_l> after n_coarse coarse steps.
+ML_ADJOINT_CASES = {
+    # two levels, fully periodic: a refined band across the domain
+    "two_level": dict(ext=(16, 128, 16), L=2, band=(slice(None), slice(7, 9), slice(None)),
+                      periodic=(True, True, True), tau0=0.8, n_coarse=3, ckpt=2),
+    # three levels, a refined patch on the floor wall (bounce-back at y = 0, 127)
+    "three_level_wall": dict(ext=(32, 128, 32), L=3, band=(slice(1, 3), slice(0, 2), slice(1, 3)),
+                             periodic=(True, False, True), tau0=0.9, n_coarse=2, ckpt=1),
+}
+
+
+def ml_adjoint_case(name, seed=11):
+    from oracle import hierarchy as hy
+    from oracle import multilevel as ml
+    from paper_2603_14982_gb300 import workloads as wl
+    c = dict(ML_ADJOINT_CASES[name])
+    ext, L = c["ext"], c["L"]
+    O0 = np.zeros(hy.block_dims(ext, 8, 0), bool)
+    O0[c["band"]] = True
+    h = hy.Hierarchy(O0, ext, 8, L, c["periodic"])
+    m = ml.MultiLevel(h, c["tau0"])
+    M0 = []
+    for l in range(L):
+        X, Y, Z = m.node_positions(l)
+        ux = 0.01 * np.sin(2 * np.pi * Y / ext[1])
+        M0.append(wl.equilibrium_field(np.ones_like(ux) + 1e-3 * np.cos(2 * np.pi * X / 16), ux, 0.3 * ux,
+                                       np.zeros_like(ux)))
+    rng = np.random.default_rng(seed)
+    F = rng.normal(0.0, 1e-5, (3,) + m.shape[0])
+    W = [rng.normal(size=(10,) + m.shape[l]) * m.stored[l].numpy() for l in range(L)]
+    c.update(O0=O0, h=h, M0=M0, F=F, W=W, stored=[m.stored[l].numpy() for l in range(L)])
+    return c
