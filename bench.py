@@ -295,6 +295,40 @@ def bench_adjoint(hl, wl, stream, n=128, steps=200, ckpt=20):
             "finite": bool(torch.isfinite(dF).all().item())}
 
 
+def bench_ml_adjoint(hl, wl, stream, pos0, n=512, fine_steps=40, ckpt=8):
+    """Forward vs checkpointed adjoint of the three-level advance (Algorithm 1
+    with both transfers) on the n^3 fine-equivalent hierarchy of the falling
+    cloud at its start, with its deposited drag and fluid fraction; FP32."""
+    import torch
+    L = 3
+    with hl.Lattice((n, n, n), levels=L, tau=0.9, periodic=(True, False, True), storage="f32",
+                    stream=stream.cuda_stream) as lat:
+        lat.rebuild_from_particles(pos0)
+        lat.deposit_particles(pos0)
+        counts = [lat.num_blocks(l) for l in range(L)]
+        start = [lat.read_moments(torch.empty((c, 10, 512), dtype=torch.float32, device="cuda"), level=l)
+                 for l, c in enumerate(counts)]
+
+        def reset():
+            for l in range(L):
+                lat.write_moments(start[l], level=l)
+
+        lat.step(8)  # loads every kernel once
+        reset()
+        t_fwd = timed(stream, lambda: lat.step(fine_steps))
+        reset()
+        t_rec = timed(stream, lambda: lat.forward_record(fine_steps, ckpt))
+        lam = torch.zeros((sum(counts), 10, 512), dtype=torch.float32, device="cuda")
+        lam[:, 1:4] = 1e-3
+        dF = torch.empty((counts[0], 3, 512), dtype=torch.float32, device="cuda")
+        t_adj = timed(stream, lambda: lat.adjoint(lam, dF))
+    return {"n": n, "levels": L, "fine_steps": fine_steps, "ckpt_every": ckpt, "blocks_per_level": counts,
+            "forward_ms": round(t_fwd, 3), "forward_record_ms": round(t_rec, 3), "adjoint_ms": round(t_adj, 3),
+            "adjoint_over_forward": round(t_adj / t_fwd, 3),
+            "record_plus_adjoint_over_forward": round((t_rec + t_adj) / t_fwd, 3),
+            "finite": bool(torch.isfinite(dF).all().item())}
+
+
 def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebuild_every=10):
     """Three-level lattice over an n^3 fine-equivalent domain driven by a falling
     particle cloud (pos0, device, not modified): rebuild at the first
@@ -373,6 +407,7 @@ def bench_extras(hl, wl):
             rec["max_du_vs_f32_over_umax"] = du / max(umax, 1e-30)
         ml[storage] = rec
     out["c3_multilevel"] = ml
+    out["c3_adjoint"] = bench_ml_adjoint(hl, wl, stream, pos0)
     return out
 
 
@@ -404,7 +439,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the multi-level, adjoint and batched workloads")
-    ap.add_argument("--only", choices=["multilevel", "adjoint", "batched"],
+    ap.add_argument("--only", choices=["multilevel", "adjoint", "batched", "ml_adjoint"],
                     help="run one secondary workload alone and print its JSON (profiling runs)")
     ap.add_argument("--adj-steps", type=int, default=200)
     ap.add_argument("--adj-ckpt", type=int, default=20)
@@ -420,6 +455,8 @@ def main():
             res = bench_adjoint(hl, wl, stream, steps=args.adj_steps, ckpt=args.adj_ckpt)
         elif args.only == "batched":
             res = bench_batched(hl, wl, stream)
+        elif args.only == "ml_adjoint":
+            res = bench_ml_adjoint(hl, wl, stream, torch.tensor(wl.particle_cloud(512), device="cuda"))
         else:
             pos0 = torch.tensor(wl.particle_cloud(512), device="cuda")
             bench_multilevel(hl, wl, stream, "f32", pos0, fine_steps=48)

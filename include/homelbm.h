@@ -193,21 +193,33 @@ int32_t hlbm_synchronize(hlbm_lattice *h);
    Synchronous.  Returns HLBM_E_NONFINITE if the mass is not finite. */
 int32_t hlbm_reduce(hlbm_lattice *h, double out[7]);
 
-/* Reverse mode of the single-level step (the paper has no adjoint; this
+/* Reverse mode of the stream-collide step (the paper has no adjoint; this
    differentiates Sec. 3.1 with the Guo force and eps*tau of Sec. 4 with
-   respect to the level-0 force field).
-   hlbm_forward_record advances n_steps steps like hlbm_step and keeps the
-   state every ckpt_every steps (device memory, one moment buffer each).
+   respect to the level-0 force field) and, on lattices whose blocks come from
+   the rebuild pipeline (hlbm_set_fine_blocks / hlbm_rebuild_from_particles),
+   of the whole multi-level advance of Algorithm 1: sub-cycled level steps,
+   the downward transfer with its temporal midpoint and the upward transfer,
+   both with their S^neq rescaling (Sec. 5.2, 5.3).
+   hlbm_forward_record advances n_steps fine steps like hlbm_step and keeps
+   the state every ckpt_every fine steps (device memory; multi-level: every
+   level's current state, and both counts must be multiples of 2^(L-1)).
    hlbm_adjoint then takes dL/dM of the final stored moments (float32 device
-   buffer, public layout [nb][10][512], rho row = d/d rho) and writes dL/dF
-   (float32 device [nb][3][512], the layout of hlbm_set_force) by recomputing
-   each checkpoint segment and stepping backwards; the force sums are FP64.
-   Device memory during the call: with FP32 storage, the K = ckpt_every states
-   and pre-collision moment fields of one segment (2 K x 40 B per node) plus
-   four float32 moment-sized buffers and the FP64 dL/dF sum (24 B per node);
-   with FP64 storage, K - 1 states (80 B per node each) and the same buffers.
-   Single-level lattices with FP32 or FP64 storage; force, eps and solids must
-   not change between the two calls.  Synchronous. */
+   buffer, public layout [nb][10][512], rho row = d/d rho; multi-level: every
+   level's blocks in level order, level 0 first) and writes dL/dF (float32
+   device [nb0][3][512], the layout of hlbm_set_force) by recomputing each
+   checkpoint segment and stepping backwards; the force sums are FP64.
+   Device memory during the call, single level: with FP32 storage, the K =
+   ckpt_every states and pre-collision moment fields of one segment (2 K x 40
+   B per node) plus four float32 moment-sized buffers and the FP64 dL/dF sum
+   (24 B per node); with FP64 storage, K - 1 states (80 B per node each) and
+   the same buffers.  Multi-level: per level step of a segment one state and
+   one pre-collision field (2 x 40 B per node of that level), the values each
+   transfer overwrites, one working copy of the checkpoint, and 2 L + 2
+   float32 moment-sized buffers of the largest level.
+   Single-level lattices with FP32 or FP64 storage, multi-level lattices with
+   FP32 storage (HLBM_E_UNSUPPORTED otherwise); force, eps and solids must not
+   change between the two calls, and a change of the block layout in between
+   makes hlbm_adjoint fail with HLBM_E_BAD_STATE.  Synchronous. */
 int32_t hlbm_forward_record(hlbm_lattice *h, int32_t n_steps, int32_t ckpt_every);
 int32_t hlbm_adjoint(hlbm_lattice *h, const float *dL_dM_dev, float *dL_dF_dev);
 

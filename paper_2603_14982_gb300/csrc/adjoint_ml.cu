@@ -480,8 +480,9 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         StepArgs a = level_args(h, l);
         a.in = op.in;
         e = adjoint_collide(a, op.pre, lamA[l], lamp, l == 0 ? dF : nullptr, st);
-        if (e == cudaSuccess) e = adjoint_push(a, lamA[l], lamp, spare, st, lamP[l]);
-        if (e == cudaSuccess) e = cudaMemsetAsync(lamP[l], 0, vals[l] * sizeof(float), st);
+        // lambda_P of level 0 stays zero: no finer level reads its previous state
+        if (e == cudaSuccess) e = adjoint_push(a, lamA[l], lamp, spare, st, l > 0 ? lamP[l] : nullptr);
+        if (e == cudaSuccess && l > 0) e = cudaMemsetAsync(lamP[l], 0, vals[l] * sizeof(float), st);
         std::swap(lamA[l], spare);
       } else if (op.kind == kDown) {
         const LevelData& F = h->lv[l];
