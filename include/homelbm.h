@@ -166,6 +166,22 @@ int32_t hlbm_set_uniform_force(hlbm_lattice *h, double fx, double fy, double fz)
    (eps = 1).  F may be NULL to return to the uniform force. */
 int32_t hlbm_set_force(hlbm_lattice *h, const float *F_dev, const float *eps_dev);
 
+/* Live drag of the coupled LBM step (Fig. 4, Sec. 5.4: streaming only, force
+   exchange, then collision).  With exchange_every = k > 0, every k-th level-0
+   step from now on (the first one included) streams, computes the drag
+     F = kappa * (1 - eps) * (vp - u*),  u* = j* / rho*
+   at every level-0 node from the streamed (pre-collision) moments, the fluid
+   fraction eps of the last hlbm_set_force / hlbm_deposit_particles (1 if
+   none) and the sediment velocity vp[3] (lattice units, host), stores it as
+   the level-0 force field (as hlbm_set_force would) and collides with it; the
+   steps in between use that field unchanged.  exchange_every = 0 turns the
+   exchange off (the field stays).  kappa and vp must be finite
+   (HLBM_E_INVALID_ARG); FP64 storage is refused (HLBM_E_UNSUPPORTED); while
+   the drag is on, hlbm_forward_record is refused (the adjoint takes F as
+   fixed).  Each exchange step holds one float32 moment-sized buffer of the
+   finest level (40 B per node) while it runs. */
+int32_t hlbm_set_drag(hlbm_lattice *h, double kappa, const double vp[3], int32_t exchange_every);
+
 /* Solid nodes of a single-level lattice, one byte per fine node (host memory,
    dense [nz][ny][nx], non-zero = solid).  Solid nodes are frozen at rest and
    fluid nodes next to them use half-way bounce-back.  NULL clears. */

@@ -17,9 +17,10 @@ Modules (each function cites the passage of the paper it follows):
                    Eq. level-selection Phi).
 * ``multilevel``   Algorithm 1 with downward/upward transfers and the S^neq
                    rescaling (Sec. 5.2, Eq. upload_S, Eq. downward_rescale).
-* ``codec``        reduced-precision moment storage (no counterpart in the paper).
-* ``adjoint``      reverse-mode gradient of the single-level step (no
-                   counterpart in the paper).
+* ``coupling``     the coupled finest-level step of Fig. 4 (streaming only,
+                   drag exchange, collision; Sec. 5.4).
+* ``adjoint``      reverse-mode gradients of the single-level step and of the
+                   multi-level advance (no counterpart in the paper).
 
 Arithmetic is float64 (complex128 for complex-step derivative checks).  Arrays
 are indexed [z, y, x]; a moment field is a tensor of shape (10, nz, ny, nx) with

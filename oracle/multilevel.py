@@ -25,6 +25,7 @@ The S^neq scale factors of the paper are not inverse to each other; the
 import numpy as np
 import torch
 
+from . import coupling as cp
 from . import lattice as lat
 from . import single_level as sl
 
@@ -117,7 +118,7 @@ def interpolate_down(Mc, nodes, periodic, k_down):
 class MultiLevel:
     """State and Algorithm 1 driver over a fixed ``oracle.hierarchy.Hierarchy``."""
 
-    def __init__(self, hier, tau0, mode="hermite", rescale="post", force=None, eps=None):
+    def __init__(self, hier, tau0, mode="hermite", rescale="post", force=None, eps=None, drag=None):
         self.h = hier
         self.L = hier.L
         self.mode = mode
@@ -125,6 +126,8 @@ class MultiLevel:
         self.tau = level_taus(tau0, self.L)
         self.force = force          # level-0 dense (3, nz, ny, nx) tensor, tuple or None
         self.eps = eps              # level-0 dense (nz, ny, nx) tensor or None
+        self.drag = drag            # (kappa, vp, every): coupled level-0 steps (``coupling``)
+        self.l0_steps = 0
         self.periodic = hier.periodic
         self.buf = [[None, None] for _ in range(self.L)]
         self.cur = [0] * self.L
@@ -182,8 +185,16 @@ class MultiLevel:
         M = self.current(l)
         force = self.force if l == 0 else None
         eps = self.eps if l == 0 else None
-        Mn = sl.step(M, self.tau[l], force=force, eps=eps, periodic=self.periodic,
-                     mode=self.mode, update=self.update[l], blocked=self.blocked[l])
+        if l == 0 and self.drag is not None and self.l0_steps % self.drag[2] == 0:
+            # S, drag exchange, C (Fig. 4); the drag is the level-0 force until the next exchange
+            Mn, self.force = cp.coupled_step(M, self.tau[0], eps, self.drag[1], self.drag[0],
+                                             periodic=self.periodic, mode=self.mode,
+                                             update=self.update[0], blocked=self.blocked[0])
+        else:
+            Mn = sl.step(M, self.tau[l], force=force, eps=eps, periodic=self.periodic,
+                         mode=self.mode, update=self.update[l], blocked=self.blocked[l])
+        if l == 0:
+            self.l0_steps += 1
         self.buf[l][1 - self.cur[l]] = Mn
         self.cur[l] = 1 - self.cur[l]
 

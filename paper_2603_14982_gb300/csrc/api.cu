@@ -526,7 +526,13 @@ int32_t hlbm_step(hlbm_lattice* h, int32_t n_fine_steps) {
   for (int32_t s = 0; s < n_fine_steps; ++s) {
     a.in = L.d_mom[L.cur];
     a.out = L.d_mom[1 - L.cur];
-    HLBM_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
+    if (exchange_due(h)) {  // coupled step: S, drag exchange, C (Fig. 4)
+      if ((rc = coupled_step(h, a))) return rc;
+      a.F = h->d_F;
+    } else {
+      HLBM_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
+    }
+    ++h->l0_steps;
     L.cur = 1 - L.cur;
     if ((rc = LatticeOps::maybe_rescale(h, L, false))) return rc;
   }
@@ -615,6 +621,8 @@ int32_t hlbm_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every
   h->ckpt.clear();
   h->rec_steps = h->rec_every = 0;
   h->rec_gen = -1;
+  if (h->drag_every > 0)
+    return fail(h, HLBM_E_UNSUPPORTED, "the adjoint takes the force field as fixed: disable the live drag first");
   if (h->device_hierarchy) {  // block layout from the rebuild pipeline: the multi-level engine
     if ((rc = ml_forward_record(h, n_steps, ckpt_every))) return rc;
     h->rec_gen = h->hier_gen;

@@ -53,6 +53,10 @@ cudaError_t launch_stream_collide_f2(int storage, const StepArgs& a, cudaStream_
 // FP32 storage: the step that also writes the pre-collision moments p to
 // a.pre_out (forward steps recomputed by the adjoint).
 cudaError_t launch_stream_collide_record(const StepArgs& a, cudaStream_t s);
+// FP32 / FP16 / BF16 storage: the streaming-only step S of a coupled step,
+// writing the pre-collision moments to a.pre_out (float32 natural order) and
+// no output state (coupling.cu collides).
+cudaError_t launch_stream_only(int storage, const StepArgs& a, cudaStream_t s);
 // Resident CTAs per SM of the persistent node-pair kernel.
 cudaError_t persistent_ctas_per_sm(int storage, int* per_sm);
 // One reverse step of the single-level stream-collide, FP64 storage (adjoint.cu): lam = dL/dM

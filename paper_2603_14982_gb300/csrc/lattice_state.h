@@ -62,6 +62,11 @@ struct hlbm_lattice {
   std::vector<void*> ckpt;
   int32_t rec_steps = 0, rec_every = 0;
   int64_t hier_gen = 0;  // bumped whenever the block layout changes
+  // live drag of the coupled step (coupling.cu): every drag_every-th level-0
+  // step streams, exchanges F = kappa (1 - eps) (vp - u*) and collides
+  double drag_kappa = 0, drag_vp[3] = {0, 0, 0};
+  int32_t drag_every = 0;
+  int64_t l0_steps = 0;  // level-0 steps since hlbm_set_drag
   int64_t rec_gen = -1;  // hier_gen of the recorded run
   std::string err;
 
@@ -88,6 +93,10 @@ int ml_check_status(hlbm_lattice* h);
 // fine steps (both multiples of 2^(L-1)), then the adjoint from dL/dM of the
 // final state (levels concatenated) to dL/dF of the level-0 force.
 int ml_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every);
+// The coupled level-0 step (coupling.cu): is the next level-0 step an
+// exchange step, and the step itself (a: level-0 arguments with in / out).
+bool exchange_due(const hlbm_lattice* h);
+int coupled_step(hlbm_lattice* h, const StepArgs& a);
 int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF);
 
 struct LatticeOps {

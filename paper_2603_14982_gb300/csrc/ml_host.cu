@@ -116,7 +116,12 @@ int streaming_collision(hlbm_lattice* h, int l) {
   a.kxyz = h->cfg.xyz_literal ? 13.5 : 27.0;
   a.nb = L.nb;
   a.scales_in = a.scales_out = L.d_scales;
-  ML_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
+  if (l == 0 && exchange_due(h)) {  // coupled step: S, drag exchange, C (Fig. 4)
+    ML_TRY(coupled_step(h, a));
+  } else {
+    ML_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
+  }
+  if (l == 0) ++h->l0_steps;
   L.cur = 1 - L.cur;
   return LatticeOps::maybe_rescale(h, L, false);
 }

@@ -24,6 +24,10 @@
 //     direction), projects to moments (Eq. rho_u_stress) and collides
 //     (Sec. 3.1; Guo forcing; mixture tau of Sec. 4).  Interface nodes (a
 //     neighbour block not stored) and solid nodes copy their input.
+// Modes: kPlain; kRecord also writes the pre-collision moments (recomputed
+// steps of the adjoint); kStreamOnly writes them instead of colliding (the
+// streaming-only step S of a coupled step, Fig. 4; the collision follows
+// once the drag has been exchanged).
 #include <utility>
 
 #include "f2_common.cuh"
@@ -42,7 +46,9 @@ using namespace f2;
 // barrier first.  The streaming phases are the ones of f2::stream_pairs
 // (which the reverse step of the adjoint instantiates) written out for the
 // moment source: this form measured 2 % faster for the forward kernel.
-template <typename T, bool kRecord = false>
+enum ScMode { kPlain = 0, kRecord = 1, kStreamOnly = 2 };
+
+template <typename T, int kMode = kPlain>
 __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, float2* f2buf, unsigned& s_miss) {
   float* fbuf = reinterpret_cast<float*>(f2buf);
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -197,13 +203,16 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
     copy_hi = copy_hi || touches_missing(x, y, z0 + 4, s_miss);
   }
   Mom<V2> mo;
+  if constexpr (kMode == kStreamOnly) {  // the collision step copies the input at these nodes
+    if (copy_lo && copy_hi) return;
+  }
   if (copy_lo && copy_hi) {
     mo = load_pair<T>(in, blk, own, sc_in);
   } else {
     V2 g[27];
     gather_all(f2buf, own_s, op.g13, g, std::make_integer_sequence<int, 27>{});
     const PreMom<V2> p = project(g);
-    if constexpr (kRecord) {  // pre-collision moments for the reverse step (natural order, float32)
+    if constexpr (kMode != kPlain) {  // pre-collision moments (natural order, float32)
       float* q = a.pre_out + blk * (kRows * kCells) + own;
       const V2 r[kRows] = {p.drho, p.jx, p.jy, p.jz, p.pxx, p.pyy, p.pzz, p.pxy, p.pxz, p.pyz};
 #pragma unroll
@@ -211,6 +220,7 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
         q[k * kCells] = r[k].v.x;
         q[k * kCells + 256] = r[k].v.y;
       }
+      if constexpr (kMode == kStreamOnly) return;
     }
     V2 fx, fy, fz;
     if (a.F != nullptr) {
@@ -245,7 +255,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
 __global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2_record(StepArgs a) {
   extern __shared__ __align__(16) float2 f2buf[];
   __shared__ unsigned s_miss;
-  sc_block<float, true>(a, a.blk0 + blockIdx.x, f2buf, s_miss);
+  sc_block<float, kRecord>(a, a.blk0 + blockIdx.x, f2buf, s_miss);
+}
+
+// The streaming-only step: pre-collision moments to a.pre_out, no collision.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) k_stream_f2_pre(StepArgs a) {
+  extern __shared__ __align__(16) float2 f2buf[];
+  __shared__ unsigned s_miss;
+  sc_block<T, kStreamOnly>(a, a.blk0 + blockIdx.x, f2buf, s_miss);
 }
 
 // Persistent CTAs (a grid sized to the resident capacity) that take blocks
@@ -380,6 +398,36 @@ cudaError_t launch_stream_collide_record(const StepArgs& a_in, cudaStream_t s) {
   if (a.pre_out == nullptr) return cudaErrorInvalidValue;
   k_stream_collide_f2_record<<<(unsigned)a.nb, kThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pre(const StepArgs& a_in, cudaStream_t s) {
+  StepArgs a = a_in;
+  const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t err =
+        cudaFuncSetAttribute(k_stream_f2_pre<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    configured = true;
+  }
+  for (int k = 0; k < 3; ++k) a.fuf[k] = float(a.fu[k]);
+  a.tauf = float(a.tau);
+  a.omf = float(a.om);
+  a.kxyzf = float(a.kxyz);
+  if (a.nb == 0) return cudaSuccess;
+  if (a.pre_out == nullptr) return cudaErrorInvalidValue;
+  k_stream_f2_pre<T><<<(unsigned)a.nb, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream_only(int storage, const StepArgs& a, cudaStream_t s) {
+  switch (storage) {
+    case HLBM_STORE_F32: return launch_pre<float>(a, s);
+    case HLBM_STORE_F16S: return launch_pre<__half>(a, s);
+    case HLBM_STORE_BF16S: return launch_pre<__nv_bfloat16>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t persistent_ctas_per_sm(int storage, int* per_sm) {

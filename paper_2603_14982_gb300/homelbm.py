@@ -66,6 +66,8 @@ _SIGS = {
     "hlbm_synchronize": (ctypes.c_int32, [ctypes.c_void_p]),
     "hlbm_reduce": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "hlbm_forward_record": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
+    "hlbm_set_drag": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.c_int32]),
     "hlbm_adjoint": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "hlbm_reduce_f32_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
@@ -244,6 +246,12 @@ class Lattice:
         pF = _ptr(F)[0] if F is not None else None
         pe = _ptr(eps)[0] if eps is not None else None
         self._check(self.lib.hlbm_set_force(self.h, pF, pe))
+
+    def set_drag(self, kappa, vp, exchange_every):
+        """Live drag F = kappa (1 - eps) (vp - u*) exchanged every ``exchange_every``
+        level-0 steps (0 = off); see hlbm_set_drag."""
+        v = (ctypes.c_double * 3)(*(float(x) for x in vp))
+        self._check(self.lib.hlbm_set_drag(self.h, float(kappa), v, int(exchange_every)))
 
     def set_solid(self, mask_dense):
         """mask_dense: numpy uint8/bool [nz][ny][nx] (fine nodes), or None."""
