@@ -329,19 +329,24 @@ def bench_ml_adjoint(hl, wl, stream, pos0, n=512, fine_steps=40, ckpt=8):
             "finite": bool(torch.isfinite(dF).all().item())}
 
 
-def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebuild_every=10):
+def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebuild_every=10, drag_every=0):
     """Three-level lattice over an n^3 fine-equivalent domain driven by a falling
     particle cloud (pos0, device, not modified): rebuild at the first
     coarse-step boundary at least rebuild_every fine steps after the last one,
     deposit of eta / eps / drag every coarse step.  Fine-equivalent MLUPS over
     the whole loop (wall clock, everything on one stream; only the rebuilds,
-    which read block counts back, wait for the device)."""
+    which read block counts back, wait for the device).  drag_every > 0: the
+    coupled step (streaming only, live drag F = 1e-4 eta (v_p - u*) with the
+    cloud's velocity v_p = (0, -1, 0), collision) every drag_every finest-level
+    steps."""
     import torch
     L = 3
     per = 2 ** (L - 1)
     pos = pos0.clone()
     with hl.Lattice((n, n, n), levels=L, tau=0.9, periodic=(True, False, True), storage=storage,
                     stream=stream.cuda_stream) as lat:
+        if drag_every:
+            lat.set_drag(1e-4, (0.0, -1.0, 0.0), drag_every)
         lat.rebuild_from_particles(pos)
         lat.deposit_particles(pos)
         torch.cuda.synchronize()
@@ -407,6 +412,11 @@ def bench_extras(hl, wl):
             rec["max_du_vs_f32_over_umax"] = du / max(umax, 1e-30)
         ml[storage] = rec
     out["c3_multilevel"] = ml
+    bench_multilevel(hl, wl, stream, "f32", pos0, fine_steps=48, drag_every=4)
+    rec, _ = bench_multilevel(hl, wl, stream, "f32", pos0, drag_every=4)
+    rec["drag_every"] = 4
+    rec["mlups_vs_uncoupled"] = round(rec["mlups_fine_equiv"] / ml["f32"]["mlups_fine_equiv"], 3)
+    out["c3_coupled"] = rec
     out["c3_adjoint"] = bench_ml_adjoint(hl, wl, stream, pos0)
     return out
 
