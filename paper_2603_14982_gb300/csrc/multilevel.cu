@@ -18,20 +18,37 @@ struct Node64 {
   double rho, ux, uy, uz, s[6];  // s = S^neq (xx, yy, zz, xy, xz, yz)
 };
 
+// Widening float -> double on the integer pipes.  The conversion is exact:
+// for a normal binary32 number the binary64 encoding keeps the sign, rebiases
+// the exponent by 1023 - 127 = 896 and appends 29 zero bits to the 23-bit
+// fraction, i.e. bits64 = sign | ((bits32 & 0x7fffffff) + (896 << 23)) << 29.
+// Zeros map to signed zeros; subnormals, infinities and NaNs (never seen on
+// a healthy lattice) take the conversion instruction.  The transfers are
+// bound by the FP64 pipe, which the conversion instruction also occupies.
+__device__ __forceinline__ double to64(double v) { return v; }
+__device__ __forceinline__ double to64(float v) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned a = b & 0x7fffffffu;
+  const unsigned long long sign = static_cast<unsigned long long>(b & 0x80000000u) << 32;
+  if (a >= 0x7f800000u || (a != 0u && a < 0x00800000u)) return double(v);
+  const unsigned long long mag = a == 0u ? 0ull : (static_cast<unsigned long long>(a) + (896ull << 23)) << 29;
+  return __longlong_as_double(static_cast<long long>(sign | mag));
+}
+
 template <typename T>
 __device__ __forceinline__ Node64 load64(const void* base, int64_t blk, int cell, const Scales* sc) {
   const auto m = load_node<T>(static_cast<const T*>(base), blk, cell, sc);
   Node64 n;
-  n.rho = 1.0 + double(m.drho);
-  n.ux = m.ux;
-  n.uy = m.uy;
-  n.uz = m.uz;
-  n.s[0] = double(mad(-m.ux, m.ux, m.sxx));
-  n.s[1] = double(mad(-m.uy, m.uy, m.syy));
-  n.s[2] = double(mad(-m.uz, m.uz, m.szz));
-  n.s[3] = double(mad(-m.ux, m.uy, m.sxy));
-  n.s[4] = double(mad(-m.ux, m.uz, m.sxz));
-  n.s[5] = double(mad(-m.uy, m.uz, m.syz));
+  n.rho = 1.0 + to64(m.drho);
+  n.ux = to64(m.ux);
+  n.uy = to64(m.uy);
+  n.uz = to64(m.uz);
+  n.s[0] = to64(mad(-m.ux, m.ux, m.sxx));
+  n.s[1] = to64(mad(-m.uy, m.uy, m.syy));
+  n.s[2] = to64(mad(-m.uz, m.uz, m.szz));
+  n.s[3] = to64(mad(-m.ux, m.uy, m.sxy));
+  n.s[4] = to64(mad(-m.ux, m.uz, m.sxz));
+  n.s[5] = to64(mad(-m.uy, m.uz, m.syz));
   return n;
 }
 
