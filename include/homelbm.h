@@ -83,6 +83,13 @@ typedef struct {
 
 typedef struct hlbm_lattice hlbm_lattice;
 
+/* Face conditions of hlbm_set_open_faces. */
+typedef enum {
+  HLBM_FACE_CLOSED = 0,   /* periodic or half-way bounce-back wall, as the axis is configured */
+  HLBM_FACE_OUTFLOW = 1,  /* convective outflow dM/dt + u_n dM/dn = 0 */
+  HLBM_FACE_INLET = 2     /* logarithmic inlet profile */
+} hlbm_face;
+
 /* Library version string (static). */
 const char *hlbm_version(void);
 
@@ -181,6 +188,26 @@ int32_t hlbm_set_force(hlbm_lattice *h, const float *F_dev, const float *eps_dev
    fixed).  Each exchange step holds one float32 moment-sized buffer of the
    finest level (40 B per node) while it runs. */
 int32_t hlbm_set_drag(hlbm_lattice *h, double kappa, const double vp[3], int32_t exchange_every);
+
+/* Open faces (the open scenes of Sec. 7): type[6] for the faces x-, x+, y-,
+   y+, z-, z+ (hlbm_face), host memory.  An open face needs a non-periodic
+   axis (it replaces the wall there).  The nodes of an open face layer keep
+   their moments in the step of their level; after every step of every level
+   they are written from the state before the step:
+   - HLBM_FACE_OUTFLOW: the convective equation dM/dt + u_n dM/dn = 0, first
+     order upwind: M_b <- M_b - c (M_b - M_i), with M_i the node one step
+     inward and c = clamp(u_n, 0, 1) its velocity along the outward normal
+     (the paper takes u_n from the nearest interior node);
+   - HLBM_FACE_INLET: density of M_i, velocity u(h) = u0 ln(1 + beta (h - h0))
+     along the inward normal (0 where 1 + beta (h - h0) <= 1), S = u u; h is
+     the node's coordinate along profile_axis in finest-level node units.
+   A node on several open faces takes the first open face in the order above.
+   HLBM_E_INVALID_ARG for an unknown type, an open face on a periodic axis, a
+   profile axis equal to an inlet face's axis or non-finite inlet values.
+   The adjoint is refused while a face is open.  May be called before or after
+   the blocks are set; the neighbour tables and bounce masks are rebuilt. */
+int32_t hlbm_set_open_faces(hlbm_lattice *h, const int32_t type[6], double u0, double beta, double h0,
+                            int32_t profile_axis);
 
 /* Solid nodes of a single-level lattice, one byte per fine node (host memory,
    dense [nz][ny][nx], non-zero = solid).  Solid nodes are frozen at rest and

@@ -25,6 +25,7 @@ The S^neq scale factors of the paper are not inverse to each other; the
 import numpy as np
 import torch
 
+from . import boundary as bd
 from . import coupling as cp
 from . import lattice as lat
 from . import single_level as sl
@@ -118,7 +119,7 @@ def interpolate_down(Mc, nodes, periodic, k_down):
 class MultiLevel:
     """State and Algorithm 1 driver over a fixed ``oracle.hierarchy.Hierarchy``."""
 
-    def __init__(self, hier, tau0, mode="hermite", rescale="post", force=None, eps=None, drag=None):
+    def __init__(self, hier, tau0, mode="hermite", rescale="post", force=None, eps=None, drag=None, open_faces=None):
         self.h = hier
         self.L = hier.L
         self.mode = mode
@@ -127,6 +128,7 @@ class MultiLevel:
         self.force = force          # level-0 dense (3, nz, ny, nx) tensor, tuple or None
         self.eps = eps              # level-0 dense (nz, ny, nx) tensor or None
         self.drag = drag            # (kappa, vp, every): coupled level-0 steps (``coupling``)
+        self.open_faces = open_faces  # (types[6], (u0, beta, h0, axis)): open faces (``boundary``)
         self.l0_steps = 0
         self.periodic = hier.periodic
         self.buf = [[None, None] for _ in range(self.L)]
@@ -142,7 +144,10 @@ class MultiLevel:
             miss = h.missing_nodes(l)
             self.shape.append(st.shape)
             self.stored.append(torch.as_tensor(st))
-            self.update.append(torch.as_tensor(st & ~miss))
+            upd = torch.as_tensor(st & ~miss)
+            if self.open_faces is not None:
+                upd &= ~bd.layer(tuple(st.shape), self.open_faces[0])
+            self.update.append(upd)
             self.down.append(np.nonzero(h.down_nodes(l)))
             self.up.append(np.nonzero(h.up_nodes(l)))
             self.blocked.append(sl.blocked_sources(st.shape, self.periodic))
@@ -193,6 +198,8 @@ class MultiLevel:
         else:
             Mn = sl.step(M, self.tau[l], force=force, eps=eps, periodic=self.periodic,
                          mode=self.mode, update=self.update[l], blocked=self.blocked[l])
+        if self.open_faces is not None:
+            Mn = bd.apply(M, Mn, self.open_faces[0], l, self.open_faces[1], stored=self.stored[l])
         if l == 0:
             self.l0_steps += 1
         self.buf[l][1 - self.cur[l]] = Mn

@@ -97,6 +97,21 @@ def step(M, tau, force=None, eps=None, periodic=(True, True, True), solid=None,
     return torch.where(keep.unsqueeze(0), M, Mn)
 
 
+def run_open(M, n_steps, tau, types, inlet=(0.0, 0.0, 0.0, 1), force=None, eps=None, periodic=(True, True, True),
+             solid=None, mode="hermite"):
+    """Steps with open faces (``oracle.boundary``): the face layers keep their
+    moments in the step and are then written from the state before it."""
+    from . import boundary as bd
+    shape = tuple(M.shape[1:])
+    keep_open = bd.layer(shape, types)
+    blocked = blocked_sources(shape, periodic, solid)
+    for _ in range(n_steps):
+        Mn = step(M, tau, force=force, eps=eps, periodic=periodic, solid=solid, mode=mode, update=~keep_open,
+                  blocked=blocked)
+        M = bd.apply(M, Mn, types, 0, inlet)
+    return M
+
+
 def run(M, n_steps, tau, **kw):
     """Apply ``step`` n times."""
     periodic = kw.get("periodic", (True, True, True))

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libhomelbm.so")
 SOURCES = ["api.cu", "stream_collide.cu", "stream_collide_f2.cu", "io_reduce.cu", "hierarchy.cu", "multilevel.cu",
-           "ml_host.cu", "adjoint.cu", "adjoint_ml.cu", "batch.cu", "coupling.cu",
+           "ml_host.cu", "adjoint.cu", "adjoint_ml.cu", "batch.cu", "coupling.cu", "boundary.cu",
            "deposit.cu"]
 HEADERS = ["hlbm_internal.h", "lbm_math.cuh", "storage.cuh", "io_reduce.h", "lattice_state.h", "hierarchy.cuh",
            "multilevel.cuh", "v2.cuh", "adjoint_math.cuh", "f2_common.cuh"]

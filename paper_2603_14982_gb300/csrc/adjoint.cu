@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(256) k_adj_collide(StepArgs a, const float* __
   const int t = threadIdx.x;
   if (t < 32) {
     const int v = t < 27 ? a.nbr[blk * 27 + t] : 0;
-    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && v == kMissing);
+    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && is_copy_nbr(v));
     if (t == 0) s_miss = mb;
   }
   __syncthreads();

@@ -176,18 +176,20 @@ void LatticeOps::build_nbr(const hlbm_lattice* h, int level, const std::vector<i
     for (int d = 0; d < 27; ++d) {
       const int off[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
       int q[3];
-      bool wall = false;
+      bool wall = false, open = false;
       for (int a = 0; a < 3; ++a) {
         q[a] = coords[b * 3 + a] + off[a];
         if (q[a] < 0 || q[a] >= dims[a]) {
-          if (h->cfg.periodic[a])
+          if (h->cfg.periodic[a]) {
             q[a] = (q[a] + dims[a]) % dims[a];
-          else
+          } else {
             wall = true;
+            open = open || ((h->open_mask() >> (2 * a + (q[a] < 0 ? 0 : 1))) & 1u) != 0u;
+          }
         }
       }
       if (wall) {
-        nbr[b * 27 + d] = kWall;
+        nbr[b * 27 + d] = open ? kOpen : kWall;
         continue;
       }
       const int64_t slot = (int64_t(q[2]) * dims[1] + q[1]) * dims[0] + q[0];
@@ -532,6 +534,7 @@ int32_t hlbm_step(hlbm_lattice* h, int32_t n_fine_steps) {
     } else {
       HLBM_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
     }
+    if ((rc = open_faces_step(h, 0, a.in, a.out))) return rc;
     ++h->l0_steps;
     L.cur = 1 - L.cur;
     if ((rc = LatticeOps::maybe_rescale(h, L, false))) return rc;
@@ -623,6 +626,7 @@ int32_t hlbm_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every
   h->rec_gen = -1;
   if (h->drag_every > 0)
     return fail(h, HLBM_E_UNSUPPORTED, "the adjoint takes the force field as fixed: disable the live drag first");
+  if (h->open_mask() != 0u) return fail(h, HLBM_E_UNSUPPORTED, "the adjoint does not cover open faces");
   if (h->device_hierarchy) {  // block layout from the rebuild pipeline: the multi-level engine
     if ((rc = ml_forward_record(h, n_steps, ckpt_every))) return rc;
     h->rec_gen = h->hier_gen;

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) k_exchange_collide(StepArgs a, DragArgs d
   const int t = threadIdx.x;  // node pair: cells t and t + 256 (pair slot t of the paired storage)
   if (t < 32) {
     const int v = t < 27 ? a.nbr[blk * 27 + t] : 0;
-    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && v == kMissing);
+    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && is_copy_nbr(v));
     if (t == 0) s_miss = mb;
   }
   __syncthreads();

@@ -280,7 +280,7 @@ __device__ __forceinline__ void stream_pairs(const Src& src, const StepArgs& a, 
 
   if (t < 32) {
     const int v = t < 27 ? a.nbr[blk * 27 + t] : 0;
-    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && v == kMissing);
+    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && is_copy_nbr(v));
     if (t == 0) s_miss = mb;
   }
   const uint8_t bf = a.bflags != nullptr ? a.bflags[blk] : 0;

@@ -181,15 +181,23 @@ __global__ void __launch_bounds__(kScanCta) k_compact_scatter(const uint8_t* __r
   skip[idx] = H ? H[i] : 0;
 }
 
+// Bit 2 a + side of open_mask: the low (side 0) or high (side 1) face of axis
+// a is open.  A neighbour beyond a non-periodic face is kOpen if any face it
+// lies beyond is open, else kWall.
+__device__ __forceinline__ unsigned beyond_faces(int v, int n, int axis) {
+  return v < 0 ? 1u << (2 * axis) : (v >= n ? 2u << (2 * axis) : 0u);
+}
+
 __global__ void k_nbr(const int32_t* __restrict__ coords, int64_t nb, const int32_t* __restrict__ slot_to_idx,
-                      GridDims d, int px, int py, int pz, int32_t* __restrict__ nbr) {
+                      GridDims d, int px, int py, int pz, unsigned open_mask, int32_t* __restrict__ nbr) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= nb * 27) return;
   const int64_t b = i / 27;
   const int dir = int(i % 27);
   int x = coords[3 * b] + dir % 3 - 1, y = coords[3 * b + 1] + (dir / 3) % 3 - 1, z = coords[3 * b + 2] + dir / 9 - 1;
+  const unsigned faces = beyond_faces(x, d.nx, 0) | beyond_faces(y, d.ny, 1) | beyond_faces(z, d.nz, 2);
   if (!wrap(x, d.nx, px) || !wrap(y, d.ny, py) || !wrap(z, d.nz, pz)) {
-    nbr[i] = kWall;
+    nbr[i] = (faces & open_mask) != 0u ? kOpen : kWall;
     return;
   }
   nbr[i] = slot_to_idx[slot_of(d, x, y, z)];  // -1 (kMissing) when not stored
@@ -395,10 +403,10 @@ cudaError_t compact_slots(const uint8_t* stored, const uint8_t* flags, const uin
 }
 
 cudaError_t neighbour_table(const int32_t* coords, int64_t nb, const int32_t* slot_to_idx, GridDims d,
-                            const int periodic[3], int32_t* nbr, cudaStream_t s) {
+                            const int periodic[3], unsigned open_mask, int32_t* nbr, cudaStream_t s) {
   if (nb == 0) return cudaSuccess;
   k_nbr<<<grid_for(nb * 27, 256), 256, 0, s>>>(coords, nb, slot_to_idx, d, periodic[0], periodic[1], periodic[2],
-                                                nbr);
+                                                open_mask, nbr);
   return cudaGetLastError();
 }
 

@@ -45,9 +45,10 @@ cudaError_t slot_flags(const uint8_t* stored, const uint8_t* H, const uint8_t* s
 cudaError_t compact_slots(const uint8_t* stored, const uint8_t* flags, const uint8_t* H, GridDims d,
                           int32_t* slot_to_idx, int32_t* coords, uint8_t* list_flags, uint8_t* skip,
                           int64_t* scratch, int64_t* count_dev, cudaStream_t s);
-// Neighbour table [nb][27] from a compacted level.
+// Neighbour table [nb][27] from a compacted level (open_mask: bit 2 axis + side
+// marks an open face; neighbours beyond it are kOpen instead of kWall).
 cudaError_t neighbour_table(const int32_t* coords, int64_t nb, const int32_t* slot_to_idx, GridDims d,
-                            const int periodic[3], int32_t* nbr, cudaStream_t s);
+                            const int periodic[3], unsigned open_mask, int32_t* nbr, cudaStream_t s);
 // Interface node lists of one level: nodes with a 26-neighbour in a block that
 // is not stored; those inside H blocks (skip != 0) go to `up` (I^u), the others
 // to `down` (I^d).  Entries are (block << 9) | cell, ascending.

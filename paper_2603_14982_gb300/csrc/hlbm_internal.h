@@ -12,6 +12,12 @@ namespace hlbm {
 // Neighbour-table sentinels: a stored block index is >= 0.
 constexpr int32_t kMissing = -1;  // inside the domain but not stored at this level
 constexpr int32_t kWall = -2;     // beyond a non-periodic face of the domain
+constexpr int32_t kOpen = -3;     // beyond an open face (convective outflow or inlet)
+
+// A neighbour block whose nodes the step cannot pull from: the nodes that
+// touch it keep their moments in the stream-collide step (interface nodes,
+// filled by a transfer; open-face nodes, filled by the boundary update).
+__host__ __device__ constexpr bool is_copy_nbr(int32_t v) { return v == kMissing || v == kOpen; }
 
 // Per-block flag bits of the step kernel.
 constexpr uint8_t kBlockSolidNear = 1;  // the block or one of its 26 neighbours holds a solid node

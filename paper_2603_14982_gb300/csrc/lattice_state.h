@@ -67,6 +67,18 @@ struct hlbm_lattice {
   double drag_kappa = 0, drag_vp[3] = {0, 0, 0};
   int32_t drag_every = 0;
   int64_t l0_steps = 0;  // level-0 steps since hlbm_set_drag
+  // open faces (boundary.cu), order x-, x+, y-, y+, z-, z+: HLBM_FACE_CLOSED,
+  // HLBM_FACE_OUTFLOW or HLBM_FACE_INLET; inlet profile u0 ln(1 + beta (h - h0))
+  // along axis inlet_axis (fine-node units)
+  int32_t face_type[6] = {0, 0, 0, 0, 0, 0};
+  double inlet_u0 = 0, inlet_beta = 0, inlet_h0 = 0;
+  int32_t inlet_axis = 1;
+  unsigned open_mask() const {
+    unsigned m = 0;
+    for (int f = 0; f < 6; ++f)
+      if (face_type[f] != 0) m |= 1u << f;
+    return m;
+  }
   int64_t rec_gen = -1;  // hier_gen of the recorded run
   std::string err;
 
@@ -97,6 +109,9 @@ int ml_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every);
 // exchange step, and the step itself (a: level-0 arguments with in / out).
 bool exchange_due(const hlbm_lattice* h);
 int coupled_step(hlbm_lattice* h, const StepArgs& a);
+// Open faces (boundary.cu): after a step of `level` from `in` to `out`, write
+// the open-face nodes of `out` from the state `in` (no-op without open faces).
+int open_faces_step(hlbm_lattice* h, int level, const void* in, void* out);
 int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF);
 
 struct LatticeOps {

@@ -121,6 +121,7 @@ int streaming_collision(hlbm_lattice* h, int l) {
   } else {
     ML_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
   }
+  ML_TRY(open_faces_step(h, l, a.in, a.out));
   if (l == 0) ++h->l0_steps;
   L.cur = 1 - L.cur;
   return LatticeOps::maybe_rescale(h, L, false);
@@ -273,7 +274,8 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     nl[l].nb = nb[l];
     if (nb[l] == 0) continue;
     if ((rc = alloc_t(h, &nl[l].d_nbr, size_t(nb[l]) * 27))) break;
-    cudaError_t e = neighbour_table(nl[l].d_coords, nb[l], nl[l].d_slot, dims_of(h, l), per, nl[l].d_nbr, st);
+    cudaError_t e =
+        neighbour_table(nl[l].d_coords, nb[l], nl[l].d_slot, dims_of(h, l), per, h->open_mask(), nl[l].d_nbr, st);
     if (e != cudaSuccess) rc = fail(h, HLBM_E_CUDA, "neighbour table: %s", cudaGetErrorString(e));
     if (rc == HLBM_OK) rc = LatticeOps::bounce(h, nl[l]);
   }

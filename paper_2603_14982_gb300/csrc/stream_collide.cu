@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(512, 1) k_stream_collide(StepArgs a) {
   if (t < 32) {
     const int v = t < 27 ? a.nbr[blk * 27 + t] : 0;
     const unsigned wb = __ballot_sync(0xffffffffu, t < 27 && v == kWall);
-    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && v == kMissing);
+    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && is_copy_nbr(v));
     if (t < 27) s_nbr[t] = v;
     if (t == 0) {
       s_wall = wb;

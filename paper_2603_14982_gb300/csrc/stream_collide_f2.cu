@@ -64,7 +64,7 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
   // missing neighbours (interface nodes): read in phase C, after the barriers
   if (t < 32) {
     const int v = t < 27 ? a.nbr[blk * 27 + t] : 0;
-    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && v == kMissing);
+    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && is_copy_nbr(v));
     if (t == 0) s_miss = mb;
   }
   const uint8_t bf = a.bflags != nullptr ? a.bflags[blk] : 0;

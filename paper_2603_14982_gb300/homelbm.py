@@ -68,6 +68,8 @@ _SIGS = {
     "hlbm_forward_record": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "hlbm_set_drag": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_int32]),
+    "hlbm_set_open_faces": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
     "hlbm_adjoint": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "hlbm_reduce_f32_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
@@ -89,6 +91,7 @@ _SIGS = {
                                              ctypes.POINTER(ctypes.c_float)]),
 }
 BATCH_ONE_LAUNCH, BATCH_GRAPH, BATCH_PER_DOMAIN, BATCH_PERSISTENT, BATCH_PERSISTENT_GRAPH = range(5)
+FACE_CLOSED, FACE_OUTFLOW, FACE_INLET = range(3)
 
 
 def exported_symbols():
@@ -252,6 +255,11 @@ class Lattice:
         level-0 steps (0 = off); see hlbm_set_drag."""
         v = (ctypes.c_double * 3)(*(float(x) for x in vp))
         self._check(self.lib.hlbm_set_drag(self.h, float(kappa), v, int(exchange_every)))
+
+    def set_open_faces(self, types, u0=0.0, beta=0.0, h0=0.0, profile_axis=1):
+        """types: 6 face conditions (x-, x+, y-, y+, z-, z+) from FACE_*; see hlbm_set_open_faces."""
+        t = (ctypes.c_int32 * 6)(*(int(v) for v in types))
+        self._check(self.lib.hlbm_set_open_faces(self.h, t, float(u0), float(beta), float(h0), int(profile_axis)))
 
     def set_solid(self, mask_dense):
         """mask_dense: numpy uint8/bool [nz][ny][nx] (fine nodes), or None."""
