@@ -329,6 +329,42 @@ def bench_ml_adjoint(hl, wl, stream, pos0, n=512, fine_steps=40, ckpt=8):
             "finite": bool(torch.isfinite(dF).all().item())}
 
 
+def bench_sparse(hl, wl, stream, n=2048, L=4, coarse_steps=4):
+    """Fine-equivalent throughput on the sparse n^3 tube-tree hierarchy (four
+    levels, bounce-back walls on every face, uniform force 1e-6 along -y, FP32,
+    static hierarchy): hierarchy build time, then coarse steps timed with CUDA
+    events after one warm-up coarse step."""
+    import torch
+    per = 2 ** (L - 1)
+    coords = wl.tube_tree_blocks(n)
+    free0 = torch.cuda.mem_get_info()[0]
+    with hl.Lattice((n, n, n), levels=L, tau=0.9, periodic=(False, False, False), storage="f32",
+                    stream=stream.cuda_stream) as lat:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.set_fine_blocks(coords)
+        lat.synchronize()
+        t_build = time.perf_counter() - t0
+        lat.set_uniform_force(0.0, -1e-6, 0.0)
+        counts = [lat.num_blocks(l) for l in range(L)]
+        used = free0 - torch.cuda.mem_get_info()[0]
+        lat.step(per)
+        t = timed(stream, lambda: lat.step(per * coarse_steps))
+        red = lat.reduce()
+    updates = coarse_steps * sum(counts[l] * 512 * 2 ** (L - 1 - l) for l in range(L))
+    fine_steps = per * coarse_steps
+    peak, _ = measured_peaks()
+    gbs = updates * 80.0 / (t / 1e3) / 1e9
+    return {"n": n, "levels": L, "blocks_per_level": counts, "tree_blocks": int(len(coords)),
+            "effective_over_actual": round(n ** 3 / (sum(counts) * 512), 1),
+            "device_bytes": int(used), "build_s": round(t_build, 3), "fine_steps": fine_steps,
+            "ms_per_fine_step": round(t / fine_steps, 3),
+            "mlups_fine_equiv": round(n ** 3 * fine_steps / (t / 1e3) / 1e6, 1),
+            "actual_updates_per_s_M": round(updates / (t / 1e3) / 1e6, 1),
+            "actual_gbs": round(gbs, 1), "actual_gbs_over_peak": round(gbs / peak, 4),
+            "mass": float(red[0]), "finite": bool(np.isfinite(red[0]))}
+
+
 def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebuild_every=10, drag_every=0):
     """Three-level lattice over an n^3 fine-equivalent domain driven by a falling
     particle cloud (pos0, device, not modified): rebuild at the first
@@ -418,6 +454,7 @@ def bench_extras(hl, wl):
     rec["mlups_vs_uncoupled"] = round(rec["mlups_fine_equiv"] / ml["f32"]["mlups_fine_equiv"], 3)
     out["c3_coupled"] = rec
     out["c3_adjoint"] = bench_ml_adjoint(hl, wl, stream, pos0)
+    out["sparse_tree_2048"] = bench_sparse(hl, wl, stream)
     return out
 
 
@@ -449,7 +486,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the multi-level, adjoint and batched workloads")
-    ap.add_argument("--only", choices=["multilevel", "adjoint", "batched", "ml_adjoint"],
+    ap.add_argument("--only", choices=["multilevel", "adjoint", "batched", "ml_adjoint", "sparse"],
                     help="run one secondary workload alone and print its JSON (profiling runs)")
     ap.add_argument("--adj-steps", type=int, default=200)
     ap.add_argument("--adj-ckpt", type=int, default=20)
@@ -465,6 +502,8 @@ def main():
             res = bench_adjoint(hl, wl, stream, steps=args.adj_steps, ckpt=args.adj_ckpt)
         elif args.only == "batched":
             res = bench_batched(hl, wl, stream)
+        elif args.only == "sparse":
+            res = bench_sparse(hl, wl, stream)
         elif args.only == "ml_adjoint":
             res = bench_ml_adjoint(hl, wl, stream, torch.tensor(wl.particle_cloud(512), device="cuda"))
         else:

@@ -29,17 +29,15 @@
 namespace hlbm {
 namespace {
 
-// Kernel parameters in the arithmetic type: the float copies for FP32 math
-// (a double-to-float conversion in the kernel would run on the FP64 pipe).
+// Kernel parameters in the arithmetic type of the one-node-per-thread
+// kernels: the float copies for FP32 math (a double-to-float conversion in
+// the kernel would run on the FP64 pipe), the doubles for FP64.
 template <typename R>
-__device__ __forceinline__ R pick(double d, float f);
-template <>
-__device__ __forceinline__ float pick<float>(double, float f) {
-  return f;
-}
-template <>
-__device__ __forceinline__ double pick<double>(double d, float) {
-  return d;
+__device__ __forceinline__ R pick(double d, float f) {
+  if constexpr (sizeof(R) == sizeof(float))
+    return f;
+  else
+    return d;
 }
 
 constexpr int kExt = 10;

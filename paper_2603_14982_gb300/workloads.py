@@ -10,12 +10,14 @@ The workload shapes follow the paper's use: a Taylor-Green vortex and a
 force-driven duct for the single-level path, a falling particle cloud that
 drives refinement (the paper's MPM particles enter only through the level
 selection Phi and the force/solid-fraction fields, Sec. 5.4), an obstacle
-channel for the gradient, and a batch of uneven periodic domains.
+channel for the gradient, a batch of uneven periodic domains, and a
+branching tube tree that refines a 2048^3 domain sparsely (the paper's airway
+scene, where refinement follows the tube walls, Sec. 7 and Table 1).
 """
 import numpy as np
 
 # Seeds per workload.
-SEED_TGV, SEED_DUCT, SEED_CLOUD, SEED_ADJOINT, SEED_BATCH = 1, 2, 3, 4, 5
+SEED_TGV, SEED_DUCT, SEED_CLOUD, SEED_ADJOINT, SEED_BATCH, SEED_TREE = 1, 2, 3, 4, 5, 17
 
 
 def rng(seed):
@@ -166,3 +168,57 @@ def batch_domains(count=64, seed=SEED_BATCH, edges=(32, 48, 64, 96, 128),
         e = int(g.choice(edges))
         out.append((e, float(g.uniform(*amp)), float(g.uniform(*tau))))
     return out
+
+
+# --- sparse domain: a branching tube tree ---
+
+def tube_tree_blocks(n_fine=2048, generations=9, seed=SEED_TREE, r0_frac=0.025, l0_frac=0.2,
+                     shrink_r=2.0 ** (-1.0 / 3.0), shrink_l=0.72, angle=0.6, block=8):
+    """Level-0 blocks (int32 (n, 3) as (bx, by, bz), sorted by slot id) that a
+    seeded binary tube tree's walls pass through.
+
+    The trunk starts near the top of the domain (y = 0.95 n) and points down
+    (-y).  Each tube splits into two whose directions turn by about ``angle``
+    rad to either side within a plane that rotates with every generation;
+    radii shrink by 2^(-1/3) per generation and lengths by ``shrink_l`` (with
+    10-15 % seeded jitter on angles and lengths).  The walls are sampled about
+    every two fine nodes.  With the defaults and four levels the hierarchy
+    stores about 40 times fewer nodes than the 2048^3 domain, the sparsity of
+    the paper's airway scene (41.4x).
+    """
+    g = rng(seed)
+    n = float(n_fine)
+    nb = n_fine // block
+    occ = np.zeros((nb, nb, nb), dtype=bool)
+    stack = [(np.array([n / 2, 0.95 * n, n / 2]), np.array([0.0, -1.0, 0.0]), np.array([1.0, 0.0, 0.0]),
+              r0_frac * n, l0_frac * n, 0)]
+    segments = []
+    while stack:
+        p, d, side, r, length, gen = stack.pop()
+        q = p + d * length
+        segments.append((p, q, r))
+        if gen + 1 >= generations:
+            continue
+        for s in (-1.0, 1.0):
+            a = angle * (1.0 + 0.15 * g.standard_normal())
+            nd = np.cos(a) * d + s * np.sin(a) * side
+            nd /= np.linalg.norm(nd)
+            ns = np.cross(nd, side)
+            ns /= np.linalg.norm(ns)
+            stack.append((q, nd, ns, r * shrink_r, length * shrink_l * (1.0 + 0.1 * g.standard_normal()), gen + 1))
+    for p, q, r in segments:
+        d = q - p
+        length = np.linalg.norm(d)
+        d = d / length
+        u = np.cross(d, [0.3, 0.5, 0.8])
+        u /= np.linalg.norm(u)
+        v = np.cross(d, u)
+        t = np.linspace(0.0, length, max(2, int(length / 2)))[:, None]
+        th = np.linspace(0.0, 2 * np.pi, max(8, int(2 * np.pi * r / 2)), endpoint=False)[None, :]
+        pts = p + t[..., None] * d + r * (np.cos(th)[..., None] * u + np.sin(th)[..., None] * v)
+        pts = pts.reshape(-1, 3)
+        pts = pts[(pts >= 0).all(axis=1) & (pts < n).all(axis=1)]
+        b = (pts // block).astype(np.int64)
+        occ[b[:, 2], b[:, 1], b[:, 0]] = True
+    z, y, x = np.nonzero(occ)
+    return np.stack([x, y, z], axis=1).astype(np.int32)
