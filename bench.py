@@ -37,7 +37,7 @@ KERNEL = "k_stream_collide_f2<float>"
 # DRAM bytes (read + write) per launch of KERNEL from one ncu capture of the
 # 192^3 duct, scaled by nodes to 256^3 (profiles/stream_collide_f2_duct192.md);
 # set to None whenever the kernel changes after that capture.
-TRAFFIC_PER_NODE = 531.9e6 / 192 ** 3
+TRAFFIC_PER_NODE = 531.8e6 / 192 ** 3
 # FP32 operations per node update of KERNEL (ncu thread-level counts of FADD,
 # FMUL, FFMA and their packed forms on the 192^3 duct, profiles/
 # stream_collide_f2_duct192.md; FMA = 2); None when not measured for the

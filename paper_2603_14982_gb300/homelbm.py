@@ -128,6 +128,19 @@ def _ptr(buf):
     raise TypeError("expected a numpy array or a torch tensor")
 
 
+def _f32(buf, what, device=False):
+    """(pointer, on_device) of a float32 buffer the library reads as float32:
+    any other dtype is refused rather than reinterpreted (a float64 tensor made
+    under torch's default dtype would otherwise be read as pairs of floats)."""
+    name = str(buf.dtype)
+    if name not in ("float32", "torch.float32"):
+        raise TypeError("%s must be float32, got %s" % (what, name))
+    p, dev = _ptr(buf)
+    if device and not dev:
+        raise TypeError("%s must be a CUDA tensor" % what)
+    return p, dev
+
+
 def _dtype_code(buf):
     name = str(buf.dtype)
     if name in ("float64", "torch.float64"):
@@ -199,7 +212,7 @@ class Lattice:
         counts = np.zeros(3, dtype=np.int64)
         if isinstance(pos, np.ndarray):
             pos = np.ascontiguousarray(pos, dtype=np.float32)
-        p, dev = _ptr(pos)
+        p, dev = _f32(pos, "particle positions")
         n = int(pos.shape[0])
         self._check(self.lib.hlbm_rebuild_from_particles(self.h, p if n else None, n, dev, counts.ctypes.data))
         return tuple(int(v) for v in counts)
@@ -234,7 +247,7 @@ class Lattice:
         wait=False returns None without waiting for the stream."""
         if isinstance(pos, np.ndarray):
             pos = np.ascontiguousarray(pos, dtype=np.float32)
-        p, dev = _ptr(pos)
+        p, dev = _f32(pos, "particle positions")
         out = ctypes.c_int64()
         self._check(self.lib.hlbm_deposit_particles(self.h, p, int(pos.shape[0]), dev, float(kappa), float(eta_max),
                                                     float(per_particle), 1 if moving else 0,
@@ -246,8 +259,8 @@ class Lattice:
 
     def set_force(self, F=None, eps=None):
         """F: torch CUDA float32 [n0][3][512] (or None), eps: [n0][512] (or None)."""
-        pF = _ptr(F)[0] if F is not None else None
-        pe = _ptr(eps)[0] if eps is not None else None
+        pF = _f32(F, "F", device=True)[0] if F is not None else None
+        pe = _f32(eps, "eps", device=True)[0] if eps is not None else None
         self._check(self.lib.hlbm_set_force(self.h, pF, pe))
 
     def set_drag(self, kappa, vp, exchange_every):
@@ -293,7 +306,8 @@ class Lattice:
         """dL_dM: torch CUDA float32 [n][10][512] of the final state (multi-level
         lattices: every level's blocks, level 0 first); dL_dF: torch CUDA
         float32 [n0][3][512] (written)."""
-        self._check(self.lib.hlbm_adjoint(self.h, _ptr(dL_dM)[0], _ptr(dL_dF)[0]))
+        self._check(self.lib.hlbm_adjoint(self.h, _f32(dL_dM, "dL_dM", device=True)[0],
+                                          _f32(dL_dF, "dL_dF", device=True)[0]))
         return dL_dF
 
     def synchronize(self):

@@ -101,3 +101,19 @@ def test_batch_rejects_fp64_and_non_periodic_domains(lib):
     assert b"periodic" in lib.hlbm_batch_last_error(None)
     assert lib.hlbm_batch_destroy(None) == hl.OK
     assert lib.hlbm_batch_step(None, 1) == hl.E_INVALID_ARG
+
+
+def test_binding_refuses_buffers_that_are_not_float32():
+    """Buffers the library reads as float32 (force, fluid fraction, particle
+    positions, adjoints) are refused in another dtype instead of being
+    reinterpreted; a CPU tensor is refused where a device pointer is needed."""
+    import torch
+    from paper_2603_14982_gb300 import homelbm as hl
+    with pytest.raises(TypeError):
+        hl._f32(np.zeros((4, 3)), "positions")
+    with pytest.raises(TypeError):
+        hl._f32(torch.zeros(4, dtype=torch.float64), "eps")
+    with pytest.raises(TypeError):
+        hl._f32(torch.zeros(4, dtype=torch.float32), "eps", device=True)
+    p, dev = hl._f32(np.zeros((4, 3), np.float32), "positions")
+    assert dev == 0 and p.value is not None

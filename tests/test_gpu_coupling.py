@@ -41,7 +41,7 @@ def test_single_level_coupled_steps_match_oracle(storage):
         lat.set_solid(solid.astype(np.uint8))
         lat.write_moments(hl.dense_to_blocks(M0))
         start = hl.blocks_to_dense(lat.read_moments(), shape)
-        lat.set_force(torch.zeros((lat.num_blocks(0), 3, 512), device="cuda"),
+        lat.set_force(torch.zeros((lat.num_blocks(0), 3, 512), dtype=torch.float32, device="cuda"),
                       torch.tensor(hl.dense_to_blocks(eps[None]), device="cuda")[:, 0].contiguous())
         lat.set_drag(KAPPA, VP, 2)
         lat.step(steps)
@@ -74,7 +74,7 @@ def test_two_level_coupled_steps_match_oracle():
             lat.write_moments(hl.dense_to_blocks(M, coords[l]), level=l)
         start = [hl.blocks_to_dense(lat.read_moments(level=l), m0.shape[l], coords[l]) for l in range(L)]
         eps = np.random.default_rng(5).uniform(0.7, 1.0, m0.shape[0]).astype(np.float32)
-        lat.set_force(torch.zeros((len(coords[0]), 3, 512), device="cuda"),
+        lat.set_force(torch.zeros((len(coords[0]), 3, 512), dtype=torch.float32, device="cuda"),
                       torch.tensor(hl.dense_to_blocks(eps[None], coords[0]), device="cuda")[:, 0].contiguous())
         lat.set_drag(KAPPA, VP, 2)
         m = ml.MultiLevel(h, 0.8, eps=torch.tensor(eps.astype(np.float64)), drag=(KAPPA, VP, 2))
@@ -98,7 +98,8 @@ def test_uniform_flow_relaxes_on_the_gpu():
     with hl.Lattice((16, 16, 16), tau=1.0, storage="f32") as lat:
         lat.set_dense()
         lat.write_moments(hl.dense_to_blocks(M0))
-        lat.set_force(torch.zeros((8, 3, 512), device="cuda"), torch.full((8, 512), 1.0 - eta, device="cuda"))
+        lat.set_force(torch.zeros((8, 3, 512), dtype=torch.float32, device="cuda"),
+                      torch.full((8, 512), 1.0 - eta, dtype=torch.float32, device="cuda"))
         lat.set_drag(KAPPA, VP, 1)
         lat.step(8)
         got = lat.read_moments()

@@ -6,12 +6,22 @@ differences, on a small channel with an obstacle; checkpointed and plain
 reverse passes must agree.
 """
 import numpy as np
+import pytest
 import torch
 
 from oracle import adjoint as adj
 from paper_2603_14982_gb300 import workloads as wl
 
-torch.set_default_dtype(torch.float64)
+
+
+@pytest.fixture(autouse=True)
+def _fp64_default_dtype():
+    """FP64 default dtype for the oracle's tensors, restored afterwards: the
+    GPU tests collected in the same session must keep torch's float32 default."""
+    old = torch.get_default_dtype()
+    torch.set_default_dtype(torch.float64)
+    yield
+    torch.set_default_dtype(old)
 
 
 def setup(n=16, steps=10):

@@ -14,6 +14,7 @@
 import math
 
 import numpy as np
+import pytest
 import torch
 
 from oracle import boundary as bd
@@ -22,7 +23,16 @@ from oracle import multilevel as ml
 from oracle import single_level as sl
 from paper_2603_14982_gb300 import workloads as wl
 
-torch.set_default_dtype(torch.float64)
+
+
+@pytest.fixture(autouse=True)
+def _fp64_default_dtype():
+    """FP64 default dtype for the oracle's tensors, restored afterwards: the
+    GPU tests collected in the same session must keep torch's float32 default."""
+    old = torch.get_default_dtype()
+    torch.set_default_dtype(torch.float64)
+    yield
+    torch.set_default_dtype(old)
 
 OUT2 = [bd.OUTFLOW, bd.OUTFLOW, 0, 0, 0, 0]
 
