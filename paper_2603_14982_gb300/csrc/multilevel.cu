@@ -246,14 +246,15 @@ __global__ void __launch_bounds__(512, 2) k_init_level(OldHierarchy o, int level
   const int x = coords[3 * b] * 8 + (cell & 7), y = coords[3 * b + 1] * 8 + ((cell >> 3) & 7),
             z = coords[3 * b + 2] * 8 + (cell >> 6);
   // a node stored at this level before the rebuild keeps its stored codes
-  // (the new level starts from the old level's scales)
+  // (the new level starts from the old level's scales).  The lookup depends on
+  // the block only, so a block stored before is copied whole by the CTA as one
+  // contiguous chunk of 16-byte words.
   const int64_t ob = lookup(o.lv[level], x, y, z);
   if (ob >= 0) {
-    const int off = node_offset<T>(cell);
-    const T* src = static_cast<const T*>(o.lv[level].mom) + ob * (kRows * kCells) + off;
-    T* dst = static_cast<T*>(out) + b * (kRows * kCells) + off;
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) dst[r * kCells] = src[r * kCells];
+    constexpr int kWords = int(kRows * kCells * sizeof(T) / sizeof(uint4));
+    const uint4* src = reinterpret_cast<const uint4*>(static_cast<const T*>(o.lv[level].mom) + ob * (kRows * kCells));
+    uint4* dst = reinterpret_cast<uint4*>(static_cast<T*>(out) + b * (kRows * kCells));
+    for (int i = cell; i < kWords; i += 512) dst[i] = src[i];
     return;
   }
   Node64 v;
