@@ -92,14 +92,14 @@ struct HaloZ {
   }
 };
 
-__device__ __forceinline__ unsigned range_mask(int v) {
+__host__ __device__ __forceinline__ unsigned range_mask(int v) {
   // bit (c+1) set when v + c lies in [0, 8), c in {-1, 0, 1}
   return ((unsigned)(v - 1) < 8u ? 1u : 0u) | ((unsigned)v < 8u ? 2u : 0u) | ((unsigned)(v + 1) < 8u ? 4u : 0u);
 }
 
 // Bit j = (cx+1) + 3 (cy+1) + 9 (cz+1) set when bit cx+1 of vx, bit cy+1 of vy
 // and bit cz+1 of vz are all set (per-axis masks as from range_mask).
-__device__ __forceinline__ unsigned dir_mask(unsigned vx, unsigned vy, unsigned vz) {
+__host__ __device__ __forceinline__ unsigned dir_mask(unsigned vx, unsigned vy, unsigned vz) {
   const unsigned mx = vx * 0x1249249u;  // vx in every 3-bit group
   const unsigned my = ((vy & 1u) * 0x7u | ((vy >> 1) & 1u) * 0x38u | ((vy >> 2) & 1u) * 0x1C0u) * 0x40201u;
   const unsigned mz = (vz & 1u) * 0x1FFu | ((vz >> 1) & 1u) * 0x3FE00u | ((vz >> 2) & 1u) * 0x7FC0000u;
@@ -139,7 +139,7 @@ __device__ __forceinline__ void gather_all(const float2* f, int own, V2 g13, V2 
 // Halo work of thread t < kHaloPairs: cls 0 = x faces (threads 0-63), 1 = y
 // faces (64-143), 2 = z faces (144-243), so that only one warp mixes two
 // classes; mir = upper face.  Node pair a = (ax, ay, az), b = (bx, by, bz).
-__device__ __forceinline__ void halo_pair(int t, int& cls, bool& mir, int& ax, int& ay, int& az, int& bx, int& by,
+__host__ __device__ __forceinline__ void halo_pair(int t, int& cls, bool& mir, int& ax, int& ay, int& az, int& bx, int& by,
                                           int& bz) {
   if (t < 64) {
     const int q = t & 31;

@@ -40,6 +40,46 @@ namespace {
 
 using namespace f2;
 
+// Geometric direction masks (node a, node b) of halo pair t: bit J set when
+// canonical direction J of that node lands inside the block.  They depend on
+// t only, so the host computes them once with the functions the halo phase
+// would use (one 8-byte load per halo thread instead of the mask arithmetic).
+__device__ uint2 g_halo_masks[kHaloPairs];
+
+void halo_masks_host(uint2* out) {
+  for (int t = 0; t < kHaloPairs; ++t) {
+    int cls, hax, hay, haz, hbx, hby, hbz;
+    bool mir;
+    halo_pair(t, cls, mir, hax, hay, haz, hbx, hby, hbz);
+    unsigned a, b;
+    if (cls == 0) {
+      a = dir_mask(7u, range_mask(hay), range_mask(haz));
+      b = dir_mask(7u, range_mask(hay), range_mask(hbz));
+    } else if (cls == 1) {
+      a = dir_mask(range_mask(hax), 7u, range_mask(haz));
+      b = dir_mask(range_mask(hax), 7u, range_mask(hbz));
+    } else {
+      a = dir_mask(range_mask(hax), range_mask(hay), 7u);
+      b = dir_mask(range_mask(hax), range_mask(hby), 7u);
+    }
+    out[t] = make_uint2(a, b);
+  }
+}
+
+// Upload the masks to the current device once.
+cudaError_t ensure_halo_masks() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  uint2 h[kHaloPairs];
+  halo_masks_host(h);
+  e = cudaMemcpyToSymbol(g_halo_masks, h, sizeof(h));
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
 // One 8^3 block of the forward step: push the own and halo populations into
 // the destination-indexed shared buffer, then gather, project and collide.
 // Leaves shared memory in use: callers that process another block must
@@ -152,6 +192,7 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
     const Coef<V2> c = make_coef(hm, kxyz);
     const int trash = kTrash + lane;
     const unsigned ma = va ? ~0u : 0u, mb = vb ? ~0u : 0u;
+    const uint2 gm = g_halo_masks[t];
     if (cls < 2) {
       int Zc[3], HA[3];
 #pragma unroll
@@ -159,7 +200,6 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
         Zc[k + 1] = 64 * ((haz + k) & 3);
         HA[k + 1] = ((haz + k) & 7) >> 2;
       }
-      const unsigned vza = range_mask(haz), vzb = range_mask(hbz);
       const int face_dst = mir ? 7 : 0;  // destination coordinate on the face axis
       if (cls == 0) {
         int YH[3], Y8[3];
@@ -168,19 +208,15 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
           YH[k + 1] = ((hay + k) & 7) >> 1;
           Y8[k + 1] = 8 * ((hay + k) & 7);
         }
-        const unsigned vy = range_mask(hay);
         HaloXY<0> s{fbuf, {0, 0, face_dst}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Zc[0], Zc[1], Zc[2]},
-                    {HA[0], HA[1], HA[2]}, dir_mask(7u, vy, vza) & ma, dir_mask(7u, vy, vzb) & mb,
-                    mir ? -1024 : 0, mir ? -512 : 0, trash};
+                    {HA[0], HA[1], HA[2]}, gm.x & ma, gm.y & mb, mir ? -1024 : 0, mir ? -512 : 0, trash};
         emit_all(c, s);
       } else {
         int X[3];
 #pragma unroll
         for (int k = -1; k <= 1; ++k) X[k + 1] = (hax + k) & 7;
-        const unsigned vx = range_mask(hax);
         HaloXY<1> s{fbuf, {X[0], X[1], X[2]}, {0, 0, face_dst >> 1}, {0, 0, 8 * face_dst}, {Zc[0], Zc[1], Zc[2]},
-                    {HA[0], HA[1], HA[2]}, dir_mask(vx, 7u, vza) & ma, dir_mask(vx, 7u, vzb) & mb,
-                    mir ? -3072 : 0, mir ? -2560 : 0, trash};
+                    {HA[0], HA[1], HA[2]}, gm.x & ma, gm.y & mb, mir ? -3072 : 0, mir ? -2560 : 0, trash};
         emit_all(c, s);
       }
     } else {
@@ -193,11 +229,9 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
         Y8a[k + 1] = 8 * ((hay + k) & 7);
         Y8b[k + 1] = 8 * ((hby + k) & 7);
       }
-      const unsigned vx = range_mask(hax);
       HaloZ s{fbuf, {X[0], X[1], X[2]}, {YHa[0], YHa[1], YHa[2]}, {YHb[0], YHb[1], YHb[2]},
-              {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, mir ? 2 * 64 * 3 + 1 : 0,
-              dir_mask(vx, range_mask(hay), 7u) & ma, dir_mask(vx, range_mask(hby), 7u) & mb, mir ? -17 * 512 : 0,
-              trash};
+              {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, mir ? 2 * 64 * 3 + 1 : 0, gm.x & ma, gm.y & mb,
+              mir ? -17 * 512 : 0, trash};
       emit_all(c, s);
     }
   }
@@ -364,6 +398,10 @@ int64_t wave_blocks() {
 
 template <typename T>
 cudaError_t launch_f2(const StepArgs& a_in, cudaStream_t s) {
+  {
+    const cudaError_t e = ensure_halo_masks();
+    if (e != cudaSuccess) return e;
+  }
   StepArgs a = a_in;
   for (int k = 0; k < 3; ++k) a.fuf[k] = float(a.fu[k]);
   a.tauf = float(a.tau);
@@ -413,6 +451,10 @@ cudaError_t launch_stream_collide_f2(int storage, const StepArgs& a, cudaStream_
 }
 
 cudaError_t launch_stream_collide_record(const StepArgs& a_in, cudaStream_t s) {
+  {
+    const cudaError_t e = ensure_halo_masks();
+    if (e != cudaSuccess) return e;
+  }
   StepArgs a = a_in;
   for (int k = 0; k < 3; ++k) a.fuf[k] = float(a.fu[k]);
   a.tauf = float(a.tau);
@@ -434,6 +476,10 @@ cudaError_t launch_stream_collide_record(const StepArgs& a_in, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_pre(const StepArgs& a_in, cudaStream_t s) {
+  {
+    const cudaError_t e = ensure_halo_masks();
+    if (e != cudaSuccess) return e;
+  }
   StepArgs a = a_in;
   const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
   static bool configured = false;
