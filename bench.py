@@ -37,7 +37,7 @@ KERNEL = "k_stream_collide_f2<float>"
 # DRAM bytes (read + write) per launch of KERNEL from one ncu capture of the
 # 192^3 duct, scaled by nodes to 256^3 (profiles/stream_collide_f2_duct192.md);
 # set to None whenever the kernel changes after that capture.
-TRAFFIC_PER_NODE = 531.8e6 / 192 ** 3
+TRAFFIC_PER_NODE = 532.1e6 / 192 ** 3
 # FP32 operations per node update of KERNEL (ncu thread-level counts of FADD,
 # FMUL, FFMA and their packed forms on the 192^3 duct, profiles/
 # stream_collide_f2_duct192.md; FMA = 2); None when not measured for the
@@ -337,7 +337,6 @@ def bench_sparse(hl, wl, stream, n=2048, L=4, coarse_steps=4):
     import torch
     per = 2 ** (L - 1)
     coords = wl.tube_tree_blocks(n)
-    free0 = torch.cuda.mem_get_info()[0]
     with hl.Lattice((n, n, n), levels=L, tau=0.9, periodic=(False, False, False), storage="f32",
                     stream=stream.cuda_stream) as lat:
         torch.cuda.synchronize()
@@ -347,7 +346,6 @@ def bench_sparse(hl, wl, stream, n=2048, L=4, coarse_steps=4):
         t_build = time.perf_counter() - t0
         lat.set_uniform_force(0.0, -1e-6, 0.0)
         counts = [lat.num_blocks(l) for l in range(L)]
-        used = free0 - torch.cuda.mem_get_info()[0]
         lat.step(per)
         t = timed(stream, lambda: lat.step(per * coarse_steps))
         red = lat.reduce()
@@ -357,7 +355,7 @@ def bench_sparse(hl, wl, stream, n=2048, L=4, coarse_steps=4):
     gbs = updates * 80.0 / (t / 1e3) / 1e9
     return {"n": n, "levels": L, "blocks_per_level": counts, "tree_blocks": int(len(coords)),
             "effective_over_actual": round(n ** 3 / (sum(counts) * 512), 1),
-            "device_bytes": int(used), "build_s": round(t_build, 3), "fine_steps": fine_steps,
+            "moment_bytes": int(sum(counts) * 512 * 40 * 2), "build_s": round(t_build, 3), "fine_steps": fine_steps,
             "ms_per_fine_step": round(t / fine_steps, 3),
             "mlups_fine_equiv": round(n ** 3 * fine_steps / (t / 1e3) / 1e6, 1),
             "actual_updates_per_s_M": round(updates / (t / 1e3) / 1e6, 1),
