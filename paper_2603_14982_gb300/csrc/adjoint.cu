@@ -685,7 +685,11 @@ __global__ void k_dF_out(const double* __restrict__ dF, float* __restrict__ out,
 
 cudaError_t adjoint_step(int storage, const StepArgs& a, const float* lam, float* lamp, double* dF, float* lam_out,
                          cudaStream_t s) {
-  const AdjArgs d{lam, lamp, dF, lam_out};
+  AdjArgs d{};
+  d.lam = lam;
+  d.lamp = lamp;
+  d.dF = dF;
+  d.lam_out = lam_out;
   switch (storage) {
     case HLBM_STORE_F64: return launch_adj<double>(a, d, s);
     default: return cudaErrorNotSupported;
@@ -696,7 +700,10 @@ cudaError_t adjoint_collide(const StepArgs& a_in, const float* pre, const float*
                             cudaStream_t s) {
   if (a_in.nb == 0) return cudaSuccess;
   const StepArgs a = with_floats(a_in);
-  const AdjArgs d{lam, lamp, dF, nullptr};
+  AdjArgs d{};
+  d.lam = lam;
+  d.lamp = lamp;
+  d.dF = dF;
   k_adj_collide<<<unsigned(a.nb), 256, 0, s>>>(a, pre, d);
   return cudaGetLastError();
 }
