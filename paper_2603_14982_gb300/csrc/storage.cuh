@@ -68,10 +68,12 @@ struct StorageTraits<__half> {
   __device__ static void store(__half* p, float v) { *p = sat_half(v); }
   __device__ static float2 load2(const __half* p) { return __half22float2(__ldg(reinterpret_cast<const __half2*>(p))); }
   __device__ static void store2(__half* p, float2 v) {
-    // convert both, then clamp the infinities of out-of-range values to the
-    // largest finite half (the same result as clamping first)
-    const __half2 lim = __float2half2_rn(65504.f), nlim = __float2half2_rn(-65504.f);
-    *reinterpret_cast<__half2*>(p) = __hmax2(__hmin2(__float22half2_rn(v), lim), nlim);
+    // one saturating conversion of both lanes (round to nearest; values
+    // beyond the largest finite half become +-65504, a NaN stays NaN):
+    // the same codes as converting and clamping, in one instruction
+    unsigned r;
+    asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(v.y), "f"(v.x));
+    *reinterpret_cast<unsigned*>(p) = r;
   }
 };
 
