@@ -16,7 +16,7 @@ sample of the same duct.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun every rank runs an independent replica (the single domain does
-not shard in this build): value = all ranks' node updates / the slowest rank.
+not shard): value = all ranks' node updates / the slowest rank.
 """
 import argparse
 import json
@@ -570,7 +570,7 @@ def main():
     if res["extras"] is not None:
         line["extras"] = res["extras"]
         if FLOP_PER_NODE is not None:
-            # the same kernel against the FP32 CUDA-core rate (it is issue-bound)
+            # the same kernel against the FP32 CUDA-core rate (the kernel is issue-bound, not HBM-bound)
             tf = args.n ** 3 * FLOP_PER_NODE / (res["ms_per_step"] / 1e3) / 1e12
             pk = res["extras"].get("fp32_sgemm_tflops")
             line["extras"]["alu_roofline"] = {

@@ -43,7 +43,7 @@ typedef enum {
   HLBM_E_CUDA = 4,        /* a CUDA runtime call failed; message has the CUDA error */
   HLBM_E_NONFINITE = 5,   /* an input field or a reduction is not finite */
   HLBM_E_TIMEOUT = 6,     /* a bounded device-side wait gave up */
-  HLBM_E_UNSUPPORTED = 7  /* valid request this build does not implement */
+  HLBM_E_UNSUPPORTED = 7  /* valid request the library does not implement */
 } hlbm_status;
 
 typedef enum {

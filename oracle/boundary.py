@@ -4,7 +4,7 @@ Test infrastructure (see ``oracle/__init__.py``).  Sec. 7 (dune and ripple
 scenes): at an outlet the boundary cells solve dM/dt + u_n dM/dn = 0 with
 u_n the fluid speed of the nearest interior neighbour along the boundary
 normal; the ripple scene drives the wind with u_x(y) = u_0 ln(1 + beta (y -
-y_0)) at the inlet.  Readings (listed in the design doc):
+y_0)) at the inlet.  Readings of what the paper leaves open:
 
 * the face layer is the outermost node layer; it keeps its moments in the
   level step and is then written from the state before the step;

@@ -4,7 +4,7 @@
 Test infrastructure (see ``oracle/__init__.py``).  Sec. 5.4 describes one
 LBM-MPM advance: after the streaming step at level 0 the fluid and sediment
 fractions and the drag are computed and fed into the collision step, and the
-MPM side runs once every few LBM steps.  Readings (listed in the design doc):
+MPM side runs once every few LBM steps.  Readings of what the paper leaves open:
 
 * the drag on the fluid is linear in the relative velocity,
   F = kappa * eta * (v_p - u*), with eta = 1 - eps the solid fraction, v_p

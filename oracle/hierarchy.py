@@ -4,7 +4,7 @@ Test infrastructure (see ``oracle/__init__.py``).  Plain numpy on dense
 boolean block grids, one per level, indexed [bz, by, bx].  Level l has block
 edge B cells of spacing 2^l (fine units); level 0 is the finest.
 
-Reading of the paper used here (listed in the design doc):
+Reading of the paper used here:
 * the level-selection function Phi (Sec. 5.4) is 0 on a level-0 block holding a
   particle and L-1 elsewhere, so the occupied set O_0 drives everything;
 * H_l = level-l blocks that have stored children: H_1 = dilate(parent(O_0)),

@@ -8,7 +8,7 @@ reconstructed by Eq. (three_order_f) from its neighbour's stored moments
 Guo body force and the mixture relaxation time eps*tau (Sec. 4, the evolution
 equation with -(f - f^eq)/(eps tau)).
 
-Readings of passages the paper leaves open (all listed in the design doc):
+Readings of passages the paper leaves open:
 * the stored moment set is the POST-collision one, so the stored velocity is
   u' = u + F/(2 rho) where u = (j* + F/2)/rho* is the physical velocity of
   Eq. (rho_u_stress);

@@ -9,7 +9,7 @@
 
 namespace hlbm {
 
-constexpr int kMaxLevels = 4;  // multi-level lattices of this build
+constexpr int kMaxLevels = 4;  // most levels a lattice may have
 
 // Read-only view of one level for the transfer kernels.
 struct LevelView {
