@@ -170,7 +170,9 @@ int32_t hlbm_set_uniform_force(hlbm_lattice *h, double fx, double fy, double fz)
 /* Per-node force F[n_blocks0][3][512] and fluid fraction eps[n_blocks0][512]
    (float32, device memory, level-0 block order) for the forcing and the mixture
    relaxation time eps*tau of Sec. 4.  Copied device-to-device; eps may be NULL
-   (eps = 1).  F may be NULL to return to the uniform force. */
+   (eps = 1).  F may be NULL to return to the uniform force.  A non-finite
+   value in either buffer returns HLBM_E_NONFINITE and changes nothing
+   (synchronous check). */
 int32_t hlbm_set_force(hlbm_lattice *h, const float *F_dev, const float *eps_dev);
 
 /* Live drag of the coupled LBM step (Fig. 4, Sec. 5.4: streaming only, force
@@ -216,7 +218,10 @@ int32_t hlbm_set_solid(hlbm_lattice *h, const uint8_t *mask_dense);
 
 /* Write / read the stored moments of a level, block-major [n][10][512].
    dtype 0 = float64, 1 = float32.  on_device 0 = host pointer, 1 = device
-   pointer.  For reads, physical_u = 1 returns u = u' - F/(2 rho) at level 0. */
+   pointer.  For reads, physical_u = 1 returns u = u' - F/(2 rho) at level 0.
+   A write whose buffer holds a non-finite value returns HLBM_E_NONFINITE and
+   leaves the level unchanged (the check waits for the stream).  A state that
+   turns non-finite while stepping is reported by hlbm_reduce. */
 int32_t hlbm_write_moments(hlbm_lattice *h, int32_t level, const void *buf, int32_t dtype,
                            int32_t on_device);
 int32_t hlbm_read_moments(hlbm_lattice *h, int32_t level, void *buf, int32_t dtype,

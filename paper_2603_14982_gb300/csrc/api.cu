@@ -361,12 +361,33 @@ int32_t hlbm_set_uniform_force(hlbm_lattice* h, double fx, double fy, double fz)
   return HLBM_OK;
 }
 
+// 1 if a device buffer (dtype 0 = f64, 1 = f32, n values) holds a non-finite
+// value, 0 if not, an hlbm status (negated) on a failure.  Synchronous.
+static int any_nonfinite(hlbm_lattice* h, const void* buf, int dtype, int64_t n) {
+  if (h->d_count == nullptr) {
+    void* p;
+    if (int rc = LatticeOps::alloc(h, &p, sizeof(unsigned long long))) return -rc;
+    h->d_count = static_cast<unsigned long long*>(p);
+  }
+  unsigned long long c = 0;
+  cudaError_t e = cudaMemsetAsync(h->d_count, 0, sizeof(c), h->stream);
+  if (e == cudaSuccess) e = count_nonfinite(buf, dtype, n, h->d_count, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&c, h->d_count, sizeof(c), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return -fail(h, HLBM_E_CUDA, "finiteness check: %s", cudaGetErrorString(e));
+  return c != 0 ? 1 : 0;
+}
+
 int32_t hlbm_set_force(hlbm_lattice* h, const float* F_dev, const float* eps_dev) {
   if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
   if (!h->have_blocks) return fail(h, HLBM_E_BAD_STATE, "set blocks before the force field");
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
   const int64_t n = h->lv[0].nb * kCells;
+  int bad = F_dev ? any_nonfinite(h, F_dev, 1, n * 3) : 0;
+  if (bad == 0 && eps_dev) bad = any_nonfinite(h, eps_dev, 1, n);
+  if (bad < 0) return -bad;
+  if (bad) return fail(h, HLBM_E_NONFINITE, "force or fluid fraction holds a non-finite value; nothing changed");
   void* v = h->d_F;
   LatticeOps::release(h, v);
   h->d_F = nullptr;
@@ -463,6 +484,9 @@ int32_t hlbm_write_moments(hlbm_lattice* h, int32_t level, const void* buf, int3
     HLBM_CUDA(h, cudaMemcpyAsync(h->d_stage, buf, bytes, cudaMemcpyHostToDevice, h->stream));
     src = h->d_stage;
   }
+  const int bad = any_nonfinite(h, src, dtype, n * kRows);
+  if (bad < 0) return -bad;
+  if (bad) return fail(h, HLBM_E_NONFINITE, "moment buffer holds a non-finite value; nothing written");
   if (L.d_scales) {
     HLBM_CUDA(h, scales_from_public(src, dtype, L.nb, L.d_scales, L.d_amax, h->stream));
     L.steps_since_rescale = 0;

@@ -177,6 +177,30 @@ cudaError_t reduce_typed(const void* src, int64_t nb, const Scales* sc, const ui
     default: return cudaErrorInvalidValue;                                \
   }
 
+namespace {
+
+template <typename V>
+__global__ void k_count_nonfinite(const V* __restrict__ buf, int64_t n, unsigned long long* count) {
+  int local = 0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    local += isfinite(buf[i]) ? 0 : 1;
+  const int block = __syncthreads_count(local != 0);
+  if (threadIdx.x == 0 && block != 0) atomicAdd(count, static_cast<unsigned long long>(block));
+}
+
+}  // namespace
+
+cudaError_t count_nonfinite(const void* buf, int dtype, int64_t n, unsigned long long* count, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t want = (n + 255) / 256;
+  const unsigned grid = unsigned(want < 4096 ? want : 4096);
+  if (dtype == 0)
+    k_count_nonfinite<double><<<grid, 256, 0, s>>>(static_cast<const double*>(buf), n, count);
+  else
+    k_count_nonfinite<float><<<grid, 256, 0, s>>>(static_cast<const float*>(buf), n, count);
+  return cudaGetLastError();
+}
+
 cudaError_t import_moments(int storage, const void* src, int dtype, void* dst, int64_t n_nodes, const Scales* sc,
                            cudaStream_t s) {
   HLBM_DISPATCH(storage, import_typed, src, dtype, dst, n_nodes, sc, s)

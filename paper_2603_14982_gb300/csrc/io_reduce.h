@@ -21,6 +21,10 @@ cudaError_t export_moments(int storage, const void* src, void* dst, int dtype, i
 cudaError_t reduce_level(int storage, const void* src, int64_t nb, const Scales* sc, const uint8_t* skip,
                          const float* F, const double* fu, double vol, double* part, double* out, cudaStream_t s);
 
+// Adds to *count (device) a positive number if any of the n values of a
+// device buffer of dtype 0 = f64, 1 = f32 is not finite (nothing otherwise).
+cudaError_t count_nonfinite(const void* buf, int dtype, int64_t n, unsigned long long* count, cudaStream_t s);
+
 // Scales (reduced-precision storages) from the amax of a public-layout buffer
 // (dtype 0 = f64, 1 = f32, device).  amax: scratch of 10 unsigned.
 cudaError_t scales_from_public(const void* src, int dtype, int64_t nb, Scales* sc, unsigned* amax, cudaStream_t s);
