@@ -271,6 +271,20 @@ int32_t hlbm_reduce(hlbm_lattice *h, double out[7]);
 int32_t hlbm_forward_record(hlbm_lattice *h, int32_t n_steps, int32_t ckpt_every);
 int32_t hlbm_adjoint(hlbm_lattice *h, const float *dL_dM_dev, float *dL_dF_dev);
 
+/* Test hook for the error paths: after `after` more successful device
+   allocations (by any handle), the next one fails and its call returns
+   HLBM_E_OOM, as a real out-of-memory would; later allocations succeed
+   again.  after < 0 clears a pending failure.  Always returns HLBM_OK.
+   After a failed allocation the handle stays safe to use and to destroy:
+   a failed rebuild (hlbm_set_fine_blocks / hlbm_rebuild_from_particles)
+   keeps the previous hierarchy and state; a failed hlbm_set_dense leaves
+   no blocks (HLBM_E_BAD_STATE until blocks are set again); a failed
+   hlbm_set_force or hlbm_deposit_particles keeps the previous fields; a
+   failed hlbm_forward_record or hlbm_adjoint frees its buffers and records
+   nothing; a failed coupled step leaves the moments of that step
+   undefined. */
+int32_t hlbm_inject_alloc_failure(int64_t after);
+
 /* Allocation-free FP64 reduction of a moment buffer the caller already holds.
  * The paper has no counterpart; this entry point exists for callers that must
  * not allocate device memory: code embedded in a host application that owns

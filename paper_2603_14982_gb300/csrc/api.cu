@@ -72,9 +72,17 @@ int LatticeOps::set_device(hlbm_lattice* h) {
   return HLBM_OK;
 }
 
+// Allocation failure injected for tests of the error paths (hlbm_inject_alloc_failure):
+// the number of device allocations still to succeed, or -1.
+static std::atomic<int64_t> g_alloc_fail_after{-1};
+
 int LatticeOps::alloc(hlbm_lattice* h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return HLBM_OK;
+  int64_t left = g_alloc_fail_after.load();
+  while (left >= 0 && !g_alloc_fail_after.compare_exchange_weak(left, left - 1)) {
+  }
+  if (left == 0) return fail(h, HLBM_E_OOM, "allocation of %zu bytes failed (injected)", bytes);
   cudaError_t e = cudaMallocAsync(p, bytes, h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -296,6 +304,7 @@ int32_t hlbm_set_dense(hlbm_lattice* h) {
   if (rc) return rc;
   LevelData& L = h->lv[0];
   LatticeOps::free_level(h, L);
+  h->have_blocks = false;  // until every buffer of the new layout is in place
   int dims[3];
   h->block_dims(0, dims);
   const int64_t nb = int64_t(dims[0]) * dims[1] * dims[2];
@@ -388,24 +397,23 @@ int32_t hlbm_set_force(hlbm_lattice* h, const float* F_dev, const float* eps_dev
   if (bad == 0 && eps_dev) bad = any_nonfinite(h, eps_dev, 1, n);
   if (bad < 0) return -bad;
   if (bad) return fail(h, HLBM_E_NONFINITE, "force or fluid fraction holds a non-finite value; nothing changed");
+  // new fields are allocated before the old ones go: a failed call changes nothing
+  void *F = nullptr, *eps = nullptr;
+  if (F_dev && (rc = LatticeOps::alloc(h, &F, size_t(n) * 3 * sizeof(float)))) return rc;
+  if (eps_dev && (rc = LatticeOps::alloc(h, &eps, size_t(n) * sizeof(float)))) {
+    LatticeOps::release(h, F);
+    return rc;
+  }
   void* v = h->d_F;
   LatticeOps::release(h, v);
-  h->d_F = nullptr;
   v = h->d_eps;
   LatticeOps::release(h, v);
-  h->d_eps = nullptr;
-  if (F_dev) {
-    void* p;
-    if ((rc = LatticeOps::alloc(h, &p, size_t(n) * 3 * sizeof(float)))) return rc;
-    h->d_F = static_cast<float*>(p);
+  h->d_F = static_cast<float*>(F);
+  h->d_eps = static_cast<float*>(eps);
+  if (F_dev)
     HLBM_CUDA(h, cudaMemcpyAsync(h->d_F, F_dev, size_t(n) * 3 * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
-  }
-  if (eps_dev) {
-    void* p;
-    if ((rc = LatticeOps::alloc(h, &p, size_t(n) * sizeof(float)))) return rc;
-    h->d_eps = static_cast<float*>(p);
+  if (eps_dev)
     HLBM_CUDA(h, cudaMemcpyAsync(h->d_eps, eps_dev, size_t(n) * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
-  }
   HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
   return HLBM_OK;
 }
@@ -651,8 +659,14 @@ int32_t hlbm_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every
   if (h->drag_every > 0)
     return fail(h, HLBM_E_UNSUPPORTED, "the adjoint takes the force field as fixed: disable the live drag first");
   if (h->open_mask() != 0u) return fail(h, HLBM_E_UNSUPPORTED, "the adjoint does not cover open faces");
+  auto drop = [h](int r) {  // a failed recording keeps no checkpoints
+    for (void*& c : h->ckpt) LatticeOps::release(h, c);
+    h->ckpt.clear();
+    h->rec_steps = h->rec_every = 0;
+    return r;
+  };
   if (h->device_hierarchy) {  // block layout from the rebuild pipeline: the multi-level engine
-    if ((rc = ml_forward_record(h, n_steps, ckpt_every))) return rc;
+    if ((rc = ml_forward_record(h, n_steps, ckpt_every))) return drop(rc);
     h->rec_gen = h->hier_gen;
     return HLBM_OK;
   }
@@ -661,14 +675,16 @@ int32_t hlbm_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every
   const int n_ck = (n_steps + ckpt_every - 1) / ckpt_every;
   for (int c = 0; c < n_ck; ++c) {
     void* p;
-    if ((rc = LatticeOps::alloc(h, &p, bytes))) return rc;
+    if ((rc = LatticeOps::alloc(h, &p, bytes))) return drop(rc);
     h->ckpt.push_back(p);
   }
   for (int32_t t = 0; t < n_steps; ++t) {
-    if (t % ckpt_every == 0)
-      HLBM_CUDA(h, cudaMemcpyAsync(h->ckpt[t / ckpt_every], L.d_mom[L.cur], bytes, cudaMemcpyDeviceToDevice,
-                                   h->stream));
-    if ((rc = hlbm_step(h, 1))) return rc;
+    if (t % ckpt_every == 0) {
+      const cudaError_t e = cudaMemcpyAsync(h->ckpt[t / ckpt_every], L.d_mom[L.cur], bytes,
+                                            cudaMemcpyDeviceToDevice, h->stream);
+      if (e != cudaSuccess) return drop(fail(h, HLBM_E_CUDA, "checkpoint copy: %s", cudaGetErrorString(e)));
+    }
+    if ((rc = hlbm_step(h, 1))) return drop(rc);
   }
   h->rec_steps = n_steps;
   h->rec_every = ckpt_every;
@@ -777,6 +793,11 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
   seg[0] = nullptr;
   release_all();
   if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
+  return HLBM_OK;
+}
+
+int32_t hlbm_inject_alloc_failure(int64_t after) {
+  g_alloc_fail_after.store(after < 0 ? -1 : after);
   return HLBM_OK;
 }
 

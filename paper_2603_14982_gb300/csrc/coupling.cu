@@ -123,13 +123,16 @@ bool exchange_due(const hlbm_lattice* h) { return h->drag_every > 0 && h->l0_ste
 int coupled_step(hlbm_lattice* h, const StepArgs& a_in) {
   const int64_t nb = h->lv[0].nb;
   int rc;
-  void* p = nullptr;
-  if (h->d_F == nullptr) {
-    if ((rc = LatticeOps::alloc(h, &p, size_t(nb) * 3 * kCells * sizeof(float)))) return rc;
-    h->d_F = static_cast<float*>(p);
-  }
   void* pre = nullptr;
   if ((rc = LatticeOps::alloc(h, &pre, size_t(nb) * kRows * kCells * sizeof(float)))) return rc;
+  if (h->d_F == nullptr) {  // allocated last: a failed step leaves no unwritten force field behind
+    void* p = nullptr;
+    if ((rc = LatticeOps::alloc(h, &p, size_t(nb) * 3 * kCells * sizeof(float)))) {
+      LatticeOps::release(h, pre);
+      return rc;
+    }
+    h->d_F = static_cast<float*>(p);
+  }
   StepArgs a = a_in;
   a.pre_out = static_cast<float*>(pre);
   DragArgs d{};

@@ -70,24 +70,26 @@ extern "C" int32_t hlbm_deposit_particles(hlbm_lattice* h, const float* pos_xyz,
   if (h->device_hierarchy && L.d_slot == nullptr)
     return fail(h, HLBM_E_BAD_STATE, "the finest level has no slot table");
   const int64_t n_nodes = L.nb * kCells;
-  void* p;
-  if (h->d_F == nullptr) {
-    if ((rc = LatticeOps::alloc(h, &p, size_t(n_nodes) * 3 * sizeof(float)))) return rc;
-    h->d_F = static_cast<float*>(p);
-  }
-  if (h->d_eps == nullptr) {
-    if ((rc = LatticeOps::alloc(h, &p, size_t(n_nodes) * sizeof(float)))) return rc;
-    h->d_eps = static_cast<float*>(p);
-  }
-  if (h->d_count == nullptr) {
-    if ((rc = LatticeOps::alloc(h, &p, sizeof(unsigned long long)))) return rc;
-    h->d_count = static_cast<unsigned long long*>(p);
-  }
+  // every buffer is allocated before any is installed in the handle: a failed
+  // call leaves no unwritten force or solid-fraction field for the next step
+  void *F = nullptr, *eps = nullptr, *cnt = nullptr, *staged = nullptr;
+  auto undo = [&](int r) {
+    LatticeOps::release(h, F);
+    LatticeOps::release(h, eps);
+    LatticeOps::release(h, cnt);
+    LatticeOps::release(h, staged);
+    return r;
+  };
+  if (h->d_F == nullptr && (rc = LatticeOps::alloc(h, &F, size_t(n_nodes) * 3 * sizeof(float)))) return undo(rc);
+  if (h->d_eps == nullptr && (rc = LatticeOps::alloc(h, &eps, size_t(n_nodes) * sizeof(float)))) return undo(rc);
+  if (h->d_count == nullptr && (rc = LatticeOps::alloc(h, &cnt, sizeof(unsigned long long)))) return undo(rc);
+  if (!on_device && n > 0 && (rc = LatticeOps::alloc(h, &staged, size_t(n) * 3 * sizeof(float)))) return undo(rc);
+  if (F) h->d_F = static_cast<float*>(F);
+  if (eps) h->d_eps = static_cast<float*>(eps);
+  if (cnt) h->d_count = static_cast<unsigned long long*>(cnt);
   const float* d_pos = pos_xyz;
-  void* staged = nullptr;
   cudaError_t e = cudaSuccess;
   if (!on_device && n > 0) {
-    if ((rc = LatticeOps::alloc(h, &staged, size_t(n) * 3 * sizeof(float)))) return rc;
     e = cudaMemcpyAsync(staged, pos_xyz, size_t(n) * 3 * sizeof(float), cudaMemcpyHostToDevice, h->stream);
     d_pos = static_cast<const float*>(staged);
   }

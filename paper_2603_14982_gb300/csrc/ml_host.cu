@@ -169,11 +169,8 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     ML_CUDA(h, cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st));
   }
   const bool has_old = h->have_blocks && h->device_hierarchy;
-  // 1. every old level at the same time: refill I^d from the coarser level
-  if (has_old)
-    for (int l = L - 2; l >= 0; --l) ML_TRY(downward(h, l, 1, true));
 
-  // 2. occupancy of level-0 blocks (Phi = 0 there)
+  // 1. occupancy of level-0 blocks (Phi = 0 there)
   const GridDims d0 = dims_of(h, 0);
   uint8_t* d_occ = nullptr;
   int* d_bad = h->d_status + 1;
@@ -186,7 +183,10 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
   if (blocks != nullptr) {
     int32_t* d_b = nullptr;
     if (n_blocks > 0) {
-      ML_TRY(alloc_t(h, &d_b, size_t(n_blocks) * 3));
+      if (int rc0 = alloc_t(h, &d_b, size_t(n_blocks) * 3)) {
+        cleanup();
+        return rc0;
+      }
       tmp.push_back(d_b);
       ML_CUDA(h, cudaMemcpyAsync(d_b, blocks, size_t(n_blocks) * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     }
@@ -195,7 +195,10 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     const float* d_p = pos;
     if (!pos_on_device && n_pos > 0) {
       float* d_copy = nullptr;
-      ML_TRY(alloc_t(h, &d_copy, size_t(n_pos) * 3));
+      if (int rc0 = alloc_t(h, &d_copy, size_t(n_pos) * 3)) {
+        cleanup();
+        return rc0;
+      }
       tmp.push_back(d_copy);
       ML_CUDA(h, cudaMemcpyAsync(d_copy, pos, size_t(n_pos) * 3 * sizeof(float), cudaMemcpyHostToDevice, st));
       d_p = d_copy;
@@ -203,7 +206,7 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     ML_CUDA(h, occupancy_from_particles(d_p, n_pos, d0, d_occ, d_bad, st));
   }
 
-  // 3. H, I, stored, flags on the dense slot grids
+  // 2. H, I, stored, flags on the dense slot grids
   std::vector<LevelData> nl(L);
   for (int l = 0; l < L; ++l) nl[l].tau = h->lv[l].tau;
   auto free_new = [&]() {
@@ -237,7 +240,7 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
                           l < L - 1 ? dims_of(h, l + 1) : dims_of(h, l), has_old ? h->lv[l].d_stored : nullptr,
                           has_old ? h->lv[l].d_H : nullptr, has_old, d_fl[l], st));
 
-  // 4. stable compaction of every level
+  // 3. stable compaction of every level
   int64_t* d_cnt = nullptr;
   int64_t max_cta = 0;
   for (int l = 0; l < L; ++l) max_cta = std::max<int64_t>(max_cta, (dims_of(h, l).slots() + 1023) / 1024);
@@ -269,7 +272,7 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
   ML_CUDA(h, cudaMemcpyAsync(nb.data(), d_tot, L * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   ML_CUDA(h, cudaStreamSynchronize(st));
 
-  // 5. neighbour tables and interface node lists
+  // 4. neighbour tables and interface node lists
   for (int l = 0; l < L && rc == HLBM_OK; ++l) {
     nl[l].nb = nb[l];
     if (nb[l] == 0) continue;
@@ -307,7 +310,7 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     if (e != cudaSuccess) rc = fail(h, HLBM_E_CUDA, "interface scatter: %s", cudaGetErrorString(e));
   }
 
-  // 6. moments: survivors keep theirs, new nodes take the transfer rules
+  // 5. moments: survivors keep theirs, new nodes take the transfer rules
   const size_t node_bytes = kRows * storage_size(h->cfg.storage);
   for (int l = 0; l < L && rc == HLBM_OK; ++l)
     for (int k = 0; k < 2 && rc == HLBM_OK; ++k)
@@ -324,6 +327,12 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     if (rc == HLBM_OK && has_old && nl[l].d_scales != nullptr && h->lv[l].d_scales != nullptr)
       ML_CUDA(h, cudaMemcpyAsync(nl[l].d_scales, h->lv[l].d_scales, sizeof(Scales), cudaMemcpyDeviceToDevice, st));
   }
+  // every old level at the same time: refill I^d from the coarser level, so
+  // that new nodes interpolate from a current interface.  This is the first
+  // write to the old state and comes after the last allocation, so a rebuild
+  // that fails for memory leaves the old hierarchy as it was.
+  if (rc == HLBM_OK && has_old)
+    for (int l = L - 2; l >= 0 && rc == HLBM_OK; --l) rc = downward(h, l, 1, true);
   if (rc) {
     free_new();
     cleanup();
@@ -356,7 +365,7 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
                                  cudaMemcpyDeviceToDevice, st));
   }
 
-  // 7. host copies of the lists; counts of refined / coarsened / deleted blocks
+  // 6. host copies of the lists; counts of refined / coarsened / deleted blocks
   unsigned long long changes[3] = {0, 0, 0};
   unsigned long long* d_changes = reinterpret_cast<unsigned long long*>(d_tot + 3 * L);
   if (counts_out != nullptr && has_old) {

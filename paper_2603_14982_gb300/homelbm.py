@@ -66,6 +66,7 @@ _SIGS = {
     "hlbm_synchronize": (ctypes.c_int32, [ctypes.c_void_p]),
     "hlbm_reduce": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "hlbm_forward_record": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
+    "hlbm_inject_alloc_failure": (ctypes.c_int32, [ctypes.c_int64]),
     "hlbm_set_drag": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_int32]),
     "hlbm_set_open_faces": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
@@ -428,6 +429,12 @@ def blocks_to_dense(Mb, shape, coords=None, fill=np.nan):
         t[c[:, 2], c[:, 1], c[:, 0]] = Mb
     t = t.reshape(nz // 8, ny // 8, nx // 8, R, 8, 8, 8).transpose(3, 0, 4, 1, 5, 2, 6)
     return np.ascontiguousarray(t.reshape(R, nz, ny, nx))
+
+
+def inject_alloc_failure(after):
+    """Test hook: the device allocation after ``after`` more successful ones
+    fails with E_OOM (after < 0 clears); see hlbm_inject_alloc_failure."""
+    load().hlbm_inject_alloc_failure(int(after))
 
 
 def make_force_autograd(lattice, n_steps, ckpt_every):
