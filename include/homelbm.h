@@ -272,7 +272,7 @@ int32_t hlbm_forward_record(hlbm_lattice *h, int32_t n_steps, int32_t ckpt_every
 int32_t hlbm_adjoint(hlbm_lattice *h, const float *dL_dM_dev, float *dL_dF_dev);
 
 /* Test hook for the error paths: after `after` more successful device
-   allocations (by any handle), the next one fails and its call returns
+   allocations (by any lattice or batch handle), the next one fails and its call returns
    HLBM_E_OOM, as a real out-of-memory would; later allocations succeed
    again.  after < 0 clears a pending failure.  Always returns HLBM_OK.
    After a failed allocation the handle stays safe to use and to destroy:

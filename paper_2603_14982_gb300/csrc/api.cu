@@ -76,13 +76,17 @@ int LatticeOps::set_device(hlbm_lattice* h) {
 // the number of device allocations still to succeed, or -1.
 static std::atomic<int64_t> g_alloc_fail_after{-1};
 
-int LatticeOps::alloc(hlbm_lattice* h, void** p, size_t bytes) {
-  *p = nullptr;
-  if (bytes == 0) return HLBM_OK;
+bool alloc_failure_injected() {
   int64_t left = g_alloc_fail_after.load();
   while (left >= 0 && !g_alloc_fail_after.compare_exchange_weak(left, left - 1)) {
   }
-  if (left == 0) return fail(h, HLBM_E_OOM, "allocation of %zu bytes failed (injected)", bytes);
+  return left == 0;
+}
+
+int LatticeOps::alloc(hlbm_lattice* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return HLBM_OK;
+  if (alloc_failure_injected()) return fail(h, HLBM_E_OOM, "allocation of %zu bytes failed (injected)", bytes);
   cudaError_t e = cudaMallocAsync(p, bytes, h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();

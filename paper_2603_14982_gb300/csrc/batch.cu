@@ -92,6 +92,8 @@ template <typename P>
 int balloc(hlbm_batch* b, P** p, size_t count) {
   *p = nullptr;
   if (count == 0) return HLBM_OK;
+  if (hlbm::alloc_failure_injected())
+    return bfail(b, HLBM_E_OOM, "allocation of %zu bytes failed (injected)", count * sizeof(P));
   void* v = nullptr;
   cudaError_t e = cudaMalloc(&v, count * sizeof(P));
   if (e != cudaSuccess) {

@@ -95,6 +95,10 @@ namespace hlbm {
 // Records an error message on h (or the global one when h is NULL) and returns code.
 int fail(hlbm_lattice* h, int code, const char* fmt, ...);
 
+// True when the device allocation about to be made is the one that
+// hlbm_inject_alloc_failure asked to fail (consumes one count otherwise).
+bool alloc_failure_injected();
+
 // Multi-level engine (ml_host.cu).
 int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_device, const int32_t* blocks,
                int64_t n_blocks, int64_t counts_out[3]);

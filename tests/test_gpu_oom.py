@@ -8,7 +8,8 @@ at every failure point that
 * the failing call returns E_OOM (nothing else, no CUDA error);
 * the handle keeps the state the header promises (the previous hierarchy and
   moments after a failed rebuild, no blocks after a failed set-up, no
-  recording after a failed forward_record);
+  recording after a failed forward_record, the state after a failed
+  autotune of a batch);
 * with the injection cleared, the same calls on the same handle give the same
   results as a run that never failed, and the handle is destroyed cleanly.
 """
@@ -229,3 +230,42 @@ def test_failed_record_and_adjoint_recover(multilevel):
             return ran
 
         assert walk(run_adjoint) >= 5
+
+
+def test_batch_create_steps_and_autotune_fail_cleanly():
+    domains = [((16, 16, 16), 0.6), ((32, 16, 24), 0.8), ((8, 8, 8), 0.55)]
+    fields = [hl.dense_to_blocks(wl.random_field((e[2], e[1], e[0]), 300 + d, du=0.03))
+              for d, (e, _) in enumerate(domains)]
+
+    def sequence(b):
+        b.set_mode(hl.BATCH_PERSISTENT)
+        for d, M in enumerate(fields):
+            b.write_moments(d, M)
+        b.step(3)
+        return [b.read_moments(d) for d in range(len(domains))]
+
+    with hl.Batch(domains, storage="f16s") as b:
+        want = sequence(b)
+
+    def run(k):
+        hl.inject_alloc_failure(k)
+        try:
+            b = hl.Batch(domains, storage="f16s")
+        except hl.HlbmError as e:           # a failed create frees what it allocated
+            assert e.code == hl.E_OOM, e
+            return False
+        with b:
+            ran = expect_oom(lambda: sequence(b))
+            hl.inject_alloc_failure(-1)
+            got = sequence(b)               # same handle, injection cleared
+            assert all(np.array_equal(g, w) for g, w in zip(got, want)), k
+            if ran:                         # the autotuner's state copy fails: nothing changes
+                hl.inject_alloc_failure(0)
+                with pytest.raises(hl.HlbmError) as ei:
+                    b.autotune(8)
+                assert ei.value.code == hl.E_OOM
+                hl.inject_alloc_failure(-1)
+                assert all(np.array_equal(b.read_moments(d), w) for d, w in enumerate(want))
+        return ran
+
+    assert walk(run) >= 8
