@@ -562,10 +562,11 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
   Mom<V2> lm;
   if (!(fz_lo && fz_hi)) {
     V2 g[27];
-    f2::gather_all(f2buf, cx.own_s, cx.g13, g, std::make_integer_sequence<int, 27>{});
+    f2::gather_all(reinterpret_cast<const float*>(f2buf) + cx.own_p, cx.g13, g,
+                   std::make_integer_sequence<int, 27>{});
     if (cp_lo || cp_hi) {
-      // an interface node's slots fed from a block that is not stored hold
-      // wrapped own pushes, not adjoints: nothing streams back from there
+      // an interface node's slots fed from a block that is not stored receive
+      // no push (they hold stale values): nothing streams back from there
       const unsigned mlo = cp_lo ? f2::missing_sources(cx.x, cx.y, cx.z0, s_miss) : 0u;
       const unsigned mhi = cp_hi ? f2::missing_sources(cx.x, cx.y, cx.z0 + 4, s_miss) : 0u;
 #pragma unroll
@@ -711,7 +712,7 @@ cudaError_t adjoint_collide(const StepArgs& a_in, const float* pre, const float*
 template <bool kFuse>
 cudaError_t launch_push2(const StepArgs& a_in, const AdjArgs& d, cudaStream_t s) {
   const StepArgs a = with_floats(a_in);
-  const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
+  const size_t smem = f2::kBufBytes;
   static bool configured = false;
   if (!configured) {
     cudaError_t e =

@@ -1,8 +1,8 @@
 // f2_common.cuh -- building blocks of the node-pair kernels (FP32 math on
 // packed pairs of nodes (z, z + 4) of an 8^3 block, 256 threads per block):
-// the destination-indexed shared population buffer and its pushes (own pairs,
-// halo pairs reflected onto the lower face of each axis, bounce-back), the
-// gather, and the assignment of halo pairs to threads.  Used by the forward
+// the padded destination-indexed shared population buffer and its pushes
+// (own pairs, halo pairs reflected onto the lower face of each axis,
+// bounce-back), the gather, and the assignment of halo pairs to threads.  Used by the forward
 // stream-collide kernel and by the reverse-step kernels of the adjoint.
 #pragma once
 #include <utility>
@@ -18,12 +18,29 @@ namespace f2 {
 constexpr int kThreads = 256;
 constexpr int kHaloPairs = 244;
 
-__host__ __device__ constexpr int slot_of(int j) { return j < 13 ? j : j - 1; }
+// Destination-indexed shared population buffer: one padded plane of kPlane
+// floats per direction j (the rest plane is not used, so that the reflection
+// of a face shifts every canonical direction by the same number of planes);
+// node (x, y, z) of the block at pidx(x, y, z).  Rows y = -1, 8 and slabs
+// z = -1, 8 are padding that pushes leaving the block through a y or z face
+// write and nothing reads; pushes leaving through an x face are predicated
+// off.  Every access of a node is at a compile-time offset from one base
+// address, the 32 lanes of a warp touch 32 consecutive words for the own
+// pushes and the gather, and kPZ is odd so that the x-face halo stores (lanes
+// along y and z) meet at most two to a bank.
+constexpr int kPY = 8, kPZ = 81, kPlane = 10 * kPZ;
+constexpr size_t kBufBytes = size_t(27) * kPlane * sizeof(float);
+__host__ __device__ constexpr int pidx(int x, int y, int z) { return x + kPY * (y + 1) + kPZ * (z + 1); }
+// plane offset of the mirror image of a canonical direction (component +1 on
+// the face axis) along axis ax: its index is lower by 2, 6 or 18
+__host__ __device__ constexpr int mirror_shift(int ax) { return -2 * (ax == 0 ? 1 : (ax == 1 ? 3 : 9)) * kPlane; }
 
+// Own pushes of a node pair: f points at node a's slot in plane 0; node b
+// sits 4 slabs higher.  xm / xp: the node has an x neighbour inside the block
+// on the low / high side.
 struct OwnPush {
-  float2* f;
-  int XH[9], Y8[3], Z64[3];  // XH[(cx+1) + 3 (cy+1)] = x' ^ (y' >> 1)
-  bool swap[3];
+  float* f;
+  bool xm, xp;
   V2 g13;
   template <int J>
   __device__ __forceinline__ void put(V2 v) {
@@ -31,66 +48,69 @@ struct OwnPush {
       g13 = v;
     } else {
       constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
-      const int s = XH[(cx + 1) + 3 * (cy + 1)] + Y8[cy + 1] + Z64[cz + 1];
-      f[slot_of(J) * 256 + s] = swap[cz + 1] ? make_float2(v.v.y, v.v.x) : v.v;
+      constexpr int off = J * kPlane + cx + kPY * cy + kPZ * cz;
+      if (cx == 0 || (cx > 0 ? xp : xm)) {
+        f[off] = v.v.x;
+        f[off + 4 * kPZ] = v.v.y;
+      }
     }
   }
 };
-
-constexpr int kTrash = 26 * 512;  // per-lane dummy float slots for masked halo stores
 
 // Halo pushes in a canonical orientation: the halo node lies just below the
-// block on the face axis and pushes the 9 directions whose component on that
-// axis is +1.  Threads on the upper face reflect their moments along the face
-// axis first (Eq. three_order_f is covariant under reflections), so canonical
-// direction J carries the population of its mirror image; d0 / d1 shift the
-// store to the mirror direction's slot (d1 for the mirrors that lie on the
-// other side of the rest index).  oka / okb: bit J set when the .x / .y value
-// of canonical direction J has a destination inside the block and a valid
-// source; other values go to the lane's trash slot.
-
-// x faces (AX = 0) and y faces (AX = 1): node pair a = (hx, hy, hz), b = hz + 4,
-// one stored pair of the same neighbour.  X / YH / Y8 / Z64 hold the actual
-// destination coordinates (swizzle parts) for canonical component c at [c+1];
-// ha[c+1]: node a lands in the high half of its pair slot.
+// block on the face axis AX and pushes the 9 directions whose component on
+// that axis is +1.  Threads on the upper face reflect their values along the
+// face axis first (Eq. three_order_f is covariant under reflections), so
+// canonical direction J carries the population of its mirror image, whose
+// plane lies mirror_shift(AX) lower.  fa / fb point at the slot, in plane 0
+// shifted by the reflection, of the destination of the direction with zero
+// components off AX; oka / okb: bit J set when direction J of node a / b
+// lands inside the block and has a valid source.
 template <int AX>
-struct HaloXY {
-  float* f;
-  int X[3], YH[3], Y8[3], Z64[3], ha[3];
+struct HaloPush {
+  float *fa, *fb;
   unsigned oka, okb;
-  int d0, d1, trash;
   template <int J>
   __device__ __forceinline__ void put(V2 v) {
     constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
-    constexpr int c = AX == 0 ? cx : cy;
+    constexpr int c = AX == 0 ? cx : (AX == 1 ? cy : cz);
     if constexpr (c == 1) {
-      constexpr bool cross = AX == 0 ? (cy == 0 && cz == 0) : (cz == 0);
-      const int p2 = 2 * (slot_of(J) * 256 + (X[cx + 1] ^ YH[cy + 1]) + Y8[cy + 1] + Z64[cz + 1]) + (cross ? d1 : d0);
-      const int h = ha[cz + 1];
-      f[((oka >> J) & 1u) ? p2 + h : trash] = v.v.x;
-      f[((okb >> J) & 1u) ? p2 + 1 - h : trash] = v.v.y;
+      constexpr int off = J * kPlane + (AX == 0 ? 0 : cx) + (AX == 1 ? 0 : kPY * cy) + (AX == 2 ? 0 : kPZ * cz);
+      if ((oka >> J) & 1u) fa[off] = v.v.x;
+      if ((okb >> J) & 1u) fb[off] = v.v.y;
     }
   }
 };
 
-// z faces: node pair a = (hx, hy, hz), b = (hx, hy + 5, hz); zoff addresses the
-// destination plane (z = 0: pair slot 0, low half; z = 7: pair slot 3, high half).
-struct HaloZ {
+// Half-way bounce-back: bit k of mlo / mhi set when the pull source x - c_k of
+// node a / b is a wall or a solid node, so slot k of the node receives its own
+// population opp(k).  f as in OwnPush.
+struct BouncePush {
   float* f;
-  int X[3], YHa[3], YHb[3], Y8a[3], Y8b[3];
-  int zoff;
-  unsigned oka, okb;
-  int d, trash;
+  unsigned mlo, mhi;
   template <int J>
   __device__ __forceinline__ void put(V2 v) {
-    constexpr int cx = Dir<J>::cx, cy = Dir<J>::cy, cz = Dir<J>::cz;
-    if constexpr (cz == 1) {
-      const int base = 2 * (slot_of(J) * 256) + zoff + d;
-      f[((oka >> J) & 1u) ? base + 2 * ((X[cx + 1] ^ YHa[cy + 1]) + Y8a[cy + 1]) : trash] = v.v.x;
-      f[((okb >> J) & 1u) ? base + 2 * ((X[cx + 1] ^ YHb[cy + 1]) + Y8b[cy + 1]) : trash] = v.v.y;
+    if constexpr (J != 13) {
+      constexpr int K = 26 - J;
+      if ((mlo >> K) & 1u) f[K * kPlane] = v.v.x;
+      if ((mhi >> K) & 1u) f[K * kPlane + 4 * kPZ] = v.v.y;
     }
   }
 };
+
+template <int J>
+__device__ __forceinline__ void gather_one(const float* f, V2 g13, V2 (&g)[27]) {
+  if constexpr (J == 13)
+    g[13] = g13;
+  else
+    g[J] = V2(f[J * kPlane], f[J * kPlane + 4 * kPZ]);
+}
+
+// The 27 values of node pair (f as in OwnPush); the rest value comes from g13.
+template <int... Js>
+__device__ __forceinline__ void gather_all(const float* f, V2 g13, V2 (&g)[27], std::integer_sequence<int, Js...>) {
+  (gather_one<Js>(f, g13, g), ...);
+}
 
 __host__ __device__ __forceinline__ unsigned range_mask(int v) {
   // bit (c+1) set when v + c lies in [0, 8), c in {-1, 0, 1}
@@ -104,36 +124,6 @@ __host__ __device__ __forceinline__ unsigned dir_mask(unsigned vx, unsigned vy, 
   const unsigned my = ((vy & 1u) * 0x7u | ((vy >> 1) & 1u) * 0x38u | ((vy >> 2) & 1u) * 0x1C0u) * 0x40201u;
   const unsigned mz = (vz & 1u) * 0x1FFu | ((vz >> 1) & 1u) * 0x3FE00u | ((vz >> 2) & 1u) * 0x7FC0000u;
   return mx & my & mz;
-}
-
-// Half-way bounce-back: bit k of mask = the pull source x - c_k of this node is
-// a wall or a solid node, so slot k of the node receives its own population opp(k).
-struct BouncePush {
-  float* f;
-  int own;  // pair slot
-  unsigned mlo, mhi;
-  template <int J>
-  __device__ __forceinline__ void put(V2 v) {
-    if constexpr (J != 13) {
-      constexpr int K = 26 - J;
-      if ((mlo >> K) & 1u) f[2 * (slot_of(K) * 256 + own)] = v.v.x;
-      if ((mhi >> K) & 1u) f[2 * (slot_of(K) * 256 + own) + 1] = v.v.y;
-    }
-  }
-};
-
-template <int J>
-__device__ __forceinline__ void gather_one(const float2* f, int own, V2 g13, V2 (&g)[27]) {
-  if constexpr (J == 13)
-    g[13] = g13;
-  else
-    g[J] = V2(f[slot_of(J) * 256 + own]);
-}
-
-template <int... Js>
-__device__ __forceinline__ void gather_all(const float2* f, int own, V2 g13, V2 (&g)[27],
-                                           std::integer_sequence<int, Js...>) {
-  (gather_one<Js>(f, own, g13, g), ...);
 }
 
 // Halo work of thread t < kHaloPairs: cls 0 = x faces (threads 0-63), 1 = y
@@ -177,7 +167,7 @@ __device__ __forceinline__ int block_dir(int hx, int hy, int hz) {
 
 // Bit K set when x - c_K of block-local node (x, y, z) lies in a neighbour
 // block whose bit is set in miss (bit (dx+1) + 3 (dy+1) + 9 (dz+1)).  Slot K
-// of such a node receives no halo push: it still holds a wrapped own push.
+// of such a node receives no push: it holds whatever the buffer held before.
 __device__ __forceinline__ unsigned missing_sources(int x, int y, int z, unsigned miss) {
   unsigned m = 0;
 #pragma unroll
@@ -243,7 +233,7 @@ __device__ __forceinline__ Mom<V2> zero_pair() {
 struct PairCtx {
   int t, lane, x, y, z0;
   int own;    // pair slot in global storage (nodes own and own + 256 in natural order)
-  int own_s;  // pair slot in shared memory
+  int own_p;  // node a's slot in plane 0 of the shared buffer
   uint8_t bf;
   bool solid_any;
   V2 g13;     // rest-direction value of the own pair
@@ -258,7 +248,7 @@ __device__ __forceinline__ PairCtx pair_ctx() {
   c.y = (c.lane >> 3) + ((w & 1) << 2);
   c.z0 = w >> 1;
   c.own = c.x + 8 * c.y + 64 * c.z0;
-  c.own_s = (c.x ^ (c.y >> 1)) + 8 * c.y + 64 * c.z0;
+  c.own_p = pidx(c.x, c.y, c.z0);
   return c;
 }
 
@@ -276,7 +266,7 @@ template <typename Src>
 __device__ __forceinline__ void stream_pairs(const Src& src, const StepArgs& a, const int64_t blk, float2* f2buf,
                                              unsigned& s_miss, PairCtx& cx) {
   float* fbuf = reinterpret_cast<float*>(f2buf);
-  const int t = cx.t, lane = cx.lane, x = cx.x, y = cx.y, z0 = cx.z0, own = cx.own, own_s = cx.own_s;
+  const int t = cx.t, x = cx.x, own = cx.own;
 
   if (t < 32) {
     const int v = t < 27 ? a.nbr[blk * 27 + t] : 0;
@@ -309,80 +299,46 @@ __device__ __forceinline__ void stream_pairs(const Src& src, const StepArgs& a, 
     }
   }
 
-  // A. push the own pair
-  OwnPush op;
-  op.f = f2buf;
-#pragma unroll
-  for (int c = -1; c <= 1; ++c) {
-    op.Y8[c + 1] = 8 * ((y + c) & 7);
-    op.Z64[c + 1] = 64 * ((z0 + c) & 3);
-    op.swap[c + 1] = (((z0 + c) & 7) >> 2) != 0;
-#pragma unroll
-    for (int cx = -1; cx <= 1; ++cx) op.XH[(cx + 1) + 3 * (c + 1)] = ((x + cx) & 7) ^ (((y + c) & 7) >> 1);
-  }
-  src.emit(m, op);
-  cx.g13 = op.g13;
-  __syncthreads();
-
-  // B. halo pairs and bounce-back
+  // A. halo pairs (before the own pair: the halo values are then dead before
+  // the own pair's are expanded)
   if (t < kHaloPairs && (va || vb)) {
     // reflect the upper-face pairs along the face axis
     Src::mirror(hm, cls, V2(mir ? -1.f : 1.f));
-    const int trash = kTrash + lane;
     const unsigned ma = va ? ~0u : 0u, mb = vb ? ~0u : 0u;
-    if (cls < 2) {
-      int Zc[3], HA[3];
-#pragma unroll
-      for (int k = -1; k <= 1; ++k) {
-        Zc[k + 1] = 64 * ((haz + k) & 3);
-        HA[k + 1] = ((haz + k) & 7) >> 2;
-      }
-      const unsigned vza = range_mask(haz), vzb = range_mask(hbz);
-      const int face_dst = mir ? 7 : 0;  // destination coordinate on the face axis
-      if (cls == 0) {
-        int YH[3], Y8[3];
-#pragma unroll
-        for (int k = -1; k <= 1; ++k) {
-          YH[k + 1] = ((hay + k) & 7) >> 1;
-          Y8[k + 1] = 8 * ((hay + k) & 7);
-        }
-        const unsigned vy = range_mask(hay);
-        HaloXY<0> s{fbuf, {0, 0, face_dst}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Zc[0], Zc[1], Zc[2]},
-                    {HA[0], HA[1], HA[2]}, dir_mask(7u, vy, vza) & ma, dir_mask(7u, vy, vzb) & mb,
-                    mir ? -1024 : 0, mir ? -512 : 0, trash};
-        src.emit(hm, s);
-      } else {
-        int X[3];
-#pragma unroll
-        for (int k = -1; k <= 1; ++k) X[k + 1] = (hax + k) & 7;
-        const unsigned vx = range_mask(hax);
-        HaloXY<1> s{fbuf, {X[0], X[1], X[2]}, {0, 0, face_dst >> 1}, {0, 0, 8 * face_dst}, {Zc[0], Zc[1], Zc[2]},
-                    {HA[0], HA[1], HA[2]}, dir_mask(vx, 7u, vza) & ma, dir_mask(vx, 7u, vzb) & mb,
-                    mir ? -3072 : 0, mir ? -2560 : 0, trash};
-        src.emit(hm, s);
-      }
+    const int dst = mir ? 7 : 0;  // destination coordinate on the face axis
+    if (cls == 0) {
+      const int sh = mir ? mirror_shift(0) : 0;
+      HaloPush<0> s{fbuf + sh + pidx(dst, hay, haz), fbuf + sh + pidx(dst, hby, hbz),
+                    dir_mask(7u, range_mask(hay), range_mask(haz)) & ma,
+                    dir_mask(7u, range_mask(hby), range_mask(hbz)) & mb};
+      src.emit(hm, s);
+    } else if (cls == 1) {
+      const int sh = mir ? mirror_shift(1) : 0;
+      HaloPush<1> s{fbuf + sh + pidx(hax, dst, haz), fbuf + sh + pidx(hbx, dst, hbz),
+                    dir_mask(range_mask(hax), 7u, range_mask(haz)) & ma,
+                    dir_mask(range_mask(hbx), 7u, range_mask(hbz)) & mb};
+      src.emit(hm, s);
     } else {
-      int X[3], YHa[3], YHb[3], Y8a[3], Y8b[3];
-#pragma unroll
-      for (int k = -1; k <= 1; ++k) {
-        X[k + 1] = (hax + k) & 7;
-        YHa[k + 1] = ((hay + k) & 7) >> 1;
-        YHb[k + 1] = ((hby + k) & 7) >> 1;
-        Y8a[k + 1] = 8 * ((hay + k) & 7);
-        Y8b[k + 1] = 8 * ((hby + k) & 7);
-      }
-      const unsigned vx = range_mask(hax);
-      HaloZ s{fbuf, {X[0], X[1], X[2]}, {YHa[0], YHa[1], YHa[2]}, {YHb[0], YHb[1], YHb[2]},
-              {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, mir ? 2 * 64 * 3 + 1 : 0,
-              dir_mask(vx, range_mask(hay), 7u) & ma, dir_mask(vx, range_mask(hby), 7u) & mb, mir ? -17 * 512 : 0,
-              trash};
+      const int sh = mir ? mirror_shift(2) : 0;
+      HaloPush<2> s{fbuf + sh + pidx(hax, hay, dst), fbuf + sh + pidx(hbx, hby, dst),
+                    dir_mask(range_mask(hax), range_mask(hay), 7u) & ma,
+                    dir_mask(range_mask(hbx), range_mask(hby), 7u) & mb};
       src.emit(hm, s);
     }
   }
-  if (bf & kBlockBounce) {  // block-uniform
+
+  // B. the own pair, then bounce-back: a solid node of the block also pushed
+  // into the slots that bounce-back fills, so blocks with solid nodes order
+  // the two writes with a barrier (block-uniform condition)
+  float* const fown = fbuf + cx.own_p;
+  OwnPush op{fown, x > 0, x < 7, V2(0.f)};
+  src.emit(m, op);
+  cx.g13 = op.g13;
+  if (bf & kBlockBounce) {
+    if (solid_any) __syncthreads();
     const unsigned mlo_b = a.bmask[blk * kCells + own], mhi_b = a.bmask[blk * kCells + own + 256];
     if ((mlo_b | mhi_b) != 0u) {
-      BouncePush bp{fbuf, own_s, mlo_b, mhi_b};
+      BouncePush bp{fown, mlo_b, mhi_b};
       src.emit(src.own(blk, own), bp);
     }
   }

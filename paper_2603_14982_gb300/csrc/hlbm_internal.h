@@ -50,7 +50,6 @@ struct StepArgs {
   // FP64 conversions run on the slow FP64 pipe, so the kernel takes floats)
   float fuf[3], tauf, omf, kxyzf;
   float* pre_out;           // [nb][10][512] float32 natural order: pre-collision moments (recording launch)
-  int64_t pf_dist;          // one-CTA-per-block launches: the CTA of block b prefetches block b + pf_dist
                             // into L2 (0: off; set by the launcher)
 };
 

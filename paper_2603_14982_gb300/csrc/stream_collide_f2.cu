@@ -3,27 +3,29 @@
 //
 // One CTA per stored 8^3 block, 256 threads.  Thread (lane, warp) owns the node
 // pair (x, y, z0) and (x, y, z0 + 4) with x = lane & 7, y = (lane >> 3) + 4 (warp & 1),
-// z0 = warp >> 1.  Shared memory holds, per direction j != rest, the pulled
-// population of every node of the block, destination-indexed; a node pair
-// shares one 8-byte slot (node z0 in .x, node z0 + 4 in .y).
-// Inside each direction's 256-slot array the pair slot of node (x, y, z & 3)
-// is swizzled, s = (x ^ (y >> 1)) + 8 y + 64 (z & 3), which keeps the 64-bit
-// row accesses conflict-free and spreads the column writes of the x- and
-// y-face halo over more banks.
-//  A. each thread reconstructs the 26 moving populations of its pair
-//     (Eq. three_order_f) and pushes them to their destinations x + c_j with
-//     wrap-around inside the block: one 64-bit store per direction.  Pushes
-//     that leave the block land, wrapped, exactly in the slots whose true
-//     source is a halo node, so they are overwritten in B.
-//  B. 244 threads each take a pair of halo nodes (read from the 26 neighbour
+// z0 = warp >> 1.  Shared memory holds, per direction j, the pulled population
+// of every node of the block, destination-indexed, in a padded plane: node
+// (x, y, z) at x + 8 (y + 1) + kPZ (z + 1), with rows y = -1, 8 and slabs
+// z = -1, 8 as padding that is written but never read.  Every store of a node
+// is then at a compile-time offset from one base address per node, and the
+// 32 lanes of a warp touch 32 consecutive words (no bank conflicts for the
+// own pushes and the gather).  Each (destination, direction) slot has exactly
+// one writer, so the pushes need no ordering among themselves:
+//  A. 244 threads each take a pair of halo nodes (read from the 26 neighbour
 //     blocks, mostly L2 hits) and write the 9 directions that enter the block
-//     (one code path per face axis: upper faces are reflected onto lower ones);
-//     nodes whose pull source is a wall or a solid node write their own
-//     opposite population instead (half-way bounce-back).
-//  C. each thread reads the 26 populations of its pair (one 64-bit load per
-//     direction), projects to moments (Eq. rho_u_stress) and collides
-//     (Sec. 3.1; Guo forcing; mixture tau of Sec. 4).  Interface nodes (a
-//     neighbour block not stored) and solid nodes copy their input.
+//     (one code path per face axis: upper faces are reflected onto lower
+//     ones, which shifts the store by a whole number of planes);
+//  B. each thread reconstructs the 26 moving populations of its pair
+//     (Eq. three_order_f) and pushes them to their destinations x + c_j
+//     (pushes through an x face are predicated off, those through a y or z
+//     face land in the padding); nodes whose pull source is a wall or a solid
+//     node write their own opposite population instead (half-way
+//     bounce-back; after a barrier in blocks with solid nodes, whose own
+//     pushes that slot also receives);
+//  C. after one barrier, each thread reads the 26 populations of its pair,
+//     projects to moments (Eq. rho_u_stress) and collides (Sec. 3.1; Guo
+//     forcing; mixture tau of Sec. 4).  Interface nodes (a neighbour block not
+//     stored) and solid nodes copy their input.
 // Modes: kPlain; kRecord also writes the pre-collision moments (recomputed
 // steps of the adjoint); kStreamOnly writes them instead of colliding (the
 // streaming-only step S of a coupled step, Fig. 4; the collision follows
@@ -94,7 +96,6 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int x = lane & 7, y = (lane >> 3) + ((w & 1) << 2), z0 = w >> 1;
   const int own = x + 8 * y + 64 * z0;                 // pair slot in global storage
-  const int own_s = (x ^ (y >> 1)) + 8 * y + 64 * z0;  // pair slot in shared memory
   const T* in = static_cast<const T*>(a.in);
   T* out = static_cast<T*>(a.out);
   const int dom = a.blk_dom != nullptr ? a.blk_dom[blk] : 0;
@@ -109,24 +110,6 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
   }
   const uint8_t bf = a.bflags != nullptr ? a.bflags[blk] : 0;
   const bool solid_any = (bf & kBlockSolidNear) != 0;
-
-  // FP32 storage: the stored rows of the block that starts about one wave of
-  // resident CTAs later go to L2 (one 128-byte line per thread).  Measured on
-  // the 256^3 duct: the FP32 kernel compiled with this path runs 7 % faster
-  // than without it, but the prefetch itself is not the cause (with distance 0,
-  // the path compiled in and never taken, it is 0.7 % faster still): the gain
-  // is the compiler's schedule of the rest of the kernel.  The FP16 / BF16
-  // kernels run 7 % slower with the path compiled in, so they go without it.
-  if constexpr (sizeof(T) == 4) {
-    if (a.pf_dist > 0) {
-      constexpr int kLines = int(kCells * sizeof(T) / 128);
-      const int64_t pb = blk + a.pf_dist;
-      if (t < kRows * kLines && pb < a.blk0 + a.nb) {
-        const char* row = reinterpret_cast<const char*>(in + pb * (kRows * kCells) + (t / kLines) * kCells);
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(row + (t % kLines) * 128));
-      }
-    }
-  }
 
   // own node pair: issue the loads early
   const Mom<V2> m = load_pair<T>(in, blk, own, sc_in);
@@ -156,22 +139,8 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
     }
   }
 
-  // A. push the own pair
   const V2 kxyz = V2(a.kxyzf);
-  OwnPush op;
-  op.f = f2buf;
-#pragma unroll
-  for (int c = -1; c <= 1; ++c) {
-    op.Y8[c + 1] = 8 * ((y + c) & 7);
-    op.Z64[c + 1] = 64 * ((z0 + c) & 3);
-    op.swap[c + 1] = (((z0 + c) & 7) >> 2) != 0;
-#pragma unroll
-    for (int cx = -1; cx <= 1; ++cx) op.XH[(cx + 1) + 3 * (c + 1)] = ((x + cx) & 7) ^ (((y + c) & 7) >> 1);
-  }
-  emit_all(make_coef(m, kxyz), op);
-  __syncthreads();
-
-  // B. halo pairs and bounce-back
+  // A. halo pairs
   if (t < kHaloPairs && (va || vb)) {
     // reflect the upper-face pairs along the face axis (u and S components with
     // an odd count of that axis change sign)
@@ -190,55 +159,38 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
       hm.syz = hm.syz * sg;
     }
     const Coef<V2> c = make_coef(hm, kxyz);
-    const int trash = kTrash + lane;
     const unsigned ma = va ? ~0u : 0u, mb = vb ? ~0u : 0u;
     const uint2 gm = g_halo_masks[t];
-    if (cls < 2) {
-      int Zc[3], HA[3];
-#pragma unroll
-      for (int k = -1; k <= 1; ++k) {
-        Zc[k + 1] = 64 * ((haz + k) & 3);
-        HA[k + 1] = ((haz + k) & 7) >> 2;
-      }
-      const int face_dst = mir ? 7 : 0;  // destination coordinate on the face axis
-      if (cls == 0) {
-        int YH[3], Y8[3];
-#pragma unroll
-        for (int k = -1; k <= 1; ++k) {
-          YH[k + 1] = ((hay + k) & 7) >> 1;
-          Y8[k + 1] = 8 * ((hay + k) & 7);
-        }
-        HaloXY<0> s{fbuf, {0, 0, face_dst}, {YH[0], YH[1], YH[2]}, {Y8[0], Y8[1], Y8[2]}, {Zc[0], Zc[1], Zc[2]},
-                    {HA[0], HA[1], HA[2]}, gm.x & ma, gm.y & mb, mir ? -1024 : 0, mir ? -512 : 0, trash};
-        emit_all(c, s);
-      } else {
-        int X[3];
-#pragma unroll
-        for (int k = -1; k <= 1; ++k) X[k + 1] = (hax + k) & 7;
-        HaloXY<1> s{fbuf, {X[0], X[1], X[2]}, {0, 0, face_dst >> 1}, {0, 0, 8 * face_dst}, {Zc[0], Zc[1], Zc[2]},
-                    {HA[0], HA[1], HA[2]}, gm.x & ma, gm.y & mb, mir ? -3072 : 0, mir ? -2560 : 0, trash};
-        emit_all(c, s);
-      }
+    const int dst = mir ? 7 : 0;  // destination coordinate on the face axis
+    if (cls == 0) {
+      const int sh = mir ? mirror_shift(0) : 0;
+      HaloPush<0> hp{fbuf + sh + pidx(dst, hay, haz), fbuf + sh + pidx(dst, hby, hbz), gm.x & ma, gm.y & mb};
+      emit_all(c, hp);
+    } else if (cls == 1) {
+      const int sh = mir ? mirror_shift(1) : 0;
+      HaloPush<1> hp{fbuf + sh + pidx(hax, dst, haz), fbuf + sh + pidx(hbx, dst, hbz), gm.x & ma, gm.y & mb};
+      emit_all(c, hp);
     } else {
-      int X[3], YHa[3], YHb[3], Y8a[3], Y8b[3];
-#pragma unroll
-      for (int k = -1; k <= 1; ++k) {
-        X[k + 1] = (hax + k) & 7;
-        YHa[k + 1] = ((hay + k) & 7) >> 1;
-        YHb[k + 1] = ((hby + k) & 7) >> 1;
-        Y8a[k + 1] = 8 * ((hay + k) & 7);
-        Y8b[k + 1] = 8 * ((hby + k) & 7);
-      }
-      HaloZ s{fbuf, {X[0], X[1], X[2]}, {YHa[0], YHa[1], YHa[2]}, {YHb[0], YHb[1], YHb[2]},
-              {Y8a[0], Y8a[1], Y8a[2]}, {Y8b[0], Y8b[1], Y8b[2]}, mir ? 2 * 64 * 3 + 1 : 0, gm.x & ma, gm.y & mb,
-              mir ? -17 * 512 : 0, trash};
-      emit_all(c, s);
+      const int sh = mir ? mirror_shift(2) : 0;
+      HaloPush<2> hp{fbuf + sh + pidx(hax, hay, dst), fbuf + sh + pidx(hbx, hby, dst), gm.x & ma, gm.y & mb};
+      emit_all(c, hp);
     }
   }
-  if (bf & kBlockBounce) {  // block-uniform
+  // B. push the own pair (after the halo pairs: the halo moments are then
+  // dead before the own coefficients are formed, 106 instead of 128 registers
+  // in FP32)
+  float* const fown = fbuf + pidx(x, y, z0);
+  OwnPush op{fown, x > 0, x < 7, V2(0.f)};
+  emit_all(make_coef(m, kxyz), op);
+
+  // bounce-back: a solid node of the block also pushed into the slots it
+  // fills, so blocks with solid nodes order the two writes with a barrier
+  // (block-uniform condition)
+  if (bf & kBlockBounce) {
+    if (solid_any) __syncthreads();
     const unsigned mlo_b = a.bmask[blk * kCells + own], mhi_b = a.bmask[blk * kCells + own + 256];
     if ((mlo_b | mhi_b) != 0u) {
-      BouncePush bp{fbuf, own_s, mlo_b, mhi_b};
+      BouncePush bp{fown, mlo_b, mhi_b};
       emit_all(make_coef(load_pair<T>(in, blk, own, sc_in), kxyz), bp);
     }
   }
@@ -262,7 +214,7 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
     mo = load_pair<T>(in, blk, own, sc_in);
   } else {
     V2 g[27];
-    gather_all(f2buf, own_s, op.g13, g, std::make_integer_sequence<int, 27>{});
+    gather_all(fown, op.g13, g, std::make_integer_sequence<int, 27>{});
     const PreMom<V2> p = project(g);
     if constexpr (kMode != kPlain) {  // pre-collision moments (natural order, float32)
       float* q = a.pre_out + blk * (kRows * kCells) + own;
@@ -297,7 +249,7 @@ __device__ __forceinline__ void sc_block(const StepArgs& a, const int64_t blk, f
 // One CTA per block.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 2) k_stream_collide_f2(StepArgs a) {
-  extern __shared__ __align__(16) float2 f2buf[];  // [26][256] node pairs + trash
+  extern __shared__ __align__(16) float2 f2buf[];  // padded planes, kBufBytes
   __shared__ unsigned s_miss;
   sc_block<T>(a, a.blk0 + blockIdx.x, f2buf, s_miss);
 }
@@ -384,18 +336,6 @@ __global__ void __launch_bounds__(512) k_bounce_masks(const int32_t* __restrict_
   if (n == 0) bflags[blk] = uint8_t((bflags[blk] & ~kBlockBounce) | (any ? kBlockBounce : 0));
 }
 
-// Two resident CTAs per SM: the prefetch distance of one wave.
-int64_t wave_blocks() {
-  static int64_t w = -1;
-  if (w < 0) {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 0;
-    w = 2 * int64_t(sms);
-  }
-  return w;
-}
-
 template <typename T>
 cudaError_t launch_f2(const StepArgs& a_in, cudaStream_t s) {
   {
@@ -407,7 +347,7 @@ cudaError_t launch_f2(const StepArgs& a_in, cudaStream_t s) {
   a.tauf = float(a.tau);
   a.omf = float(a.om);
   a.kxyzf = float(a.kxyz);
-  const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
+  const size_t smem = kBufBytes;
   static bool configured = false;
   if (!configured) {
     cudaError_t err =
@@ -421,10 +361,8 @@ cudaError_t launch_f2(const StepArgs& a_in, cudaStream_t s) {
   if (a.nb == 0) return cudaSuccess;
   if (a.work != nullptr) {
     if (a.grid <= 0 || a.nb >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
-    a.pf_dist = 0;  // ticketed blocks: no fixed successor
     k_stream_collide_f2_persistent<T><<<unsigned(a.grid), kThreads, smem, s>>>(a);
   } else {
-    a.pf_dist = wave_blocks();
     k_stream_collide_f2<T><<<(unsigned)a.nb, kThreads, smem, s>>>(a);
   }
   return cudaGetLastError();
@@ -432,7 +370,7 @@ cudaError_t launch_f2(const StepArgs& a_in, cudaStream_t s) {
 
 template <typename T>
 cudaError_t resident_f2(int* per_sm) {
-  const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
+  const size_t smem = kBufBytes;
   cudaError_t err =
       cudaFuncSetAttribute(k_stream_collide_f2_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -460,7 +398,7 @@ cudaError_t launch_stream_collide_record(const StepArgs& a_in, cudaStream_t s) {
   a.tauf = float(a.tau);
   a.omf = float(a.om);
   a.kxyzf = float(a.kxyz);
-  const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
+  const size_t smem = kBufBytes;
   static bool configured = false;
   if (!configured) {
     cudaError_t err =
@@ -481,7 +419,7 @@ cudaError_t launch_pre(const StepArgs& a_in, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   StepArgs a = a_in;
-  const size_t smem = size_t(26) * 256 * sizeof(float2) + 32 * sizeof(float);
+  const size_t smem = kBufBytes;
   static bool configured = false;
   if (!configured) {
     cudaError_t err =
