@@ -50,7 +50,6 @@ struct StepArgs {
   // FP64 conversions run on the slow FP64 pipe, so the kernel takes floats)
   float fuf[3], tauf, omf, kxyzf;
   float* pre_out;           // [nb][10][512] float32 natural order: pre-collision moments (recording launch)
-                            // into L2 (0: off; set by the launcher)
 };
 
 // FP64 storage: one node per thread (stream_collide.cu).  Other storages: the
