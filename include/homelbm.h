@@ -285,6 +285,14 @@ int32_t hlbm_adjoint(hlbm_lattice *h, const float *dL_dM_dev, float *dL_dF_dev);
    undefined. */
 int32_t hlbm_inject_alloc_failure(int64_t after);
 
+/* Test hook: writes to out_dev[i] the binary64 -> binary32 round-to-nearest-
+   even narrowing that the interface transfers apply to their FP64 sums
+   (integer arithmetic for results in the normal binary32 range), and to
+   hw_dev[i] the CUDA conversion instruction's result, for n device values
+   in_dev.  Synchronous; HLBM_E_INVALID_ARG for n < 0 or NULL buffers with
+   n > 0. */
+int32_t hlbm_test_narrow(const double *in_dev, float *out_dev, float *hw_dev, int64_t n);
+
 /* Allocation-free FP64 reduction of a moment buffer the caller already holds.
  * The paper has no counterpart; this entry point exists for callers that must
  * not allocate device memory: code embedded in a host application that owns

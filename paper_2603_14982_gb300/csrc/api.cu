@@ -13,6 +13,7 @@
 #include "hlbm_internal.h"
 #include "io_reduce.h"
 #include "lattice_state.h"
+#include "multilevel.cuh"
 
 using namespace hlbm;
 
@@ -797,6 +798,15 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
   seg[0] = nullptr;
   release_all();
   if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
+  return HLBM_OK;
+}
+
+int32_t hlbm_test_narrow(const double* in_dev, float* out_dev, float* hw_dev, int64_t n) {
+  if (n < 0 || (n > 0 && (in_dev == nullptr || out_dev == nullptr || hw_dev == nullptr)))
+    return fail(nullptr, HLBM_E_INVALID_ARG, "bad buffers");
+  cudaError_t e = test_narrow(in_dev, out_dev, hw_dev, n, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(nullptr, HLBM_E_CUDA, "narrowing test: %s", cudaGetErrorString(e));
   return HLBM_OK;
 }
 

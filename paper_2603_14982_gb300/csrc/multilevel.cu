@@ -2,12 +2,15 @@
 // initialisation of blocks created by a rebuild (Sec. 5.2, Sec. 6.3).
 //
 // Each stencil node's moments are read from storage and split into
-// (rho, u, S^neq = S - u u) in FP32 (one fused multiply-add per S^neq entry,
-// rounded once); the weighted sums over the stencil and the temporal midpoint
-// are accumulated in FP64 with exact power-of-two weights; the result is
-// rescaled and recombined as S = k S^neq + u u (S^eq formed from the
-// interpolated velocity) in FP32.  FP64 work is kept to the accumulation: on
-// GB300 the FP64 pipe runs at a small fraction of the FP32 rate.
+// (delta rho, u, S^neq = S - u u) in FP32 (one fused multiply-add per S^neq
+// entry, rounded once); the weighted sums over the stencil and the temporal
+// midpoint are accumulated in FP64 with exact power-of-two weights (the
+// weights sum to one, so interpolating delta rho = rho - 1 is interpolating
+// rho); the result is rescaled and recombined as S = k S^neq + u u (S^eq
+// formed from the interpolated velocity) in FP32.  FP64 work is kept to the
+// accumulation: on GB300 the FP64 pipe runs at a small fraction of the FP32
+// rate, so the widening and the narrowing conversions run on the integer
+// pipes.
 #include "hlbm_internal.h"
 #include "multilevel.cuh"
 
@@ -15,7 +18,7 @@ namespace hlbm {
 namespace {
 
 struct Node64 {
-  double rho, ux, uy, uz, s[6];  // s = S^neq (xx, yy, zz, xy, xz, yz)
+  double drho, ux, uy, uz, s[6];  // drho = rho - 1; s = S^neq (xx, yy, zz, xy, xz, yz)
 };
 
 // Widening float -> double on the integer pipes.  The conversion is exact:
@@ -35,11 +38,39 @@ __device__ __forceinline__ double to64(float v) {
   return __longlong_as_double(static_cast<long long>(sign | mag));
 }
 
+// Narrowing binary64 -> binary32 with round-to-nearest-even on the integer
+// pipes (IEEE 754): for results in the normal binary32 range the 52-bit
+// fraction is cut to 23 bits and rounded on the 29 dropped bits, ties to
+// even; the carry of a round-up propagates into the exponent (up to
+// infinity).  Zeros keep their sign; all other inputs (binary32 subnormal or
+// overflow range, infinities, NaNs) take the conversion instruction.
+__device__ __forceinline__ float to32(double v) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned hi = unsigned(bits >> 32), lo = unsigned(bits);
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  if (ex - 897u > 253u) {  // biased exponent outside [897, 1150]
+    if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+    return __double2float_rn(v);
+  }
+  const unsigned keep = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u))) ? 1u : 0u;
+  return __uint_as_float(((hi & 0x80000000u) | ((ex - 896u) << 23) | keep) + up);
+}
+
+template <typename R>
+__device__ __forceinline__ R narrow(double v) {
+  if constexpr (sizeof(R) == 8)
+    return v;
+  else
+    return to32(v);
+}
+
 template <typename T>
 __device__ __forceinline__ Node64 load64(const void* base, int64_t blk, int cell, const Scales* sc) {
   const auto m = load_node<T>(static_cast<const T*>(base), blk, cell, sc);
   Node64 n;
-  n.rho = 1.0 + to64(m.drho);
+  n.drho = to64(m.drho);
   n.ux = to64(m.ux);
   n.uy = to64(m.uy);
   n.uz = to64(m.uz);
@@ -57,22 +88,22 @@ __device__ __forceinline__ void store64(void* base, int64_t blk, int cell, const
                                         const Scales* sc) {
   using R = typename StorageTraits<T>::R;
   Mom<R> m;
-  const R ux = R(n.ux), uy = R(n.uy), uz = R(n.uz), kk = R(k);
-  m.drho = R(n.rho - 1.0);
+  const R ux = narrow<R>(n.ux), uy = narrow<R>(n.uy), uz = narrow<R>(n.uz), kk = R(k);
+  m.drho = narrow<R>(n.drho);
   m.ux = ux;
   m.uy = uy;
   m.uz = uz;
-  m.sxx = mad(kk, R(n.s[0]), ux * ux);
-  m.syy = mad(kk, R(n.s[1]), uy * uy);
-  m.szz = mad(kk, R(n.s[2]), uz * uz);
-  m.sxy = mad(kk, R(n.s[3]), ux * uy);
-  m.sxz = mad(kk, R(n.s[4]), ux * uz);
-  m.syz = mad(kk, R(n.s[5]), uy * uz);
+  m.sxx = mad(kk, narrow<R>(n.s[0]), ux * ux);
+  m.syy = mad(kk, narrow<R>(n.s[1]), uy * uy);
+  m.szz = mad(kk, narrow<R>(n.s[2]), uz * uz);
+  m.sxy = mad(kk, narrow<R>(n.s[3]), ux * uy);
+  m.sxz = mad(kk, narrow<R>(n.s[4]), ux * uz);
+  m.syz = mad(kk, narrow<R>(n.s[5]), uy * uz);
   store_node<T>(static_cast<T*>(base), blk, cell, m, sc);
 }
 
 __device__ __forceinline__ void axpy(Node64& acc, double w, const Node64& v) {
-  acc.rho += w * v.rho;
+  acc.drho += w * v.drho;
   acc.ux += w * v.ux;
   acc.uy += w * v.uy;
   acc.uz += w * v.uz;
@@ -82,7 +113,7 @@ __device__ __forceinline__ void axpy(Node64& acc, double w, const Node64& v) {
 
 __device__ __forceinline__ Node64 zero64() {
   Node64 n;
-  n.rho = n.ux = n.uy = n.uz = 0.0;
+  n.drho = n.ux = n.uy = n.uz = 0.0;
 #pragma unroll
   for (int r = 0; r < 6; ++r) n.s[r] = 0.0;
   return n;
@@ -260,8 +291,7 @@ __global__ void __launch_bounds__(512, 2) k_init_level(OldHierarchy o, int level
   Node64 v;
   if (!resolve<T, kMaxLevels - 1>(o, level, x, y, z, v)) {
     atomicExch(status, 2);
-    v = zero64();
-    v.rho = 1.0;
+    v = zero64();  // rest state
   }
   store64<T>(out, b, cell, v, 1.0, out_sc);
 }
@@ -290,7 +320,21 @@ cudaError_t init_typed(const OldHierarchy& o, int level, const int32_t* coords, 
   return cudaGetLastError();
 }
 
+__global__ void k_test_narrow(const double* __restrict__ in, float* __restrict__ out, float* __restrict__ hw,
+                              int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = to32(in[i]);
+  hw[i] = __double2float_rn(in[i]);
+}
+
 }  // namespace
+
+cudaError_t test_narrow(const double* in, float* out, float* hw, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_test_narrow<<<unsigned((n + 255) / 256), 256, 0, s>>>(in, out, hw, n);
+  return cudaGetLastError();
+}
 
 #define HLBM_ML_DISPATCH(storage, fn, ...)                        \
   switch (storage) {                                              \

@@ -57,4 +57,8 @@ struct OldHierarchy {
 cudaError_t init_new_level(int storage, const OldHierarchy& old, int level, const int32_t* coords, int64_t nb,
                            void* out, const Scales* out_sc, int* status, cudaStream_t s);
 
+// Test hook: the transfers' binary64 -> binary32 narrowing of n device values
+// into out, and the conversion instruction's result into hw.
+cudaError_t test_narrow(const double* in, float* out, float* hw, int64_t n, cudaStream_t s);
+
 }  // namespace hlbm

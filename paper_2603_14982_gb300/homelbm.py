@@ -67,6 +67,7 @@ _SIGS = {
     "hlbm_reduce": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "hlbm_forward_record": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "hlbm_inject_alloc_failure": (ctypes.c_int32, [ctypes.c_int64]),
+    "hlbm_test_narrow": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "hlbm_set_drag": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_int32]),
     "hlbm_set_open_faces": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
