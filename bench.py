@@ -338,21 +338,24 @@ def bench_ml_adjoint(hl, wl, stream, pos0, n=512, fine_steps=40, ckpt=8):
             "finite": bool(torch.isfinite(dF).all().item())}
 
 
-def bench_sparse(hl, wl, stream, n=2048, L=4, coarse_steps=4):
+def bench_sparse(hl, wl, stream, n=2048, L=4, coarse_steps=4, lookup=0):
     """Fine-equivalent throughput on the sparse n^3 tube-tree hierarchy (four
     levels, bounce-back walls on every face, uniform force 1e-6 along -y, FP32,
     static hierarchy): hierarchy build time, then coarse steps timed with CUDA
-    events after one warm-up coarse step."""
+    events after one warm-up coarse step.  lookup: block lookup mode (0 dense
+    slot tables, 1 spatial hash)."""
     import torch
     per = 2 ** (L - 1)
     coords = wl.tube_tree_blocks(n)
     with hl.Lattice((n, n, n), levels=L, tau=0.9, periodic=(False, False, False), storage="f32",
                     stream=stream.cuda_stream) as lat:
+        lat.set_block_lookup(lookup)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         lat.set_fine_blocks(coords)
         lat.synchronize()
         t_build = time.perf_counter() - t0
+        mode, table_bytes = lat.block_lookup()
         lat.set_uniform_force(0.0, -1e-6, 0.0)
         counts = [lat.num_blocks(l) for l in range(L)]
         lat.step(per)
@@ -369,7 +372,8 @@ def bench_sparse(hl, wl, stream, n=2048, L=4, coarse_steps=4):
             "mlups_fine_equiv": round(n ** 3 * fine_steps / (t / 1e3) / 1e6, 1),
             "actual_updates_per_s_M": round(updates / (t / 1e3) / 1e6, 1),
             "actual_gbs": round(gbs, 1), "actual_gbs_over_peak": round(gbs / peak, 4),
-            "mass": float(red[0]), "finite": bool(np.isfinite(red[0]))}
+            "mass": float(red[0]), "finite": bool(np.isfinite(red[0])),
+            "block_lookup": "hash" if mode == 1 else "slot tables", "lookup_table_bytes": int(table_bytes)}
 
 
 def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebuild_every=10, drag_every=0):
@@ -462,6 +466,9 @@ def bench_extras(hl, wl):
     out["c3_coupled"] = rec
     out["c3_adjoint"] = bench_ml_adjoint(hl, wl, stream, pos0)
     out["sparse_tree_2048"] = bench_sparse(hl, wl, stream)
+    hashed = bench_sparse(hl, wl, stream, lookup=1)
+    out["sparse_tree_2048_hash"] = {k: hashed[k] for k in ("ms_per_fine_step", "mlups_fine_equiv", "build_s",
+                                                           "block_lookup", "lookup_table_bytes", "mass")}
     return out
 
 

@@ -133,6 +133,25 @@ int32_t hlbm_set_fine_blocks(hlbm_lattice *h, const int32_t *coords_xyz, int64_t
 int32_t hlbm_rebuild_from_particles(hlbm_lattice *h, const float *pos_xyz, int64_t n, int32_t on_device,
                                     int64_t counts_out[3]);
 
+/* Block lookup by position of the rebuilt hierarchies (Sec. 6.1: each
+   level's table of active tiles, found through a spatial hash).  mode 0
+   (default): a dense slot table per level (int32 per block slot of the
+   domain).  mode 1: a spatial hash per level (open addressing, linear
+   probing, at most half full: 12 bytes per table entry, 2 to 4 entries per
+   stored block); the dense slot table is then dropped after each rebuild.
+   The neighbour tables, the interface transfers, the moment carry-over of a
+   rebuild, the particle deposit and the multi-level adjoint use whichever is
+   present; results are identical.  Takes effect at once for levels already
+   built by the rebuild pipeline (a failed allocation leaves them as they
+   were) and for every later rebuild.  The rebuild itself still works on
+   dense per-level grids.  HLBM_E_INVALID_ARG for another mode. */
+int32_t hlbm_set_block_lookup(hlbm_lattice *h, int32_t mode);
+
+/* The block lookup mode and the device bytes the lookup tables of all levels
+   hold now (dense slot tables: 4 bytes per block slot of a level; hashes: 12
+   bytes per table entry).  Host outputs; HLBM_E_INVALID_ARG for NULL. */
+int32_t hlbm_get_block_lookup(const hlbm_lattice *h, int32_t *mode, int64_t *table_bytes);
+
 /* Interface nodes of a level as (block << 9) | node, ascending: which = 0 the
    downward set I^d (filled from level+1 by the downward transfer), which = 1
    the upward set I^u (filled from level-1 by the upward transfer).  Host

@@ -37,6 +37,7 @@ constexpr int64_t kBlockVals = int64_t(kRows) * kCells;
 __device__ __forceinline__ int64_t find_block(const LevelView& v, int x, int y, int z) {
   const int bx = x >> 3, by = y >> 3, bz = z >> 3;
   if (bx < 0 || by < 0 || bz < 0 || bx >= v.d.nx || by >= v.d.ny || bz >= v.d.nz) return -1;
+  if (v.hash.keys != nullptr) return hash_find(v.hash, bx, by, bz);
   return v.slot[(int64_t(bz) * v.d.ny + by) * v.d.nx + bx];
 }
 
@@ -266,6 +267,7 @@ LevelView level_view(const hlbm_lattice* h, int l, const void* mom, const void* 
   LevelView v{};
   v.d = level_dims(h, l);
   v.slot = L.d_slot;
+  v.hash = BlockHash{L.d_hkeys, L.d_hvals, L.hcap ? L.hcap - 1u : 0u};
   v.coords = L.d_coords;
   v.mom = mom;
   v.mom_other = other;

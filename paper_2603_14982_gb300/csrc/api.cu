@@ -121,9 +121,10 @@ void LatticeOps::free_level(hlbm_lattice* h, LevelData& L) {
   release(h, v);
   L.d_skip = nullptr;
   for (void** q : {(void**)&L.d_coords, (void**)&L.d_slot, (void**)&L.d_H, (void**)&L.d_stored, (void**)&L.d_down,
-                   (void**)&L.d_up, (void**)&L.d_scales, (void**)&L.d_amax}) {
+                   (void**)&L.d_up, (void**)&L.d_scales, (void**)&L.d_amax, (void**)&L.d_hkeys, (void**)&L.d_hvals}) {
     release(h, *q);
   }
+  L.hcap = 0;
   L.n_down = L.n_up = 0;
   L.nb = 0;
   L.coords.clear();
@@ -798,6 +799,86 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
   seg[0] = nullptr;
   release_all();
   if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
+  return HLBM_OK;
+}
+
+int32_t hlbm_set_block_lookup(hlbm_lattice* h, int32_t mode) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (mode != 0 && mode != 1) return fail(h, HLBM_E_INVALID_ARG, "block lookup mode must be 0 (slot table) or 1 (hash)");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  if (h->device_hierarchy && h->have_blocks) {
+    // convert the stored levels now; every allocation comes first, so a failed
+    // call leaves the levels as they were
+    const int L = h->cfg.num_levels;
+    std::vector<void*> a(size_t(2 * L), nullptr);
+    std::vector<uint32_t> cap(size_t(L), 0);
+    auto undo = [&](int r) {
+      for (void*& p : a) LatticeOps::release(h, p);
+      return r;
+    };
+    for (int l = 0; l < L; ++l) {
+      LevelData& X = h->lv[l];
+      int dims[3];
+      h->block_dims(l, dims);
+      const GridDims d{dims[0], dims[1], dims[2]};
+      if (mode == 1 && X.d_hkeys == nullptr && X.nb > 0) {
+        cap[size_t(l)] = hash_capacity(X.nb);
+        if ((rc = LatticeOps::alloc(h, &a[size_t(2 * l)], cap[size_t(l)] * sizeof(unsigned long long))) ||
+            (rc = LatticeOps::alloc(h, &a[size_t(2 * l + 1)], cap[size_t(l)] * sizeof(int32_t))))
+          return undo(rc);
+      } else if (mode == 0 && X.d_slot == nullptr) {
+        if ((rc = LatticeOps::alloc(h, &a[size_t(2 * l)], size_t(d.slots()) * sizeof(int32_t)))) return undo(rc);
+      }
+    }
+    for (int l = 0; l < L; ++l) {
+      LevelData& X = h->lv[l];
+      int dims[3];
+      h->block_dims(l, dims);
+      const GridDims d{dims[0], dims[1], dims[2]};
+      cudaError_t e = cudaSuccess;
+      if (mode == 1 && a[size_t(2 * l)] != nullptr) {
+        X.d_hkeys = static_cast<unsigned long long*>(a[size_t(2 * l)]);
+        X.d_hvals = static_cast<int32_t*>(a[size_t(2 * l + 1)]);
+        X.hcap = cap[size_t(l)];
+        a[size_t(2 * l)] = a[size_t(2 * l + 1)] = nullptr;
+        e = build_block_hash(X.d_coords, X.nb, X.d_hkeys, X.d_hvals, X.hcap, h->stream);
+        void* v = X.d_slot;
+        LatticeOps::release(h, v);
+        X.d_slot = nullptr;
+      } else if (mode == 0 && a[size_t(2 * l)] != nullptr) {
+        X.d_slot = static_cast<int32_t*>(a[size_t(2 * l)]);
+        a[size_t(2 * l)] = nullptr;
+        e = slot_table(X.d_coords, X.nb, d, X.d_slot, h->stream);
+        void* v = X.d_hkeys;
+        LatticeOps::release(h, v);
+        X.d_hkeys = nullptr;
+        v = X.d_hvals;
+        LatticeOps::release(h, v);
+        X.d_hvals = nullptr;
+        X.hcap = 0;
+      }
+      if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "block lookup: %s", cudaGetErrorString(e));
+    }
+    HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  h->block_lookup = mode;
+  return HLBM_OK;
+}
+
+int32_t hlbm_get_block_lookup(const hlbm_lattice* h, int32_t* mode, int64_t* table_bytes) {
+  hlbm_lattice* hm = const_cast<hlbm_lattice*>(h);
+  if (h == nullptr || mode == nullptr || table_bytes == nullptr) return fail(hm, HLBM_E_INVALID_ARG, "NULL argument");
+  *mode = h->block_lookup;
+  int64_t bytes = 0;
+  for (int l = 0; l < h->cfg.num_levels; ++l) {
+    const LevelData& X = h->lv[l];
+    int dims[3];
+    h->block_dims(l, dims);
+    if (X.d_slot != nullptr) bytes += int64_t(dims[0]) * dims[1] * dims[2] * int64_t(sizeof(int32_t));
+    if (X.d_hkeys != nullptr) bytes += int64_t(X.hcap) * int64_t(sizeof(unsigned long long) + sizeof(int32_t));
+  }
+  *table_bytes = bytes;
   return HLBM_OK;
 }
 

@@ -186,7 +186,8 @@ extern "C" int32_t hlbm_set_open_faces(hlbm_lattice* h, const int32_t type[6], d
       int dims[3];
       h->block_dims(l, dims);
       const cudaError_t e = neighbour_table(L.d_coords, L.nb, L.d_slot, GridDims{dims[0], dims[1], dims[2]},
-                                            h->cfg.periodic, h->open_mask(), L.d_nbr, h->stream);
+                                            h->cfg.periodic, h->open_mask(), L.d_nbr, h->stream,
+                                            BlockHash{L.d_hkeys, L.d_hvals, L.hcap ? L.hcap - 1u : 0u});
       if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "neighbour table: %s", cudaGetErrorString(e));
     } else {
       std::vector<int32_t> slot_to_idx(size_t(L.nb)), nbr;

@@ -17,7 +17,8 @@ namespace hlbm {
 namespace {
 
 __global__ void k_count_particles(const float* __restrict__ pos, int64_t n, int nx, int ny, int nz, int bdx, int bdy,
-                                  const int32_t* __restrict__ slot, unsigned* cnt, unsigned long long* outside) {
+                                  const int32_t* __restrict__ slot, BlockHash hash, unsigned* cnt,
+                                  unsigned long long* outside) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
@@ -29,7 +30,7 @@ __global__ void k_count_particles(const float* __restrict__ pos, int64_t n, int 
   const int y = min(max(int(floorf(py)), 0), ny - 1);
   const int z = min(max(int(floorf(pz)), 0), nz - 1);
   const int64_t s = (int64_t(z >> 3) * bdy + (y >> 3)) * bdx + (x >> 3);
-  const int64_t b = slot != nullptr ? slot[s] : s;
+  const int64_t b = hash.keys != nullptr ? hash_find(hash, x >> 3, y >> 3, z >> 3) : (slot != nullptr ? slot[s] : s);
   if (b < 0) {
     atomicAdd(outside, 1ull);
     return;
@@ -67,8 +68,8 @@ extern "C" int32_t hlbm_deposit_particles(hlbm_lattice* h, const float* pos_xyz,
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
   LevelData& L = h->lv[0];
-  if (h->device_hierarchy && L.d_slot == nullptr)
-    return fail(h, HLBM_E_BAD_STATE, "the finest level has no slot table");
+  if (h->device_hierarchy && L.d_slot == nullptr && L.d_hkeys == nullptr)
+    return fail(h, HLBM_E_BAD_STATE, "the finest level has no block table");
   const int64_t n_nodes = L.nb * kCells;
   // every buffer is allocated before any is installed in the handle: a failed
   // call leaves no unwritten force or solid-fraction field for the next step
@@ -100,6 +101,7 @@ extern "C" int32_t hlbm_deposit_particles(hlbm_lattice* h, const float* pos_xyz,
   if (e == cudaSuccess && n > 0) {
     k_count_particles<<<unsigned((n + 255) / 256), 256, 0, h->stream>>>(
         d_pos, n, h->cfg.nx, h->cfg.ny, h->cfg.nz, dims[0], dims[1], h->device_hierarchy ? L.d_slot : nullptr,
+        BlockHash{L.d_hkeys, L.d_hvals, L.hcap ? L.hcap - 1u : 0u},
         reinterpret_cast<unsigned*>(h->d_eps), h->d_count);
     e = cudaGetLastError();
   }

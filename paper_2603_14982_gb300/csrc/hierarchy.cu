@@ -189,7 +189,8 @@ __device__ __forceinline__ unsigned beyond_faces(int v, int n, int axis) {
 }
 
 __global__ void k_nbr(const int32_t* __restrict__ coords, int64_t nb, const int32_t* __restrict__ slot_to_idx,
-                      GridDims d, int px, int py, int pz, unsigned open_mask, int32_t* __restrict__ nbr) {
+                      GridDims d, int px, int py, int pz, unsigned open_mask, int32_t* __restrict__ nbr,
+                      BlockHash hash) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= nb * 27) return;
   const int64_t b = i / 27;
@@ -200,7 +201,24 @@ __global__ void k_nbr(const int32_t* __restrict__ coords, int64_t nb, const int3
     nbr[i] = (faces & open_mask) != 0u ? kOpen : kWall;
     return;
   }
-  nbr[i] = slot_to_idx[slot_of(d, x, y, z)];  // -1 (kMissing) when not stored
+  // -1 (kMissing) when not stored
+  nbr[i] = slot_to_idx != nullptr ? slot_to_idx[slot_of(d, x, y, z)] : int32_t(hash_find(hash, x, y, z));
+}
+
+__global__ void k_hash_insert(const int32_t* __restrict__ coords, int64_t nb, unsigned long long* keys,
+                              int32_t* vals, uint32_t mask) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  const unsigned long long key = block_key(coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]);
+  uint32_t s = hash_slot(key) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {  // the table is at most half full
+    const unsigned long long prev = atomicCAS(keys + s, kEmptyKey, key);
+    if (prev == kEmptyKey || prev == key) {
+      vals[s] = int32_t(i);
+      return;
+    }
+    s = (s + 1u) & mask;
+  }
 }
 
 // Node classification per block (one CTA of 512 threads): a node is an
@@ -403,10 +421,40 @@ cudaError_t compact_slots(const uint8_t* stored, const uint8_t* flags, const uin
 }
 
 cudaError_t neighbour_table(const int32_t* coords, int64_t nb, const int32_t* slot_to_idx, GridDims d,
-                            const int periodic[3], unsigned open_mask, int32_t* nbr, cudaStream_t s) {
+                            const int periodic[3], unsigned open_mask, int32_t* nbr, cudaStream_t s,
+                            BlockHash hash) {
   if (nb == 0) return cudaSuccess;
+  if (slot_to_idx == nullptr && hash.keys == nullptr) return cudaErrorInvalidValue;
   k_nbr<<<grid_for(nb * 27, 256), 256, 0, s>>>(coords, nb, slot_to_idx, d, periodic[0], periodic[1], periodic[2],
-                                                open_mask, nbr);
+                                                open_mask, nbr, hash);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_slot_scatter(const int32_t* __restrict__ coords, int64_t nb, GridDims d, int32_t* slot_to_idx) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < nb) slot_to_idx[slot_of(d, coords[3 * i], coords[3 * i + 1], coords[3 * i + 2])] = int32_t(i);
+}
+}  // namespace
+
+cudaError_t slot_table(const int32_t* coords, int64_t nb, GridDims d, int32_t* slot_to_idx, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(slot_to_idx, 0xff, size_t(d.slots()) * sizeof(int32_t), s);
+  if (e != cudaSuccess || nb == 0) return e;
+  k_slot_scatter<<<grid_for(nb, 256), 256, 0, s>>>(coords, nb, d, slot_to_idx);
+  return cudaGetLastError();
+}
+
+uint32_t hash_capacity(int64_t nb) {
+  uint32_t c = 64;
+  while (int64_t(c) < 2 * nb && c < (1u << 31)) c <<= 1;
+  return c;
+}
+
+cudaError_t build_block_hash(const int32_t* coords, int64_t nb, unsigned long long* keys, int32_t* vals,
+                             uint32_t capacity, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(keys, 0xff, size_t(capacity) * sizeof(unsigned long long), s);
+  if (e != cudaSuccess || nb == 0) return e;
+  k_hash_insert<<<grid_for(nb, 256), 256, 0, s>>>(coords, nb, keys, vals, capacity - 1u);
   return cudaGetLastError();
 }
 

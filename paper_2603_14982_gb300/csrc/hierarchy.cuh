@@ -23,6 +23,51 @@ struct GridDims {
 
 constexpr uint8_t kFlagLeaf = 1, kFlagBorder = 2, kFlagNew = 4, kFlagRefine = 8, kFlagCoarsen = 16;
 
+// Spatial-hash variant of a level's block table (Sec. 6.1: the active tiles
+// of each level are found by position through a spatial hash): open
+// addressing with linear probing over a power-of-two table of 64-bit keys
+// (bz << 42 | by << 21 | bx; all ones = empty), at most half full.  The slot
+// of a key is the SplitMix64 finaliser (Steele, Lea and Flood, OOPSLA 2014)
+// of the key, masked.
+constexpr unsigned long long kEmptyKey = ~0ull;
+struct BlockHash {
+  const unsigned long long* keys = nullptr;  // null: the level uses its dense slot table
+  const int32_t* vals = nullptr;
+  uint32_t mask = 0;  // capacity - 1
+};
+
+__host__ __device__ inline unsigned long long block_key(int bx, int by, int bz) {
+  return (static_cast<unsigned long long>(bz) << 42) | (static_cast<unsigned long long>(by) << 21) |
+         static_cast<unsigned long long>(bx);
+}
+
+__host__ __device__ inline uint32_t hash_slot(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return static_cast<uint32_t>(z ^ (z >> 31));
+}
+
+// Block index at block coordinates (bx, by, bz) inside the grid, or -1.
+__device__ inline int64_t hash_find(const BlockHash& h, int bx, int by, int bz) {
+  const unsigned long long key = block_key(bx, by, bz);
+  uint32_t s = hash_slot(key) & h.mask;
+  for (uint32_t i = 0; i <= h.mask; ++i) {
+    const unsigned long long k = h.keys[s];
+    if (k == key) return h.vals[s];
+    if (k == kEmptyKey) return -1;
+    s = (s + 1u) & h.mask;
+  }
+  return -1;
+}
+
+// Dense slot table (all slots -1, then slot of block i = i) from a compacted level.
+cudaError_t slot_table(const int32_t* coords, int64_t nb, GridDims d, int32_t* slot_to_idx, cudaStream_t s);
+// Capacity of the hash table of a level with nb blocks: a power of two >= 2 nb.
+uint32_t hash_capacity(int64_t nb);
+// Fill keys (all set to kEmptyKey first) and vals from a compacted level.
+cudaError_t build_block_hash(const int32_t* coords, int64_t nb, unsigned long long* keys, int32_t* vals,
+                             uint32_t capacity, cudaStream_t s);
+
 // Occupancy of level-0 blocks from particle positions (fine-cell units, x y z
 // float32); non-finite positions are counted in *bad and ignored.
 cudaError_t occupancy_from_particles(const float* pos, int64_t n, GridDims d0, uint8_t* occ, int* bad, cudaStream_t s);
@@ -47,8 +92,10 @@ cudaError_t compact_slots(const uint8_t* stored, const uint8_t* flags, const uin
                           int64_t* scratch, int64_t* count_dev, cudaStream_t s);
 // Neighbour table [nb][27] from a compacted level (open_mask: bit 2 axis + side
 // marks an open face; neighbours beyond it are kOpen instead of kWall).
+// slot_to_idx null: neighbours found through hash instead.
 cudaError_t neighbour_table(const int32_t* coords, int64_t nb, const int32_t* slot_to_idx, GridDims d,
-                            const int periodic[3], unsigned open_mask, int32_t* nbr, cudaStream_t s);
+                            const int periodic[3], unsigned open_mask, int32_t* nbr, cudaStream_t s,
+                            BlockHash hash = BlockHash{});
 // Interface node lists of one level: nodes with a 26-neighbour in a block that
 // is not stored; those inside H blocks (skip != 0) go to `up` (I^u), the others
 // to `down` (I^d).  Entries are (block << 9) | cell, ascending.

@@ -26,7 +26,10 @@ struct LevelData {
   uint8_t* d_skip = nullptr;       // [nb] 1 = covered by a finer level (left out of reductions) or null
   // hierarchy built on the device (multi-level lattices and rebuilds)
   int32_t* d_coords = nullptr;     // [slots][3] capacity, first nb used
-  int32_t* d_slot = nullptr;       // [slots] slot -> block index or -1
+  int32_t* d_slot = nullptr;       // [slots] slot -> block index or -1 (null with a spatial hash)
+  unsigned long long* d_hkeys = nullptr;  // spatial-hash block table (block lookup mode 1), else null
+  int32_t* d_hvals = nullptr;
+  uint32_t hcap = 0;
   uint8_t* d_H = nullptr;          // [slots] block has stored finer children
   uint8_t* d_stored = nullptr;     // [slots] block is stored
   int64_t n_down = 0, n_up = 0;    // interface node counts (I^d, I^u)
@@ -54,6 +57,7 @@ struct hlbm_lattice {
   double* d_red = nullptr;  // reduction scratch
   size_t red_n = 0;
   bool device_hierarchy = false;  // levels were built by the device rebuild pipeline
+  int block_lookup = 0;           // 0: dense per-level slot tables, 1: spatial hash (hlbm_set_block_lookup)
   double kup[8] = {0}, kdown[8] = {0};  // S^neq factors between level l and l+1
   int* d_status = nullptr;    // device status word of the transfer kernels (0 = ok)
   unsigned long long* d_count = nullptr;  // scratch counter (particles dropped by a deposit)

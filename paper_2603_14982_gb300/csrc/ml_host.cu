@@ -47,6 +47,7 @@ LevelView view_of(const LevelData& L, GridDims d) {
   LevelView v;
   v.d = d;
   v.slot = L.d_slot;
+  v.hash = BlockHash{L.d_hkeys, L.d_hvals, L.hcap ? L.hcap - 1u : 0u};
   v.coords = L.d_coords;
   v.mom = L.d_mom[L.cur];
   v.mom_other = L.d_mom[1 - L.cur];
@@ -272,13 +273,29 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
   ML_CUDA(h, cudaMemcpyAsync(nb.data(), d_tot, L * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   ML_CUDA(h, cudaStreamSynchronize(st));
 
-  // 4. neighbour tables and interface node lists
+  // 4. neighbour tables and interface node lists; with the spatial-hash block
+  // table, each level's hash is built from its list first, the neighbour
+  // table is found through it, and the dense slot table is dropped
   for (int l = 0; l < L && rc == HLBM_OK; ++l) {
     nl[l].nb = nb[l];
     if (nb[l] == 0) continue;
     if ((rc = alloc_t(h, &nl[l].d_nbr, size_t(nb[l]) * 27))) break;
-    cudaError_t e =
-        neighbour_table(nl[l].d_coords, nb[l], nl[l].d_slot, dims_of(h, l), per, h->open_mask(), nl[l].d_nbr, st);
+    const int32_t* slot = nl[l].d_slot;
+    BlockHash hash{};
+    if (h->block_lookup == 1) {
+      nl[l].hcap = hash_capacity(nb[l]);
+      if ((rc = alloc_t(h, &nl[l].d_hkeys, nl[l].hcap))) break;
+      if ((rc = alloc_t(h, &nl[l].d_hvals, nl[l].hcap))) break;
+      cudaError_t e = build_block_hash(nl[l].d_coords, nb[l], nl[l].d_hkeys, nl[l].d_hvals, nl[l].hcap, st);
+      if (e != cudaSuccess) {
+        rc = fail(h, HLBM_E_CUDA, "block hash: %s", cudaGetErrorString(e));
+        break;
+      }
+      hash = BlockHash{nl[l].d_hkeys, nl[l].d_hvals, nl[l].hcap - 1u};
+      slot = nullptr;
+    }
+    cudaError_t e = neighbour_table(nl[l].d_coords, nb[l], slot, dims_of(h, l), per, h->open_mask(), nl[l].d_nbr, st,
+                                    hash);
     if (e != cudaSuccess) rc = fail(h, HLBM_E_CUDA, "neighbour table: %s", cudaGetErrorString(e));
     if (rc == HLBM_OK) rc = LatticeOps::bounce(h, nl[l]);
   }
@@ -392,6 +409,11 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
   for (auto& X : h->lv) LatticeOps::free_level(h, X);
   for (int l = 0; l < L; ++l) {
     nl[l].cur = 0;
+    if (h->block_lookup == 1 && nl[l].d_hkeys != nullptr) {  // the hash replaces the slot table
+      void* v = nl[l].d_slot;
+      LatticeOps::release(h, v);
+      nl[l].d_slot = nullptr;
+    }
     h->lv[l] = nl[l];
   }
   // the level-0 force field refers to the old block list

@@ -123,6 +123,7 @@ __device__ __forceinline__ Node64 zero64() {
 __device__ __forceinline__ int64_t lookup(const LevelView& v, int x, int y, int z) {
   const int bx = x >> 3, by = y >> 3, bz = z >> 3;
   if (bx < 0 || by < 0 || bz < 0 || bx >= v.d.nx || by >= v.d.ny || bz >= v.d.nz) return -1;
+  if (v.hash.keys != nullptr) return hash_find(v.hash, bx, by, bz);
   return v.slot[(int64_t(bz) * v.d.ny + by) * v.d.nx + bx];
 }
 

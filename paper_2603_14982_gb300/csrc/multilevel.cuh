@@ -20,6 +20,7 @@ struct LevelView {
   const void* mom_other;      // the other ping-pong buffer
   int64_t nb;
   const Scales* sc;           // row scales (reduced-precision storage) or null
+  BlockHash hash;             // spatial-hash block table, used instead of slot when set
 };
 
 struct TransferArgs {

@@ -67,6 +67,9 @@ _SIGS = {
     "hlbm_reduce": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "hlbm_forward_record": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "hlbm_inject_alloc_failure": (ctypes.c_int32, [ctypes.c_int64]),
+    "hlbm_set_block_lookup": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "hlbm_get_block_lookup": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                               ctypes.POINTER(ctypes.c_int64)]),
     "hlbm_test_narrow": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "hlbm_set_drag": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_int32]),
@@ -218,6 +221,16 @@ class Lattice:
         n = int(pos.shape[0])
         self._check(self.lib.hlbm_rebuild_from_particles(self.h, p if n else None, n, dev, counts.ctypes.data))
         return tuple(int(v) for v in counts)
+
+    def set_block_lookup(self, mode):
+        """0: dense per-level slot tables (default); 1: spatial hash per level."""
+        self._check(self.lib.hlbm_set_block_lookup(self.h, int(mode)))
+
+    def block_lookup(self):
+        """(mode, device bytes of the lookup tables of all levels)."""
+        mode, nbytes = ctypes.c_int32(), ctypes.c_int64()
+        self._check(self.lib.hlbm_get_block_lookup(self.h, ctypes.byref(mode), ctypes.byref(nbytes)))
+        return mode.value, nbytes.value
 
     def interface_nodes(self, level, which):
         """int32 array of (block << 9) | node of I^d (which=0) or I^u (which=1)."""
