@@ -135,8 +135,12 @@ def job_mlups(nodes, steps, world, seconds):
     return world * nodes * steps / seconds / 1e6
 
 
-def duct_lattice(hl, n, stream):
-    lat = hl.Lattice((n, n, n), tau=0.55, periodic=(True, False, False), storage="f32", stream=stream)
+STORAGE_BYTES = {"f32": BYTES_PER_NODE_F32, "f16s": 40.0, "bf16s": 40.0}
+STORAGE_KERNEL = {"f32": KERNEL, "f16s": "k_stream_collide_f2<__half>", "bf16s": "k_stream_collide_f2<__nv_bfloat16>"}
+
+
+def duct_lattice(hl, n, stream, storage="f32"):
+    lat = hl.Lattice((n, n, n), tau=0.55, periodic=(True, False, False), storage=storage, stream=stream)
     lat.set_dense()
     lat.set_uniform_force(1e-6, 0.0, 0.0)
     return lat
@@ -157,7 +161,7 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.Stream()
     n = args.n
     nodes = n ** 3
-    lat = duct_lattice(hl, n, stream.cuda_stream)
+    lat = duct_lattice(hl, n, stream.cuda_stream, args.storage)
     lat.cfg.device = dev
     # --- device-resident timing
     for _ in range(args.warmup):
@@ -184,7 +188,7 @@ def run_gpu(args, rank, world):
     M0 = hl.dense_to_blocks(wl.rest_field((n, n, n)).astype(np.float32))
     host_in = torch.from_numpy(M0).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    lat = duct_lattice(hl, n, stream.cuda_stream)
+    lat = duct_lattice(hl, n, stream.cuda_stream, args.storage)
     lat.write_moments(host_in.numpy())
     lat.step(2)
     lat.synchronize()
@@ -497,6 +501,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s"],
+                    help="moment storage of the duct (the metric's configuration is f32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the multi-level, adjoint and batched workloads")
@@ -531,8 +537,8 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     config = {"workload": "duct %d^3, periodic x, bounce-back y/z, 8^3 blocks, tau 0.55, F=1e-6" % args.n,
-              "nodes": args.n ** 3, "storage": "f32", "l2": "inputs (2 x %.0f MB) larger than the 129 MB L2"
-              % (args.n ** 3 * 40 / 1e6), "parallelism": "replicas x%d" % world}
+              "nodes": args.n ** 3, "storage": args.storage, "l2": "inputs (2 x %.0f MB) larger than the 129 MB L2"
+              % (args.n ** 3 * STORAGE_BYTES[args.storage] / 2 / 1e6), "parallelism": "replicas x%d" % world}
 
     if args.impl == "reference":
         if rank != 0:
@@ -557,7 +563,11 @@ def main():
             torch.distributed.destroy_process_group()
         return
     peak, peak_kind = measured_peaks()
-    achieved = args.n ** 3 * BYTES_PER_NODE_F32 / (res["ms_per_step"] / 1e3) / 1e9
+    bpn = STORAGE_BYTES[args.storage]
+    achieved = args.n ** 3 * bpn / (res["ms_per_step"] / 1e3) / 1e9
+    # DRAM bytes per node update from the ncu captures of the 192^3 duct (the
+    # FP32 and FP16 kernels; none taken for BF16)
+    traffic = {"f32": TRAFFIC_PER_NODE, "f16s": 253.3e6 / 192 ** 3}.get(args.storage)
     line = {
         "metric": METRIC,
         "value": round(res["value"], 1),
@@ -569,14 +579,14 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": args.storage,
         "data": "synthetic",
         "config": config,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
-                     "traffic": None if TRAFFIC_PER_NODE is None else round(TRAFFIC_PER_NODE * args.n ** 3),
-                     "kernel": KERNEL, "peak_kind": peak_kind,
-                     "bytes_per_node": BYTES_PER_NODE_F32},
+                     "traffic": None if traffic is None else round(traffic * args.n ** 3),
+                     "kernel": STORAGE_KERNEL[args.storage], "peak_kind": peak_kind,
+                     "bytes_per_node": bpn},
         "e2e": {"value": round(res["e2e_value"], 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(res["e2e_bytes"] // args.steps),
                 "d2h_bytes_per_step": int((res["e2e_bytes"] + 56) // args.steps)},
@@ -590,7 +600,7 @@ def main():
             tf = args.n ** 3 * FLOP_PER_NODE / (res["ms_per_step"] / 1e3) / 1e12
             pk = res["extras"].get("fp32_sgemm_tflops")
             line["extras"]["alu_roofline"] = {
-                "kernel": KERNEL, "flop_per_node": FLOP_PER_NODE, "achieved_tflops": round(tf, 2),
+                "kernel": STORAGE_KERNEL[args.storage], "flop_per_node": FLOP_PER_NODE, "achieved_tflops": round(tf, 2),
                 "peak_tflops": pk, "peak_kind": "cuBLAS SGEMM 8192^3, TF32 off, measured in this run",
                 "frac": round(tf / pk, 4) if pk else None}
     if not args.no_cpu_baseline and world == 1:
