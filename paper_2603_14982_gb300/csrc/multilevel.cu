@@ -297,19 +297,23 @@ __global__ void __launch_bounds__(512, 2) k_init_level(OldHierarchy o, int level
   store64<T>(out, b, cell, v, 1.0, out_sc);
 }
 
-inline unsigned blocks_for(int64_t n) { return unsigned((n + 255) / 256); }
+// 64-thread CTAs for the transfers: at 130 to 140 registers a thread (the
+// downward transfer), seven fit on an SM where one 256-thread CTA did, and
+// the last wave of a small launch is finer grained.
+constexpr int kTransferThreads = 64;
+inline unsigned blocks_for(int64_t n) { return unsigned((n + kTransferThreads - 1) / kTransferThreads); }
 
 template <typename T>
 cudaError_t down_typed(const TransferArgs& a, cudaStream_t s) {
   if (a.n_nodes == 0) return cudaSuccess;
-  k_down<T><<<blocks_for(a.n_nodes), 256, 0, s>>>(a);
+  k_down<T><<<blocks_for(a.n_nodes), kTransferThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t up_typed(const TransferArgs& a, cudaStream_t s) {
   if (a.n_nodes == 0) return cudaSuccess;
-  k_up<T><<<blocks_for(a.n_nodes), 256, 0, s>>>(a);
+  k_up<T><<<blocks_for(a.n_nodes), kTransferThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
