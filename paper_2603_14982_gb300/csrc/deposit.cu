@@ -38,6 +38,31 @@ __global__ void k_count_particles(const float* __restrict__ pos, int64_t n, int 
   atomicAdd(cnt + b * kCells + (x & 7) + 8 * (y & 7) + 64 * (z & 7), 1u);
 }
 
+// eps = 1 - eta and the drag F_y = -kappa eta of the first kTableCounts
+// particle counts, evaluated on the host with the formula of k_fields; counts
+// at or above `sat` take entry `sat` (eta has reached eta_max there).
+constexpr int kTableCounts = 64;
+struct FieldTable {
+  float eps[kTableCounts];
+  float fy[kTableCounts];
+  int sat;
+};
+
+// The same fields from the table: no FP64 work on the device (the FP64 rate
+// of GB300 made the formula the kernel's limit), bit-identical results.
+__global__ void k_fields_table(float* eps, float* F, int64_t n_nodes, FieldTable t) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  const unsigned c = reinterpret_cast<const unsigned*>(eps)[i];
+  const int k = c >= unsigned(t.sat) ? t.sat : int(c);
+  eps[i] = t.eps[k];
+  const int64_t b = i / kCells, j = i % kCells;
+  float* Fb = F + b * 3 * kCells + j;
+  Fb[0] = 0.f;
+  Fb[kCells] = t.fy[k];
+  Fb[2 * kCells] = 0.f;
+}
+
 __global__ void k_fields(float* eps, float* F, int64_t n_nodes, double kappa, double eta_max, double per_particle,
                          int moving) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -106,8 +131,26 @@ extern "C" int32_t hlbm_deposit_particles(hlbm_lattice* h, const float* pos_xyz,
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && n_nodes > 0) {
-    k_fields<<<unsigned((n_nodes + 255) / 256), 256, 0, h->stream>>>(h->d_eps, h->d_F, n_nodes, kappa, eta_max,
-                                                                      per_particle, moving ? 1 : 0);
+    // the count at which eta reaches eta_max, if the table covers it
+    int sat = -1;
+    for (int c = 0; c < kTableCounts; ++c)
+      if (per_particle * double(c) >= eta_max) {
+        sat = c;
+        break;
+      }
+    if (sat >= 0) {
+      FieldTable t{};
+      t.sat = sat;
+      for (int c = 0; c <= sat; ++c) {  // the formula of k_fields, in the same FP64 operations
+        const double eta = std::fmin(eta_max, per_particle * double(c));
+        t.eps[c] = float(1.0 - eta);
+        t.fy[c] = moving ? float(-kappa * eta) : 0.f;
+      }
+      k_fields_table<<<unsigned((n_nodes + 255) / 256), 256, 0, h->stream>>>(h->d_eps, h->d_F, n_nodes, t);
+    } else {
+      k_fields<<<unsigned((n_nodes + 255) / 256), 256, 0, h->stream>>>(h->d_eps, h->d_F, n_nodes, kappa, eta_max,
+                                                                        per_particle, moving ? 1 : 0);
+    }
     e = cudaGetLastError();
   }
   unsigned long long out_h = 0;
