@@ -380,7 +380,8 @@ def bench_sparse(hl, wl, stream, n=2048, L=4, coarse_steps=4, lookup=0):
             "block_lookup": "hash" if mode == 1 else "slot tables", "lookup_table_bytes": int(table_bytes)}
 
 
-def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebuild_every=10, drag_every=0):
+def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebuild_every=10, drag_every=0,
+                     profile=False):
     """Three-level lattice over an n^3 fine-equivalent domain driven by a falling
     particle cloud (pos0, device, not modified): rebuild at the first
     coarse-step boundary at least rebuild_every fine steps after the last one,
@@ -401,6 +402,8 @@ def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebui
         lat.rebuild_from_particles(pos)
         lat.deposit_particles(pos)
         torch.cuda.synchronize()
+        if profile:  # stream time per kernel class over the timed loop (CUDA events in the library)
+            lat.set_profiling(True)
         t_reb = 0.0
         updates = 0
         updates0 = 0   # finest-level updates (they also read the force and fluid-fraction fields)
@@ -426,6 +429,10 @@ def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebui
             lat.deposit_particles(pos, moving=bool(k < fine_steps // per - 1), wait=False)
         lat.synchronize()
         t_tot = time.perf_counter() - t0
+        prof = None
+        if profile:
+            prof = {k: {"ms": round(v[0], 3), "spans": v[1]} for k, v in lat.profile().items()}
+            lat.set_profiling(False)
         # deposit cost alone (input preparation, not part of the method)
         t_dep = timed(stream, lambda: [lat.deposit_particles(pos, wait=False) for _ in range(10)]) / 10
         red = lat.reduce()
@@ -441,7 +448,7 @@ def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebui
             "total_s": round(t_tot, 4), "rebuild_s": round(t_reb, 4), "rebuild_ms_each": round(1e3 * t_reb / rebuilds, 3),
             "deposit_ms_each": round(t_dep, 4),
             "blocks_per_level_end": counts, "mass_rel_drift": float(red[0] / n ** 3 - 1.0),
-            "finite": bool(np.isfinite(red[0]))}, moms
+            "finite": bool(np.isfinite(red[0])), **({"profile": prof} if prof is not None else {})}, moms
 
 
 def bench_extras(hl, wl):
@@ -508,6 +515,8 @@ def main():
                     help="skip the multi-level, adjoint and batched workloads")
     ap.add_argument("--only", choices=["multilevel", "adjoint", "batched", "ml_adjoint", "sparse"],
                     help="run one secondary workload alone and print its JSON (profiling runs)")
+    ap.add_argument("--profile", action="store_true",
+                    help="with --only multilevel: stream time per kernel class from the library's CUDA events")
     ap.add_argument("--adj-steps", type=int, default=200)
     ap.add_argument("--adj-ckpt", type=int, default=20)
     args = ap.parse_args()
@@ -529,7 +538,7 @@ def main():
         else:
             pos0 = torch.tensor(wl.particle_cloud(512), device="cuda")
             bench_multilevel(hl, wl, stream, "f32", pos0, fine_steps=48)
-            res = bench_multilevel(hl, wl, stream, "f32", pos0)[0]
+            res = bench_multilevel(hl, wl, stream, "f32", pos0, profile=args.profile)[0]
         print(json.dumps({"only": args.only, "result": res}))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

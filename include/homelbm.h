@@ -133,6 +133,20 @@ int32_t hlbm_set_fine_blocks(hlbm_lattice *h, const int32_t *coords_xyz, int64_t
 int32_t hlbm_rebuild_from_particles(hlbm_lattice *h, const float *pos_xyz, int64_t n, int32_t on_device,
                                     int64_t counts_out[3]);
 
+/* Per-handle profile: with on != 0, the library records CUDA events on the
+   handle's stream around each phase it launches and sums the stream time
+   between them per class: 0 stream-collide of every level (coupled steps
+   included), 1 downward transfers, 2 upward transfers, 3 open-face updates,
+   4 hierarchy rebuilds (whole calls), 5 particle deposits, 6 recordings and
+   adjoints (whole calls; they contain classes 0-2), 7 FP64 reductions.
+   Off by default; turning it off keeps the totals. */
+int32_t hlbm_set_profiling(hlbm_lattice *h, int32_t on);
+
+/* Totals of the profile so far: ms_out[c] (milliseconds of stream time) and
+   count_out[c] (spans) for the 8 classes above, host arrays.  Synchronises
+   the handle's stream.  reset != 0 zeroes the totals after reading. */
+int32_t hlbm_get_profile(hlbm_lattice *h, double ms_out[8], int64_t count_out[8], int32_t reset);
+
 /* Block lookup by position of the rebuilt hierarchies (Sec. 6.1: each
    level's table of active tiles, found through a spatial hash).  mode 0
    (default): a dense slot table per level (int32 per block slot of the

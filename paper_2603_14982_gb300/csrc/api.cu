@@ -84,6 +84,61 @@ bool alloc_failure_injected() {
   return left == 0;
 }
 
+ProfScope::ProfScope(hlbm_lattice* h, int cls) : h_(h), cls_(cls) {
+  if (!h->prof.on) return;
+  if (!h->prof.pool.empty()) {
+    a_ = h->prof.pool.back();
+    h->prof.pool.pop_back();
+  } else if (cudaEventCreate(&a_) != cudaSuccess) {
+    cudaGetLastError();
+    a_ = nullptr;
+    return;
+  }
+  if (cudaEventRecord(a_, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    h->prof.pool.push_back(a_);
+    a_ = nullptr;
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (a_ == nullptr) return;
+  cudaEvent_t b = nullptr;
+  if (!h_->prof.pool.empty()) {
+    b = h_->prof.pool.back();
+    h_->prof.pool.pop_back();
+  } else if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaGetLastError();
+    h_->prof.pool.push_back(a_);
+    return;
+  }
+  if (cudaEventRecord(b, h_->stream) != cudaSuccess) {
+    cudaGetLastError();
+    h_->prof.pool.push_back(a_);
+    h_->prof.pool.push_back(b);
+    return;
+  }
+  h_->prof.pending.push_back(Profile::Span{cls_, a_, b});
+}
+
+int profile_collect(hlbm_lattice* h) {
+  if (h->prof.pending.empty()) return HLBM_OK;
+  HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (const Profile::Span& sp : h->prof.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) {
+      h->prof.ms[sp.cls] += double(ms);
+      ++h->prof.count[sp.cls];
+    } else {
+      cudaGetLastError();
+    }
+    h->prof.pool.push_back(sp.a);
+    h->prof.pool.push_back(sp.b);
+  }
+  h->prof.pending.clear();
+  return HLBM_OK;
+}
+
 int LatticeOps::alloc(hlbm_lattice* h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return HLBM_OK;
@@ -299,6 +354,11 @@ int32_t hlbm_destroy(hlbm_lattice* h) {
   v = h->d_count;
   LatticeOps::release(h, v);
   if (h->stream) cudaStreamSynchronize(h->stream);  // the frees are ordered on the stream
+  for (const Profile::Span& sp : h->prof.pending) {
+    cudaEventDestroy(sp.a);
+    cudaEventDestroy(sp.b);
+  }
+  for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   delete h;
   return HLBM_OK;
 }
@@ -566,13 +626,19 @@ int32_t hlbm_step(hlbm_lattice* h, int32_t n_fine_steps) {
   for (int32_t s = 0; s < n_fine_steps; ++s) {
     a.in = L.d_mom[L.cur];
     a.out = L.d_mom[1 - L.cur];
-    if (exchange_due(h)) {  // coupled step: S, drag exchange, C (Fig. 4)
-      if ((rc = coupled_step(h, a))) return rc;
-      a.F = h->d_F;
-    } else {
-      HLBM_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
+    {
+      ProfScope ps(h, kProfStreamCollide);
+      if (exchange_due(h)) {  // coupled step: S, drag exchange, C (Fig. 4)
+        if ((rc = coupled_step(h, a))) return rc;
+        a.F = h->d_F;
+      } else {
+        HLBM_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
+      }
     }
-    if ((rc = open_faces_step(h, 0, a.in, a.out))) return rc;
+    if (h->open_mask() != 0u) {
+      ProfScope ps(h, kProfOpenFaces);
+      if ((rc = open_faces_step(h, 0, a.in, a.out))) return rc;
+    }
     ++h->l0_steps;
     L.cur = 1 - L.cur;
     if ((rc = LatticeOps::maybe_rescale(h, L, false))) return rc;
@@ -594,6 +660,7 @@ int32_t hlbm_reduce(hlbm_lattice* h, double out[7]) {
   if (!h->have_blocks) return fail(h, HLBM_E_BAD_STATE, "no blocks are stored");
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
+  ProfScope prof_scope(h, kProfReduce);
   int64_t nbmax = 0;
   for (auto& L : h->lv) nbmax = L.nb > nbmax ? L.nb : nbmax;
   const size_t need = size_t(nbmax) * 7 + 2 * 8;
@@ -658,6 +725,7 @@ int32_t hlbm_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every
   if (n_steps <= 0 || ckpt_every <= 0) return fail(h, HLBM_E_INVALID_ARG, "n_steps and ckpt_every must be positive");
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
+  ProfScope prof_scope(h, kProfAdjoint);
   for (void*& c : h->ckpt) LatticeOps::release(h, c);
   h->ckpt.clear();
   h->rec_steps = h->rec_every = 0;
@@ -705,6 +773,7 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
   if (h->rec_gen != h->hier_gen) return fail(h, HLBM_E_BAD_STATE, "the block layout changed after hlbm_forward_record");
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
+  ProfScope prof_scope(h, kProfAdjoint);
   if (h->device_hierarchy) return ml_adjoint(h, dL_dM_dev, dL_dF_dev);
   LevelData& L = h->lv[0];
   const int64_t nb = L.nb;
@@ -799,6 +868,31 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
   seg[0] = nullptr;
   release_all();
   if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
+  return HLBM_OK;
+}
+
+int32_t hlbm_set_profiling(hlbm_lattice* h, int32_t on) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  h->prof.on = on != 0;
+  return HLBM_OK;
+}
+
+int32_t hlbm_get_profile(hlbm_lattice* h, double ms_out[8], int64_t count_out[8], int32_t reset) {
+  if (h == nullptr || ms_out == nullptr || count_out == nullptr)
+    return fail(h, HLBM_E_INVALID_ARG, "NULL argument");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  if ((rc = profile_collect(h))) return rc;
+  for (int c = 0; c < kProfClasses; ++c) {
+    ms_out[c] = h->prof.ms[c];
+    count_out[c] = h->prof.count[c];
+    if (reset) {
+      h->prof.ms[c] = 0.0;
+      h->prof.count[c] = 0;
+    }
+  }
   return HLBM_OK;
 }
 

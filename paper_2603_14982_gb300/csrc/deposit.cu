@@ -92,6 +92,7 @@ extern "C" int32_t hlbm_deposit_particles(hlbm_lattice* h, const float* pos_xyz,
   if (!h->have_blocks) return fail(h, HLBM_E_BAD_STATE, "set blocks before depositing particles");
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
+  ProfScope prof_scope(h, kProfDeposit);
   LevelData& L = h->lv[0];
   if (h->device_hierarchy && L.d_slot == nullptr && L.d_hkeys == nullptr)
     return fail(h, HLBM_E_BAD_STATE, "the finest level has no block table");

@@ -12,6 +12,32 @@ namespace hlbm {
 
 constexpr int kRescaleEvery = 32;  // steps between scale refreshes of FP16/BF16 storage
 
+// Kernel classes of the per-handle profile (hlbm_set_profiling): stream time
+// between CUDA events recorded on the handle's stream around each phase.
+enum ProfClass {
+  kProfStreamCollide = 0,  // stream-collide of every level (coupled steps included)
+  kProfDown,               // downward transfers
+  kProfUp,                 // upward transfers
+  kProfOpenFaces,          // open-face updates
+  kProfRebuild,            // hierarchy rebuilds (whole call)
+  kProfDeposit,            // particle deposits
+  kProfAdjoint,            // recordings and adjoints (whole calls)
+  kProfReduce,             // FP64 reductions
+  kProfClasses
+};
+
+struct Profile {
+  bool on = false;
+  struct Span {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Span> pending;       // recorded, not yet read
+  std::vector<cudaEvent_t> pool;   // events free for reuse
+  double ms[kProfClasses] = {};
+  int64_t count[kProfClasses] = {};
+};
+
 struct LevelData {
   int64_t nb = 0;                  // stored blocks
   std::vector<int32_t> coords;     // host copy [nb][3] (bx, by, bz), ascending slot id
@@ -52,6 +78,7 @@ struct hlbm_lattice {
   float* d_F = nullptr;    // level-0 force [nb0][3][512] or null
   float* d_eps = nullptr;  // level-0 fluid fraction [nb0][512] or null
   bool have_blocks = false;
+  hlbm::Profile prof;
   void* d_stage = nullptr;  // staging for host moment I/O
   size_t stage_bytes = 0;
   double* d_red = nullptr;  // reduction scratch
@@ -93,6 +120,24 @@ struct hlbm_lattice {
     dims[2] = cfg.nz / s;
   }
 };
+
+namespace hlbm {
+// Records one span of class `cls` on h->stream while profiling is on.
+class ProfScope {
+ public:
+  ProfScope(hlbm_lattice* h, int cls);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  hlbm_lattice* h_;
+  int cls_;
+  cudaEvent_t a_ = nullptr;
+};
+// Reads every finished span into the totals (synchronises the stream).
+int profile_collect(hlbm_lattice* h);
+}  // namespace hlbm
 
 namespace hlbm {
 

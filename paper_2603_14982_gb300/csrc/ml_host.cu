@@ -59,6 +59,7 @@ LevelView view_of(const LevelData& L, GridDims d) {
 // Transfers of Algorithm 1 ------------------------------------------------------
 
 int downward(hlbm_lattice* h, int l, int s, bool refresh) {
+  ProfScope prof_scope(h, kProfDown);
   LevelData& F = h->lv[l];
   LevelData& C = h->lv[l + 1];
   if (F.n_down == 0) return HLBM_OK;
@@ -79,6 +80,7 @@ int downward(hlbm_lattice* h, int l, int s, bool refresh) {
 }
 
 int upward(hlbm_lattice* h, int l) {
+  ProfScope prof_scope(h, kProfUp);
   LevelData& F = h->lv[l];
   LevelData& C = h->lv[l + 1];
   if (C.n_up == 0) return HLBM_OK;
@@ -117,12 +119,18 @@ int streaming_collision(hlbm_lattice* h, int l) {
   a.kxyz = h->cfg.xyz_literal ? 13.5 : 27.0;
   a.nb = L.nb;
   a.scales_in = a.scales_out = L.d_scales;
-  if (l == 0 && exchange_due(h)) {  // coupled step: S, drag exchange, C (Fig. 4)
-    ML_TRY(coupled_step(h, a));
-  } else {
-    ML_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
+  {
+    ProfScope prof_scope(h, kProfStreamCollide);
+    if (l == 0 && exchange_due(h)) {  // coupled step: S, drag exchange, C (Fig. 4)
+      ML_TRY(coupled_step(h, a));
+    } else {
+      ML_CUDA(h, launch_stream_collide(h->cfg.storage, a, h->stream));
+    }
   }
-  ML_TRY(open_faces_step(h, l, a.in, a.out));
+  if (h->open_mask() != 0u) {
+    ProfScope prof_scope(h, kProfOpenFaces);
+    ML_TRY(open_faces_step(h, l, a.in, a.out));
+  }
   if (l == 0) ++h->l0_steps;
   L.cur = 1 - L.cur;
   return LatticeOps::maybe_rescale(h, L, false);
@@ -162,6 +170,7 @@ int ml_check_status(hlbm_lattice* h) {
 
 int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_device, const int32_t* blocks,
                int64_t n_blocks, int64_t counts_out[3]) {
+  ProfScope prof_scope(h, kProfRebuild);
   const int L = h->cfg.num_levels;
   cudaStream_t st = h->stream;
   const int per[3] = {h->cfg.periodic[0], h->cfg.periodic[1], h->cfg.periodic[2]};

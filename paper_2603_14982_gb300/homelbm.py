@@ -68,6 +68,9 @@ _SIGS = {
     "hlbm_forward_record": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "hlbm_inject_alloc_failure": (ctypes.c_int32, [ctypes.c_int64]),
     "hlbm_set_block_lookup": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "hlbm_set_profiling": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "hlbm_get_profile": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     "hlbm_get_block_lookup": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                                ctypes.POINTER(ctypes.c_int64)]),
     "hlbm_test_narrow": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
@@ -225,6 +228,18 @@ class Lattice:
     def set_block_lookup(self, mode):
         """0: dense per-level slot tables (default); 1: spatial hash per level."""
         self._check(self.lib.hlbm_set_block_lookup(self.h, int(mode)))
+
+    PROFILE_CLASSES = ("stream_collide", "down", "up", "open_faces", "rebuild", "deposit", "adjoint", "reduce")
+
+    def set_profiling(self, on=True):
+        self._check(self.lib.hlbm_set_profiling(self.h, 1 if on else 0))
+
+    def profile(self, reset=False):
+        """{class: (ms of stream time, spans)} so far (synchronises)."""
+        ms = (ctypes.c_double * 8)()
+        cnt = (ctypes.c_int64 * 8)()
+        self._check(self.lib.hlbm_get_profile(self.h, ms, cnt, 1 if reset else 0))
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(self.PROFILE_CLASSES)}
 
     def block_lookup(self):
         """(mode, device bytes of the lookup tables of all levels)."""
