@@ -18,19 +18,25 @@ namespace f2 {
 constexpr int kThreads = 256;
 constexpr int kHaloPairs = 244;
 
-// Destination-indexed shared population buffer: one padded plane of kPlane
-// floats per direction j (the rest plane is not used, so that the reflection
-// of a face shifts every canonical direction by the same number of planes);
-// node (x, y, z) of the block at pidx(x, y, z).  Rows y = -1, 8 and slabs
-// z = -1, 8 are padding that pushes leaving the block through a y or z face
-// write and nothing reads; pushes leaving through an x face are predicated
-// off.  Every access of a node is at a compile-time offset from one base
-// address, the 32 lanes of a warp touch 32 consecutive words for the own
-// pushes and the gather, and kPZ is odd so that the x-face halo stores (lanes
-// along y and z) meet at most two to a bank.
-constexpr int kPY = 8, kPZ = 81, kPlane = 10 * kPZ;
-constexpr size_t kBufBytes = size_t(27) * kPlane * sizeof(float);
+// Destination-indexed shared population buffer: one padded plane per
+// direction j (the rest plane is not used, so that the reflection of a face
+// shifts every canonical direction by the same number of planes); node
+// (x, y, z) of the block at pidx(x, y, z) of plane j, which starts at
+// j kPlane.  Rows y = -1, 8 and slabs z = -1, 8 are padding that pushes
+// leaving the block through a y or z face write and nothing reads; pushes
+// leaving through an x face are predicated off.  Padding is shared where it
+// can be: row y = 8 of slab z overlaps row y = -1 of slab z + 1 (slab stride
+// kPZ = 73 < 10 rows of 8), and slab z = 8 of plane j overlaps slab z = -1 of
+// plane j + 1 (plane stride 9 slabs), so padding writes may land on each
+// other but never on a node's slot.  This keeps the buffer at 71 KB, which
+// leaves room beside two CTAs' buffers for a 60 KB L1 (the staging of the
+// halo loads).  Every access of a node is at a compile-time offset from one
+// base address, the 32 lanes of a warp touch 32 consecutive words for the
+// own pushes and the gather, and kPZ is odd so that the x-face halo stores
+// (lanes along y and z) meet at most two to a bank.
+constexpr int kPY = 8, kPZ = 73, kPlane = 9 * kPZ;
 __host__ __device__ constexpr int pidx(int x, int y, int z) { return x + kPY * (y + 1) + kPZ * (z + 1); }
+constexpr size_t kBufBytes = size_t(26 * kPlane + pidx(7, 8, 8) + 1) * sizeof(float);
 // plane offset of the mirror image of a canonical direction (component +1 on
 // the face axis) along axis ax: its index is lower by 2, 6 or 18
 __host__ __device__ constexpr int mirror_shift(int ax) { return -2 * (ax == 0 ? 1 : (ax == 1 ? 3 : 9)) * kPlane; }

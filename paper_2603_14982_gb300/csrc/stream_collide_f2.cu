@@ -6,7 +6,8 @@
 // z0 = warp >> 1.  Shared memory holds, per direction j, the pulled population
 // of every node of the block, destination-indexed, in a padded plane: node
 // (x, y, z) at x + 8 (y + 1) + kPZ (z + 1), with rows y = -1, 8 and slabs
-// z = -1, 8 as padding that is written but never read.  Every store of a node
+// z = -1, 8 as padding that is written but never read (and shared between
+// neighbouring rows, slabs and planes).  Every store of a node
 // is then at a compile-time offset from one base address per node, and the
 // 32 lanes of a warp touch 32 consecutive words (no bank conflicts for the
 // own pushes and the gather).  Each (destination, direction) slot has exactly
