@@ -55,7 +55,12 @@ typedef enum {
 
 typedef enum {
   /* S^neq of the stored post-collision moments scales with (tau-1) times the
-     lattice velocity gradient: k_up = 2 (tau_c-1)/(tau_f-1), k_down = 1/k_up. */
+     lattice velocity gradient: k_up = 2 (tau_c-1)/(tau_f-1), k_down = 1/k_up.
+     The factor changes sign where the levels' tau lie on both sides of 1 and
+     grows without bound as a level's tau approaches 1: hlbm_create refuses
+     (HLBM_E_INVALID_ARG) a tau_finest whose factors leave [1/100, 100] in
+     magnitude for FP32, FP16 and BF16 storage ([1e-6, 1e6] for FP64), since
+     the transfers multiply the rounding of the stored S by |k|. */
   HLBM_RESCALE_POST = 0,
   /* Chapman-Enskog scaling of the pre-collision S^neq: k_up = 2 tau_c/tau_f. */
   HLBM_RESCALE_PRE = 1,
@@ -115,6 +120,32 @@ int32_t hlbm_set_dense(hlbm_lattice *h);
    coordinates (bx, by, bz) of level 0.  On the first call every stored node is
    at rest; later calls carry the moments over like a rebuild. */
 int32_t hlbm_set_fine_blocks(hlbm_lattice *h, const int32_t *coords_xyz, int64_t n);
+
+/* Set the block hierarchy explicitly, one level per call (Sec. 5.1 and 6.1:
+   each level stores its leaf and border blocks; Sec. 5.3: neighbouring
+   levels overlap and levels two apart are separated).  coords_xyz: host
+   int32 [n][3] block coordinates (bx, by, bz) of the blocks stored at
+   `level` (block edge 8 << level fine nodes), copied; any order.  The call
+   that stages the last level not yet staged since the previous explicit
+   hierarchy validates all levels and installs them like a rebuild: block
+   lists in ascending slot order, flags against the previous hierarchy,
+   neighbour tables and interface nodes, moments carried over (every node at
+   rest on the first hierarchy).  With H_l the level-l blocks whose children
+   are stored or internal and I_l the blocks of H_l whose 26 in-domain
+   neighbours are all in H_l, the hierarchy must satisfy, else
+   HLBM_E_INVALID_ARG (message names the first failing block), the staged
+   lists are dropped and the lattice keeps its previous state:
+   - every coordinate inside the level's block grid, no block listed twice;
+   - no stored block is internal (in I_l);
+   - every stored block below the top has a parent that is stored or internal;
+   - every child of a block in H_{l+1} is stored or internal, and the top
+     level stores every block that is not internal;
+   - overlap and separation: H_l is a union of 3x3x3-block cubes (H_l equals
+     the one-block dilation of I_l), so every refined region keeps one coarse
+     block of overlap;
+   - 2:1 grading: H_{l+1} contains the one-block dilation of parent(H_l).
+   Every hierarchy hlbm_rebuild_from_particles builds passes.  Synchronous. */
+int32_t hlbm_set_blocks(hlbm_lattice *h, int32_t level, const int32_t *coords_xyz, int64_t n);
 
 /* Rebuild the block hierarchy from a particle cloud (Sec. 6.3): occupancy of
    level-0 blocks (Phi), the has-children sets H_l (one-block dilation of the

@@ -19,6 +19,8 @@ Modules (each function cites the passage of the paper it follows):
                    rescaling (Sec. 5.2, Eq. upload_S, Eq. downward_rescale).
 * ``coupling``     the coupled finest-level step of Fig. 4 (streaming only,
                    drag exchange, collision; Sec. 5.4).
+* ``deposit``      solid fraction, fluid fraction and drag force per finest
+                   node from particle counts (Sec. 4, Sec. 5.4).
 * ``adjoint``      reverse-mode gradients of the single-level step and of the
                    multi-level advance (no counterpart in the paper).
 

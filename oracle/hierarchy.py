@@ -107,16 +107,21 @@ def occupancy(pos, extent_xyz, B):
 
 
 class Hierarchy:
-    """Block sets of every level for one occupancy O_0."""
+    """Block sets of every level for one occupancy O_0 (or, through ``from_H``,
+    for given has-children sets H_l)."""
 
-    def __init__(self, O0, extent_xyz, B, L, periodic):
+    def __init__(self, O0, extent_xyz, B, L, periodic, H=None):
         self.extent, self.B, self.L, self.periodic = tuple(extent_xyz), B, L, tuple(periodic)
         self.dims = [block_dims(extent_xyz, B, l) for l in range(L)]
-        H = [np.zeros(self.dims[0], dtype=bool)]
-        if L > 1:
-            H.append(dilate(parent(O0), periodic))
-            for l in range(2, L):
-                H.append(dilate(parent(H[l - 1]), periodic))
+        if H is None:
+            H = [np.zeros(self.dims[0], dtype=bool)]
+            if L > 1:
+                H.append(dilate(parent(O0), periodic))
+                for l in range(2, L):
+                    H.append(dilate(parent(H[l - 1]), periodic))
+        else:
+            H = [np.asarray(g, dtype=bool) for g in H]
+            O0 = np.zeros(self.dims[0], dtype=bool)
         I = [np.zeros(self.dims[0], dtype=bool)] + [internal(H[l], periodic) for l in range(1, L)]
         stored = []
         for l in range(L):
@@ -131,6 +136,13 @@ class Hierarchy:
                 b |= stored[l] & children(stored[l + 1])
             border.append(b)
         self.O0, self.H, self.I, self.stored, self.border = O0, H, I, stored, border
+
+    @classmethod
+    def from_H(cls, H, extent_xyz, B, L, periodic):
+        """The hierarchy of given has-children sets H[l] (H[0] empty): a level
+        can be refined in regions no finer level needs (a level-selection
+        function Phi that takes intermediate levels, Sec. 5.4)."""
+        return cls(None, extent_xyz, B, L, periodic, H=H)
 
     # ---- block lists in ascending linear slot id z*(nby*nbx) + y*nbx + x
     def blocks(self, l):

@@ -307,16 +307,26 @@ int32_t hlbm_create(const hlbm_config* cfg, hlbm_lattice** out) {
     h->lv[l].tau = tau;
     tau = tau / 2.0 + 0.25;  // Sec. 5.2 with k = 1
   }
+  // Largest |k_up| or |k_down| accepted.  The transfers multiply the S^neq
+  // of a node (S - u u, formed from the stored S) by k, so the rounding of the
+  // stored S (about 6e-8 of |S| in FP32) grows by |k|; 100 keeps it below the
+  // 1e-5 per-step tolerance of the FP32 path.  FP64 storage rounds at 1.1e-16
+  // and accepts 1e6.  The post-collision factor 2 (tau_c - 1)/(tau_f - 1)
+  // reaches these bounds where a level's tau is close to 1.
+  const double kmax = cfg->storage == HLBM_STORE_F64 ? 1e6 : 100.0;
   for (int l = 0; l + 1 < cfg->num_levels; ++l) {
     const double tf = h->lv[l].tau, tc = h->lv[l + 1].tau;
     if (cfg->rescale_mode == HLBM_RESCALE_POST) {
-      if (std::fabs(tf - 1.0) < 1e-9 || std::fabs(tc - 1.0) < 1e-9) {
+      const double ku = std::fabs(tf - 1.0) > 0.0 ? 2.0 * (tc - 1.0) / (tf - 1.0) : HUGE_VAL;
+      if (!(std::fabs(ku) <= kmax && std::fabs(ku) >= 1.0 / kmax)) {
         delete h;
         return fail(nullptr, HLBM_E_INVALID_ARG,
-                    "post-collision rescaling needs tau != 1 on every level (tau_%d = %g, tau_%d = %g)", l, tf, l + 1,
-                    tc);
+                    "post-collision rescaling between levels %d and %d (tau %g and %g) needs factors within "
+                    "[1/%g, %g] in magnitude, got k_up = %g: move tau_finest away from the value that puts a "
+                    "level's tau near 1",
+                    l, l + 1, tf, tc, kmax, kmax, ku);
       }
-      h->kup[l] = 2.0 * (tc - 1.0) / (tf - 1.0);
+      h->kup[l] = ku;
       h->kdown[l] = 1.0 / h->kup[l];
     } else if (cfg->rescale_mode == HLBM_RESCALE_PRE) {
       h->kup[l] = 2.0 * tc / tf;
@@ -1003,6 +1013,15 @@ int32_t hlbm_set_fine_blocks(hlbm_lattice* h, const int32_t* coords_xyz, int64_t
         return fail(h, HLBM_E_INVALID_ARG, "block %lld coordinate %d = %d outside [0, %d)", (long long)i, a,
                     coords_xyz[3 * i + a], dims[a]);
   return ml_rebuild(h, nullptr, 0, 0, coords_xyz, n, nullptr);
+}
+
+int32_t hlbm_set_blocks(hlbm_lattice* h, int32_t level, const int32_t* coords_xyz, int64_t n) {
+  if (h == nullptr) return fail(nullptr, HLBM_E_INVALID_ARG, "handle is NULL");
+  if (level < 0 || level >= h->cfg.num_levels) return fail(h, HLBM_E_INVALID_ARG, "level %d out of range", level);
+  if (n < 0 || (n > 0 && coords_xyz == nullptr)) return fail(h, HLBM_E_INVALID_ARG, "bad block list");
+  int rc = LatticeOps::set_device(h);
+  if (rc) return rc;
+  return ml_set_blocks(h, level, coords_xyz, n);
 }
 
 int32_t hlbm_rebuild_from_particles(hlbm_lattice* h, const float* pos_xyz, int64_t n, int32_t on_device,

@@ -111,6 +111,10 @@ struct hlbm_lattice {
     return m;
   }
   int64_t rec_gen = -1;  // hier_gen of the recorded run
+  // hlbm_set_blocks: block lists of the levels staged since the last
+  // installed explicit hierarchy ([level] -> coordinates; staged[level] set)
+  std::vector<std::vector<int32_t>> staged_blocks;
+  std::vector<uint8_t> staged;
   std::string err;
 
   void block_dims(int level, int dims[3]) const {
@@ -149,8 +153,15 @@ int fail(hlbm_lattice* h, int code, const char* fmt, ...);
 bool alloc_failure_injected();
 
 // Multi-level engine (ml_host.cu).
+// H_given: per level, the has-children set on the dense slot grid (level 0
+// all zero); when set, the occupancy inputs are ignored and the hierarchy
+// follows from these sets.
 int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_device, const int32_t* blocks,
-               int64_t n_blocks, int64_t counts_out[3]);
+               int64_t n_blocks, int64_t counts_out[3],
+               const std::vector<std::vector<uint8_t>>* H_given = nullptr);
+// Stage the explicit block list of one level (hlbm_set_blocks); installs the
+// hierarchy once every level is staged.
+int ml_set_blocks(hlbm_lattice* h, int level, const int32_t* coords_xyz, int64_t n);
 int ml_advance_coarse(hlbm_lattice* h, int64_t n_coarse);
 int ml_check_status(hlbm_lattice* h);
 // Reverse mode of the multi-level advance, FP32 storage (adjoint_ml.cu):

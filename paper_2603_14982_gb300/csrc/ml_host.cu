@@ -169,7 +169,7 @@ int ml_check_status(hlbm_lattice* h) {
 // Rebuild ---------------------------------------------------------------------
 
 int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_device, const int32_t* blocks,
-               int64_t n_blocks, int64_t counts_out[3]) {
+               int64_t n_blocks, int64_t counts_out[3], const std::vector<std::vector<uint8_t>>* H_given) {
   ProfScope prof_scope(h, kProfRebuild);
   const int L = h->cfg.num_levels;
   cudaStream_t st = h->stream;
@@ -190,7 +190,9 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     for (void*& p : tmp) LatticeOps::release(h, p);
   };
   ML_CUDA(h, cudaMemsetAsync(d_bad, 0, sizeof(int), st));
-  if (blocks != nullptr) {
+  if (H_given != nullptr) {
+    // explicit hierarchy: the has-children sets come from the caller
+  } else if (blocks != nullptr) {
     int32_t* d_b = nullptr;
     if (n_blocks > 0) {
       if (int rc0 = alloc_t(h, &d_b, size_t(n_blocks) * 3)) {
@@ -239,8 +241,14 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     return rc;
   }
   ML_CUDA(h, cudaMemsetAsync(nl[0].d_H, 0, size_t(d0.slots()), st));
-  for (int l = 1; l < L; ++l)
-    ML_CUDA(h, dilate_parent(l == 1 ? d_occ : nl[l - 1].d_H, dims_of(h, l - 1), nl[l].d_H, dims_of(h, l), per, st));
+  for (int l = 1; l < L; ++l) {
+    if (H_given != nullptr)
+      ML_CUDA(h, cudaMemcpyAsync(nl[l].d_H, (*H_given)[l].data(), size_t(dims_of(h, l).slots()),
+                                 cudaMemcpyHostToDevice, st));
+    else
+      ML_CUDA(h,
+              dilate_parent(l == 1 ? d_occ : nl[l - 1].d_H, dims_of(h, l - 1), nl[l].d_H, dims_of(h, l), per, st));
+  }
   for (int l = 0; l < L; ++l)
     ML_CUDA(h, internal_stored(nl[l].d_H, l < L - 1 ? nl[l + 1].d_H : nullptr, dims_of(h, l),
                                l < L - 1 ? dims_of(h, l + 1) : dims_of(h, l), per, l >= 1, d_I[l], nl[l].d_stored,
@@ -443,6 +451,171 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
   ML_TRY(ml_check_status(h));
   if (bad) return fail(h, HLBM_E_NONFINITE, "%d particle positions are not finite (ignored)", bad);
   return HLBM_OK;
+}
+
+// Explicit hierarchies (hlbm_set_blocks) -----------------------------------------
+
+namespace {
+
+// A dense per-level block grid on the host, indexed like the slot tables.
+struct HostGrid {
+  GridDims d;
+  std::vector<uint8_t> v;
+  explicit HostGrid(GridDims dd) : d(dd), v(size_t(dd.slots()), 0) {}
+  uint8_t& at(int x, int y, int z) { return v[(size_t(z) * d.ny + y) * d.nx + x]; }
+  uint8_t at(int x, int y, int z) const { return v[(size_t(z) * d.ny + y) * d.nx + x]; }
+};
+
+// Value of G at (x+dx, y+dy, z+dz): wrapped on periodic axes, `fill` beyond a wall.
+uint8_t nbr_of(const HostGrid& G, int x, int y, int z, int dx, int dy, int dz, const int per[3], uint8_t fill) {
+  int c[3] = {x + dx, y + dy, z + dz};
+  const int n[3] = {G.d.nx, G.d.ny, G.d.nz};
+  for (int a = 0; a < 3; ++a) {
+    if (c[a] >= 0 && c[a] < n[a]) continue;
+    if (!per[a]) return fill;
+    c[a] = (c[a] % n[a] + n[a]) % n[a];
+  }
+  return G.at(c[0], c[1], c[2]);
+}
+
+// One-block dilation in the 26-neighbourhood (clipped at walls) or erosion
+// (a block whose every in-domain neighbour is set: the internal blocks).
+HostGrid morph(const HostGrid& G, const int per[3], bool erode) {
+  HostGrid out(G.d);
+  for (int z = 0; z < G.d.nz; ++z)
+    for (int y = 0; y < G.d.ny; ++y)
+      for (int x = 0; x < G.d.nx; ++x) {
+        uint8_t r = G.at(x, y, z);
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const uint8_t q = nbr_of(G, x, y, z, dx, dy, dz, per, erode ? 1 : 0);
+              r = erode ? uint8_t(r & q) : uint8_t(r | q);
+            }
+        out.at(x, y, z) = r;
+      }
+  return out;
+}
+
+// Level-(l+1) grid: a block is set if any of its 2x2x2 children is set.
+HostGrid parent_of(const HostGrid& G, GridDims du) {
+  HostGrid out(du);
+  for (int z = 0; z < G.d.nz; ++z)
+    for (int y = 0; y < G.d.ny; ++y)
+      for (int x = 0; x < G.d.nx; ++x)
+        if (G.at(x, y, z)) out.at(x >> 1, y >> 1, z >> 1) = 1;
+  return out;
+}
+
+}  // namespace
+
+int ml_set_blocks(hlbm_lattice* h, int level, const int32_t* coords, int64_t n) {
+  const int L = h->cfg.num_levels;
+  if (int(h->staged.size()) != L) {
+    h->staged.assign(size_t(L), 0);
+    h->staged_blocks.assign(size_t(L), {});
+  }
+  const GridDims d = dims_of(h, level);
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t* c = coords + 3 * i;
+    if (c[0] < 0 || c[0] >= d.nx || c[1] < 0 || c[1] >= d.ny || c[2] < 0 || c[2] >= d.nz)
+      return fail(h, HLBM_E_INVALID_ARG, "level %d block %lld (%d, %d, %d) is outside the %d x %d x %d block grid",
+                  level, (long long)i, c[0], c[1], c[2], d.nx, d.ny, d.nz);
+  }
+  h->staged_blocks[size_t(level)].assign(coords, coords + 3 * n);
+  h->staged[size_t(level)] = 1;
+  for (int l = 0; l < L; ++l)
+    if (!h->staged[size_t(l)]) return HLBM_OK;  // wait for the other levels
+
+  // every level staged: validate and install.  The staged lists are consumed
+  // either way.
+  std::vector<std::vector<int32_t>> lists;
+  lists.swap(h->staged_blocks);
+  h->staged.assign(size_t(L), 0);
+  h->staged_blocks.assign(size_t(L), {});
+  const int per[3] = {h->cfg.periodic[0], h->cfg.periodic[1], h->cfg.periodic[2]};
+  std::vector<HostGrid> S, H, I;
+  for (int l = 0; l < L; ++l) {
+    S.emplace_back(dims_of(h, l));
+    const std::vector<int32_t>& c = lists[size_t(l)];
+    for (size_t i = 0; i < c.size() / 3; ++i) {
+      uint8_t& cell = S[size_t(l)].at(c[3 * i], c[3 * i + 1], c[3 * i + 2]);
+      if (cell)
+        return fail(h, HLBM_E_INVALID_ARG, "level %d block (%d, %d, %d) is listed twice", l, c[3 * i],
+                    c[3 * i + 1], c[3 * i + 2]);
+      cell = 1;
+    }
+  }
+  // bottom-up: H_l = blocks with stored or internal children, I_l = H_l blocks
+  // whose every in-domain neighbour is in H_l (covered, not stored)
+  H.emplace_back(dims_of(h, 0));
+  I.emplace_back(dims_of(h, 0));
+  for (int l = 1; l < L; ++l) {
+    HostGrid R = S[size_t(l - 1)];
+    for (size_t q = 0; q < R.v.size(); ++q) R.v[q] |= I[size_t(l - 1)].v[q];
+    H.push_back(parent_of(R, dims_of(h, l)));
+    I.push_back(morph(H.back(), per, true));
+    for (size_t q = 0; q < H.back().v.size(); ++q) I.back().v[q] &= H.back().v[q];
+  }
+  for (int l = 0; l < L; ++l) {
+    const GridDims dl = dims_of(h, l);
+    for (int z = 0; z < dl.nz; ++z)
+      for (int y = 0; y < dl.ny; ++y)
+        for (int x = 0; x < dl.nx; ++x) {
+          const bool st = S[size_t(l)].at(x, y, z) != 0, in = I[size_t(l)].at(x, y, z) != 0;
+          if (st && in)
+            return fail(h, HLBM_E_INVALID_ARG,
+                        "level %d block (%d, %d, %d) is stored but internal: it and its 26 neighbours all have "
+                        "finer children (Sec. 6.1 stores leaf and border blocks only)",
+                        l, x, y, z);
+          if (l + 1 < L) {
+            const bool pst = S[size_t(l + 1)].at(x >> 1, y >> 1, z >> 1) != 0;
+            const bool pin = I[size_t(l + 1)].at(x >> 1, y >> 1, z >> 1) != 0;
+            const bool refined = H[size_t(l + 1)].at(x >> 1, y >> 1, z >> 1) != 0;
+            if (st && !pst && !pin)
+              return fail(h, HLBM_E_INVALID_ARG,
+                          "level %d block (%d, %d, %d) has a parent that is neither stored nor internal at level %d",
+                          l, x, y, z, l + 1);
+            if (refined && !in && !st)
+              return fail(h, HLBM_E_INVALID_ARG,
+                          "level %d block (%d, %d, %d) is missing: its parent at level %d has other children, so "
+                          "all 8 must be stored or internal",
+                          l, x, y, z, l + 1);
+          } else if (!st && !in) {
+            return fail(h, HLBM_E_INVALID_ARG,
+                        "top level %d block (%d, %d, %d) is missing: the top level covers every block that is not "
+                        "internal",
+                        l, x, y, z);
+          }
+        }
+  }
+  // overlap and separation: every refined set is a union of 3x3x3-block
+  // cubes (each refined block lies within one block of a block whose whole
+  // neighbourhood is refined), so a finer region keeps one coarse block of
+  // overlap with the coarser level; and a region refined at level l - 1 is
+  // surrounded by one level-(l+1) block of level-l blocks (2:1 grading: two
+  // levels apart never touch)
+  for (int l = 1; l < L; ++l) {
+    const HostGrid open = morph(I[size_t(l)], per, false);
+    for (size_t q = 0; q < open.v.size(); ++q)
+      if (open.v[q] != H[size_t(l)].v[q])
+        return fail(h, HLBM_E_INVALID_ARG,
+                    "level %d: the region refined below level %d is not a union of 3x3x3-block cubes at slot %lld "
+                    "(the finer level needs one level-%d block of overlap around it)",
+                    l - 1, l, (long long)q, l);
+    if (l + 1 < L) {
+      const HostGrid need = morph(parent_of(H[size_t(l)], dims_of(h, l + 1)), per, false);
+      for (size_t q = 0; q < need.v.size(); ++q)
+        if (need.v[q] && !H[size_t(l + 1)].v[q])
+          return fail(h, HLBM_E_INVALID_ARG,
+                      "level %d slot %lld: a block next to the level-%d region is not refined (2:1 grading needs "
+                      "one level-%d block of level-%d cells around every level-%d region)",
+                      l + 1, (long long)q, l - 1, l + 1, l, l - 1);
+    }
+  }
+  std::vector<std::vector<uint8_t>> Hv(static_cast<size_t>(L));
+  for (int l = 0; l < L; ++l) Hv[size_t(l)] = H[size_t(l)].v;
+  return ml_rebuild(h, nullptr, 0, 0, nullptr, 0, nullptr, &Hv);
 }
 
 }  // namespace hlbm

@@ -48,6 +48,7 @@ _SIGS = {
     "hlbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hlbm_set_dense": (ctypes.c_int32, [ctypes.c_void_p]),
     "hlbm_set_fine_blocks": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "hlbm_set_blocks": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64]),
     "hlbm_rebuild_from_particles": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                      ctypes.c_int32, ctypes.c_void_p]),
     "hlbm_get_interface_nodes": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
@@ -214,6 +215,12 @@ class Lattice:
         """coords: int32 (n, 3) level-0 block coordinates (bx, by, bz) where Phi = 0."""
         c = np.ascontiguousarray(np.asarray(coords, dtype=np.int32).reshape(-1, 3))
         self._check(self.lib.hlbm_set_fine_blocks(self.h, c.ctypes.data if len(c) else None, len(c)))
+
+    def set_blocks(self, level, coords):
+        """coords: int32 (n, 3) block coordinates (bx, by, bz) stored at `level`;
+        the call that completes every level installs the hierarchy."""
+        c = np.ascontiguousarray(np.asarray(coords, dtype=np.int32).reshape(-1, 3))
+        self._check(self.lib.hlbm_set_blocks(self.h, int(level), c.ctypes.data if len(c) else None, len(c)))
 
     def rebuild_from_particles(self, pos):
         """pos: float32 (n, 3) numpy (host) or torch CUDA tensor; returns (refined, coarsened, deleted)."""

@@ -115,27 +115,6 @@ def fall(pos, steps, floor=0.5):
     return out
 
 
-def cloud_force_fields(pos, shape_fine, kappa=1e-4, eta_max=0.4, per_particle=0.25, moving=True):
-    """Per-cell solid fraction eta, fluid fraction eps = 1 - eta and drag force.
-
-    eta(x) = min(eta_max, per_particle * count(x)) with nearest-cell counts,
-    F = (0, -kappa*eta, 0) while the particles move, 0 once they rest.
-    Returns (F[3, nz, ny, nx], eps[nz, ny, nx]) as float64.
-    """
-    nz, ny, nx = shape_fine
-    ijk = np.floor(pos.astype(np.float64)).astype(np.int64)
-    ijk[:, 0] = np.clip(ijk[:, 0], 0, nx - 1)
-    ijk[:, 1] = np.clip(ijk[:, 1], 0, ny - 1)
-    ijk[:, 2] = np.clip(ijk[:, 2], 0, nz - 1)
-    cnt = np.zeros((nz, ny, nx))
-    np.add.at(cnt, (ijk[:, 2], ijk[:, 1], ijk[:, 0]), 1.0)
-    eta = np.minimum(eta_max, per_particle * cnt)
-    F = np.zeros((3, nz, ny, nx))
-    if moving:
-        F[1] = -kappa * eta
-    return F, 1.0 - eta
-
-
 # --- gradient workload: channel with a central obstacle ---
 
 def obstacle_mask(n, lo=None, hi=None):

@@ -30,7 +30,7 @@ def declared_symbols():
 def test_header_declares_the_boundary():
     names = declared_symbols()
     for must in ("hlbm_create", "hlbm_set_dense", "hlbm_set_force", "hlbm_step", "hlbm_read_moments",
-                 "hlbm_write_moments", "hlbm_reduce", "hlbm_destroy", "hlbm_get_blocks"):
+                 "hlbm_write_moments", "hlbm_reduce", "hlbm_destroy", "hlbm_get_blocks", "hlbm_set_blocks"):
         assert must in names
 
 
@@ -51,6 +51,8 @@ def test_version_and_null_handling(lib):
     (dict(extent=(20, 16, 16)), hl.E_INVALID_ARG),          # not a multiple of 8
     (dict(extent=(16, 16, 16), tau=0.5), hl.E_INVALID_ARG),  # tau must exceed 1/2
     (dict(extent=(16, 16, 16), storage=9), hl.E_INVALID_ARG),
+    # post-collision rescale factor k_up = -249 between the two levels (|k| > 100 outside FP64)
+    (dict(extent=(16, 128, 16), levels=2, tau=1.002, storage="f32"), hl.E_INVALID_ARG),
 ])
 def test_create_rejects_bad_config(lib, kw, code):
     with pytest.raises(hl.HlbmError) as ei:

@@ -1,14 +1,15 @@
-"""Particle deposit (hlbm_deposit_particles) against the seeded input generator.
+"""Particle deposit (hlbm_deposit_particles) against the oracle's deposit.
 
-The GPU fields must equal workloads.cloud_force_fields (FP64 rounded once to
+The GPU fields must equal oracle.deposit.fields (FP64 rounded once to
 float32) exactly.  There is no getter for the fields, so each case steps the
-lattice once with the deposited fields and once with the generator's fields
+lattice once with the deposited fields and once with the oracle's fields
 passed through hlbm_set_force: the two results must be bit-identical.
 """
 import numpy as np
 import pytest
 import torch
 
+from oracle import deposit as dp
 from paper_2603_14982_gb300 import homelbm as hl
 from paper_2603_14982_gb300 import workloads as wl
 
@@ -21,7 +22,7 @@ def set_fields(lat, F, eps):
 
 
 @pytest.mark.parametrize("moving", [True, False])
-def test_single_level_deposit_matches_generator(moving):
+def test_single_level_deposit_matches_oracle(moving):
     ext = (32, 24, 16)
     shape = (16, 24, 32)
     g = np.random.default_rng(11)
@@ -31,7 +32,7 @@ def test_single_level_deposit_matches_generator(moving):
     pos[10:500] = np.array([5.5, 6.5, 7.5], dtype=np.float32)   # eta saturates at 0.4
     M0b = hl.dense_to_blocks(wl.random_field(shape, 12, du=0.02))
     ok = np.isfinite(pos).all(axis=1)
-    F, eps = wl.cloud_force_fields(pos[ok], shape, moving=moving)
+    F, eps = dp.fields(pos[ok], shape, moving=moving)
     with hl.Lattice(ext, tau=0.9, periodic=(True, False, True)) as lat:
         lat.set_dense()
         lat.write_moments(M0b)
@@ -68,7 +69,7 @@ def test_three_level_deposit_on_rebuilt_hierarchy():
             lat.step(4)
             return [lat.read_moments(level=l) for l in range(3)], dropped
         got, dropped = run(pos=torch.tensor(pos, device="cuda"))
-        F, eps = wl.cloud_force_fields(pos, (128, 128, 128))
+        F, eps = dp.fields(pos, (128, 128, 128))
         ref, _ = run(fields=(hl.dense_to_blocks(F, coords), hl.dense_to_blocks(eps[None], coords)[:, 0]))
     assert dropped == 0   # every particle sits in a stored finest-level block
     assert n[0] > 0

@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import deposit as dp
 from oracle import hierarchy as hy
 from oracle import multilevel as ml
 from paper_2603_14982_gb300 import homelbm as hl
@@ -133,17 +134,30 @@ def shear(A, n):
     return fn
 
 
+@pytest.mark.parametrize("tau0", [0.8, 1.2, 1.45])
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-11), ("f32", 2e-5)])
-def test_two_level_shear_wave_matches_oracle(storage, tol):
+def test_two_level_shear_wave_matches_oracle(storage, tol, tau0):
+    """tau0 = 1.2 and 1.45 put the levels on both sides of tau = 1 (negative
+    post-collision factors, k_down = -0.67 and -9)."""
     ext = (16, 128, 16)
     O0 = np.zeros(hy.block_dims(ext, 8, 0), bool)
     O0[:, 7:9, :] = True
-    h, m, lat = _setup(ext, 2, O0, (True, True, True), 0.8, shear(0.01, 128), storage)
+    h, m, lat = _setup(ext, 2, O0, (True, True, True), tau0, shear(0.01, 128), storage)
     with lat:
         for k in range(3):
             m.coarse_step()
             lat.step(2)
             _compare(lat, m, tol * (k + 1), 0.01)
+
+
+def test_post_rescale_factor_bound():
+    """tau0 = 1.002 gives k_up = -249 between levels 0 and 1: refused for FP32
+    storage (|k| > 100), accepted for FP64; tau0 = 1.01 (k_up = -49) is accepted."""
+    with pytest.raises(hl.HlbmError) as e:
+        hl.Lattice((16, 128, 16), levels=2, tau=1.002, storage="f32")
+    assert e.value.code == hl.E_INVALID_ARG
+    hl.Lattice((16, 128, 16), levels=2, tau=1.002, storage="f64").close()
+    hl.Lattice((16, 128, 16), levels=2, tau=1.01, storage="f32").close()
 
 
 def test_three_level_matches_oracle_fp64():
@@ -240,7 +254,7 @@ def cloud128_oracle():
     ext = (128, 128, 128)
     per = (True, False, True)
     pos = wl.particle_cloud(128, count=2_000_000 // 64)
-    F, eps = wl.cloud_force_fields(pos, (128, 128, 128))
+    F, eps = dp.fields(pos, (128, 128, 128))
     h = hy.from_particles(pos, ext, 8, 3, per)
     m = ml.MultiLevel(h, 0.9, force=torch.tensor(F.astype(np.float32).astype(np.float64)),
                       eps=torch.tensor(eps.astype(np.float32).astype(np.float64)))
