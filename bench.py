@@ -37,12 +37,12 @@ KERNEL = "k_stream_collide_f2<float>"
 # DRAM bytes (read + write) per launch of KERNEL from one ncu capture of the
 # 192^3 duct, scaled by nodes to 256^3 (profiles/stream_collide_f2_duct192.md);
 # set to None whenever the kernel changes after that capture.
-TRAFFIC_PER_NODE = 531.9e6 / 192 ** 3
+TRAFFIC_PER_NODE = (289.213696e6 + 242.401536e6) / 192 ** 3
 # FP32 operations per node update of KERNEL (ncu thread-level counts of FADD,
 # FMUL, FFMA and their packed forms on the 192^3 duct, profiles/
 # stream_collide_f2_duct192.md; FMA = 2); None when not measured for the
 # current kernel.
-FLOP_PER_NODE = 544.9
+FLOP_PER_NODE = 531.3
 
 
 def measured_peaks():
@@ -451,10 +451,29 @@ def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebui
             "finite": bool(np.isfinite(red[0])), **({"profile": prof} if prof is not None else {})}, moms
 
 
+def bench_duct_storage(hl, stream, storage, n=256, steps=100, warmup=10):
+    """The same duct in another moment storage: device time per step, MLUPS and
+    the algorithmic bytes (40 per node in FP16/BF16-scaled storage) over the
+    measured HBM peak."""
+    lat = duct_lattice(hl, n, stream.cuda_stream, storage)
+    try:
+        lat.step(warmup)
+        ms = timed(stream, lambda: lat.step(steps)) / steps
+        mass = lat.reduce()[0]
+    finally:
+        lat.close()
+    peak, _ = measured_peaks()
+    bpn = STORAGE_BYTES[storage]
+    return {"storage": storage, "ms_per_step": round(ms, 5), "mlups": round(n ** 3 / ms / 1e3, 1),
+            "bytes_per_node": bpn, "frac": round(n ** 3 * bpn / (ms / 1e3) / 1e9 / peak, 4),
+            "mass_rel_drift": float(mass / n ** 3 - 1.0)}
+
+
 def bench_extras(hl, wl):
     import torch
     stream = torch.cuda.Stream()
-    out = {"c5_batched": bench_batched(hl, wl, stream), "c4_adjoint": bench_adjoint(hl, wl, stream),
+    out = {"duct_f16s": bench_duct_storage(hl, stream, "f16s"), "duct_bf16s": bench_duct_storage(hl, stream, "bf16s"),
+           "c5_batched": bench_batched(hl, wl, stream), "c4_adjoint": bench_adjoint(hl, wl, stream),
            "fp32_sgemm_tflops": round(fp32_sgemm_tflops(), 1)}
     ml = {}
     ref = None
@@ -483,22 +502,39 @@ def bench_extras(hl, wl):
     return out
 
 
-def cpu_oracle_sample(n_sample=64, steps=12):
-    """The FP64 CPU oracle on an n_sample^3 duct of the same kind (bounded sample)."""
+def cpu_oracle_sample(n_sample=64, steps=12, threads=None):
+    """The FP64 CPU oracle on an n_sample^3 duct of the same kind (bounded sample),
+    on `threads` host threads (default: torch's, normally every core)."""
     import torch
     from oracle import single_level as sl
     from paper_2603_14982_gb300 import workloads as wl
 
-    M = torch.tensor(wl.rest_field((n_sample,) * 3))
-    blocked = sl.blocked_sources(M.shape[1:], (True, False, False))
-    sl.step(M, 0.55, force=(1e-6, 0, 0), periodic=(True, False, False), blocked=blocked)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        M = sl.step(M, 0.55, force=(1e-6, 0, 0), periodic=(True, False, False), blocked=blocked)
-    dt = time.perf_counter() - t0
-    return {"value": n_sample ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": torch.get_num_threads(),
-            "kind": "oracle", "sample": "%d^3 duct of the same kind, %d steps, FP64 torch CPU, %.1f s" %
-            (n_sample, steps, dt)}
+    prev = torch.get_num_threads()
+    if threads is not None:
+        torch.set_num_threads(threads)
+    try:
+        M = torch.tensor(wl.rest_field((n_sample,) * 3))
+        blocked = sl.blocked_sources(M.shape[1:], (True, False, False))
+        sl.step(M, 0.55, force=(1e-6, 0, 0), periodic=(True, False, False), blocked=blocked)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            M = sl.step(M, 0.55, force=(1e-6, 0, 0), periodic=(True, False, False), blocked=blocked)
+        dt = time.perf_counter() - t0
+        used = torch.get_num_threads()
+    finally:
+        torch.set_num_threads(prev)
+    return {"value": n_sample ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": used,
+            "kind": "oracle", "sample": "%d^3 duct of the same kind, %d steps, FP64 torch CPU, %d threads, %.1f s" %
+            (n_sample, steps, used, dt)}
+
+
+def cpu_baseline():
+    """The oracle on every host core and on one, with the host's core count."""
+    allc = cpu_oracle_sample(128, 16)
+    one = cpu_oracle_sample(64, 6, threads=1)
+    allc["single_thread"] = {"value": one["value"], "unit": "MLUPS", "cores": 1, "sample": one["sample"]}
+    allc["nproc"] = os.cpu_count()
+    return allc
 
 
 def main():
@@ -554,6 +590,7 @@ def main():
             return
         steps = max(1, min(args.steps, 8))
         cb = cpu_oracle_sample(128, steps)
+        cb["nproc"] = os.cpu_count()
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS",
                           "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -613,7 +650,25 @@ def main():
                 "peak_tflops": pk, "peak_kind": "cuBLAS SGEMM 8192^3, TF32 off, measured in this run",
                 "frac": round(tf / pk, 4) if pk else None}
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_oracle_sample(128, 16)
+        line["cpu_baseline"] = cpu_baseline()
+    ex = res["extras"]
+    if ex is not None:
+        # compact figures of the secondary workloads, last on the line
+        c5 = ex["c5_batched"]["f16s"]
+        c3 = ex["c3_multilevel"]
+        line["summary"] = {
+            "duct_f32_frac": line["roofline"]["frac"],
+            "duct_f16s_mlups": ex["duct_f16s"]["mlups"], "duct_f16s_frac": ex["duct_f16s"]["frac"],
+            "duct_f16s_over_f32": round(ex["duct_f16s"]["mlups"] / line["value"], 3),
+            "c5_mlups": c5["mlups"], "c5_frac": round(c5["hbm_gbs"] / peak, 4), "c5_mode": c5["mode"],
+            "c4_adjoint_over_forward": ex["c4_adjoint"]["adjoint_over_forward"],
+            "c3_f32_mlups": c3["f32"]["mlups_fine_equiv"],
+            "c3_actual_gbs_over_peak": c3["f32"]["actual_gbs_over_peak"],
+            "c3_f16s_over_f32": round(c3["f16s"]["mlups_fine_equiv"] / c3["f32"]["mlups_fine_equiv"], 3),
+            "c3_rebuild_share": round(c3["f32"]["rebuild_s"] / c3["f32"]["total_s"], 4),
+            "c3_adjoint_over_forward": ex["c3_adjoint"]["adjoint_over_forward"],
+            "sparse_2048_mlups": ex["sparse_tree_2048"]["mlups_fine_equiv"],
+        }
     print(json.dumps(line))
     if world > 1:
         import torch

@@ -364,9 +364,16 @@ int32_t hlbm_test_narrow(const double *in_dev, float *out_dev, float *hw_dev, in
  * budget, or contexts where allocation would synchronise the device.
  *
  * mom_dev:  float32 device buffer in the public layout [n_blocks][10][512]
- *           (rho in row 0, as written by hlbm_read_moments with on_device = 1).
+ *           (rho in row 0), as written by hlbm_read_moments with on_device = 1
+ *           and physical_u = 0: the velocity rows must hold the stored
+ *           velocity u' = u + F/(2 rho), since this call subtracts F/(2 rho)
+ *           itself (a buffer read with physical_u = 1 would be shifted twice).
+ *           Every node of every block is summed with unit volume: the result
+ *           equals hlbm_reduce for single-level lattices only (hlbm_reduce
+ *           leaves out blocks covered by a finer level and weights level l
+ *           by 8^l).
  * F_dev:    float32 device force [n_blocks][3][512], or NULL to use (fx, fy, fz);
- *           the velocity summed is u - F/(2 rho).
+ *           the velocity summed is u' - F/(2 rho).
  * out_dev:  five doubles in device memory, overwritten with mass, momentum
  *           (3) and kinetic energy.
  * stream:   cudaStream_t (NULL = legacy default stream); the call is

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -671,9 +672,9 @@ int32_t hlbm_reduce(hlbm_lattice* h, double out[7]) {
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
   ProfScope prof_scope(h, kProfReduce);
-  int64_t nbmax = 0;
-  for (auto& L : h->lv) nbmax = L.nb > nbmax ? L.nb : nbmax;
-  const size_t need = size_t(nbmax) * 7 + 2 * 8;
+  size_t scratch = 0;
+  for (auto& L : h->lv) scratch = std::max(scratch, reduce_scratch_doubles(L.nb));
+  const size_t need = scratch + 2 * 8;
   if (h->red_n < need) {
     void* v = h->d_red;
     LatticeOps::release(h, v);
@@ -684,15 +685,18 @@ int32_t hlbm_reduce(hlbm_lattice* h, double out[7]) {
     h->d_red = static_cast<double*>(p);
     h->red_n = need;
   }
-  double* d_out = h->d_red + size_t(nbmax) * 7;  // [0..4] this level, [8..15] unused
+  double* d_out = h->d_red + scratch;  // [0..4] this level, [8..15] unused
   double total[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int l = 0; l < h->cfg.num_levels; ++l) {
     LevelData& L = h->lv[l];
     if (L.nb == 0) continue;
     HLBM_CUDA(h, cudaMemsetAsync(d_out, 0, 8 * sizeof(double), h->stream));
     const double vol = std::ldexp(1.0, 3 * l);
+    // the force (field or uniform) acts on level 0 only, so only level 0's
+    // stored velocity carries the F / (2 rho) shift
+    const double no_force[3] = {0.0, 0.0, 0.0};
     HLBM_CUDA(h, reduce_level(h->cfg.storage, L.d_mom[L.cur], L.nb, L.d_scales, L.d_skip, l == 0 ? h->d_F : nullptr,
-                              h->fu, vol, h->d_red, d_out, h->stream));
+                              l == 0 ? h->fu : no_force, vol, h->d_red, d_out, h->stream));
     double r[8];
     HLBM_CUDA(h, cudaMemcpyAsync(r, d_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     HLBM_CUDA(h, cudaStreamSynchronize(h->stream));

@@ -66,68 +66,194 @@ __global__ void k_export(const T* __restrict__ src, Out* __restrict__ dst, int64
   p[9 * kCells] = Out(m.syz);
 }
 
-// Per-block FP64 partial sums: one CTA of 512 threads per block, warp shuffles
-// then shared memory.  Blocks whose `skip` byte is set (covered by a finer
-// level) contribute zero.  part[blk][7] = mass, momentum (3), KE, 0, 0.
-template <typename T>
-__global__ void __launch_bounds__(512) k_reduce_blocks(const T* __restrict__ src, const Scales* sc,
-                                                      const uint8_t* __restrict__ skip, const float* __restrict__ F,
-                                                      double fx, double fy, double fz, double vol,
-                                                      double* __restrict__ part) {
-  const int64_t blk = blockIdx.x;
-  const int t = threadIdx.x;
-  double v[5] = {0, 0, 0, 0, 0};
-  if (skip == nullptr || skip[blk] == 0) {
-    const auto m = load_node<T>(src, blk, t, sc);
-    const double rho = 1.0 + double(m.drho);
-    if (F != nullptr) {
-      const float* Fp = F + blk * 3 * kCells + t;
-      fx = Fp[0];
-      fy = Fp[kCells];
-      fz = Fp[2 * kCells];
+// FP64 sums over the stored blocks of a level (blocks whose `skip` byte is
+// set -- covered by a finer level -- contribute nothing).  GB300 runs FP64 at
+// about 2 operations per cycle per SM, so the per-node work stays in FP32 and
+// the sums are carried to FP64 accuracy in FP32 arithmetic:
+//  * mass   = vol (N + sum delta_rho)            (delta_rho is stored exactly);
+//  * mom_a  = vol (sum u'_a + sum delta_rho u'_a - sum F_a / 2), since
+//    rho u_a = rho u'_a - F_a / 2 exactly for the stored velocity
+//    u' = u + F / (2 rho); the products delta_rho u'_a are split exactly into
+//    a rounded product and its FMA residual;
+//  * KE     = vol sum rho |u|^2 / 2 with u = u' - F / (2 rho) per node (FP32
+//    per node: a few units of 6e-8 relative per term).
+// Each thread walks its nodes with a grid stride and sums every term with
+// the cascaded "Sum2" of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26(6),
+// 2005): Knuth's error-free TwoSum keeps the running sum s and accumulates
+// every rounding error in e, so that s + e carries the sum as if in twice
+// the working precision (error about (n eps)^2 times the summed magnitudes).
+// The pair is widened to FP64 once per thread and summed in FP64 across the
+// grid.  Only rows 0-3 (delta_rho, u) are read.  FP64 storage sums plain FP64.
+//
+// part[cta][kRedSlots]: N, sum delta_rho, sum u' (3), sum delta_rho u' (3),
+// sum F (3; force field only), sum of the kinetic energies.
+constexpr int kRedThreads = 256;
+constexpr int kRedSlots = 12;
+
+template <typename R>
+struct CompSum {
+  R s = 0, e = 0;
+  // s + e += x; the FP32 form is TwoSum, written with intrinsics that the
+  // compiler neither contracts nor reorders
+  __device__ __forceinline__ void add(R x) {
+    if constexpr (sizeof(R) == 4) {
+      const float t = __fadd_rn(s, x);
+      const float bp = __fsub_rn(t, s);
+      const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+      s = t;
+      e = __fadd_rn(e, err);
+    } else {
+      s += x;
     }
-    // the force shift F / (2 rho) is O(F): a float reciprocal keeps it exact to
-    // far below the FP64 sums' rounding while avoiding FP64 divisions
-    const double hir = 0.5 * double(__frcp_rn(float(rho)));
-    const double ux = double(m.ux) - fx * hir;
-    const double uy = double(m.uy) - fy * hir;
-    const double uz = double(m.uz) - fz * hir;
-    v[0] = rho * vol;
-    v[1] = rho * ux * vol;
-    v[2] = rho * uy * vol;
-    v[3] = rho * uz * vol;
-    v[4] = 0.5 * rho * (ux * ux + uy * uy + uz * uz) * vol;
   }
-  __shared__ double s[16][5];
+  // s + e += a b, with the product's rounding error (an FMA residual) exact
+  __device__ __forceinline__ void add_prod(R a, R b) {
+    if constexpr (sizeof(R) == 4) {
+      const float p = __fmul_rn(a, b);
+      add(p);
+      e = __fadd_rn(e, __fmaf_rn(a, b, -p));
+    } else {
+      s += a * b;
+    }
+  }
+  __device__ __forceinline__ double value() const { return double(s) + double(e); }
+};
+
+// Four consecutive row values at p (16-byte aligned for float, 8 for the
+// 2-byte codes, 32 for double), decoded with the row's scale.
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, float dec, typename StorageTraits<T>::R (&v)[4]) {
+  if constexpr (sizeof(T) == 8) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+  } else if constexpr (sizeof(T) == 4) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+  } else {
+    const uint2 a = __ldg(reinterpret_cast<const uint2*>(p));
+    const T* h = reinterpret_cast<const T*>(&a);
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    double x = v[k];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if ((t & 31) == 0) s[t >> 5][k] = x;
+    for (int j = 0; j < 4; ++j) v[j] = StorageTraits<T>::R(h[j]) * dec;
   }
-  __syncthreads();
-  if (t < 5) {
-    double x = 0;
-    for (int w = 0; w < 16; ++w) x += s[w][t];
-    part[blk * 7 + t] = x;
-  }
-  if (t == 5 || t == 6) part[blk * 7 + t] = 0.0;
 }
 
-// Sum part[n][7] into out[7] (one CTA; fixed order, deterministic).
-__global__ void __launch_bounds__(256) k_reduce_final(const double* __restrict__ part, int64_t n, double* out) {
-  __shared__ double s[256];
-  for (int k = 0; k < 5; ++k) {
-    double x = 0;
-    for (int64_t i = threadIdx.x; i < n; i += 256) x += part[i * 7 + k];
-    s[threadIdx.x] = x;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-      __syncthreads();
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_reduce_sums(const T* __restrict__ src, int64_t nb, const Scales* sc,
+                                                            const uint8_t* __restrict__ skip,
+                                                            const float* __restrict__ F, float fx, float fy, float fz,
+                                                            double* __restrict__ part) {
+  using R = typename StorageTraits<T>::R;
+  CompSum<R> drho, u[3], du[3], f[3], ke;
+  int64_t n_own = 0;
+  float dec[4] = {1.f, 1.f, 1.f, 1.f};
+  if constexpr (StorageTraits<T>::kNeq)
+    for (int r = 0; r < 4; ++r) dec[r] = sc->dec[r];
+  constexpr int kQuads = kCells / 4;  // four consecutive row positions per item
+  const int64_t n = nb * kQuads;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t blk = i / kQuads;
+    if (skip != nullptr && skip[blk]) continue;
+    const int k0 = 4 * int(i % kQuads);  // first position in the row (node order of the storage)
+    const T* p = src + blk * (kRows * kCells) + k0;
+    R d[4], ux[4], uy[4], uz[4];
+    load4<T>(p, dec[0], d);
+    load4<T>(p + kCells, dec[1], ux);
+    load4<T>(p + 2 * kCells, dec[2], uy);
+    load4<T>(p + 3 * kCells, dec[3], uz);
+    R gx[4] = {fx, fx, fx, fx}, gy[4] = {fy, fy, fy, fy}, gz[4] = {fz, fz, fz, fz};
+    if (F != nullptr) {
+      // force field in natural node order: positions k0..k0+3 of a paired
+      // row are the nodes c, c + 256, c + 1, c + 257 with c = k0 / 2
+      const float* Fb = F + blk * 3 * kCells;
+      const int c = StorageTraits<T>::kPaired ? k0 >> 1 : k0;
+      float q[3][4];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if constexpr (StorageTraits<T>::kPaired) {
+          const float2 lo = __ldg(reinterpret_cast<const float2*>(Fb + a * kCells + c));
+          const float2 hi = __ldg(reinterpret_cast<const float2*>(Fb + a * kCells + c + 256));
+          q[a][0] = lo.x;
+          q[a][1] = hi.x;
+          q[a][2] = lo.y;
+          q[a][3] = hi.y;
+        } else {
+          const float4 v4 = __ldg(reinterpret_cast<const float4*>(Fb + a * kCells + c));
+          q[a][0] = v4.x;
+          q[a][1] = v4.y;
+          q[a][2] = v4.z;
+          q[a][3] = v4.w;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        gx[j] = q[0][j];
+        gy[j] = q[1][j];
+        gz[j] = q[2][j];
+        f[0].add(gx[j]);
+        f[1].add(gy[j]);
+        f[2].add(gz[j]);
+      }
     }
-    if (threadIdx.x == 0) out[k] += s[0];
-    __syncthreads();
+    n_own += 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      drho.add(d[j]);
+      u[0].add(ux[j]);
+      u[1].add(uy[j]);
+      u[2].add(uz[j]);
+      du[0].add_prod(d[j], ux[j]);
+      du[1].add_prod(d[j], uy[j]);
+      du[2].add_prod(d[j], uz[j]);
+      const R rho = R(1) + d[j];
+      const R hir = R(0.5) / rho;
+      const R vx = ux[j] - gx[j] * hir, vy = uy[j] - gy[j] * hir, vz = uz[j] - gz[j] * hir;
+      ke.add(R(0.5) * rho * (vx * vx + vy * vy + vz * vz));
+    }
+  }
+  double v[kRedSlots] = {double(n_own), drho.value(), u[0].value(), u[1].value(), u[2].value(), du[0].value(),
+                         du[1].value(), du[2].value(), f[0].value(), f[1].value(), f[2].value(), ke.value()};
+  __shared__ double s[kRedThreads / 32][kRedSlots];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kRedSlots; ++q) {
+    double x = v[q];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) s[w][q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < kRedSlots) {
+    double x = 0;
+    for (int j = 0; j < kRedThreads / 32; ++j) x += s[j][threadIdx.x];
+    part[int64_t(blockIdx.x) * kRedSlots + threadIdx.x] = x;
+  }
+}
+
+// Sum the per-CTA partials (warp q sums slot q; fixed order, deterministic)
+// and add this level's mass, momentum (3) and kinetic energy, times the cell
+// volume, to out[0..4].  Uniform force (field null): sum F = N F.
+__global__ void __launch_bounds__(32 * kRedSlots) k_reduce_combine(const double* __restrict__ part, int n_part,
+                                                                   int field, double fx, double fy, double fz,
+                                                                   double vol, double* out) {
+  __shared__ double tot[kRedSlots];
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double x = 0;
+  for (int j = lane; j < n_part; j += 32) x += part[int64_t(j) * kRedSlots + q];
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  if (lane == 0) tot[q] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double N = tot[0];
+    const double Fs[3] = {field ? tot[8] : N * fx, field ? tot[9] : N * fy, field ? tot[10] : N * fz};
+    out[0] += vol * (N + tot[1]);
+    for (int a = 0; a < 3; ++a) out[1 + a] += vol * (tot[2 + a] + tot[5 + a] - 0.5 * Fs[a]);
+    out[4] += vol * tot[11];
   }
 }
 
@@ -160,9 +286,10 @@ template <typename T>
 cudaError_t reduce_typed(const void* src, int64_t nb, const Scales* sc, const uint8_t* skip, const float* F,
                          const double* fu, double vol, double* part, double* out, cudaStream_t s) {
   if (nb == 0) return cudaSuccess;
-  k_reduce_blocks<T><<<unsigned(nb), 512, 0, s>>>(static_cast<const T*>(src), sc, skip, F, fu[0], fu[1], fu[2], vol,
-                                                  part);
-  k_reduce_final<<<1, 256, 0, s>>>(part, nb, out);
+  const int grid = reduce_ctas(nb);
+  k_reduce_sums<T><<<unsigned(grid), kRedThreads, 0, s>>>(static_cast<const T*>(src), nb, sc, skip, F, float(fu[0]),
+                                                          float(fu[1]), float(fu[2]), part);
+  k_reduce_combine<<<1, 32 * kRedSlots, 0, s>>>(part, grid, F != nullptr ? 1 : 0, fu[0], fu[1], fu[2], vol, out);
   return cudaGetLastError();
 }
 
@@ -215,6 +342,14 @@ cudaError_t reduce_level(int storage, const void* src, int64_t nb, const Scales*
                          const float* F, const double* fu, double vol, double* part, double* out, cudaStream_t s) {
   HLBM_DISPATCH(storage, reduce_typed, src, nb, sc, skip, F, fu, vol, part, out, s)
 }
+
+int reduce_ctas(int64_t nb) {
+  // about 64 nodes per thread at full size; at most 8 CTAs per SM of 152
+  const int64_t want = (nb * kCells + int64_t(kRedThreads) * 64 - 1) / (int64_t(kRedThreads) * 64);
+  return int(want < 1 ? 1 : (want > 1216 ? 1216 : want));
+}
+
+size_t reduce_scratch_doubles(int64_t nb) { return size_t(reduce_ctas(nb)) * kRedSlots; }
 
 }  // namespace hlbm
 

@@ -17,9 +17,13 @@ cudaError_t export_moments(int storage, const void* src, void* dst, int dtype, i
                            const float* F, const double* fu, int physical, cudaStream_t s);
 
 // Adds the level's mass, momentum and kinetic energy (times vol) to out[0..4]
-// (device).  part is scratch of nb*7 doubles.  Blocks with skip[b] != 0 are left out.
+// (device).  part is scratch of reduce_scratch_doubles(nb) doubles.  Blocks
+// with skip[b] != 0 are left out.
 cudaError_t reduce_level(int storage, const void* src, int64_t nb, const Scales* sc, const uint8_t* skip,
                          const float* F, const double* fu, double vol, double* part, double* out, cudaStream_t s);
+// CTAs of the reduction over nb blocks, and the scratch it needs.
+int reduce_ctas(int64_t nb);
+size_t reduce_scratch_doubles(int64_t nb);
 
 // Adds to *count (device) a positive number if any of the n values of a
 // device buffer of dtype 0 = f64, 1 = f32 is not finite (nothing otherwise).

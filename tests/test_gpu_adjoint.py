@@ -6,8 +6,8 @@ physical velocity u = u' - F/(2 rho), as a function of the per-node force F.
   FP64 reverse-mode gradient, relative to max |dL/dF|: 1e-4 (FP32 storage),
   1e-6 (FP64 storage: the adjoint variables and dL/dF are float32);
 * the 128^3 channel with the 16^3 obstacle, 200 steps, checkpoints every 20:
-  the FP32 adjoint against central differences of the FP64 GPU forward on
-  sampled cells, within 1e-4 relative.
+  the FP32 adjoint against central differences of the FP64 GPU forward on 32
+  random fluid cells of the whole channel, within 1e-4 of max |dL/dF|.
 """
 import numpy as np
 import pytest
@@ -92,14 +92,14 @@ def test_obstacle_channel_128_central_differences():
     M0 = wl.rest_field(shape)
     per = (True, False, False)
     L, g = gpu_gradient(M0, F.astype(np.float64), solid, extent, steps, ckpt, 0.55, "f32", per)
-    # central differences with the FP64 forward on sampled fluid cells near the outlet plane
+    # central differences with the FP64 forward on 32 random fluid cells of
+    # the whole channel, one random force component each
     rng = np.random.default_rng(5)
     cells = []
-    while len(cells) < 6:
-        z, y = rng.integers(8, n - 8, 2)
-        x = int(rng.integers(n - 40, n))
+    while len(cells) < 32:
+        z, y, x = (int(v) for v in rng.integers(0, n, 3))
         if not solid[z, y, x]:
-            cells.append((int(z), int(y), x, int(rng.integers(0, 3))))
+            cells.append((z, y, x, int(rng.integers(0, 3))))
     with hl.Lattice(extent, tau=0.55, periodic=per, storage="f64") as lat:
         lat.set_dense()
         lat.set_solid(solid)
@@ -117,6 +117,8 @@ def test_obstacle_channel_128_central_differences():
 
         coords, _ = lat.blocks(0)
         index = {tuple(c): i for i, c in enumerate(coords.tolist())}
+        gmax = np.abs(g).max()
+        worst = 0.0
         for (z, y, x, a) in cells:
             b = index[(x // 8, y // 8, z // 8)]
             c = (x % 8) + 8 * (y % 8) + 64 * (z % 8)
@@ -128,4 +130,6 @@ def test_obstacle_channel_128_central_differences():
             hp = float(Fp[b, a, c] - Fb0[b, a, c])   # the float32 step actually taken
             hm = float(Fb0[b, a, c] - Fm[b, a, c])
             fd = (L_of(Fp) - L_of(Fm)) / (hp + hm)
-            assert abs(g[a, z, y, x] - fd) <= 1e-4 * np.abs(g).max() + 1e-3 * abs(fd), (z, y, x, a, g[a, z, y, x], fd)
+            worst = max(worst, abs(g[a, z, y, x] - fd) / gmax)
+            assert abs(g[a, z, y, x] - fd) <= 1e-4 * gmax, (z, y, x, a, g[a, z, y, x], fd, gmax)
+    print("C4 central differences: 32 cells, max |g - fd| / max |g| = %.2e" % worst)

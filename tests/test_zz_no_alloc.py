@@ -61,6 +61,38 @@ def test_noalloc_reduce_matches_handle_reduce_twice(use_field):
     assert np.array_equal(outs[0], outs[1])
 
 
+def test_noalloc_address_survives_lattice_create_and_destroy():
+    """The cached device address of the scratch stays valid across lattices:
+    a call before a lattice exists, a call while one lives and a call after
+    it is destroyed agree, and the result matches hlbm_reduce of that lattice."""
+    from paper_2603_14982_gb300 import build as B
+    B.build()
+    lib = hl.load()
+    shape = (16, 24, 32)
+    M0 = hl.dense_to_blocks(wl.random_field(shape, 5)).astype(np.float32)
+    mom = torch.tensor(M0, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    fu = (1e-5, 0.0, -2e-5)
+
+    def call():
+        out = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
+        assert _noalloc(lib, mom, None, fu, out, stream) == hl.OK, lib.hlbm_last_error(None)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    before = call()
+    with hl.Lattice((32, 24, 16), tau=0.7, periodic=(True, True, True), stream=stream) as lat:
+        lat.set_dense()
+        lat.set_uniform_force(*fu)
+        lat.write_moments(mom)
+        ref = lat.reduce()[:5]
+        during = call()
+    after = call()
+    assert np.array_equal(before, during) and np.array_equal(before, after)
+    scale = np.array([abs(ref[0]), ref[0] * 0.02, ref[0] * 0.02, ref[0] * 0.02, abs(ref[4])])
+    assert np.all(np.abs(before - ref) <= 1e-5 * scale), (before, ref)
+
+
 def test_noalloc_rejects_sizes_beyond_the_maximum():
     lib = hl.load()
     out = torch.zeros(5, dtype=torch.float64, device="cuda")
