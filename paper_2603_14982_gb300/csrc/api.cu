@@ -177,7 +177,7 @@ void LatticeOps::free_level(hlbm_lattice* h, LevelData& L) {
   release(h, v);
   L.d_skip = nullptr;
   for (void** q : {(void**)&L.d_coords, (void**)&L.d_slot, (void**)&L.d_H, (void**)&L.d_stored, (void**)&L.d_down,
-                   (void**)&L.d_up, (void**)&L.d_scales, (void**)&L.d_amax, (void**)&L.d_hkeys, (void**)&L.d_hvals}) {
+                   (void**)&L.d_up, (void**)&L.d_down_acc, (void**)&L.d_scales, (void**)&L.d_amax, (void**)&L.d_hkeys, (void**)&L.d_hvals}) {
     release(h, *q);
   }
   L.hcap = 0;
@@ -212,8 +212,12 @@ int LatticeOps::maybe_rescale(hlbm_lattice* h, LevelData& L, bool force) {
   if (!reduced(h) || L.nb == 0) return HLBM_OK;
   if (!force && ++L.steps_since_rescale < kRescaleEvery) return HLBM_OK;
   L.steps_since_rescale = 0;
-  HLBM_CUDA(h, rescale_storage(h->cfg.storage, L.d_mom[L.cur], L.nb, L.d_scales, L.d_scales + 1, L.d_amax,
-                               h->stream));
+  // both buffers share the scales, and the downward transfer reads the
+  // coarser level's previous state after its step: a periodic refit
+  // re-encodes that buffer too (a forced refit follows a write or a rebuild,
+  // after which the other buffer is rewritten before it is read)
+  HLBM_CUDA(h, rescale_storage_both(h->cfg.storage, L.d_mom[L.cur], force ? nullptr : L.d_mom[1 - L.cur], L.nb,
+                                    L.d_scales, L.d_scales + 1, L.d_amax, h->stream));
   return HLBM_OK;
 }
 

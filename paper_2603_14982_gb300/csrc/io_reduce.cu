@@ -580,15 +580,18 @@ __global__ void __launch_bounds__(512) k_reencode(T* buf, const Scales* from, co
   store_node<T>(buf, blockIdx.x, threadIdx.x, m, to + d);
 }
 
+// other (optional): a second buffer encoded with the same scales (the other
+// ping-pong buffer of a level), re-encoded with the new scales as well.
 template <typename T>
 cudaError_t rescale_typed(void* buf, int64_t nb, const int32_t* dom, int n_dom, Scales* cur, Scales* tmp,
-                          unsigned* amax, cudaStream_t s) {
+                          unsigned* amax, cudaStream_t s, void* other = nullptr) {
   if (nb == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(amax, 0, size_t(n_dom) * kRows * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   k_amax_storage<T><<<unsigned(nb), 512, 0, s>>>(static_cast<const T*>(buf), cur, amax, dom);
   k_set_scales<<<unsigned((n_dom * kRows + 255) / 256), 256, 0, s>>>(amax, tmp, n_dom);
   k_reencode<T><<<unsigned(nb), 512, 0, s>>>(static_cast<T*>(buf), cur, tmp, dom);
+  if (other != nullptr) k_reencode<T><<<unsigned(nb), 512, 0, s>>>(static_cast<T*>(other), cur, tmp, dom);
   e = cudaMemcpyAsync(cur, tmp, size_t(n_dom) * sizeof(Scales), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -612,6 +615,15 @@ cudaError_t scales_from_public(const void* src, int dtype, int64_t nb, Scales* s
 cudaError_t rescale_storage(int storage, void* buf, int64_t nb, Scales* cur, Scales* tmp, unsigned* amax,
                             cudaStream_t s) {
   return rescale_storage_domains(storage, buf, nb, nullptr, 1, cur, tmp, amax, s);
+}
+
+cudaError_t rescale_storage_both(int storage, void* buf, void* other, int64_t nb, Scales* cur, Scales* tmp,
+                                 unsigned* amax, cudaStream_t s) {
+  switch (storage) {
+    case HLBM_STORE_F16S: return rescale_typed<__half>(buf, nb, nullptr, 1, cur, tmp, amax, s, other);
+    case HLBM_STORE_BF16S: return rescale_typed<__nv_bfloat16>(buf, nb, nullptr, 1, cur, tmp, amax, s, other);
+    default: return cudaSuccess;
+  }
 }
 
 cudaError_t rescale_storage_domains(int storage, void* buf, int64_t nb, const int32_t* dom, int n_dom, Scales* cur,

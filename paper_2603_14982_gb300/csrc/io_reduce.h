@@ -36,6 +36,10 @@ cudaError_t scales_from_public(const void* src, int dtype, int64_t nb, Scales* s
 // place (no-op for FP32 / FP64 storage).  tmp: a second Scales in device memory.
 cudaError_t rescale_storage(int storage, void* buf, int64_t nb, Scales* cur, Scales* tmp, unsigned* amax,
                             cudaStream_t s);
+// The same, re-encoding a second buffer that shares the scales (the other
+// ping-pong buffer of a level) with the same change of scales.
+cudaError_t rescale_storage_both(int storage, void* buf, void* other, int64_t nb, Scales* cur, Scales* tmp,
+                                 unsigned* amax, cudaStream_t s);
 // The same for a buffer holding blocks of n_dom domains with their own scales:
 // dom[b] is block b's domain, cur / tmp hold n_dom Scales, amax n_dom * 10.
 cudaError_t rescale_storage_domains(int storage, void* buf, int64_t nb, const int32_t* dom, int n_dom, Scales* cur,

@@ -61,6 +61,8 @@ struct LevelData {
   int64_t n_down = 0, n_up = 0;    // interface node counts (I^d, I^u)
   int32_t* d_down = nullptr;       // [n_down] (block << 9) | cell
   int32_t* d_up = nullptr;         // [n_up]
+  double* d_down_acc = nullptr;    // [n_down][10] FP64 stencil sums of the old coarse state (step s = 1,
+                                   // reused at s = 2)
   // reduced-precision storage: row scales shared by both buffers, a spare
   // Scales for re-encoding, and the amax scratch
   Scales* d_scales = nullptr;      // [2]

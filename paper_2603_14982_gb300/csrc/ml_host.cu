@@ -72,6 +72,7 @@ int downward(hlbm_lattice* h, int l, int s, bool refresh) {
   a.n_nodes = F.n_down;
   a.avg = (!refresh && s == 2) ? 1 : 0;
   a.use_other = (!refresh && s == 1) ? 1 : 0;
+  a.acc_old = refresh ? nullptr : F.d_down_acc;
   a.k = h->kdown[l];
   for (int ax = 0; ax < 3; ++ax) a.periodic[ax] = h->cfg.periodic[ax];
   a.status = h->d_status;
@@ -340,6 +341,7 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     if (nb[l] == 0) continue;
     if ((rc = alloc_t(h, &nl[l].d_down, size_t(nl[l].n_down) + 1))) break;
     if ((rc = alloc_t(h, &nl[l].d_up, size_t(nl[l].n_up) + 1))) break;
+    if (l + 1 < L && (rc = alloc_t(h, &nl[l].d_down_acc, size_t(nl[l].n_down) * 10 + 1))) break;
     cudaError_t e = interface_scatter(nl[l].d_nbr, nl[l].d_skip, nb[l], d_ioff[l], nl[l].d_down, nl[l].d_up, st);
     if (e != cudaSuccess) rc = fail(h, HLBM_E_CUDA, "interface scatter: %s", cudaGetErrorString(e));
   }
@@ -391,12 +393,11 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     for (int l = 0; l < L; ++l)
       if (nb[l]) ML_CUDA(h, cudaMemsetAsync(nl[l].d_mom[0], 0, size_t(nb[l]) * kCells * node_bytes, st));
   }
+  // only the current buffer needs the state: every level steps (writing the
+  // other buffer) before anything reads its previous state
   for (int l = 0; l < L; ++l) {
     nl[l].cur = 0;
     ML_TRY(LatticeOps::maybe_rescale(h, nl[l], true));
-    if (nb[l])
-      ML_CUDA(h, cudaMemcpyAsync(nl[l].d_mom[1], nl[l].d_mom[0], size_t(nb[l]) * kCells * node_bytes,
-                                 cudaMemcpyDeviceToDevice, st));
   }
 
   // 6. host copies of the lists; counts of refined / coarsened / deleted blocks

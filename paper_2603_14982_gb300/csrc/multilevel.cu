@@ -175,11 +175,25 @@ __global__ void k_down(TransferArgs a) {
   }
   Node64 acc = zero64();
   const void* cur = a.use_other ? a.coarse.mom_other : a.coarse.mom;
+  // step 2 with the old state's sums kept from step 1: half of them plus half
+  // the new state's sums (the midpoint is linear in rho, u and S^neq)
+  const bool reuse = a.avg && a.acc_old != nullptr;
+  if (reuse) {
+    const double* o = a.acc_old + k * 10;
+    acc.drho = 0.5 * o[0];
+    acc.ux = 0.5 * o[1];
+    acc.uy = 0.5 * o[2];
+    acc.uz = 0.5 * o[3];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) acc.s[r] = 0.5 * o[4 + r];
+    cur = a.coarse.mom;
+  }
+  const double wt = reuse ? 0.5 * w : w;
 #pragma unroll
   for (int q = 0; q < 8; q += 2) {
     if (q >= nq) break;
     const bool two = q + 1 < nq;
-    if (a.avg) {
+    if (a.avg && !reuse) {
       // temporal midpoint of the old (other) and new (current) coarse states,
       // taken per field on rho, u and S^neq
       const Node64 o0 = load64<T>(a.coarse.mom_other, cb[q], cc[q], a.coarse.sc);
@@ -199,9 +213,18 @@ __global__ void k_down(TransferArgs a) {
       const Node64 v0 = load64<T>(cur, cb[q], cc[q], a.coarse.sc);
       Node64 v1 = zero64();
       if (two) v1 = load64<T>(cur, cb[q + 1], cc[q + 1], a.coarse.sc);
-      axpy(acc, w, v0);
-      if (two) axpy(acc, w, v1);
+      axpy(acc, wt, v0);
+      if (two) axpy(acc, wt, v1);
     }
+  }
+  if (a.use_other && a.acc_old != nullptr) {  // step 1: keep the old state's sums for step 2
+    double* o = a.acc_old + k * 10;
+    o[0] = acc.drho;
+    o[1] = acc.ux;
+    o[2] = acc.uy;
+    o[3] = acc.uz;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) o[4 + r] = acc.s[r];
   }
   store64<T>(a.out, b, cell, acc, a.k, a.out_sc);
 }

@@ -34,6 +34,9 @@ struct TransferArgs {
   double k;                   // S^neq factor
   int periodic[3];
   int* status;                // set to 1 if a stencil node is not stored
+  double* acc_old;            // down, optional [n_nodes][10]: step 1 stores the FP64 stencil sums of the
+                              // old coarse state there; step 2 reuses them instead of re-reading the
+                              // old state (it is the same state: the coarse level does not step between)
 };
 
 // DownwardTransfer of Algorithm 1 (Eq. downward_rescale) into I^d nodes of the fine level.

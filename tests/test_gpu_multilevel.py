@@ -224,6 +224,39 @@ def test_two_level_reduced_precision(storage, tol):
         _compare(lat, m, tol, 0.01)
 
 
+def shear_and_bump(A, n, bump, at):
+    """shear(A, n) plus a Gaussian bump of u_x (peak `bump`, width 2 fine
+    nodes) at fine position `at` = (x, y, z)."""
+    base = shear(A, n)
+
+    def fn(X, Y, Z):
+        M = base(X, Y, Z)
+        g = bump * np.exp(-((X - at[0]) ** 2 + (Y - at[1]) ** 2 + (Z - at[2]) ** 2) / 8.0)
+        ux = M[1] + g
+        return wl.equilibrium_field(M[0], ux, M[2], M[3])
+    return fn
+
+
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+def test_scale_refit_keeps_the_previous_state_readable(storage):
+    """A velocity bump of 0.03 in the coarse-only region diffuses to a few 1e-3
+    within the coarse level's first 32 steps, so its periodic scale refit
+    changes the velocity row's exponent.  The downward transfer of the next
+    fine steps reads the coarse level's previous state, which the refit must
+    re-encode with the new scales too; the run stays within the FP16/BF16
+    bound of the FP64 oracle through the refit."""
+    ext = (16, 128, 16)
+    O0 = np.zeros(hy.block_dims(ext, 8, 0), bool)
+    O0[:, 7:9, :] = True
+    h, m, lat = _setup(ext, 2, O0, (True, True, True), 0.8, shear_and_bump(0.002, 128, 0.03, (8, 16, 8)), storage)
+    tol = {"f16s": 3e-2, "bf16s": 0.2}[storage]
+    with lat:
+        for _ in range(34):
+            m.coarse_step()
+            lat.step(2)
+        _compare(lat, m, tol, 0.002)
+
+
 def test_full_size_falling_cloud_hierarchy_bit_exact():
     """The 512^3 three-level domain with the 2M-particle cloud (bench workload):
     block lists, flags, interface nodes and change counts equal the oracle's at
