@@ -249,7 +249,10 @@ def test_scale_refit_keeps_the_previous_state_readable(storage):
     O0 = np.zeros(hy.block_dims(ext, 8, 0), bool)
     O0[:, 7:9, :] = True
     h, m, lat = _setup(ext, 2, O0, (True, True, True), 0.8, shear_and_bump(0.002, 128, 0.03, (8, 16, 8)), storage)
-    tol = {"f16s": 3e-2, "bf16s": 0.2}[storage]
+    # bounds over 34 coarse steps: FP16 as the 3-step test (3e-2), BF16 (8-bit
+    # significand, 2^-8 per rounding) 0.4; a previous state decoded with the
+    # wrong exponent gives 0.85 (FP16) and 0.91 (BF16) here
+    tol = {"f16s": 3e-2, "bf16s": 0.4}[storage]
     with lat:
         for _ in range(34):
             m.coarse_step()
