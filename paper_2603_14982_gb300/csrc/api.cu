@@ -177,7 +177,7 @@ void LatticeOps::free_level(hlbm_lattice* h, LevelData& L) {
   release(h, v);
   L.d_skip = nullptr;
   for (void** q : {(void**)&L.d_coords, (void**)&L.d_slot, (void**)&L.d_H, (void**)&L.d_stored, (void**)&L.d_down,
-                   (void**)&L.d_up, (void**)&L.d_down_acc, (void**)&L.d_scales, (void**)&L.d_amax, (void**)&L.d_hkeys, (void**)&L.d_hvals}) {
+                   (void**)&L.d_up, (void**)&L.d_down_acc, (void**)&L.d_list_flags, (void**)&L.d_scales, (void**)&L.d_amax, (void**)&L.d_hkeys, (void**)&L.d_hvals}) {
     release(h, *q);
   }
   L.hcap = 0;
@@ -185,6 +185,21 @@ void LatticeOps::free_level(hlbm_lattice* h, LevelData& L) {
   L.nb = 0;
   L.coords.clear();
   L.flags.clear();
+  L.host_lists = false;
+}
+
+int LatticeOps::host_lists(hlbm_lattice* h, LevelData& L) {
+  if (L.host_lists) return HLBM_OK;
+  L.coords.resize(size_t(L.nb) * 3);
+  L.flags.resize(size_t(L.nb));
+  if (L.nb > 0) {
+    HLBM_CUDA(h, cudaMemcpyAsync(L.coords.data(), L.d_coords, size_t(L.nb) * 3 * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, h->stream));
+    HLBM_CUDA(h, cudaMemcpyAsync(L.flags.data(), L.d_list_flags, size_t(L.nb), cudaMemcpyDeviceToHost, h->stream));
+    HLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  L.host_lists = true;
+  return HLBM_OK;
 }
 
 static bool reduced(const hlbm_lattice* h) {
@@ -398,6 +413,7 @@ int32_t hlbm_set_dense(hlbm_lattice* h) {
     slot_to_idx[s] = int32_t(s);
   }
   L.flags.assign(size_t(nb), 1);  // leaf
+  L.host_lists = true;
   std::vector<int32_t> nbr;
   LatticeOps::build_nbr(h, 0, L.coords, slot_to_idx, nbr);
   L.nb = nb;
@@ -432,10 +448,15 @@ int32_t hlbm_get_blocks(const hlbm_lattice* h, int32_t level, int32_t* out, int6
   hlbm_lattice* hm = const_cast<hlbm_lattice*>(h);
   if (h == nullptr || n == nullptr) return fail(hm, HLBM_E_INVALID_ARG, "NULL argument");
   if (level < 0 || level >= h->cfg.num_levels) return fail(hm, HLBM_E_INVALID_ARG, "level %d out of range", level);
-  const LevelData& L = h->lv[level];
+  LevelData& L = hm->lv[level];
   *n = L.nb;
   if (cap < L.nb) return fail(hm, HLBM_E_INVALID_ARG, "capacity %lld < %lld blocks", (long long)cap, (long long)L.nb);
   if (L.nb > 0 && out == nullptr) return fail(hm, HLBM_E_INVALID_ARG, "out is NULL");
+  if (!L.host_lists) {
+    int rc = LatticeOps::set_device(hm);
+    if (rc == HLBM_OK) rc = LatticeOps::host_lists(hm, L);
+    if (rc) return rc;
+  }
   if (L.nb > 0) std::memcpy(out, L.coords.data(), size_t(L.nb) * 3 * sizeof(int32_t));
   if (flags_out && L.nb > 0) std::memcpy(flags_out, L.flags.data(), size_t(L.nb));
   return HLBM_OK;
@@ -513,6 +534,7 @@ int32_t hlbm_set_solid(hlbm_lattice* h, const uint8_t* mask) {
   LatticeOps::release(h, v);
   L.d_bflags = nullptr;
   if (mask == nullptr) return LatticeOps::bounce(h, L);
+  if ((rc = LatticeOps::host_lists(h, L))) return rc;
   int dims[3];
   h->block_dims(0, dims);
   const int nx = h->cfg.nx, ny = h->cfg.ny;

@@ -40,8 +40,11 @@ struct Profile {
 
 struct LevelData {
   int64_t nb = 0;                  // stored blocks
-  std::vector<int32_t> coords;     // host copy [nb][3] (bx, by, bz), ascending slot id
+  std::vector<int32_t> coords;     // host copy [nb][3] (bx, by, bz), ascending slot id (see host_lists)
   std::vector<uint8_t> flags;      // host copy [nb] leaf/border/new/refine/coarsen bits
+  bool host_lists = false;         // coords / flags hold the current lists (copied from the device on
+                                   // demand for hierarchies built on the device)
+  uint8_t* d_list_flags = nullptr; // [nb] flags of the device-built list
   int32_t* d_nbr = nullptr;        // [nb][27]
   void* d_mom[2] = {nullptr, nullptr};  // ping-pong moment buffers [nb][10][512]
   int cur = 0;                     // buffer holding the current state
@@ -191,6 +194,8 @@ struct LatticeOps {
   static int maybe_rescale(hlbm_lattice* h, LevelData& L, bool force);
   // (Re)compute d_bflags / d_bmask of a level from its neighbour table and solids.
   static int bounce(hlbm_lattice* h, LevelData& L);
+  // Make L.coords / L.flags current (one device-to-host copy after a rebuild).
+  static int host_lists(hlbm_lattice* h, LevelData& L);
   static void build_nbr(const hlbm_lattice* h, int level, const std::vector<int32_t>& coords,
                         const std::vector<int32_t>& slot_to_idx, std::vector<int32_t>& nbr);
 };

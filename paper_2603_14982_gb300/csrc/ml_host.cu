@@ -277,7 +277,7 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     if ((rc = alloc_t(h, &nl[l].d_coords, ns * 3))) break;
     if ((rc = alloc_t(h, &nl[l].d_skip, ns))) break;
     if ((rc = alloc_t(h, &d_lflags[l], ns))) break;
-    tmp.push_back(d_lflags[l]);
+    nl[l].d_list_flags = d_lflags[l];
     cudaError_t e = compact_slots(nl[l].d_stored, d_fl[l], nl[l].d_H, dims_of(h, l), nl[l].d_slot, nl[l].d_coords,
                                   d_lflags[l], nl[l].d_skip, d_cnt, d_tot + l, st);
     if (e != cudaSuccess) rc = fail(h, HLBM_E_CUDA, "compaction: %s", cudaGetErrorString(e));
@@ -410,19 +410,14 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
                                d_changes, st));
     ML_CUDA(h, cudaMemcpyAsync(changes, d_changes, sizeof(changes), cudaMemcpyDeviceToHost, st));
   }
-  for (int l = 0; l < L; ++l) {
-    nl[l].coords.resize(size_t(nb[l]) * 3);
-    nl[l].flags.resize(size_t(nb[l]));
-    if (nb[l]) {
-      ML_CUDA(h, cudaMemcpyAsync(nl[l].coords.data(), nl[l].d_coords, size_t(nb[l]) * 3 * sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, st));
-      ML_CUDA(h, cudaMemcpyAsync(nl[l].flags.data(), d_lflags[l], size_t(nb[l]), cudaMemcpyDeviceToHost, st));
-    }
-  }
+  // the host copies of the block lists are made on demand (hlbm_get_blocks);
+  // one readback brings the status words (transfer status, dropped particles)
+  for (int l = 0; l < L; ++l) nl[l].host_lists = false;
+  int status[2] = {0, 0};
+  ML_CUDA(h, cudaMemcpyAsync(status, h->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   ML_CUDA(h, cudaStreamSynchronize(st));
   const int64_t refined = int64_t(changes[0]), coarsened = int64_t(changes[1]), deleted = int64_t(changes[2]);
-  int bad = 0;
-  ML_CUDA(h, cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));
+  const int bad = status[1];
   cleanup();
   for (auto& X : h->lv) LatticeOps::free_level(h, X);
   for (int l = 0; l < L; ++l) {
@@ -449,7 +444,8 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     counts_out[1] = coarsened;
     counts_out[2] = deleted;
   }
-  ML_TRY(ml_check_status(h));
+  if (status[0] == 1) return fail(h, HLBM_E_BAD_STATE, "a transfer stencil reached a node that is not stored");
+  if (status[0] == 2) return fail(h, HLBM_E_BAD_STATE, "rebuild: a new node had no source at any level");
   if (bad) return fail(h, HLBM_E_NONFINITE, "%d particle positions are not finite (ignored)", bad);
   return HLBM_OK;
 }

@@ -154,7 +154,7 @@ __global__ void k_down(TransferArgs a) {
   // 1), an odd one two (weight 1/2 each); the weights are exact in FP64
   const int nx = hi[0] != lo[0] ? 2 : 1, ny = hi[1] != lo[1] ? 2 : 1, nz = hi[2] != lo[2] ? 2 : 1;
   const int nq = nx * ny * nz;
-  const double w = 1.0 / double(nq);
+  const double w = nq == 1 ? 1.0 : (nq == 2 ? 0.5 : (nq == 4 ? 0.25 : 0.125));  // 1/nq, exact
   // all stencil lookups first (independent loads), then the node loads two
   // corners at a time so that their latencies overlap
   int64_t cb[8];
