@@ -245,6 +245,7 @@ struct AdjArgs {
   const float* pre_prev;  // fused push: recorded p of the previous step
   float* lamp_out;        // fused push: dL/dp of the previous step
   const float* lam_add;   // plain push: added to lam_out at every node, or null
+  float* lam_add_clear;   // the same buffer when it is to be left zero after the read, or null
 };
 
 // Shared part: the block's ext buffer filled with the forward pull (PULL) or
@@ -607,6 +608,14 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
       const V2 add[kRows] = {q.drho, q.jx, q.jy, q.jz, q.pxx, q.pyy, q.pzz, q.pxy, q.pxz, q.pyz};
 #pragma unroll
       for (int r = 0; r < kRows; ++r) out[r] = out[r] + add[r];
+      if (d.lam_add_clear != nullptr) {  // this thread is the only reader of its pair
+        float* z = d.lam_add_clear + blk * (kRows * kCells) + own;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          z[r * kCells] = 0.f;
+          z[r * kCells + 256] = 0.f;
+        }
+      }
     }
     store_pair10(d.lam_out, blk, own, out, false, false);
   }
@@ -726,12 +735,13 @@ cudaError_t launch_push2(const StepArgs& a_in, const AdjArgs& d, cudaStream_t s)
 }
 
 cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp, float* lam_out, cudaStream_t s,
-                         const float* lam_add) {
+                         float* lam_add, bool clear_add) {
   AdjArgs d{};
   d.lam = lam;
   d.lamp = const_cast<float*>(lamp);
   d.lam_out = lam_out;
   d.lam_add = lam_add;
+  d.lam_add_clear = clear_add ? lam_add : nullptr;
   return launch_push2<false>(a, d, s);
 }
 

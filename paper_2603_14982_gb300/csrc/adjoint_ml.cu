@@ -378,6 +378,14 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
   // pre-collision buffer per SC operation, undo logs per transfer
   std::vector<void*> work(L, nullptr);
   for (int l = 0; l < L; ++l) get(vals[l] * sizeof(float), &work[l]);
+  // FP64 stencil sums of the old coarse state kept from step 1 to step 2 of
+  // the recomputed downward transfers, as in the forward advance
+  std::vector<double*> acc(L, nullptr);
+  for (int l = 0; l + 1 < L; ++l) {
+    void* p;
+    get((size_t(h->lv[l].n_down) * 10 + 1) * sizeof(double), &p);
+    acc[l] = static_cast<double*>(p);
+  }
   std::vector<Op> seg_ops;
   for (int c = 0; c < k_coarse; ++c) seg_ops.insert(seg_ops.end(), step_ops.begin(), step_ops.end());
   for (Op& op : seg_ops) {
@@ -449,6 +457,7 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         t.n_nodes = F.n_down;
         t.avg = op.s == 2 ? 1 : 0;
         t.use_other = op.s == 1 ? 1 : 0;
+        t.acc_old = acc[l];
         t.k = h->kdown[l];
         for (int ax = 0; ax < 3; ++ax) t.periodic[ax] = h->cfg.periodic[ax];
         t.status = h->d_status;
@@ -483,8 +492,8 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         a.in = op.in;
         e = adjoint_collide(a, op.pre, lamA[l], lamp, l == 0 ? dF : nullptr, st);
         // lambda_P of level 0 stays zero: no finer level reads its previous state
-        if (e == cudaSuccess) e = adjoint_push(a, lamA[l], lamp, spare, st, l > 0 ? lamP[l] : nullptr);
-        if (e == cudaSuccess && l > 0) e = cudaMemsetAsync(lamP[l], 0, vals[l] * sizeof(float), st);
+        // lambda_P is added and left zero by the same pass
+        if (e == cudaSuccess) e = adjoint_push(a, lamA[l], lamp, spare, st, l > 0 ? lamP[l] : nullptr, true);
         std::swap(lamA[l], spare);
       } else if (op.kind == kDown) {
         const LevelData& F = h->lv[l];

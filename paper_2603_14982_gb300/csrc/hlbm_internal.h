@@ -75,11 +75,12 @@ cudaError_t adjoint_dF_to_float(const double* dF, float* out, int64_t n, cudaStr
 // (elementwise: lamp = (dC/dp)^T lam, dF += (dC/dF)^T lam unless dF is null;
 // solid and interface nodes get lamp = 0) then adjoint_push (lam_out = dL/dM
 // of the step's input a.in; solid nodes copy lam, interface nodes add it to
-// what streams back; lam_add, if set, is added at every node).
+// what streams back; lam_add, if set, is added at every node and, with
+// clear_add, left zero behind).
 cudaError_t adjoint_collide(const StepArgs& a, const float* pre, const float* lam, float* lamp, double* dF,
                             cudaStream_t s);
 cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp, float* lam_out, cudaStream_t s,
-                         const float* lam_add = nullptr);
+                         float* lam_add = nullptr, bool clear_add = false);
 // adjoint_push of a step fused with adjoint_collide of the step before it
 // (recorded p = pre_prev): writes that step's lamp to lamp_out, adds to dF.
 // The step's own lam_out is not stored.
