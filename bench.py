@@ -37,7 +37,7 @@ KERNEL = "k_stream_collide_f2<float>"
 # DRAM bytes (read + write) per launch of KERNEL from one ncu capture of the
 # 192^3 duct, scaled by nodes to 256^3 (profiles/stream_collide_f2_duct192.md);
 # set to None whenever the kernel changes after that capture.
-TRAFFIC_PER_NODE = (289.213696e6 + 242.401536e6) / 192 ** 3
+TRAFFIC_PER_NODE = (289.211648e6 + 242.613504e6) / 192 ** 3
 # FP32 operations per node update of KERNEL (ncu thread-level counts of FADD,
 # FMUL, FFMA and their packed forms on the 192^3 duct, profiles/
 # stream_collide_f2_duct192.md; FMA = 2); None when not measured for the
@@ -613,7 +613,7 @@ def main():
     achieved = args.n ** 3 * bpn / (res["ms_per_step"] / 1e3) / 1e9
     # DRAM bytes per node update from the ncu captures of the 192^3 duct (the
     # FP32 and FP16 kernels; none taken for BF16)
-    traffic = {"f32": TRAFFIC_PER_NODE, "f16s": 253.3e6 / 192 ** 3}.get(args.storage)
+    traffic = {"f32": TRAFFIC_PER_NODE, "f16s": (147.631104e6 + 106.398720e6) / 192 ** 3}.get(args.storage)
     line = {
         "metric": METRIC,
         "value": round(res["value"], 1),
