@@ -152,6 +152,67 @@ def test_duct_256_sampled_nodes_one_step():
     assert abs(r1[0] - r0[0]) / r0[0] < 1e-9
 
 
+def test_duct_256_1000_steps_every_node_against_the_oracle():
+    """The benchmark's workload run to its end: 256^3 nodes, tau 0.55, force
+    1e-6 along x, periodic in x, bounce-back walls in y and z, 1000 steps from
+    rest, FP32 storage and arithmetic, one launch per step as the bench times it.
+
+    The flow does not depend on x, so every x-plane of the lattice must equal
+    the FP64 oracle run on a single 256 x 256 plane (one node, periodic in x):
+    all ten moments of all 16.7 M nodes are compared with it.
+
+    Bounds, per moment row against its scale (max |oracle| of the row: about
+    U = 1e-3 for u_x, U^2 for S_xx): delta_rho and u within 1e-4, since one
+    FP32 rounding of u near U is 2^-24 U = 6e-8 U and 1000 steps of roundings
+    that never cancel stay below 6e-5 U.  The S rows are sums of products of
+    u-sized terms, so each step leaves them an error of a few roundings of U,
+    not of U^2, and that error does not grow: S^neq relaxes by the factor
+    1 - 1/tau = -0.82 every step.  Their bound is 8 roundings of U,
+    8 2^-24 U / U^2 = 4.8e-4 of the row scale.
+
+    The oracle's u_x also follows the transient square-duct series (walls half
+    a cell outside the first and last fluid layers) to 1 % of the centre
+    value: a lattice of this spacing misses the continuum solution by 0.92 %
+    in the first layers after 1000 steps, where the boundary layer is about
+    four cells thick.  The series is summed to 799 terms (399 terms differ
+    from it by 1e-4 of the centre value; 199 terms by 3e-3)."""
+    from tests.test_oracle_single_level import duct_series
+    n, tau, g, steps = 256, 0.55, 1e-6, 1000
+    with hl.Lattice((n, n, n), tau=tau, periodic=(True, False, False), storage="f32") as lat:
+        lat.set_dense()
+        lat.set_uniform_force(g, 0.0, 0.0)
+        lat.step(steps)
+        M = torch.empty((lat.num_blocks(), 10, 512), dtype=torch.float32, device="cuda")
+        lat.read_moments(M)
+        coords, _ = lat.blocks(0)
+    ref = torch.tensor(wl.rest_field((n, n, 1)))
+    ref = sl.run(ref, steps, tau, force=(g, 0.0, 0.0), periodic=(True, False, False))   # [10][z][y][1]
+    # the oracle plane gathered to every block's nodes on the device (cell = x + 8 y + 64 z)
+    cell = torch.arange(512, device="cuda")
+    c = torch.tensor(coords, dtype=torch.int64, device="cuda")
+    Y = c[:, 1:2] * 8 + (cell // 8) % 8
+    Z = c[:, 2:3] * 8 + cell // 64
+    R = ref[:, :, :, 0].cuda()[:, Z, Y]                                   # [10][blocks][512]
+    d = (M.double().permute(1, 0, 2) - R).abs().reshape(10, -1).amax(dim=1).cpu().numpy()
+    del R, M
+    scales = row_scales(ref.numpy(), 1e-3)
+    err = d / scales
+    print("256^3 duct, 1000 FP32 steps, every node: max |gpu - oracle| / row scale per moment", err)
+    bound = np.array([1e-4] * 4 + [8 * 2.0 ** -24 * scales[1] / s for s in scales[4:]])
+    assert (err < bound).all(), (err, bound)
+    # the oracle against the continuum solution
+    u = sl.physical_velocity(ref, (g, 0.0, 0.0))[0][:, :, 0].numpy()     # [z][y]
+    nu = (tau - 0.5) / 3
+    idx = np.arange(n)
+    centre = duct_series(n, g, nu, steps, np.array([n // 2]), np.array([n // 2]), terms=799)[0]
+    worst = 0.0
+    for z, y in [(np.full(n, n // 2), idx), (idx, np.full(n, n // 2)), (idx, idx)]:
+        ua = duct_series(n, g, nu, steps, y.astype(float), z.astype(float), terms=799)
+        worst = max(worst, float(np.abs(u[z, y] - ua).max() / centre))
+    print("oracle u_x against the series: max error / centre value %.2e" % worst)
+    assert worst < 1e-2, worst
+
+
 # ------------------------------------------------------------ reduced-precision storage
 # Codes of delta_rho, u and S^neq are scaled so each row's amax sits below 2^13:
 # one rounding costs at most 2^-11 (fp16) / 2^-8 (bf16) of the row amax times
