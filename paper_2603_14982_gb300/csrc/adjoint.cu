@@ -244,8 +244,9 @@ struct AdjArgs {
   float* lam_out;         // dL/dM of the step's input [nb][10][512]
   const float* pre_prev;  // fused push: recorded p of the previous step
   float* lamp_out;        // fused push: dL/dp of the previous step
-  const float* lam_add;   // plain push: added to lam_out at every node, or null
+  const float* lam_add;   // added to the push's output at every node, or null
   float* lam_add_clear;   // the same buffer when it is to be left zero after the read, or null
+  float* raw_out;         // fused push: the output at pass-through nodes (solid or interface), or null
 };
 
 // Shared part: the block's ext buffer filled with the forward pull (PULL) or
@@ -532,15 +533,20 @@ __device__ __forceinline__ Mom<V2> as_mom(const PreMom<V2>& q) {
 
 // Reverse step, part 2 (node pairs): gbar streamed back to the pull sources,
 // weighted moments transposing the 17 Hermite coefficients, (dA/dM)^T at the
-// step's input moments: lambda of the step's input.  kFuse: instead of storing
-// it, go on with part 1 of the previous step at the same node (its transposed
-// collision needs only this node's lambda and recorded p), writing that step's
-// lambda_p to d.lamp_out and its force term to d.dF.  Solid nodes keep
-// lambda = d.lam (nothing streams into them).  The plain form also serves the
-// multi-level adjoint: interface nodes (a neighbour block not stored) copy
-// their input in the forward step, so d.lam passes through and adds to what
-// streams back from the nodes that pull from them; d.lam_add, if set, is
-// added everywhere.  The fused form is for lattices without interface nodes.
+// step's input moments: lambda of the step's input.  Solid nodes keep
+// lambda = d.lam (nothing streams into them); interface nodes (a neighbour
+// block not stored) copy their input in the forward step, so d.lam passes
+// through and adds to what streams back from the nodes that pull from them;
+// d.lam_add, if set, is added everywhere.  Solid and interface nodes are the
+// pass-through nodes; d.lam is read only there.
+// kFuse: instead of storing lambda, go on with part 1 of the previous step at
+// the same node (its transposed collision needs only this node's lambda and
+// recorded p), writing that step's lambda_p to d.lamp_out (zero at
+// pass-through nodes, as part 1 leaves it) and its force term to d.dF; lambda
+// itself is kept only at the pass-through nodes, in d.raw_out if set (the
+// multi-level adjoint reads it there: the transfers' own nodes are interface
+// nodes).  d.raw_out may equal d.lam: each thread reads and writes its own
+// pair only.
 template <typename T, bool kFuse>
 __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjArgs d) {
   extern __shared__ __align__(16) float2 f2buf[];
@@ -556,7 +562,7 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
     fz_hi = a.solid[blk * kCells + own + 256] != 0;
   }
   bool cp_lo = false, cp_hi = false;  // interface nodes
-  if (!kFuse && s_miss != 0u) {
+  if (s_miss != 0u) {
     cp_lo = !fz_lo && f2::touches_missing(cx.x, cx.y, cx.z0, s_miss);
     cp_hi = !fz_hi && f2::touches_missing(cx.x, cx.y, cx.z0 + 4, s_miss);
   }
@@ -582,41 +588,61 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
     const Coef<V2> gh = adjoint_moments(gh_in);
     lm = coef_vjp(load_pair<T>(static_cast<const T*>(a.in), blk, own, a.scales_in), gh, V2(a.kxyzf));
   }
+  V2 out[kRows] = {lm.drho, lm.ux, lm.uy, lm.uz, lm.sxx, lm.syy, lm.szz, lm.sxy, lm.sxz, lm.syz};
+  const bool pt_lo = fz_lo || cp_lo, pt_hi = fz_hi || cp_hi;
+  if ((pt_lo || pt_hi) && d.lam != nullptr) {
+    const PreMom<V2> q = LamSource{d.lam}.pair(blk, own);
+    const V2 lam[kRows] = {q.drho, q.jx, q.jy, q.jz, q.pxx, q.pyy, q.pzz, q.pxy, q.pxz, q.pyz};
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const float lo = fz_lo ? lam[r].v.x : (cp_lo ? out[r].v.x + lam[r].v.x : out[r].v.x);
+      const float hi = fz_hi ? lam[r].v.y : (cp_hi ? out[r].v.y + lam[r].v.y : out[r].v.y);
+      out[r] = V2(lo, hi);
+    }
+  }
+  if (d.lam_add != nullptr) {
+    const PreMom<V2> q = LamSource{d.lam_add}.pair(blk, own);
+    const V2 add[kRows] = {q.drho, q.jx, q.jy, q.jz, q.pxx, q.pyy, q.pzz, q.pxy, q.pxz, q.pyz};
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) out[r] = out[r] + add[r];
+    if (d.lam_add_clear != nullptr) {  // this thread is the only reader of its pair
+      float* z = d.lam_add_clear + blk * (kRows * kCells) + own;
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        z[r * kCells] = 0.f;
+        z[r * kCells + 256] = 0.f;
+      }
+    }
+  }
   if constexpr (kFuse) {
-    if (fz_lo && fz_hi) {
+    if (d.raw_out != nullptr && (pt_lo || pt_hi)) {
+      float* q = d.raw_out + blk * (kRows * kCells) + own;
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        if (pt_lo) q[r * kCells] = out[r].v.x;
+        if (pt_hi) q[r * kCells + 256] = out[r].v.y;
+      }
+    }
+    if (pt_lo && pt_hi) {
       V2 z[kRows];
 #pragma unroll
       for (int r = 0; r < kRows; ++r) z[r] = V2(0.f);
       store_pair10(d.lamp_out, blk, own, z, true, true);
       return;
     }
-    collide_adj_pair(a, blk, own, LamSource{d.pre_prev}.pair(blk, own), lm, fz_lo, fz_hi, d.lamp_out, d.dF);
+    Mom<V2> lo;
+    lo.drho = out[0];
+    lo.ux = out[1];
+    lo.uy = out[2];
+    lo.uz = out[3];
+    lo.sxx = out[4];
+    lo.syy = out[5];
+    lo.szz = out[6];
+    lo.sxy = out[7];
+    lo.sxz = out[8];
+    lo.syz = out[9];
+    collide_adj_pair(a, blk, own, LamSource{d.pre_prev}.pair(blk, own), lo, pt_lo, pt_hi, d.lamp_out, d.dF);
   } else {
-    V2 out[kRows] = {lm.drho, lm.ux, lm.uy, lm.uz, lm.sxx, lm.syy, lm.szz, lm.sxy, lm.sxz, lm.syz};
-    if (fz_lo || fz_hi || cp_lo || cp_hi) {
-      const PreMom<V2> q = LamSource{d.lam}.pair(blk, own);
-      const V2 lam[kRows] = {q.drho, q.jx, q.jy, q.jz, q.pxx, q.pyy, q.pzz, q.pxy, q.pxz, q.pyz};
-#pragma unroll
-      for (int r = 0; r < kRows; ++r) {
-        const float lo = fz_lo ? lam[r].v.x : (cp_lo ? out[r].v.x + lam[r].v.x : out[r].v.x);
-        const float hi = fz_hi ? lam[r].v.y : (cp_hi ? out[r].v.y + lam[r].v.y : out[r].v.y);
-        out[r] = V2(lo, hi);
-      }
-    }
-    if (d.lam_add != nullptr) {
-      const PreMom<V2> q = LamSource{d.lam_add}.pair(blk, own);
-      const V2 add[kRows] = {q.drho, q.jx, q.jy, q.jz, q.pxx, q.pyy, q.pzz, q.pxy, q.pxz, q.pyz};
-#pragma unroll
-      for (int r = 0; r < kRows; ++r) out[r] = out[r] + add[r];
-      if (d.lam_add_clear != nullptr) {  // this thread is the only reader of its pair
-        float* z = d.lam_add_clear + blk * (kRows * kCells) + own;
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-          z[r * kCells] = 0.f;
-          z[r * kCells + 256] = 0.f;
-        }
-      }
-    }
     store_pair10(d.lam_out, blk, own, out, false, false);
   }
 }
@@ -746,12 +772,17 @@ cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp,
 }
 
 cudaError_t adjoint_push_collide(const StepArgs& a, const float* lamp, const float* pre_prev, float* lamp_out,
-                                 double* dF, cudaStream_t s) {
+                                 double* dF, cudaStream_t s, const float* lam, float* raw_out, float* lam_add,
+                                 bool clear_add) {
   AdjArgs d{};
+  d.lam = lam;
   d.lamp = const_cast<float*>(lamp);
   d.pre_prev = pre_prev;
   d.lamp_out = lamp_out;
   d.dF = dF;
+  d.raw_out = raw_out;
+  d.lam_add = lam_add;
+  d.lam_add_clear = clear_add ? lam_add : nullptr;
   return launch_push2<true>(a, d, s);
 }
 

@@ -24,6 +24,8 @@
 #include <cstring>
 #include <vector>
 
+#include "adjoint_math.cuh"
+#include "f2_common.cuh"
 #include "hierarchy.cuh"
 #include "hlbm_internal.h"
 #include "lattice_state.h"
@@ -57,25 +59,127 @@ __device__ __forceinline__ void load_f32(const void* base, int64_t blk, int cell
   for (int r = 0; r < kRows; ++r) m[r] = p[r * kCells];
 }
 
-// Adds to the adjoint of stored moments m (delta_rho, u, S) the contribution
-// of a weighted S^neq = S - u u split: lam_rho, lam_u (before the split) and
+// The adjoint, with respect to stored moments m (delta_rho, u, S), of a
+// weighted S^neq = S - u u split: lam_rho, lam_u (before the split) and
 // lam_sn, all times w.
-__device__ __forceinline__ void add_split_adjoint(float* lam, const float (&m)[kRows], float w, float lrho,
-                                                  const float (&lu)[3], const float (&lsn)[6], bool atomic) {
+__device__ __forceinline__ void split_adjoint(const float (&m)[kRows], float w, float lrho, const float (&lu)[3],
+                                              const float (&lsn)[6], float (&v)[kRows]) {
   const float ux = m[1], uy = m[2], uz = m[3];
-  float v[kRows];
   v[0] = w * lrho;
   v[1] = w * (lu[0] - (2.f * ux * lsn[0] + uy * lsn[3] + uz * lsn[4]));
   v[2] = w * (lu[1] - (2.f * uy * lsn[1] + ux * lsn[3] + uz * lsn[5]));
   v[3] = w * (lu[2] - (2.f * uz * lsn[2] + ux * lsn[4] + uy * lsn[5]));
 #pragma unroll
   for (int r = 0; r < 6; ++r) v[4 + r] = w * lsn[r];
+}
+
+__device__ __forceinline__ void add10(float* lam, const float (&v)[kRows], bool atomic) {
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
     if (atomic)
       atomicAdd(lam + r * kCells, v[r]);
     else
       lam[r * kCells] += v[r];
+  }
+}
+
+// Pass-through nodes of a level: solid nodes and nodes next to a neighbour
+// block that is not stored (interface nodes), which copy their input in the
+// forward step.  Bit (cell & 31) of word [blk][cell >> 5], natural order.
+__global__ void __launch_bounds__(kCells) k_passthrough_bits(const int32_t* __restrict__ nbr,
+                                                             const uint8_t* __restrict__ bflags,
+                                                             const uint8_t* __restrict__ solid,
+                                                             uint32_t* __restrict__ bits) {
+  __shared__ unsigned s_miss;
+  const int64_t blk = blockIdx.x;
+  const int t = threadIdx.x;
+  if (t < 32) {
+    const int v = t < 27 ? nbr[blk * 27 + t] : 0;
+    const unsigned mb = __ballot_sync(0xffffffffu, t < 27 && is_copy_nbr(v));
+    if (t == 0) s_miss = mb;
+  }
+  __syncthreads();
+  bool p = s_miss != 0u && f2::touches_missing(t & 7, (t >> 3) & 7, t >> 6, s_miss);
+  if (bflags != nullptr && (bflags[blk] & kBlockSolidNear)) p = p || solid[blk * kCells + t] != 0;
+  const unsigned b = __ballot_sync(0xffffffffu, p);
+  if ((t & 31) == 0) bits[blk * (kCells / 32) + (t >> 5)] = b;
+}
+
+// Where an addition to a level's lambda goes.  A plain level (pt null) holds
+// lambda in raw.  A fused level holds, after the reverse stream of its last
+// reversed step (which applied the transposed collision of the step before
+// it), mu = lambda_p of that earlier step at ordinary nodes (zero at
+// pass-through nodes) and lambda itself at pass-through nodes, in raw.  An
+// addition dlam at an ordinary node of a fused level goes through that
+// transposed collision (recorded p = pre): (dC/dp)^T dlam into mu and, on the
+// level with the force field, (dC/dF)^T dlam into dL/dF; the map is linear in
+// dlam, so additions may come one by one.
+struct LamTarget {
+  const uint32_t* pt;  // pass-through bits, or null (plain)
+  float* raw;
+  float* mu;
+  const float* pre;
+  const float* F;      // force field [nb][3][512] or null (uniform fu)
+  const float* eps;    // fluid fraction [nb][512] or null
+  float fu[3];
+  float om, tau;
+  double* dF;          // dL/dF [nb][3][512] or null
+};
+
+__device__ __forceinline__ void add_lambda(const LamTarget& g, int64_t blk, int cell, const float (&v)[kRows],
+                                           bool atomic) {
+  const int64_t o = blk * kBlockVals + cell;
+  if (g.pt == nullptr || ((g.pt[blk * (kCells / 32) + (cell >> 5)] >> (cell & 31)) & 1u)) {
+    add10(g.raw + o, v, atomic);
+    return;
+  }
+  const float* q = g.pre + o;
+  PreMom<float> p;
+  p.drho = q[0];
+  p.jx = q[kCells];
+  p.jy = q[2 * kCells];
+  p.jz = q[3 * kCells];
+  p.pxx = q[4 * kCells];
+  p.pyy = q[5 * kCells];
+  p.pzz = q[6 * kCells];
+  p.pxy = q[7 * kCells];
+  p.pxz = q[8 * kCells];
+  p.pyz = q[9 * kCells];
+  float fx = g.fu[0], fy = g.fu[1], fz = g.fu[2];
+  if (g.F != nullptr) {
+    const float* f = g.F + blk * 3 * kCells + cell;
+    fx = f[0];
+    fy = f[kCells];
+    fz = f[2 * kCells];
+  }
+  const float om = g.eps != nullptr ? 1.f / (g.tau * g.eps[blk * kCells + cell]) : g.om;
+  Mom<float> lo;
+  lo.drho = v[0];
+  lo.ux = v[1];
+  lo.uy = v[2];
+  lo.uz = v[3];
+  lo.sxx = v[4];
+  lo.syy = v[5];
+  lo.szz = v[6];
+  lo.sxy = v[7];
+  lo.sxz = v[8];
+  lo.syz = v[9];
+  PreMom<float> lp;
+  float lfx, lfy, lfz;
+  collide_vjp(p, fx, fy, fz, om, lo, lp, lfx, lfy, lfz);
+  const float w[kRows] = {lp.drho, lp.jx, lp.jy, lp.jz, lp.pxx, lp.pyy, lp.pzz, lp.pxy, lp.pxz, lp.pyz};
+  add10(g.mu + o, w, atomic);
+  if (g.dF != nullptr) {
+    double* d = g.dF + blk * 3 * kCells + cell;
+    if (atomic) {
+      atomicAdd(d, double(lfx));
+      atomicAdd(d + kCells, double(lfy));
+      atomicAdd(d + 2 * kCells, double(lfz));
+    } else {
+      d[0] += double(lfx);
+      d[kCells] += double(lfy);
+      d[2 * kCells] += double(lfz);
+    }
   }
 }
 
@@ -86,8 +190,8 @@ struct DownAdjArgs {
   int avg;                 // 1: s = 2 (temporal midpoint), 0: s = 1 (old state only)
   float k;                 // S^neq factor of the transfer
   int periodic[3];
-  float* lam_fine;         // lambda_A_l, natural order: read at I^d, then zeroed
-  float* lam_new;          // lambda_A_{l+1} (s = 2)
+  float* lam_fine;         // lambda_A_l at pass-through nodes, natural order: read at I^d, then zeroed
+  LamTarget lam_new;       // lambda_A_{l+1} (s = 2)
   float* lam_old;          // lambda_P_{l+1}
 };
 
@@ -154,12 +258,14 @@ __global__ void k_down_adj(DownAdjArgs a) {
 #pragma unroll
   for (int r = 0; r < 6; ++r) lsn[r] = a.k * L[4 + r];
   for (int q = 0; q < nq; ++q) {
-    float m[kRows];
+    float m[kRows], v[kRows];
     load_f32(a.coarse.mom_other, cb[q], cc[q], m);
-    add_split_adjoint(a.lam_old + cb[q] * kBlockVals + cc[q], m, a.avg ? 0.5f * w : w, L[0], lu, lsn, true);
+    split_adjoint(m, a.avg ? 0.5f * w : w, L[0], lu, lsn, v);
+    add10(a.lam_old + cb[q] * kBlockVals + cc[q], v, true);
     if (a.avg) {
       load_f32(a.coarse.mom, cb[q], cc[q], m);
-      add_split_adjoint(a.lam_new + cb[q] * kBlockVals + cc[q], m, 0.5f * w, L[0], lu, lsn, true);
+      split_adjoint(m, 0.5f * w, L[0], lu, lsn, v);
+      add_lambda(a.lam_new, cb[q], cc[q], v, true);
     }
   }
 }
@@ -169,8 +275,8 @@ struct UpAdjArgs {
   const int32_t* nodes;    // I^u_{l+1}: (block << 9) | cell of the coarse level
   int64_t n_nodes;
   float k;                 // S^neq factor of the transfer
-  float* lam_fine;         // lambda_A_l
-  float* lam_coarse;       // lambda_A_{l+1}: read at I^u, then zeroed
+  LamTarget lam_fine;      // lambda_A_l
+  float* lam_coarse;       // lambda_A_{l+1} at pass-through nodes: read at I^u, then zeroed
 };
 
 // Transposed upward transfer: the coarse node stores (rho_f - 1, u_f,
@@ -197,13 +303,14 @@ __global__ void k_up_adj(UpAdjArgs a) {
   float m[kRows];
   load_f32(a.fine.mom, fb, fc, m);
   const float ux = m[1], uy = m[2], uz = m[3], e = 1.f - a.k;
-  float* lf = a.lam_fine + fb * kBlockVals + fc;
-  lf[0] += L[0];
-  lf[kCells] += L[1] + e * (2.f * ux * L[4] + uy * L[7] + uz * L[8]);
-  lf[2 * kCells] += L[2] + e * (2.f * uy * L[5] + ux * L[7] + uz * L[9]);
-  lf[3 * kCells] += L[3] + e * (2.f * uz * L[6] + ux * L[8] + uy * L[9]);
+  float dl[kRows];
+  dl[0] = L[0];
+  dl[1] = L[1] + e * (2.f * ux * L[4] + uy * L[7] + uz * L[8]);
+  dl[2] = L[2] + e * (2.f * uy * L[5] + ux * L[7] + uz * L[9]);
+  dl[3] = L[3] + e * (2.f * uz * L[6] + ux * L[8] + uy * L[9]);
 #pragma unroll
-  for (int r = 4; r < kRows; ++r) lf[r * kCells] += a.k * L[r];
+  for (int r = 4; r < kRows; ++r) dl[r] = a.k * L[r];
+  add_lambda(a.lam_fine, fb, fc, dl, false);
 }
 
 // Undo log of the transfers: the 10 stored values of each listed node.
@@ -386,8 +493,28 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
     get((size_t(h->lv[l].n_down) * 10 + 1) * sizeof(double), &p);
     acc[l] = static_cast<double*>(p);
   }
+  // lambda at the pass-through nodes of a fused level, and the pass-through bits
+  std::vector<float*> raw(L, nullptr);
+  std::vector<uint32_t*> ptb(L, nullptr);
+  for (int l = 0; l < L; ++l) {
+    void* p;
+    get(vals[l] * sizeof(float), &p);
+    raw[l] = static_cast<float*>(p);
+    get(size_t(h->lv[l].nb) * (kCells / 32) * sizeof(uint32_t) + sizeof(uint32_t), &p);
+    ptb[l] = static_cast<uint32_t*>(p);
+  }
   std::vector<Op> seg_ops;
   for (int c = 0; c < k_coarse; ++c) seg_ops.insert(seg_ops.end(), step_ops.begin(), step_ops.end());
+  // the level's previous SC in the segment, for every SC (-1: the first)
+  std::vector<int> prev_sc(seg_ops.size(), -1);
+  {
+    std::vector<int> last(L, -1);
+    for (size_t i = 0; i < seg_ops.size(); ++i)
+      if (seg_ops[i].kind == kSC) {
+        prev_sc[i] = last[seg_ops[i].l];
+        last[seg_ops[i].l] = int(i);
+      }
+  }
   for (Op& op : seg_ops) {
     void* p;
     if (op.kind == kSC) {
@@ -413,6 +540,38 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
     off += vals[l];
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(dF, 0, size_t(h->lv[0].nb) * 3 * kCells * sizeof(double), st);
+  for (int l = 0; l < L && e == cudaSuccess; ++l) {
+    const LevelData& Lv = h->lv[l];
+    if (Lv.nb == 0) continue;
+    k_passthrough_bits<<<unsigned(Lv.nb), kCells, 0, st>>>(Lv.d_nbr, Lv.d_bflags, Lv.d_solid, ptb[l]);
+    e = cudaGetLastError();
+  }
+  // Per level: plain (lamA holds lambda) or fused (lamA holds mu, raw holds
+  // lambda at the pass-through nodes; fpre is the recorded p of the level's
+  // next SC to reverse, whose transposed collision mu already includes).
+  // Within a segment every SC but the level's first is reversed fused with
+  // the transposed collision of the SC before it.
+  std::vector<char> fused(L, 0);
+  std::vector<const float*> fpre(L, nullptr);
+  auto target = [&](int l) {
+    LamTarget g{};
+    if (!fused[l]) {
+      g.raw = lamA[l];
+      return g;
+    }
+    const StepArgs a = level_args(h, l);
+    g.pt = ptb[l];
+    g.raw = raw[l];
+    g.mu = lamA[l];
+    g.pre = fpre[l];
+    g.F = a.F;
+    g.eps = a.eps;
+    for (int ax = 0; ax < 3; ++ax) g.fu[ax] = float(a.fu[ax]);
+    g.om = float(a.om);
+    g.tau = float(a.tau);
+    g.dF = l == 0 ? dF : nullptr;
+    return g;
+  };
 
   for (int sgi = n_seg - 1; sgi >= 0 && e == cudaSuccess; --sgi) {
     const int nc = (n_coarse - sgi * k_coarse) < k_coarse ? (n_coarse - sgi * k_coarse) : k_coarse;
@@ -490,10 +649,25 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         if (h->lv[l].nb == 0) continue;
         StepArgs a = level_args(h, l);
         a.in = op.in;
-        e = adjoint_collide(a, op.pre, lamA[l], lamp, l == 0 ? dF : nullptr, st);
-        // lambda_P of level 0 stays zero: no finer level reads its previous state
-        // lambda_P is added and left zero by the same pass
-        if (e == cudaSuccess) e = adjoint_push(a, lamA[l], lamp, spare, st, l > 0 ? lamP[l] : nullptr, true);
+        const float* lp_in = lamA[l];  // lambda_p of this SC
+        const float* pass = raw[l];    // lambda at its pass-through nodes
+        if (!fused[l]) {
+          e = adjoint_collide(a, op.pre, lamA[l], lamp, l == 0 ? dF : nullptr, st);
+          lp_in = lamp;
+          pass = lamA[l];
+        }
+        // lambda_P is added and left zero by the same pass; lambda_P of level 0
+        // stays zero (no finer level reads its previous state)
+        float* add = l > 0 ? lamP[l] : nullptr;
+        if (e == cudaSuccess && prev_sc[i] >= 0) {
+          const float* pp = seg_ops[size_t(prev_sc[i])].pre;
+          e = adjoint_push_collide(a, lp_in, pp, spare, l == 0 ? dF : nullptr, st, pass, raw[l], add, true);
+          fused[l] = 1;
+          fpre[l] = pp;
+        } else if (e == cudaSuccess) {
+          e = adjoint_push(a, pass, lp_in, spare, st, add, true);
+          fused[l] = 0;
+        }
         std::swap(lamA[l], spare);
       } else if (op.kind == kDown) {
         const LevelData& F = h->lv[l];
@@ -506,8 +680,8 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         d.avg = op.s == 2 ? 1 : 0;
         d.k = float(h->kdown[l]);
         for (int ax = 0; ax < 3; ++ax) d.periodic[ax] = h->cfg.periodic[ax];
-        d.lam_fine = lamA[l];
-        d.lam_new = lamA[l + 1];
+        d.lam_fine = fused[l] ? raw[l] : lamA[l];
+        d.lam_new = target(l + 1);
         d.lam_old = lamP[l + 1];
         k_down_adj<<<grid_for(F.n_down), 256, 0, st>>>(d);
         k_scatter_nodes<<<grid_for(F.n_down), 256, 0, st>>>(static_cast<float*>(op.in), F.d_down, F.n_down,
@@ -521,8 +695,8 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         u.nodes = C.d_up;
         u.n_nodes = C.n_up;
         u.k = float(h->kup[l]);
-        u.lam_fine = lamA[l];
-        u.lam_coarse = lamA[l + 1];
+        u.lam_fine = target(l);
+        u.lam_coarse = fused[l + 1] ? raw[l + 1] : lamA[l + 1];
         k_up_adj<<<grid_for(C.n_up), 256, 0, st>>>(u);
         k_scatter_nodes<<<grid_for(C.n_up), 256, 0, st>>>(static_cast<float*>(op.in), C.d_up, C.n_up, op.undo);
       }

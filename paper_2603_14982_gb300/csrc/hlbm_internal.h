@@ -83,9 +83,12 @@ cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp,
                          float* lam_add = nullptr, bool clear_add = false);
 // adjoint_push of a step fused with adjoint_collide of the step before it
 // (recorded p = pre_prev): writes that step's lamp to lamp_out, adds to dF.
-// The step's own lam_out is not stored.
+// The step's own lam_out is stored only at the pass-through (solid and
+// interface) nodes, into raw_out if it is set; lam, lam_add and clear_add as
+// for adjoint_push (raw_out may equal lam).
 cudaError_t adjoint_push_collide(const StepArgs& a, const float* lamp, const float* pre_prev, float* lamp_out,
-                                 double* dF, cudaStream_t s);
+                                 double* dF, cudaStream_t s, const float* lam = nullptr, float* raw_out = nullptr,
+                                 float* lam_add = nullptr, bool clear_add = false);
 
 // Per-node bounce masks and the kBlockBounce flag from a neighbour table and
 // an optional solid mask (bflags must hold kBlockSolidNear where solids are near).
