@@ -241,6 +241,7 @@ struct AdjArgs {
   const float* lam;       // dL/dM of the step's output [nb][10][512] (node-pair push: copied at solid nodes)
   float* lamp;            // dL/dp of the pre-collision moments [nb][10][512]
   double* dF;             // accumulated dL/dF [nb][3][512]
+  float* dFs;             // FP32 dL/dF of the current checkpoint segment, used instead of dF when set
   float* lam_out;         // dL/dM of the step's input [nb][10][512]
   const float* pre_prev;  // fused push: recorded p of the previous step
   float* lamp_out;        // fused push: dL/dp of the previous step
@@ -476,13 +477,14 @@ __device__ __forceinline__ void store_pair10(float* p, int64_t blk, int cell, co
 
 // Transposed collision of a node pair (cells c and c + 256 of block blk) from
 // its recorded pre-collision moments p and lambda' = dL/dM of the step's
-// output: stores lambda_p = (dC/dp)^T lambda' and adds (dC/dF)^T lambda' to dF
-// (FP64; skipped when dF_all is null).  Frozen halves (fz_lo / fz_hi: solid
+// output: stores lambda_p = (dC/dp)^T lambda' and adds (dC/dF)^T lambda' to
+// dFs_all (FP32, the sum over one checkpoint segment) if set, else to dF_all
+// (FP64; skipped when both are null).  Frozen halves (fz_lo / fz_hi: solid
 // or interface nodes, which copy their input) get lambda_p = 0 and no force
 // term.
 __device__ __forceinline__ void collide_adj_pair(const StepArgs& a, int64_t blk, int c, const PreMom<V2>& p,
                                                  const Mom<V2>& lo, bool fz_lo, bool fz_hi, float* lamp,
-                                                 double* dF_all) {
+                                                 double* dF_all, float* dFs_all) {
   V2 fx, fy, fz;
   if (a.F != nullptr) {
     const float* Fp = a.F + blk * 3 * kCells + c;
@@ -502,6 +504,20 @@ __device__ __forceinline__ void collide_adj_pair(const StepArgs& a, int64_t blk,
   collide_vjp(p, fx, fy, fz, om, lo, lp, lfx, lfy, lfz);
   const V2 out[kRows] = {lp.drho, lp.jx, lp.jy, lp.jz, lp.pxx, lp.pyy, lp.pzz, lp.pxy, lp.pxz, lp.pyz};
   store_pair10(lamp, blk, c, out, fz_lo, fz_hi);
+  if (dFs_all != nullptr) {
+    float* dF = dFs_all + blk * 3 * kCells + c;
+    if (!fz_lo) {
+      dF[0] += lfx.v.x;
+      dF[kCells] += lfy.v.x;
+      dF[2 * kCells] += lfz.v.x;
+    }
+    if (!fz_hi) {
+      dF[256] += lfx.v.y;
+      dF[kCells + 256] += lfy.v.y;
+      dF[2 * kCells + 256] += lfz.v.y;
+    }
+    return;
+  }
   if (dF_all == nullptr) return;
   double* dF = dF_all + blk * 3 * kCells + c;
   if (!fz_lo) {
@@ -641,7 +657,8 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
     lo.sxy = out[7];
     lo.sxz = out[8];
     lo.syz = out[9];
-    collide_adj_pair(a, blk, own, LamSource{d.pre_prev}.pair(blk, own), lo, pt_lo, pt_hi, d.lamp_out, d.dF);
+    collide_adj_pair(a, blk, own, LamSource{d.pre_prev}.pair(blk, own), lo, pt_lo, pt_hi, d.lamp_out, d.dF,
+                     d.dFs);
   } else {
     store_pair10(d.lam_out, blk, own, out, false, false);
   }
@@ -677,7 +694,7 @@ __global__ void __launch_bounds__(256) k_adj_collide(StepArgs a, const float* __
     return;
   }
   collide_adj_pair(a, blk, t, LamSource{pre}.pair(blk, t), as_mom(LamSource{d.lam}.pair(blk, t)), fz_lo, fz_hi,
-                   d.lamp, d.dF);
+                   d.lamp, d.dF, d.dFs);
 }
 
 StepArgs with_floats(const StepArgs& a_in) {
@@ -717,6 +734,15 @@ __global__ void k_dF_out(const double* __restrict__ dF, float* __restrict__ out,
   if (i < n) out[i] = float(dF[i]);
 }
 
+// The FP64 sum over segments takes one segment's FP32 sum, which restarts at zero.
+__global__ void k_dF_flush(double* __restrict__ dF, float* __restrict__ dFs, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) {
+    dF[i] += double(dFs[i]);
+    dFs[i] = 0.f;
+  }
+}
+
 }  // namespace
 
 cudaError_t adjoint_step(int storage, const StepArgs& a, const float* lam, float* lamp, double* dF, float* lam_out,
@@ -733,13 +759,14 @@ cudaError_t adjoint_step(int storage, const StepArgs& a, const float* lam, float
 }
 
 cudaError_t adjoint_collide(const StepArgs& a_in, const float* pre, const float* lam, float* lamp, double* dF,
-                            cudaStream_t s) {
+                            cudaStream_t s, float* dFs) {
   if (a_in.nb == 0) return cudaSuccess;
   const StepArgs a = with_floats(a_in);
   AdjArgs d{};
   d.lam = lam;
   d.lamp = lamp;
   d.dF = dF;
+  d.dFs = dFs;
   k_adj_collide<<<unsigned(a.nb), 256, 0, s>>>(a, pre, d);
   return cudaGetLastError();
 }
@@ -773,17 +800,24 @@ cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp,
 
 cudaError_t adjoint_push_collide(const StepArgs& a, const float* lamp, const float* pre_prev, float* lamp_out,
                                  double* dF, cudaStream_t s, const float* lam, float* raw_out, float* lam_add,
-                                 bool clear_add) {
+                                 bool clear_add, float* dFs) {
   AdjArgs d{};
   d.lam = lam;
   d.lamp = const_cast<float*>(lamp);
   d.pre_prev = pre_prev;
   d.lamp_out = lamp_out;
   d.dF = dF;
+  d.dFs = dFs;
   d.raw_out = raw_out;
   d.lam_add = lam_add;
   d.lam_add_clear = clear_add ? lam_add : nullptr;
   return launch_push2<true>(a, d, s);
+}
+
+cudaError_t adjoint_dF_flush(double* dF, float* dFs, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_dF_flush<<<unsigned((n + 255) / 256), 256, 0, s>>>(dF, dFs, n);
+  return cudaGetLastError();
 }
 
 cudaError_t adjoint_dF_to_float(const double* dF, float* out, int64_t n, cudaStream_t s) {

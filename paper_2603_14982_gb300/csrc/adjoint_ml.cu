@@ -123,7 +123,7 @@ struct LamTarget {
   const float* eps;    // fluid fraction [nb][512] or null
   float fu[3];
   float om, tau;
-  double* dF;          // dL/dF [nb][3][512] or null
+  float* dF;           // dL/dF of the current checkpoint segment [nb][3][512] (FP32), or null
 };
 
 __device__ __forceinline__ void add_lambda(const LamTarget& g, int64_t blk, int cell, const float (&v)[kRows],
@@ -170,15 +170,15 @@ __device__ __forceinline__ void add_lambda(const LamTarget& g, int64_t blk, int 
   const float w[kRows] = {lp.drho, lp.jx, lp.jy, lp.jz, lp.pxx, lp.pyy, lp.pzz, lp.pxy, lp.pxz, lp.pyz};
   add10(g.mu + o, w, atomic);
   if (g.dF != nullptr) {
-    double* d = g.dF + blk * 3 * kCells + cell;
+    float* d = g.dF + blk * 3 * kCells + cell;
     if (atomic) {
-      atomicAdd(d, double(lfx));
-      atomicAdd(d + kCells, double(lfy));
-      atomicAdd(d + 2 * kCells, double(lfz));
+      atomicAdd(d, lfx);
+      atomicAdd(d + kCells, lfy);
+      atomicAdd(d + 2 * kCells, lfz);
     } else {
-      d[0] += double(lfx);
-      d[kCells] += double(lfy);
-      d[2 * kCells] += double(lfz);
+      d[0] += lfx;
+      d[kCells] += lfy;
+      d[2 * kCells] += lfz;
     }
   }
 }
@@ -464,7 +464,10 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
   // adjoints (each sized for the largest level, so that buffers can swap)
   std::vector<float*> lamA(L), lamP(L);
   float *spare = nullptr, *lamp = nullptr;
+  // dL/dF: an FP32 sum per checkpoint segment (dFs), added to the FP64 sum
+  // over segments (dF) when the segment is done
   double* dF = nullptr;
+  float* dFs = nullptr;
   for (int l = 0; l < L; ++l) {
     void* p;
     get(vmax * sizeof(float), &p);
@@ -480,6 +483,8 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
     lamp = static_cast<float*>(p);
     get(size_t(h->lv[0].nb) * 3 * kCells * sizeof(double), &p);
     dF = static_cast<double*>(p);
+    get(size_t(h->lv[0].nb) * 3 * kCells * sizeof(float), &p);
+    dFs = static_cast<float*>(p);
   }
   // segment buffers: working copies of the checkpoint, one output and one
   // pre-collision buffer per SC operation, undo logs per transfer
@@ -540,6 +545,7 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
     off += vals[l];
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(dF, 0, size_t(h->lv[0].nb) * 3 * kCells * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dFs, 0, size_t(h->lv[0].nb) * 3 * kCells * sizeof(float), st);
   for (int l = 0; l < L && e == cudaSuccess; ++l) {
     const LevelData& Lv = h->lv[l];
     if (Lv.nb == 0) continue;
@@ -569,7 +575,7 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
     for (int ax = 0; ax < 3; ++ax) g.fu[ax] = float(a.fu[ax]);
     g.om = float(a.om);
     g.tau = float(a.tau);
-    g.dF = l == 0 ? dF : nullptr;
+    g.dF = l == 0 ? dFs : nullptr;
     return g;
   };
 
@@ -652,7 +658,7 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         const float* lp_in = lamA[l];  // lambda_p of this SC
         const float* pass = raw[l];    // lambda at its pass-through nodes
         if (!fused[l]) {
-          e = adjoint_collide(a, op.pre, lamA[l], lamp, l == 0 ? dF : nullptr, st);
+          e = adjoint_collide(a, op.pre, lamA[l], lamp, nullptr, st, l == 0 ? dFs : nullptr);
           lp_in = lamp;
           pass = lamA[l];
         }
@@ -661,7 +667,7 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         float* add = l > 0 ? lamP[l] : nullptr;
         if (e == cudaSuccess && prev_sc[i] >= 0) {
           const float* pp = seg_ops[size_t(prev_sc[i])].pre;
-          e = adjoint_push_collide(a, lp_in, pp, spare, l == 0 ? dF : nullptr, st, pass, raw[l], add, true);
+          e = adjoint_push_collide(a, lp_in, pp, spare, nullptr, st, pass, raw[l], add, true, l == 0 ? dFs : nullptr);
           fused[l] = 1;
           fpre[l] = pp;
         } else if (e == cudaSuccess) {
@@ -702,6 +708,7 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
       }
       if (e == cudaSuccess) e = cudaGetLastError();
     }
+    if (e == cudaSuccess) e = adjoint_dF_flush(dF, dFs, h->lv[0].nb * 3 * kCells, st);
   }
   if (e == cudaSuccess)
     e = adjoint_dF_to_float(dF, dL_dF, h->lv[0].nb * 3 * kCells, st);

@@ -833,10 +833,13 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
   // (one float32 buffer per step of a segment), so the reverse step needs no
   // second streaming pass; FP64 storage recomputes the pull in its reverse step.
   const bool record = h->cfg.storage == HLBM_STORE_F32;
-  void *lam0, *lam1, *lamp, *lamp2, *dF;
+  // dL/dF: an FP32 sum per checkpoint segment (dFs, FP32 storage), added to
+  // the FP64 sum over segments (dF) when the segment is done
+  void *lam0, *lam1, *lamp, *lamp2, *dF, *dFs = nullptr;
   std::vector<void*> seg(size_t(K) + 1, nullptr), pre(record ? size_t(K) : 0, nullptr);
   if ((rc = get(lam_elems * 4, &lam0)) || (rc = get(lam_elems * 4, &lam1)) || (rc = get(lam_elems * 4, &lamp)) ||
-      (rc = get(lam_elems * 4, &lamp2)) || (rc = get(size_t(nb) * 3 * kCells * sizeof(double), &dF))) {
+      (rc = get(lam_elems * 4, &lamp2)) || (rc = get(size_t(nb) * 3 * kCells * sizeof(double), &dF)) ||
+      (record && (rc = get(size_t(nb) * 3 * kCells * sizeof(float), &dFs)))) {
     release_all();
     return rc;
   }
@@ -854,6 +857,7 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
   int c = 0;
   cudaError_t e = cudaMemcpyAsync(lam[0], dL_dM_dev, lam_elems * 4, cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(dF, 0, size_t(nb) * 3 * kCells * sizeof(double), h->stream);
+  if (e == cudaSuccess && dFs != nullptr) e = cudaMemsetAsync(dFs, 0, size_t(nb) * 3 * kCells * sizeof(float), h->stream);
   StepArgs a = level0_args(h);
   const int n_seg = (n + K - 1) / K;
   for (int s = n_seg - 1; s >= 0 && e == cudaSuccess; --s) {
@@ -876,15 +880,17 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
       }
       a.pre_out = nullptr;
       a.in = seg[ns - 1];
+      float* dfs = static_cast<float*>(dFs);
       if (e == cudaSuccess)
         e = adjoint_collide(a, static_cast<const float*>(pre[ns - 1]), s == n_seg - 1 ? lam[0] : lam[1], lp[q],
-                            static_cast<double*>(dF), h->stream);
+                            static_cast<double*>(dF), h->stream, dfs);
       for (int i = ns - 1; i >= 1 && e == cudaSuccess; --i) {
         a.in = seg[i];
         e = adjoint_push_collide(a, lp[q], static_cast<const float*>(pre[i - 1]), lp[1 - q], static_cast<double*>(dF),
-                                 h->stream);
+                                 h->stream, nullptr, nullptr, nullptr, false, dfs);
         q = 1 - q;
       }
+      if (e == cudaSuccess) e = adjoint_dF_flush(static_cast<double*>(dF), dfs, nb * 3 * kCells, h->stream);
       if (s > 0 && e == cudaSuccess) {
         a.in = seg[0];
         e = adjoint_push(a, lam[0], lp[q], lam[1], h->stream);

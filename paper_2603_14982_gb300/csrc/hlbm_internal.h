@@ -78,7 +78,7 @@ cudaError_t adjoint_dF_to_float(const double* dF, float* out, int64_t n, cudaStr
 // what streams back; lam_add, if set, is added at every node and, with
 // clear_add, left zero behind).
 cudaError_t adjoint_collide(const StepArgs& a, const float* pre, const float* lam, float* lamp, double* dF,
-                            cudaStream_t s);
+                            cudaStream_t s, float* dFs = nullptr);
 cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp, float* lam_out, cudaStream_t s,
                          float* lam_add = nullptr, bool clear_add = false);
 // adjoint_push of a step fused with adjoint_collide of the step before it
@@ -88,7 +88,11 @@ cudaError_t adjoint_push(const StepArgs& a, const float* lam, const float* lamp,
 // for adjoint_push (raw_out may equal lam).
 cudaError_t adjoint_push_collide(const StepArgs& a, const float* lamp, const float* pre_prev, float* lamp_out,
                                  double* dF, cudaStream_t s, const float* lam = nullptr, float* raw_out = nullptr,
-                                 float* lam_add = nullptr, bool clear_add = false);
+                                 float* lam_add = nullptr, bool clear_add = false, float* dFs = nullptr);
+// dFs (FP32, [nb][3][512]), where a call takes it, receives the force terms
+// instead of dF: the sum over one checkpoint segment.  adjoint_dF_flush adds
+// it to the FP64 dF and zeroes it.
+cudaError_t adjoint_dF_flush(double* dF, float* dFs, int64_t n, cudaStream_t s);
 
 // Per-node bounce masks and the kBlockBounce flag from a neighbour table and
 // an optional solid mask (bflags must hold kBlockSolidNear where solids are near).
