@@ -199,14 +199,23 @@ struct DownAdjArgs {
 //   rho = sum_j w_j rho_j, u = sum_j w_j u_j, sn = sum_j w_j (S_j - u_j u_j),
 //   stored (rho - 1, u, k sn + u u)
 // over the distinct coarse stencil nodes j (and over the old and new states
-// with weight 1/2 each at s = 2).  Coarse nodes are shared between fine
-// nodes, so their adjoints are accumulated with atomics.
-__global__ void k_down_adj(DownAdjArgs a) {
+// with weight 1/2 each at s = 2).  With lam = dL/d(stored) at n, the adjoint
+// with respect to (rho, u, sn) at n is the seed
+//   (lam_rho, lam_u + (d(u u)/du)^T lam_S, k lam_S),
+// and coarse node j receives, for every fine node n whose stencil holds it,
+// w_j times the transposed split S^neq = S - u_j u_j of the seed, taken at
+// j's own moments.  That map is linear in the seed, so j sums the weighted
+// seeds of its fine nodes first and applies it once: two passes, no atomics.
+
+// Pass 1, per I^d node: its seed, written over its lambda (which ends here:
+// the transfer overwrote the node).
+__global__ void k_down_adj_seed(DownAdjArgs a) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= a.n_nodes) return;
   const int32_t v = a.nodes[k];
   const int64_t b = v >> 9;
   const int cell = v & 511;
+  float* lf = a.lam_fine + b * kBlockVals + cell;
   const int32_t* c = a.fine.coords + 3 * b;
   const int p[3] = {c[0] * 8 + (cell & 7), c[1] * 8 + ((cell >> 3) & 7), c[2] * 8 + (cell >> 6)};
   const int n[3] = {a.coarse.d.nx * 8, a.coarse.d.ny * 8, a.coarse.d.nz * 8};
@@ -218,25 +227,28 @@ __global__ void k_down_adj(DownAdjArgs a) {
   const float w = 1.f / float(nq);
   int64_t cb[8];
   int cc[8];
-  for (int q = 0; q < nq; ++q) {
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
     const int qx = q % nx, qy = (q / nx) % ny, qz = q / (nx * ny);
     const int x = qx ? hi[0] : lo[0], y = qy ? hi[1] : lo[1], z = qz ? hi[2] : lo[2];
-    cb[q] = find_block(a.coarse, x, y, z);
+    cb[q] = q < nq ? find_block(a.coarse, x, y, z) : 0;
     cc[q] = node_cell(x, y, z);
-    if (cb[q] < 0) return;  // the forward transfer reported this already
+    ok = ok && cb[q] >= 0;
   }
-  // lambda at the fine node; the transfer overwrote the node, so its own
-  // adjoint ends here
-  float* lf = a.lam_fine + b * kBlockVals + cell;
+  if (!ok) {  // the forward transfer reported this already
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) lf[r * kCells] = 0.f;
+    return;
+  }
   float L[kRows];
 #pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    L[r] = lf[r * kCells];
-    lf[r * kCells] = 0.f;
-  }
+  for (int r = 0; r < kRows; ++r) L[r] = lf[r * kCells];
   // the interpolated velocity (FP64 sums as in the forward transfer)
   double su[3] = {0.0, 0.0, 0.0};
-  for (int q = 0; q < nq; ++q) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (q >= nq) break;
     float m[kRows];
     if (a.avg) {
       float o[kRows];
@@ -250,24 +262,167 @@ __global__ void k_down_adj(DownAdjArgs a) {
   }
   const float ux = float(su[0]), uy = float(su[1]), uz = float(su[2]);
   // adjoint of stored S = k sn + u u and of u
-  float lu[3];
-  lu[0] = L[1] + 2.f * ux * L[4] + uy * L[7] + uz * L[8];
-  lu[1] = L[2] + 2.f * uy * L[5] + ux * L[7] + uz * L[9];
-  lu[2] = L[3] + 2.f * uz * L[6] + ux * L[8] + uy * L[9];
-  float lsn[6];
+  lf[kCells] = L[1] + 2.f * ux * L[4] + uy * L[7] + uz * L[8];
+  lf[2 * kCells] = L[2] + 2.f * uy * L[5] + ux * L[7] + uz * L[9];
+  lf[3 * kCells] = L[3] + 2.f * uz * L[6] + ux * L[8] + uy * L[9];
 #pragma unroll
-  for (int r = 0; r < 6; ++r) lsn[r] = a.k * L[4 + r];
-  for (int q = 0; q < nq; ++q) {
-    float m[kRows], v[kRows];
-    load_f32(a.coarse.mom_other, cb[q], cc[q], m);
-    split_adjoint(m, a.avg ? 0.5f * w : w, L[0], lu, lsn, v);
-    add10(a.lam_old + cb[q] * kBlockVals + cc[q], v, true);
-    if (a.avg) {
-      load_f32(a.coarse.mom, cb[q], cc[q], m);
-      split_adjoint(m, 0.5f * w, L[0], lu, lsn, v);
-      add_lambda(a.lam_new, cb[q], cc[q], v, true);
+  for (int r = 4; r < kRows; ++r) lf[r * kCells] = a.k * L[r];
+}
+
+// Fine nodes along one axis whose stencil holds coarse index X (n coarse
+// nodes, 2n fine): 2X - 1 (wrapped on a periodic axis), 2X, 2X + 1, each
+// with its stencil width (1 or 2) along the axis, and whether it exists.
+__device__ __forceinline__ void fine_candidates(int X, int n, int periodic, int (&p)[3], int (&wdt)[3],
+                                                bool (&ok)[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int q = 2 * X + d - 1;
+    ok[d] = q >= 0 || periodic;
+    if (q < 0) q += 2 * n;
+    int lo, hi;
+    stencil_axis(q, n, periodic, lo, hi);
+    ok[d] = ok[d] && (lo == X || hi == X);
+    p[d] = q;
+    wdt[d] = lo != hi ? 2 : 1;
+  }
+}
+
+// Pass 2, per coarse node that some I^d stencil holds: the weighted seeds of
+// its fine nodes (bits: the I^d nodes of the fine level), the transposed split
+// at its old and, at s = 2, new moments, added to lambda_P and lambda_A.
+__global__ void k_down_adj_gather(DownAdjArgs a, const int32_t* __restrict__ targets, int64_t n_targets,
+                                  const uint32_t* __restrict__ fine_bits) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n_targets) return;
+  const int32_t v = targets[t];
+  const int64_t cb = v >> 9;
+  const int cc = v & 511;
+  const int32_t* c = a.coarse.coords + 3 * cb;
+  const int X[3] = {c[0] * 8 + (cc & 7), c[1] * 8 + ((cc >> 3) & 7), c[2] * 8 + (cc >> 6)};
+  const int n[3] = {a.coarse.d.nx * 8, a.coarse.d.ny * 8, a.coarse.d.nz * 8};
+  int px[3], py[3], pz[3], wx[3], wy[3], wz[3];
+  bool okx[3], oky[3], okz[3];
+  fine_candidates(X[0], n[0], a.periodic[0], px, wx, okx);
+  fine_candidates(X[1], n[1], a.periodic[1], py, wy, oky);
+  fine_candidates(X[2], n[2], a.periodic[2], pz, wz, okz);
+  float acc[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) acc[r] = 0.f;
+#pragma unroll
+  for (int iz = 0; iz < 3; ++iz)
+#pragma unroll
+    for (int iy = 0; iy < 3; ++iy)
+#pragma unroll
+      for (int ix = 0; ix < 3; ++ix) {
+        if (!(okx[ix] && oky[iy] && okz[iz])) continue;
+        const int64_t fb = find_block(a.fine, px[ix], py[iy], pz[iz]);
+        if (fb < 0) continue;
+        const int fc = node_cell(px[ix], py[iy], pz[iz]);
+        if (!((__ldg(fine_bits + fb * (kCells / 32) + (fc >> 5)) >> (fc & 31)) & 1u)) continue;
+        const float w = 1.f / float(wx[ix] * wy[iy] * wz[iz]);
+        const float* sd = a.lam_fine + fb * kBlockVals + fc;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) acc[r] = fmaf(w, sd[r * kCells], acc[r]);
+      }
+  const float lu[3] = {acc[1], acc[2], acc[3]};
+  const float lsn[6] = {acc[4], acc[5], acc[6], acc[7], acc[8], acc[9]};
+  float m[kRows], dl[kRows];
+  load_f32(a.coarse.mom_other, cb, cc, m);
+  split_adjoint(m, a.avg ? 0.5f : 1.f, acc[0], lu, lsn, dl);
+  add10(a.lam_old + cb * kBlockVals + cc, dl, false);
+  if (a.avg) {
+    load_f32(a.coarse.mom, cb, cc, m);
+    split_adjoint(m, 0.5f, acc[0], lu, lsn, dl);
+    add_lambda(a.lam_new, cb, cc, dl, false);
+  }
+}
+
+// Set-up of the gather, once per adjoint: bit of every I^d node of the fine
+// level, and bit of every coarse node that an I^d stencil holds.
+__global__ void k_mark_down(DownAdjArgs a, uint32_t* __restrict__ fine_bits, uint32_t* __restrict__ coarse_bits) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= a.n_nodes) return;
+  const int32_t v = a.nodes[k];
+  const int64_t b = v >> 9;
+  const int cell = v & 511;
+  atomicOr(fine_bits + b * (kCells / 32) + (cell >> 5), 1u << (cell & 31));
+  const int32_t* c = a.fine.coords + 3 * b;
+  const int p[3] = {c[0] * 8 + (cell & 7), c[1] * 8 + ((cell >> 3) & 7), c[2] * 8 + (cell >> 6)};
+  const int n[3] = {a.coarse.d.nx * 8, a.coarse.d.ny * 8, a.coarse.d.nz * 8};
+  int lo[3], hi[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) stencil_axis(p[ax], n[ax], a.periodic[ax], lo[ax], hi[ax]);
+  for (int q = 0; q < 8; ++q) {
+    const int x = (q & 1) ? hi[0] : lo[0], y = (q & 2) ? hi[1] : lo[1], z = (q & 4) ? hi[2] : lo[2];
+    const int64_t cb = find_block(a.coarse, x, y, z);
+    if (cb < 0) continue;
+    const int cc = node_cell(x, y, z);
+    atomicOr(coarse_bits + cb * (kCells / 32) + (cc >> 5), 1u << (cc & 31));
+  }
+}
+
+// Set bits of a level's node bitmap listed as (block << 9) | cell, in block
+// order: per-block counts, one exclusive scan, then the scatter.
+__global__ void __launch_bounds__(kCells) k_bits_count(const uint32_t* __restrict__ bits, int64_t* __restrict__ counts) {
+  __shared__ int s_cnt[kCells / 32];
+  const int64_t b = blockIdx.x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) s_cnt[w] = __popc(bits[b * (kCells / 32) + w]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int i = 0; i < kCells / 32; ++i) s += s_cnt[i];
+    counts[b] = s;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_counts_scan(int64_t* __restrict__ counts, int64_t nb,
+                                                      int64_t* __restrict__ total) {
+  __shared__ int64_t s_part[1024];
+  const int t = threadIdx.x;
+  const int64_t per = (nb + blockDim.x - 1) / blockDim.x;
+  const int64_t b0 = min(nb, int64_t(t) * per), b1 = min(nb, b0 + per);
+  int64_t sum = 0;
+  for (int64_t b = b0; b < b1; ++b) sum += counts[b];
+  s_part[t] = sum;
+  __syncthreads();
+  if (t == 0) {
+    int64_t run = 0;
+    for (int i = 0; i < int(blockDim.x); ++i) {
+      const int64_t c = s_part[i];
+      s_part[i] = run;
+      run += c;
+    }
+    *total = run;
+  }
+  __syncthreads();
+  int64_t run = s_part[t];
+  for (int64_t b = b0; b < b1; ++b) {
+    const int64_t c = counts[b];
+    counts[b] = run;
+    run += c;
+  }
+}
+
+__global__ void __launch_bounds__(kCells) k_bits_scatter(const uint32_t* __restrict__ bits,
+                                                         const int64_t* __restrict__ offs, int32_t* __restrict__ out) {
+  __shared__ int s_off[kCells / 32];
+  const int64_t b = blockIdx.x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t word = bits[b * (kCells / 32) + w];
+  if (lane == 0) s_off[w] = __popc(word);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int i = 0; i < kCells / 32; ++i) {
+      const int c = s_off[i];
+      s_off[i] = s;
+      s += c;
     }
   }
+  __syncthreads();
+  if (!((word >> lane) & 1u)) return;
+  out[offs[b] + s_off[w] + __popc(word & ((1u << lane) - 1u))] = int32_t((b << 9) | threadIdx.x);
 }
 
 struct UpAdjArgs {
@@ -324,14 +479,21 @@ __global__ void k_gather_nodes(const float* __restrict__ buf, const int32_t* __r
   for (int r = 0; r < kRows; ++r) log[k * kRows + r] = p[r * kCells];
 }
 
+// Puts the logged values back; lam, if set, is zeroed at the same nodes
+// (natural order).
 __global__ void k_scatter_nodes(float* __restrict__ buf, const int32_t* __restrict__ nodes, int64_t n,
-                                const float* __restrict__ log) {
+                                const float* __restrict__ log, float* __restrict__ lam) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int32_t v = nodes[k];
   float* p = buf + int64_t(v >> 9) * kBlockVals + node_offset<float>(v & 511);
 #pragma unroll
   for (int r = 0; r < kRows; ++r) p[r * kCells] = log[k * kRows + r];
+  if (lam != nullptr) {
+    float* q = lam + int64_t(v >> 9) * kBlockVals + (v & 511);
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) q[r * kCells] = 0.f;
+  }
 }
 
 inline unsigned grid_for(int64_t n) { return unsigned((n + 255) / 256); }
@@ -552,6 +714,60 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
     k_passthrough_bits<<<unsigned(Lv.nb), kCells, 0, st>>>(Lv.d_nbr, Lv.d_bflags, Lv.d_solid, ptb[l]);
     e = cudaGetLastError();
   }
+  // The gather of the transposed downward transfers: per level pair, the I^d
+  // bits of the fine level and the list of coarse nodes the I^d stencils hold
+  std::vector<uint32_t*> fbits(L, nullptr);
+  std::vector<int32_t*> tgt(L, nullptr);
+  std::vector<int64_t> n_tgt(L, 0);
+  {
+    std::vector<uint32_t*> cbits(L, nullptr);
+    std::vector<int64_t*> cnt(L, nullptr);
+    int64_t* d_tot = nullptr;
+    void* p;
+    if (get(size_t(L) * sizeof(int64_t), &p) == HLBM_OK) d_tot = static_cast<int64_t*>(p);
+    for (int l = 0; l + 1 < L && rc == HLBM_OK; ++l) {
+      const LevelData &F = h->lv[l], &C = h->lv[l + 1];
+      if (F.n_down == 0 || C.nb == 0) continue;
+      if (get(size_t(F.nb) * (kCells / 32) * sizeof(uint32_t), &p)) break;
+      fbits[l] = static_cast<uint32_t*>(p);
+      if (get(size_t(C.nb) * (kCells / 32) * sizeof(uint32_t), &p)) break;
+      cbits[l] = static_cast<uint32_t*>(p);
+      if (get(size_t(C.nb) * sizeof(int64_t), &p)) break;
+      cnt[l] = static_cast<int64_t*>(p);
+    }
+    for (int l = 0; l + 1 < L && rc == HLBM_OK && e == cudaSuccess; ++l) {
+      if (cnt[l] == nullptr) continue;
+      const LevelData &F = h->lv[l], &C = h->lv[l + 1];
+      e = cudaMemsetAsync(fbits[l], 0, size_t(F.nb) * (kCells / 32) * sizeof(uint32_t), st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(cbits[l], 0, size_t(C.nb) * (kCells / 32) * sizeof(uint32_t), st);
+      if (e != cudaSuccess) break;
+      DownAdjArgs d{};
+      d.fine = level_view(h, l, nullptr, nullptr);
+      d.coarse = level_view(h, l + 1, nullptr, nullptr);
+      d.nodes = F.d_down;
+      d.n_nodes = F.n_down;
+      for (int ax = 0; ax < 3; ++ax) d.periodic[ax] = h->cfg.periodic[ax];
+      k_mark_down<<<grid_for(F.n_down), 256, 0, st>>>(d, fbits[l], cbits[l]);
+      k_bits_count<<<unsigned(C.nb), kCells, 0, st>>>(cbits[l], cnt[l]);
+      k_counts_scan<<<1, 1024, 0, st>>>(cnt[l], C.nb, d_tot + l);
+      e = cudaGetLastError();
+    }
+    std::vector<int64_t> tot(size_t(L), 0);
+    if (rc == HLBM_OK && e == cudaSuccess) e = cudaMemcpyAsync(tot.data(), d_tot, L * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (rc == HLBM_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (int l = 0; l + 1 < L && rc == HLBM_OK && e == cudaSuccess; ++l) {
+      if (cnt[l] == nullptr || tot[size_t(l)] == 0) continue;
+      if (get(size_t(tot[size_t(l)]) * sizeof(int32_t), &p)) break;
+      tgt[l] = static_cast<int32_t*>(p);
+      n_tgt[l] = tot[size_t(l)];
+      k_bits_scatter<<<unsigned(h->lv[l + 1].nb), kCells, 0, st>>>(cbits[l], cnt[l], tgt[l]);
+      e = cudaGetLastError();
+    }
+    if (rc != HLBM_OK) {
+      release_all();
+      return rc;
+    }
+  }
   // Per level: plain (lamA holds lambda) or fused (lamA holds mu, raw holds
   // lambda at the pass-through nodes; fpre is the recorded p of the level's
   // next SC to reverse, whose transposed collision mu already includes).
@@ -689,9 +905,10 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         d.lam_fine = fused[l] ? raw[l] : lamA[l];
         d.lam_new = target(l + 1);
         d.lam_old = lamP[l + 1];
-        k_down_adj<<<grid_for(F.n_down), 256, 0, st>>>(d);
+        k_down_adj_seed<<<grid_for(F.n_down), 256, 0, st>>>(d);
+        if (n_tgt[l] > 0) k_down_adj_gather<<<grid_for(n_tgt[l]), 256, 0, st>>>(d, tgt[l], n_tgt[l], fbits[l]);
         k_scatter_nodes<<<grid_for(F.n_down), 256, 0, st>>>(static_cast<float*>(op.in), F.d_down, F.n_down,
-                                                            op.undo);
+                                                            op.undo, d.lam_fine);
       } else {
         const LevelData& C = h->lv[l + 1];
         if (C.n_up == 0) continue;
@@ -704,7 +921,8 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         u.lam_fine = target(l);
         u.lam_coarse = fused[l + 1] ? raw[l + 1] : lamA[l + 1];
         k_up_adj<<<grid_for(C.n_up), 256, 0, st>>>(u);
-        k_scatter_nodes<<<grid_for(C.n_up), 256, 0, st>>>(static_cast<float*>(op.in), C.d_up, C.n_up, op.undo);
+        k_scatter_nodes<<<grid_for(C.n_up), 256, 0, st>>>(static_cast<float*>(op.in), C.d_up, C.n_up, op.undo,
+                                                          nullptr);
       }
       if (e == cudaSuccess) e = cudaGetLastError();
     }
