@@ -73,14 +73,9 @@ __device__ __forceinline__ void split_adjoint(const float (&m)[kRows], float w, 
   for (int r = 0; r < 6; ++r) v[4 + r] = w * lsn[r];
 }
 
-__device__ __forceinline__ void add10(float* lam, const float (&v)[kRows], bool atomic) {
+__device__ __forceinline__ void add10(float* lam, const float (&v)[kRows]) {
 #pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    if (atomic)
-      atomicAdd(lam + r * kCells, v[r]);
-    else
-      lam[r * kCells] += v[r];
-  }
+  for (int r = 0; r < kRows; ++r) lam[r * kCells] += v[r];
 }
 
 // Pass-through nodes of a level: solid nodes and nodes next to a neighbour
@@ -113,7 +108,8 @@ __global__ void __launch_bounds__(kCells) k_passthrough_bits(const int32_t* __re
 // addition dlam at an ordinary node of a fused level goes through that
 // transposed collision (recorded p = pre): (dC/dp)^T dlam into mu and, on the
 // level with the force field, (dC/dF)^T dlam into dL/dF; the map is linear in
-// dlam, so additions may come one by one.
+// dlam, so additions may come one by one.  Each node has one writer per
+// launch (no atomics).
 struct LamTarget {
   const uint32_t* pt;  // pass-through bits, or null (plain)
   float* raw;
@@ -126,11 +122,10 @@ struct LamTarget {
   float* dF;           // dL/dF of the current checkpoint segment [nb][3][512] (FP32), or null
 };
 
-__device__ __forceinline__ void add_lambda(const LamTarget& g, int64_t blk, int cell, const float (&v)[kRows],
-                                           bool atomic) {
+__device__ __forceinline__ void add_lambda(const LamTarget& g, int64_t blk, int cell, const float (&v)[kRows]) {
   const int64_t o = blk * kBlockVals + cell;
   if (g.pt == nullptr || ((g.pt[blk * (kCells / 32) + (cell >> 5)] >> (cell & 31)) & 1u)) {
-    add10(g.raw + o, v, atomic);
+    add10(g.raw + o, v);
     return;
   }
   const float* q = g.pre + o;
@@ -168,18 +163,12 @@ __device__ __forceinline__ void add_lambda(const LamTarget& g, int64_t blk, int 
   float lfx, lfy, lfz;
   collide_vjp(p, fx, fy, fz, om, lo, lp, lfx, lfy, lfz);
   const float w[kRows] = {lp.drho, lp.jx, lp.jy, lp.jz, lp.pxx, lp.pyy, lp.pzz, lp.pxy, lp.pxz, lp.pyz};
-  add10(g.mu + o, w, atomic);
+  add10(g.mu + o, w);
   if (g.dF != nullptr) {
     float* d = g.dF + blk * 3 * kCells + cell;
-    if (atomic) {
-      atomicAdd(d, lfx);
-      atomicAdd(d + kCells, lfy);
-      atomicAdd(d + 2 * kCells, lfz);
-    } else {
-      d[0] += lfx;
-      d[kCells] += lfy;
-      d[2 * kCells] += lfz;
-    }
+    d[0] += lfx;
+    d[kCells] += lfy;
+    d[2 * kCells] += lfz;
   }
 }
 
@@ -329,11 +318,11 @@ __global__ void k_down_adj_gather(DownAdjArgs a, const int32_t* __restrict__ tar
   float m[kRows], dl[kRows];
   load_f32(a.coarse.mom_other, cb, cc, m);
   split_adjoint(m, a.avg ? 0.5f : 1.f, acc[0], lu, lsn, dl);
-  add10(a.lam_old + cb * kBlockVals + cc, dl, false);
+  add10(a.lam_old + cb * kBlockVals + cc, dl);
   if (a.avg) {
     load_f32(a.coarse.mom, cb, cc, m);
     split_adjoint(m, 0.5f, acc[0], lu, lsn, dl);
-    add_lambda(a.lam_new, cb, cc, dl, false);
+    add_lambda(a.lam_new, cb, cc, dl);
   }
 }
 
@@ -465,7 +454,7 @@ __global__ void k_up_adj(UpAdjArgs a) {
   dl[3] = L[3] + e * (2.f * uz * L[6] + ux * L[8] + uy * L[9]);
 #pragma unroll
   for (int r = 4; r < kRows; ++r) dl[r] = a.k * L[r];
-  add_lambda(a.lam_fine, fb, fc, dl, false);
+  add_lambda(a.lam_fine, fb, fc, dl);
 }
 
 // Undo log of the transfers: the 10 stored values of each listed node.
