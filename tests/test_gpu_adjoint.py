@@ -80,6 +80,7 @@ def test_gradient_matches_oracle_reverse_mode(storage, tol):
     assert abs(Lg - Lo.item()) <= 1e-5 * abs(Lo.item())
     fluid = ~solid.astype(bool)
     err = np.abs(g - go)[:, fluid].max() / np.abs(go).max()
+    print("%s adjoint, 12 steps with an obstacle: max |g - oracle| / max |g| = %.2e" % (storage, err))
     assert err < tol, err
 
 

@@ -71,6 +71,7 @@ def test_ml_adjoint_matches_oracle_reverse_mode(name):
     scale = np.abs(ref).max()
     assert scale > 0
     err = np.abs(got - ref).max() / scale
+    print("%s multi-level adjoint: max |g - oracle| / max |g| = %.2e" % (name, err))
     assert err < 1e-4, err
 
 
@@ -94,6 +95,7 @@ def test_ml_adjoint_matches_central_differences():
     rng = np.random.default_rng(23)
     h = 2.0 ** -17  # exact in FP32 next to |F| ~ 1e-5
     scale = np.abs(got).max()
+    worst = 0.0
     for _ in range(4):
         b, r, n = int(rng.integers(len(coords[0]))), int(rng.integers(3)), int(rng.integers(512))
         x = coords[0][b, 0] * 8 + n % 8
@@ -104,6 +106,8 @@ def test_ml_adjoint_matches_central_differences():
         Fm[r, z, y, x] -= h
         fd = (loss(Fp) - loss(Fm)) / (float(np.float32(F32[r, z, y, x] + h)) - float(np.float32(F32[r, z, y, x] - h)))
         assert abs(fd - got[b, r, n]) < 1e-4 * scale, (b, r, n, fd, got[b, r, n])
+        worst = max(worst, abs(fd - got[b, r, n]) / scale)
+    print("multi-level adjoint, central differences on 4 cells: max |g - fd| / max |g| = %.2e" % worst)
 
 
 def test_ml_autograd_function_and_refusals():
