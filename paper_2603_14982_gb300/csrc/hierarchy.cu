@@ -360,16 +360,29 @@ __global__ void k_count_changes(const uint8_t* __restrict__ hn, const uint8_t* _
   const unsigned r = __ballot_sync(0xffffffffu, in && hn[i] && !ho[i]);
   const unsigned c = __ballot_sync(0xffffffffu, in && !hn[i] && ho[i]);
   const unsigned d = __ballot_sync(0xffffffffu, in && so[i] && !sn[i]);
+  const unsigned a = __ballot_sync(0xffffffffu, in && sn[i] && !so[i]);
   if ((threadIdx.x & 31) == 0) {
     if (r) atomicAdd(out + 0, (unsigned long long)__popc(r));
     if (c) atomicAdd(out + 1, (unsigned long long)__popc(c));
     if (d) atomicAdd(out + 2, (unsigned long long)__popc(d));
+    if (a) atomicAdd(out + 3, (unsigned long long)__popc(a));
   }
+}
+
+__global__ void k_clear_change_flags(uint8_t* __restrict__ f, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = uint8_t(f[i] & (kFlagLeaf | kFlagBorder));
 }
 
 inline unsigned grid_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t clear_change_flags(uint8_t* flags, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_clear_change_flags<<<grid_for(n, 256), 256, 0, s>>>(flags, n);
+  return cudaGetLastError();
+}
 
 cudaError_t occupancy_from_particles(const float* pos, int64_t n, GridDims d0, uint8_t* occ, int* bad,
                                      cudaStream_t s) {

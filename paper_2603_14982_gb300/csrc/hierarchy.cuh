@@ -106,8 +106,13 @@ cudaError_t interface_count(const int32_t* nbr, const uint8_t* skip, int64_t nb,
 cudaError_t interface_scatter(const int32_t* nbr, const uint8_t* skip, int64_t nb, const int64_t* scratch,
                               int32_t* down, int32_t* up, cudaStream_t s);
 
-// Adds to counts_dev[0..2] the slots newly in H (refined), newly out of H
-// (coarsened) and stored before but not now (deleted) on one level's grid.
+// Keeps only the leaf / border bits of n list flags (an unchanged hierarchy:
+// nothing is new, refined or coarsened).
+cudaError_t clear_change_flags(uint8_t* flags, int64_t n, cudaStream_t s);
+
+// Adds to counts_dev[0..3] the slots newly in H (refined), newly out of H
+// (coarsened), stored before but not now (deleted) and stored now but not
+// before (added) on one level's grid.
 cudaError_t count_changes(const uint8_t* H_new, const uint8_t* H_old, const uint8_t* stored_new,
                           const uint8_t* stored_old, int64_t slots, unsigned long long* counts_dev, cudaStream_t s);
 

@@ -287,9 +287,50 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     cleanup();
     return rc;
   }
+  // changes against the installed hierarchy, read back with the block counts
+  unsigned long long changes[4] = {0, 0, 0, 0};
+  unsigned long long* d_changes = reinterpret_cast<unsigned long long*>(d_tot + 3 * L);
+  if (has_old) {
+    ML_CUDA(h, cudaMemsetAsync(d_changes, 0, 4 * sizeof(unsigned long long), st));
+    for (int l = 0; l < L; ++l)
+      ML_CUDA(h, count_changes(nl[l].d_H, h->lv[l].d_H, nl[l].d_stored, h->lv[l].d_stored, dims_of(h, l).slots(),
+                               d_changes, st));
+    ML_CUDA(h, cudaMemcpyAsync(changes, d_changes, sizeof(changes), cudaMemcpyDeviceToHost, st));
+  }
   std::vector<int64_t> nb(L);
   ML_CUDA(h, cudaMemcpyAsync(nb.data(), d_tot, L * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   ML_CUDA(h, cudaStreamSynchronize(st));
+  if (has_old && changes[0] == 0 && changes[1] == 0 && changes[2] == 0 && changes[3] == 0) {
+    // the same hierarchy: the installed levels stay (lists, neighbour and
+    // interface tables, moments); what the full path does to unchanged blocks
+    // is done in place: the interface refill from the coarser level and the
+    // scale refit, and the list flags keep their leaf / border bits only
+    free_new();
+    cleanup();
+    int rc1 = HLBM_OK;
+    for (int l = L - 2; l >= 0 && rc1 == HLBM_OK; --l) rc1 = downward(h, l, 1, true);
+    for (int l = 0; l < L && rc1 == HLBM_OK; ++l) {
+      LevelData& X = h->lv[l];
+      if (X.d_list_flags != nullptr) ML_CUDA(h, clear_change_flags(X.d_list_flags, X.nb, st));
+      X.host_lists = false;
+      rc1 = LatticeOps::maybe_rescale(h, X, true);
+    }
+    if (rc1) return rc1;
+    int status[2] = {0, 0};
+    ML_CUDA(h, cudaMemcpyAsync(status, h->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    ML_CUDA(h, cudaStreamSynchronize(st));
+    void* v = h->d_F;
+    LatticeOps::release(h, v);
+    h->d_F = nullptr;
+    v = h->d_eps;
+    LatticeOps::release(h, v);
+    h->d_eps = nullptr;
+    ++h->hier_gen;
+    if (counts_out != nullptr) counts_out[0] = counts_out[1] = counts_out[2] = 0;
+    if (status[0] == 1) return fail(h, HLBM_E_BAD_STATE, "a transfer stencil reached a node that is not stored");
+    if (status[1]) return fail(h, HLBM_E_NONFINITE, "%d particle positions are not finite (ignored)", status[1]);
+    return HLBM_OK;
+  }
 
   // 4. neighbour tables and interface node lists; with the spatial-hash block
   // table, each level's hash is built from its list first, the neighbour
@@ -400,16 +441,8 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     ML_TRY(LatticeOps::maybe_rescale(h, nl[l], true));
   }
 
-  // 6. host copies of the lists; counts of refined / coarsened / deleted blocks
-  unsigned long long changes[3] = {0, 0, 0};
-  unsigned long long* d_changes = reinterpret_cast<unsigned long long*>(d_tot + 3 * L);
-  if (counts_out != nullptr && has_old) {
-    ML_CUDA(h, cudaMemsetAsync(d_changes, 0, 3 * sizeof(unsigned long long), st));
-    for (int l = 0; l < L; ++l)
-      ML_CUDA(h, count_changes(nl[l].d_H, h->lv[l].d_H, nl[l].d_stored, h->lv[l].d_stored, dims_of(h, l).slots(),
-                               d_changes, st));
-    ML_CUDA(h, cudaMemcpyAsync(changes, d_changes, sizeof(changes), cudaMemcpyDeviceToHost, st));
-  }
+  // 6. the counts of refined / coarsened / deleted blocks came back with the
+  // block counts
   // the host copies of the block lists are made on demand (hlbm_get_blocks);
   // one readback brings the status words (transfer status, dropped particles)
   for (int l = 0; l < L; ++l) nl[l].host_lists = false;
