@@ -53,15 +53,21 @@ __global__ void k_dilate_parent(const uint8_t* __restrict__ src, GridDims ds, ui
   const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= d.slots()) return;
   const int x = int(q % d.nx), y = int((q / d.nx) % d.ny), z = int(q / (int64_t(d.nx) * d.ny));
-  uint8_t hit = 0;
-  for (int dz = -1; dz <= 1 && !hit; ++dz)
-    for (int dy = -1; dy <= 1 && !hit; ++dy)
-      for (int dx = -1; dx <= 1 && !hit; ++dx) {
+  // all loads independent (no early exit): the two x-children of a child row
+  // are one aligned 16-bit word (the finer grid is 2 d.nx wide)
+  unsigned hit = 0;
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
         int a = x + dx, b = y + dy, c = z + dz;
         if (!wrap(a, d.nx, px) || !wrap(b, d.ny, py) || !wrap(c, d.nz, pz)) continue;
-        for (int k = 0; k < 8 && !hit; ++k) {
-          const int cx = 2 * a + (k & 1), cy = 2 * b + ((k >> 1) & 1), cz = 2 * c + (k >> 2);
-          hit = src[slot_of(ds, cx, cy, cz)];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int cy = 2 * b + (k & 1), cz = 2 * c + (k >> 1);
+          hit |= __ldg(reinterpret_cast<const uint16_t*>(src + slot_of(ds, 2 * a, cy, cz)));
         }
       }
   H[q] = hit ? 1 : 0;
