@@ -572,6 +572,14 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
   const LamSource src{d.lamp};
   f2::stream_pairs(src, a, blk, f2buf, s_miss, cx);
   const int own = cx.own;
+  // the fused epilogue's reads from global memory, issued before the gather
+  // and the transposed arithmetic so that their latency overlaps them
+  PreMom<V2> pp_early;
+  Mom<V2> in_early;
+  if constexpr (kFuse) {
+    pp_early = LamSource{d.pre_prev}.pair(blk, own);
+    in_early = load_pair<T>(static_cast<const T*>(a.in), blk, own, a.scales_in);
+  }
   bool fz_lo = false, fz_hi = false;  // solid nodes: M'(y) = M(y)
   if (cx.solid_any) {
     fz_lo = a.solid[blk * kCells + own] != 0;
@@ -602,7 +610,10 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
 #pragma unroll
     for (int j = 0; j < 27; ++j) gh_in[j] = g[26 - j];
     const Coef<V2> gh = adjoint_moments(gh_in);
-    lm = coef_vjp(load_pair<T>(static_cast<const T*>(a.in), blk, own, a.scales_in), gh, V2(a.kxyzf));
+    if constexpr (kFuse)
+      lm = coef_vjp(in_early, gh, V2(a.kxyzf));
+    else
+      lm = coef_vjp(load_pair<T>(static_cast<const T*>(a.in), blk, own, a.scales_in), gh, V2(a.kxyzf));
   }
   V2 out[kRows] = {lm.drho, lm.ux, lm.uy, lm.uz, lm.sxx, lm.syy, lm.szz, lm.sxy, lm.sxz, lm.syz};
   const bool pt_lo = fz_lo || cp_lo, pt_hi = fz_hi || cp_hi;
@@ -657,8 +668,7 @@ __global__ void __launch_bounds__(f2::kThreads, 2) k_adj_push2(StepArgs a, AdjAr
     lo.sxy = out[7];
     lo.sxz = out[8];
     lo.syz = out[9];
-    collide_adj_pair(a, blk, own, LamSource{d.pre_prev}.pair(blk, own), lo, pt_lo, pt_hi, d.lamp_out, d.dF,
-                     d.dFs);
+    collide_adj_pair(a, blk, own, pp_early, lo, pt_lo, pt_hi, d.lamp_out, d.dF, d.dFs);
   } else {
     store_pair10(d.lam_out, blk, own, out, false, false);
   }
