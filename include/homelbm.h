@@ -160,7 +160,11 @@ int32_t hlbm_set_blocks(hlbm_lattice *h, int32_t level, const int32_t *coords_xy
    refined (newly in H), coarsened (newly out of H) and deleted blocks summed
    over levels.  Must be called at a coarse-step boundary.  The level-0 force
    field is dropped (set it again for the new block list).  Non-finite
-   positions are ignored and reported with HLBM_E_NONFINITE after the rebuild. */
+   positions are ignored and reported with HLBM_E_NONFINITE after the rebuild.
+   A hierarchy equal to the installed one (no block refined, coarsened,
+   deleted or added on any level) keeps the installed levels, lists and
+   moments; the interfaces are refilled from the coarser level and the flags
+   lose their new / refine / coarsen bits, as a full rebuild would leave them. */
 int32_t hlbm_rebuild_from_particles(hlbm_lattice *h, const float *pos_xyz, int64_t n, int32_t on_device,
                                     int64_t counts_out[3]);
 
