@@ -451,6 +451,45 @@ def bench_multilevel(hl, wl, stream, storage, pos0, n=512, fine_steps=500, rebui
             "finite": bool(np.isfinite(red[0])), **({"profile": prof} if prof is not None else {})}, moms
 
 
+def bench_open_dune(hl, wl, stream, open_faces=True, extent=(512, 128, 256), fine_steps=64):
+    """Three-level channel over a resting sand heap (a dune-shaped seeded
+    particle cloud on the floor): logarithmic inlet at x-, convective outflow
+    at x+ and on the top face, bounce-back floor, periodic z; the hierarchy
+    from the heap, the fluid fraction deposited from it.  With
+    open_faces=False the same lattice is periodic in x (the open faces'
+    cost is the difference).  Device time of fine_steps fine steps (CUDA
+    events), then the open-face updates' share from the library's profile."""
+    import torch
+    L, per = 3, 4
+    pos = torch.tensor(wl.sand_heap(extent), device="cuda")
+    periodic = (not open_faces, False, True)
+    with hl.Lattice(extent, levels=L, tau=0.9, periodic=periodic, storage="f32", stream=stream.cuda_stream) as lat:
+        if open_faces:
+            lat.set_open_faces([hl.FACE_INLET, hl.FACE_OUTFLOW, hl.FACE_CLOSED, hl.FACE_OUTFLOW,
+                                hl.FACE_CLOSED, hl.FACE_CLOSED], u0=0.005, beta=1.0, h0=0.0, profile_axis=1)
+        lat.rebuild_from_particles(pos)
+        lat.deposit_particles(pos, moving=False)
+        counts = [lat.num_blocks(l) for l in range(L)]
+        lat.step(2 * per)
+        ms = timed(stream, lambda: lat.step(fine_steps))
+        lat.set_profiling(True)
+        lat.step(fine_steps)
+        prof = lat.profile()
+        lat.set_profiling(False)
+        red = lat.reduce()
+    updates = sum(counts[l] * 512 * 2 ** (L - 1 - l) for l in range(L)) * fine_steps // per
+    updates0 = counts[0] * 512 * fine_steps
+    actual_gbs = (updates * 80.0 + updates0 * 16.0) / (ms / 1e3) / 1e9
+    peak, _ = measured_peaks()
+    prof_total = sum(v[0] for v in prof.values())
+    return {"extent": list(extent), "open_faces": bool(open_faces), "levels": L, "blocks_per_level": counts,
+            "fine_steps": fine_steps, "ms_per_fine_step": round(ms / fine_steps, 4),
+            "mlups_fine_equiv": round(extent[0] * extent[1] * extent[2] * fine_steps / ms / 1e3, 1),
+            "actual_gbs": round(actual_gbs, 1), "actual_gbs_over_peak": round(actual_gbs / peak, 4),
+            "open_face_share": round(prof["open_faces"][0] / prof_total, 4) if prof_total > 0 else 0.0,
+            "mass": float(red[0]), "finite": bool(np.isfinite(red[0]))}
+
+
 def bench_duct_storage(hl, stream, storage, n=256, steps=100, warmup=10):
     """The same duct in another moment storage: device time per step, MLUPS and
     the algorithmic bytes (40 per node in FP16/BF16-scaled storage) over the
@@ -495,6 +534,10 @@ def bench_extras(hl, wl):
     rec["mlups_vs_uncoupled"] = round(rec["mlups_fine_equiv"] / ml["f32"]["mlups_fine_equiv"], 3)
     out["c3_coupled"] = rec
     out["c3_adjoint"] = bench_ml_adjoint(hl, wl, stream, pos0)
+    dune = bench_open_dune(hl, wl, stream)
+    closed = bench_open_dune(hl, wl, stream, open_faces=False)
+    dune["ms_per_fine_step_periodic_x"] = closed["ms_per_fine_step"]
+    out["f3_open_dune"] = dune
     out["sparse_tree_2048"] = bench_sparse(hl, wl, stream)
     hashed = bench_sparse(hl, wl, stream, lookup=1)
     out["sparse_tree_2048_hash"] = {k: hashed[k] for k in ("ms_per_fine_step", "mlups_fine_equiv", "build_s",
@@ -549,7 +592,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the multi-level, adjoint and batched workloads")
-    ap.add_argument("--only", choices=["multilevel", "adjoint", "batched", "ml_adjoint", "sparse"],
+    ap.add_argument("--only", choices=["multilevel", "adjoint", "batched", "ml_adjoint", "sparse", "open_dune"],
                     help="run one secondary workload alone and print its JSON (profiling runs)")
     ap.add_argument("--profile", action="store_true",
                     help="with --only multilevel: stream time per kernel class from the library's CUDA events")
@@ -571,6 +614,9 @@ def main():
             res = bench_sparse(hl, wl, stream)
         elif args.only == "ml_adjoint":
             res = bench_ml_adjoint(hl, wl, stream, torch.tensor(wl.particle_cloud(512), device="cuda"))
+        elif args.only == "open_dune":
+            res = bench_open_dune(hl, wl, stream)
+            res["ms_per_fine_step_periodic_x"] = bench_open_dune(hl, wl, stream, open_faces=False)["ms_per_fine_step"]
         else:
             pos0 = torch.tensor(wl.particle_cloud(512), device="cuda")
             bench_multilevel(hl, wl, stream, "f32", pos0, fine_steps=48)
@@ -668,6 +714,9 @@ def main():
             "c3_rebuild_share": round(c3["f32"]["rebuild_s"] / c3["f32"]["total_s"], 4),
             "c3_adjoint_over_forward": ex["c3_adjoint"]["adjoint_over_forward"],
             "sparse_2048_mlups": ex["sparse_tree_2048"]["mlups_fine_equiv"],
+            "open_dune_mlups": ex["f3_open_dune"]["mlups_fine_equiv"],
+            "open_dune_over_periodic": round(ex["f3_open_dune"]["ms_per_fine_step_periodic_x"] /
+                                             ex["f3_open_dune"]["ms_per_fine_step"], 3),
         }
     print(json.dumps(line))
     if world > 1:

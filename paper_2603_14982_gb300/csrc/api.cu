@@ -164,6 +164,9 @@ void LatticeOps::free_level(hlbm_lattice* h, LevelData& L) {
   void* v = L.d_nbr;
   release(h, v);
   L.d_nbr = nullptr;
+  v = L.d_open;
+  release(h, v);
+  L.d_open = nullptr;
   v = L.d_bflags;
   release(h, v);
   L.d_bflags = nullptr;
@@ -643,6 +646,7 @@ int32_t hlbm_step(hlbm_lattice* h, int32_t n_fine_steps) {
     return fail(h, HLBM_E_INVALID_ARG, "n_fine_steps must be a non-negative multiple of %d", per);
   int rc = LatticeOps::set_device(h);
   if (rc) return rc;
+  if ((rc = LatticeOps::open_lists(h))) return rc;  // before anything is written
   if (h->device_hierarchy) return ml_advance_coarse(h, n_fine_steps / per);
   LevelData& L = h->lv[0];
   StepArgs a{};

@@ -27,6 +27,7 @@ namespace {
 struct OpenArgs {
   const void* in;
   void* out;
+  const int32_t* open;    // [nb + 1]: blocks with an open neighbour, then their count
   const int32_t* nbr;
   const int32_t* coords;  // [nb][3] block coordinates, or null: dense slot order
   GridDims d;             // block grid of the level
@@ -43,17 +44,30 @@ __device__ __forceinline__ R comp(const Mom<R>& m, int a) {
   return a == 0 ? m.ux : (a == 1 ? m.uy : m.uz);
 }
 
+// The blocks with an open neighbour, one warp per block, in any order (each
+// block's face update touches only its own nodes).
+__global__ void k_open_list(const int32_t* __restrict__ nbr, int64_t nb, int32_t* __restrict__ list) {
+  const int64_t blk = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (blk >= nb) return;
+  const bool o = lane < 27 && nbr[blk * 27 + lane] == kOpen;
+  if (__ballot_sync(0xffffffffu, o) != 0u && lane == 0) list[atomicAdd(&list[nb], 1)] = int32_t(blk);
+}
+
+template <typename T>
+__device__ __forceinline__ void open_face_block(const OpenArgs& a, int64_t blk);
+
+// One CTA per listed block, a fixed grid walking the list.
 template <typename T>
 __global__ void __launch_bounds__(512) k_open_faces(OpenArgs a) {
+  const int n = a.open[a.nb];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) open_face_block<T>(a, a.open[i]);
+}
+
+template <typename T>
+__device__ __forceinline__ void open_face_block(const OpenArgs& a, int64_t blk) {
   using R = typename StorageTraits<T>::R;
-  __shared__ int s_open;
-  const int64_t blk = blockIdx.x;
   const int cell = threadIdx.x;
-  if (cell == 0) s_open = 0;
-  __syncthreads();
-  if (cell < 27 && a.nbr[blk * 27 + cell] == kOpen) s_open = 1;
-  __syncthreads();
-  if (!s_open) return;
   int c[3];
   if (a.coords != nullptr) {
     c[0] = a.coords[3 * blk];
@@ -117,12 +131,33 @@ __global__ void __launch_bounds__(512) k_open_faces(OpenArgs a) {
 
 }  // namespace
 
+int LatticeOps::open_lists(hlbm_lattice* h) {
+  if (h->open_mask() == 0u || !h->have_blocks) return HLBM_OK;
+  for (int l = 0; l < h->cfg.num_levels; ++l) {
+    LevelData& L = h->lv[l];
+    if (L.nb == 0 || L.d_open != nullptr) continue;
+    void* p = nullptr;
+    int rc = LatticeOps::alloc(h, &p, size_t(L.nb + 1) * sizeof(int32_t));
+    if (rc) return rc;
+    L.d_open = static_cast<int32_t*>(p);
+    cudaError_t e = cudaMemsetAsync(L.d_open + L.nb, 0, sizeof(int32_t), h->stream);
+    if (e == cudaSuccess) {
+      k_open_list<<<unsigned((L.nb * 32 + 255) / 256), 256, 0, h->stream>>>(L.d_nbr, L.nb, L.d_open);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "open faces: %s", cudaGetErrorString(e));
+  }
+  return HLBM_OK;
+}
+
 int open_faces_step(hlbm_lattice* h, int level, const void* in, void* out) {
   const LevelData& L = h->lv[level];
   if (L.nb == 0 || h->open_mask() == 0u) return HLBM_OK;
+  if (L.d_open == nullptr) return fail(h, HLBM_E_BAD_STATE, "open faces: the block list was not made");
   OpenArgs a{};
   a.in = in;
   a.out = out;
+  a.open = L.d_open;
   a.nbr = L.d_nbr;
   a.coords = h->device_hierarchy ? L.d_coords : nullptr;
   int dims[3];
@@ -136,7 +171,7 @@ int open_faces_step(hlbm_lattice* h, int level, const void* in, void* out) {
   a.h0 = float(h->inlet_h0);
   a.axis = h->inlet_axis;
   a.sc = L.d_scales;
-  const unsigned grid = unsigned(L.nb);
+  const unsigned grid = unsigned(L.nb < 1216 ? L.nb : 1216);  // 8 CTAs of 512 per SM on 152 SMs
   switch (h->cfg.storage) {
     case HLBM_STORE_F64: k_open_faces<double><<<grid, 512, 0, h->stream>>>(a); break;
     case HLBM_STORE_F32: k_open_faces<float><<<grid, 512, 0, h->stream>>>(a); break;
@@ -178,9 +213,13 @@ extern "C" int32_t hlbm_set_open_faces(hlbm_lattice* h, const int32_t type[6], d
   h->inlet_h0 = h0;
   h->inlet_axis = profile_axis;
   if (!h->have_blocks) return HLBM_OK;
-  // rebuild the neighbour tables and bounce masks of the stored levels
+  // rebuild the neighbour tables and bounce masks of the stored levels (the
+  // lists of open blocks are made again by the next step)
   for (int l = 0; l < h->cfg.num_levels; ++l) {
     LevelData& L = h->lv[l];
+    void* v = L.d_open;
+    LatticeOps::release(h, v);
+    L.d_open = nullptr;
     if (L.nb == 0) continue;
     if (h->device_hierarchy) {
       int dims[3];

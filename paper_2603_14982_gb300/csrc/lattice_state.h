@@ -46,6 +46,8 @@ struct LevelData {
                                    // demand for hierarchies built on the device)
   uint8_t* d_list_flags = nullptr; // [nb] flags of the device-built list
   int32_t* d_nbr = nullptr;        // [nb][27]
+  int32_t* d_open = nullptr;       // [nb + 1]: the blocks with an open neighbour, their count last (made
+                                   // by the first step with open faces; dropped with the neighbour tables)
   void* d_mom[2] = {nullptr, nullptr};  // ping-pong moment buffers [nb][10][512]
   int cur = 0;                     // buffer holding the current state
   double tau = 0;                  // level relaxation time
@@ -196,6 +198,7 @@ struct LatticeOps {
   static int bounce(hlbm_lattice* h, LevelData& L);
   // Make L.coords / L.flags current (one device-to-host copy after a rebuild).
   static int host_lists(hlbm_lattice* h, LevelData& L);
+  static int open_lists(hlbm_lattice* h);
   static void build_nbr(const hlbm_lattice* h, int level, const std::vector<int32_t>& coords,
                         const std::vector<int32_t>& slot_to_idx, std::vector<int32_t>& nbr);
 };

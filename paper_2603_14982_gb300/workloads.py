@@ -108,6 +108,26 @@ def particle_cloud(n_fine, count=2_000_000, seed=SEED_CLOUD, box=(0.2, 0.4, 0.2)
     return pos.astype(np.float32)
 
 
+def sand_heap(extent, count=600_000, seed=SEED_CLOUD, x0_frac=0.4, sigma_frac=0.12, height_frac=0.25):
+    """Particles (float32 (count, 3), fine-node units) filling a dune-shaped heap
+    on the floor y = 0 of an extent = (nx, ny, nz) domain: the heap spans z,
+    its height along x is height_frac ny exp(-((x - x0) / sigma)^2 / 2) with
+    x0 = x0_frac nx and sigma = sigma_frac nx; particles are drawn uniformly
+    under that profile (seeded)."""
+    nx, ny, nz = extent
+    g = np.random.default_rng(seed)
+    x0, sig, top = x0_frac * nx, sigma_frac * nx, height_frac * ny
+    out = np.empty((0, 3))
+    while len(out) < count:  # rejection sampling of the area under the profile
+        m = 2 * (count - len(out)) + 1024
+        x = g.uniform(0.0, nx, m)
+        y = g.uniform(0.0, top, m)
+        keep = y < top * np.exp(-0.5 * ((x - x0) / sig) ** 2)
+        z = g.uniform(0.0, nz, m)
+        out = np.concatenate([out, np.stack([x, y + 0.5, z], axis=1)[keep]])
+    return out[:count].astype(np.float32)
+
+
 def fall(pos, steps, floor=0.5):
     """Move the cloud down by one cell per step, clamped at the floor."""
     out = pos.copy()
