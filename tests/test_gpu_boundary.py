@@ -50,6 +50,31 @@ def test_single_level_open_faces_match_oracle(storage):
     assert err.max() < steps * RP_TOL[storage], err
 
 
+def test_faces_changed_between_steps():
+    """Faces changed after steps have run: the neighbour tables and the lists
+    of open blocks are made again, and the next steps follow the oracle with
+    the new faces (outflow at both x ends first, then inlet / outflow)."""
+    ext = (32, 16, 16)
+    shape = (16, 16, 32)
+    per = (False, False, True)
+    M0 = wl.random_field(shape, 43, du=0.01)
+    M0[1] += 0.03
+    M0[4] = M0[1] * M0[1]
+    with hl.Lattice(ext, tau=0.8, periodic=per, storage="f32") as lat:
+        lat.set_dense()
+        lat.set_open_faces([hl.FACE_OUTFLOW, hl.FACE_OUTFLOW, 0, 0, 0, 0])
+        lat.write_moments(hl.dense_to_blocks(M0))
+        lat.step(3)
+        lat.set_open_faces(TYPES, *INLET)
+        start = hl.blocks_to_dense(lat.read_moments(), shape)
+        lat.step(4)
+        got = hl.blocks_to_dense(lat.read_moments(), shape)
+    ref = sl.run_open(torch.tensor(start), 4, 0.8, TYPES, inlet=INLET, periodic=per).numpy()
+    assert np.abs(ref[1, :, :, 0]).max() > 0.04
+    err = rel_err(got, ref, row_scales(ref, 0.03))
+    assert err.max() < 4 * RP_TOL["f32"], err
+
+
 def test_two_level_open_faces_match_oracle():
     ext = (16, 128, 16)
     L = 2
