@@ -212,7 +212,11 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_sums(const T* __restrict
       du[1].add_prod(d[j], uy[j]);
       du[2].add_prod(d[j], uz[j]);
       const R rho = R(1) + d[j];
-      const R hir = R(0.5) / rho;
+      R hir;
+      if constexpr (sizeof(R) == sizeof(float))
+        hir = __fdividef(0.5f, rho);  // the kinetic-energy products are FP32 anyway
+      else
+        hir = R(0.5) / rho;
       const R vx = ux[j] - gx[j] * hir, vy = uy[j] - gy[j] * hir, vz = uz[j] - gz[j] * hir;
       ke.add(R(0.5) * rho * (vx * vx + vy * vy + vz * vz));
     }
@@ -286,7 +290,18 @@ template <typename T>
 cudaError_t reduce_typed(const void* src, int64_t nb, const Scales* sc, const uint8_t* skip, const float* F,
                          const double* fu, double vol, double* part, double* out, cudaStream_t s) {
   if (nb == 0) return cudaSuccess;
-  const int grid = reduce_ctas(nb);
+  // one wave: no more CTAs than stay resident (the scratch is sized for
+  // reduce_ctas(nb), an upper bound)
+  static int resident = 0;
+  if (resident == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_reduce_sums<T>, kRedThreads, 0);
+    if (e != cudaSuccess) return e;
+    resident = sms * per_sm > 0 ? sms * per_sm : 1;
+  }
+  const int grid = reduce_ctas(nb) < resident ? reduce_ctas(nb) : resident;
   k_reduce_sums<T><<<unsigned(grid), kRedThreads, 0, s>>>(static_cast<const T*>(src), nb, sc, skip, F, float(fu[0]),
                                                           float(fu[1]), float(fu[2]), part);
   k_reduce_combine<<<1, 32 * kRedSlots, 0, s>>>(part, grid, F != nullptr ? 1 : 0, fu[0], fu[1], fu[2], vol, out);
