@@ -6,7 +6,8 @@ oracle's FP64 reverse mode and against central finite differences.
   rescaling, interface copy nodes and bounce-back, with checkpoint segments
   of one and two coarse steps; within 1e-4 of the largest gradient entry;
 * the same gradient against central differences of the GPU's own FP64-storage
-  forward run at single cells;
+  forward run at single cells, on the small cases and on the full-size
+  512^3 hierarchy of the 2M-particle cloud;
 * the torch.autograd.Function over all levels gives the same gradient;
 * a rebuild between the recorded run and the adjoint is refused, and so is
   reduced-precision storage.
@@ -141,3 +142,61 @@ def test_ml_autograd_function_and_refusals():
         with pytest.raises(hl.HlbmError) as ei:
             lat.forward_record(2 * per, per)
         assert ei.value.code == hl.E_UNSUPPORTED
+
+
+def test_ml_adjoint_full_size_cloud_central_differences():
+    """The 512^3 three-level hierarchy of the 2M-particle cloud (the one the
+    multi-level benchmarks use), 8 fine steps from rest under a seeded force
+    field, checkpoints every 4: dL/dF of L = sum_l <W_l, M_l> (W seeded on
+    every stored node) from the FP32 adjoint against central differences of
+    the GPU's FP64-storage forward run at 4 level-0 entries (the largest, and
+    three drawn among those above 1 % of it), within 1e-4 of max |dL/dF| as
+    on the small cases."""
+    from paper_2603_14982_gb300 import workloads as wl
+    n, L, steps, ckpt = 512, 3, 8, 4
+    ext, per = (n, n, n), (True, False, True)
+    pos = torch.tensor(wl.particle_cloud(n), device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(29)
+    with hl.Lattice(ext, levels=L, tau=0.9, periodic=per, storage="f32") as lat:
+        lat.rebuild_from_particles(pos)
+        counts = [lat.num_blocks(l) for l in range(L)]
+        F = 1e-5 * torch.randn((counts[0], 3, 512), generator=gen, device="cuda", dtype=torch.float32)
+        W = [torch.randn((c, 10, 512), generator=gen, device="cuda", dtype=torch.float32) for c in counts]
+        lat.set_force(F)
+        lat.forward_record(steps, ckpt)
+        g = torch.empty((counts[0], 3, 512), dtype=torch.float32, device="cuda")
+        lat.adjoint(torch.cat(W), g)
+    g = g.double()
+    scale = float(g.abs().max())
+    assert scale > 0 and torch.isfinite(g).all()
+
+    def loss(Fp):
+        with hl.Lattice(ext, levels=L, tau=0.9, periodic=per, storage="f64") as lat:
+            lat.rebuild_from_particles(pos)
+            assert [lat.num_blocks(l) for l in range(L)] == counts
+            lat.set_force(Fp)
+            lat.step(steps)
+            total = 0.0
+            for l in range(L):
+                M = torch.empty((counts[l], 10, 512), dtype=torch.float64, device="cuda")
+                lat.read_moments(M, level=l)
+                total += float((M * W[l].double()).sum())
+            return total
+
+    # the largest entry and three random entries above 1 % of it
+    flat = g.abs().flatten()
+    big = torch.nonzero(flat > 0.01 * scale).flatten().cpu().numpy()
+    rng = np.random.default_rng(31)
+    picks = [int(torch.argmax(flat))] + [int(v) for v in rng.choice(big, 3, replace=False)]
+    h = 2.0 ** -17
+    worst = 0.0
+    for k in picks:
+        b, r, c = k // (3 * 512), (k // 512) % 3, k % 512
+        Fp, Fm = F.clone(), F.clone()
+        Fp[b, r, c] += h
+        Fm[b, r, c] -= h
+        fd = (loss(Fp) - loss(Fm)) / (float(Fp[b, r, c]) - float(Fm[b, r, c]))
+        worst = max(worst, abs(fd - float(g[b, r, c])) / scale)
+        assert abs(fd - float(g[b, r, c])) < 1e-4 * scale, (b, r, c, fd, float(g[b, r, c]), scale)
+    print("512^3 cloud hierarchy, multi-level adjoint against central differences: max |g - fd| / max |g| = %.2e"
+          % worst)
