@@ -308,6 +308,58 @@ def test_full_size_falling_cloud_hierarchy_bit_exact():
             prev = h
 
 
+def _cloud_run(storage, fine_steps=96, rebuild_every=12, n=512):
+    """The multi-level benchmark's loop on the 512^3 cloud (a rebuild every 12
+    fine steps, the deposit every coarse step, the cloud falling one cell per
+    step) in one storage; the final moments of every level (CUDA float64)
+    and the block counts."""
+    L, per = 3, 4
+    pos0 = torch.tensor(wl.particle_cloud(n), device="cuda")
+    pos = pos0.clone()
+    with hl.Lattice((n, n, n), levels=L, tau=0.9, periodic=(True, False, True), storage=storage) as lat:
+        lat.rebuild_from_particles(pos)
+        lat.deposit_particles(pos)
+        since = 0
+        for k in range(fine_steps // per):
+            lat.step(per)
+            since += per
+            pos[:, 1] = torch.clamp(pos[:, 1] - per, min=0.5)
+            if since >= rebuild_every:
+                lat.rebuild_from_particles(pos)
+                since = 0
+            lat.deposit_particles(pos, moving=bool(k < fine_steps // per - 1))
+        out = []
+        for l in range(L):
+            M = torch.empty((lat.num_blocks(l), 10, 512), dtype=torch.float64, device="cuda")
+            out.append(lat.read_moments(M, level=l))
+    return out
+
+
+def test_cloud_512_full_run_against_fp64_storage():
+    """The full-size three-level cloud workload (96 fine steps, 8 rebuilds,
+    deposits) in FP32, FP16- and BF16-scaled storage against the same run in
+    FP64 storage, the GPU path that matches the FP64 oracle to 1e-11 on every
+    case checked: max error per moment row over the row's scale (floors 1 for
+    rho, 1e-3 for u, 1e-6 for S).  Bounds: the per-coarse-step bounds of the
+    two-level tests times the 24 coarse steps (FP32 2e-5, FP16 1e-2; BF16 is
+    reported, its velocity resolution being the 2^-8 of bf16)."""
+    ref = _cloud_run("f64")
+    for storage, bound in (("f32", 24 * 2e-5), ("f16s", 24 * 1e-2), ("bf16s", None)):
+        got = _cloud_run(storage)
+        worst = 0.0
+        for l, (a, b) in enumerate(zip(got, ref)):
+            assert a.shape == b.shape, (storage, l)
+            R = b.permute(1, 0, 2).reshape(10, -1)
+            sc = R.abs().amax(dim=1).cpu().numpy()
+            sc = np.maximum(sc, np.array([1.0] + [1e-3] * 3 + [1e-6] * 6))
+            d = (a - b).permute(1, 0, 2).reshape(10, -1).abs().amax(dim=1).cpu().numpy()
+            worst = max(worst, float((d / sc).max()))
+        print("512^3 cloud, 96 fine steps with 8 rebuilds, %s against FP64 storage: max error / row scale %.3e"
+              % (storage, worst))
+        if bound is not None:
+            assert worst < bound, (storage, worst)
+
+
 CLOUD128_COARSE_STEPS = 4
 
 
