@@ -378,6 +378,8 @@ int32_t hlbm_destroy(hlbm_lattice* h) {
   for (void*& c : h->ckpt) LatticeOps::release(h, c);
   void* v = h->d_status;
   LatticeOps::release(h, v);
+  v = h->d_prev_occ;
+  LatticeOps::release(h, v);
   v = h->d_red;
   LatticeOps::release(h, v);
   v = h->d_F;

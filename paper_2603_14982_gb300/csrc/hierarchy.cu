@@ -375,6 +375,13 @@ __global__ void k_count_changes(const uint8_t* __restrict__ hn, const uint8_t* _
   }
 }
 
+__global__ void k_count_diff(const uint8_t* __restrict__ a, const uint8_t* __restrict__ b, int64_t n,
+                             unsigned long long* count) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const unsigned m = __ballot_sync(0xffffffffu, i < n && a[i] != b[i]);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(count, (unsigned long long)__popc(m));
+}
+
 __global__ void k_clear_change_flags(uint8_t* __restrict__ f, int64_t n) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n) f[i] = uint8_t(f[i] & (kFlagLeaf | kFlagBorder));
@@ -383,6 +390,12 @@ __global__ void k_clear_change_flags(uint8_t* __restrict__ f, int64_t n) {
 inline unsigned grid_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t count_diff(const uint8_t* a, const uint8_t* b, int64_t n, unsigned long long* count, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_count_diff<<<grid_for(n, 256), 256, 0, s>>>(a, b, n, count);
+  return cudaGetLastError();
+}
 
 cudaError_t clear_change_flags(uint8_t* flags, int64_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;

@@ -106,6 +106,9 @@ cudaError_t interface_count(const int32_t* nbr, const uint8_t* skip, int64_t nb,
 cudaError_t interface_scatter(const int32_t* nbr, const uint8_t* skip, int64_t nb, const int64_t* scratch,
                               int32_t* down, int32_t* up, cudaStream_t s);
 
+// Adds to *count the positions where a and b (n bytes each) differ.
+cudaError_t count_diff(const uint8_t* a, const uint8_t* b, int64_t n, unsigned long long* count, cudaStream_t s);
+
 // Keeps only the leaf / border bits of n list flags (an unchanged hierarchy:
 // nothing is new, refined or coarsened).
 cudaError_t clear_change_flags(uint8_t* flags, int64_t n, cudaStream_t s);

@@ -94,6 +94,8 @@ struct hlbm_lattice {
   int block_lookup = 0;           // 0: dense per-level slot tables, 1: spatial hash (hlbm_set_block_lookup)
   double kup[8] = {0}, kdown[8] = {0};  // S^neq factors between level l and l+1
   int* d_status = nullptr;    // device status word of the transfer kernels (0 = ok)
+  uint8_t* d_prev_occ = nullptr;  // level-0 occupancy the installed hierarchy was built from (particle
+                                  // or block-list rebuilds), or null
   unsigned long long* d_count = nullptr;  // scratch counter (particles dropped by a deposit)
   // forward run recorded for the adjoint: states at steps 0, K, 2K, ...
   // (multi-level: one buffer per level and checkpoint, [c * L + l])

@@ -219,6 +219,69 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     ML_CUDA(h, occupancy_from_particles(d_p, n_pos, d0, d_occ, d_bad, st));
   }
 
+  // The level-0 occupancy of this call becomes the reference of the next
+  // one (particle and block-list rebuilds; an explicit hierarchy has none).
+  auto adopt_occupancy = [&]() {
+    void* v = h->d_prev_occ;
+    LatticeOps::release(h, v);
+    h->d_prev_occ = nullptr;
+    if (H_given == nullptr) {
+      h->d_prev_occ = d_occ;
+      tmp[0] = nullptr;  // d_occ: kept, not released with the temporaries
+    }
+  };
+
+  // The same hierarchy as the installed one: the installed levels stay
+  // (lists, neighbour and interface tables, moments); what the full path
+  // does to surviving blocks is done in place: the interface refill from the
+  // coarser level and the scale refit, and the list flags keep their leaf /
+  // border bits only.
+  auto keep_installed = [&]() -> int {
+    adopt_occupancy();
+    cleanup();
+    int rc1 = HLBM_OK;
+    for (int l = L - 2; l >= 0 && rc1 == HLBM_OK; --l) rc1 = downward(h, l, 1, true);
+    for (int l = 0; l < L && rc1 == HLBM_OK; ++l) {
+      LevelData& X = h->lv[l];
+      if (X.d_list_flags != nullptr) ML_CUDA(h, clear_change_flags(X.d_list_flags, X.nb, st));
+      X.host_lists = false;
+      rc1 = LatticeOps::maybe_rescale(h, X, true);
+    }
+    if (rc1) return rc1;
+    int status[2] = {0, 0};
+    ML_CUDA(h, cudaMemcpyAsync(status, h->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    ML_CUDA(h, cudaStreamSynchronize(st));
+    void* v = h->d_F;
+    LatticeOps::release(h, v);
+    h->d_F = nullptr;
+    v = h->d_eps;
+    LatticeOps::release(h, v);
+    h->d_eps = nullptr;
+    ++h->hier_gen;
+    if (counts_out != nullptr) counts_out[0] = counts_out[1] = counts_out[2] = 0;
+    if (status[0] == 1) return fail(h, HLBM_E_BAD_STATE, "a transfer stencil reached a node that is not stored");
+    if (status[1]) return fail(h, HLBM_E_NONFINITE, "%d particle positions are not finite (ignored)", status[1]);
+    return HLBM_OK;
+  };
+
+  // The hierarchy derives from the level-0 occupancy alone: the occupancy of
+  // the installed hierarchy again means the same hierarchy, found before any
+  // set or table is built.
+  if (has_old && H_given == nullptr && h->d_prev_occ != nullptr) {
+    unsigned long long* d_diff = nullptr;
+    if (int rc0 = alloc_t(h, &d_diff, 1)) {
+      cleanup();
+      return rc0;
+    }
+    tmp.push_back(d_diff);
+    unsigned long long diff = 1;
+    ML_CUDA(h, cudaMemsetAsync(d_diff, 0, sizeof(unsigned long long), st));
+    ML_CUDA(h, count_diff(d_occ, h->d_prev_occ, d0.slots(), d_diff, st));
+    ML_CUDA(h, cudaMemcpyAsync(&diff, d_diff, sizeof(diff), cudaMemcpyDeviceToHost, st));
+    ML_CUDA(h, cudaStreamSynchronize(st));
+    if (diff == 0) return keep_installed();
+  }
+
   // 2. H, I, stored, flags on the dense slot grids
   std::vector<LevelData> nl(L);
   for (int l = 0; l < L; ++l) nl[l].tau = h->lv[l].tau;
@@ -301,35 +364,8 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
   ML_CUDA(h, cudaMemcpyAsync(nb.data(), d_tot, L * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   ML_CUDA(h, cudaStreamSynchronize(st));
   if (has_old && changes[0] == 0 && changes[1] == 0 && changes[2] == 0 && changes[3] == 0) {
-    // the same hierarchy: the installed levels stay (lists, neighbour and
-    // interface tables, moments); what the full path does to unchanged blocks
-    // is done in place: the interface refill from the coarser level and the
-    // scale refit, and the list flags keep their leaf / border bits only
     free_new();
-    cleanup();
-    int rc1 = HLBM_OK;
-    for (int l = L - 2; l >= 0 && rc1 == HLBM_OK; --l) rc1 = downward(h, l, 1, true);
-    for (int l = 0; l < L && rc1 == HLBM_OK; ++l) {
-      LevelData& X = h->lv[l];
-      if (X.d_list_flags != nullptr) ML_CUDA(h, clear_change_flags(X.d_list_flags, X.nb, st));
-      X.host_lists = false;
-      rc1 = LatticeOps::maybe_rescale(h, X, true);
-    }
-    if (rc1) return rc1;
-    int status[2] = {0, 0};
-    ML_CUDA(h, cudaMemcpyAsync(status, h->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    ML_CUDA(h, cudaStreamSynchronize(st));
-    void* v = h->d_F;
-    LatticeOps::release(h, v);
-    h->d_F = nullptr;
-    v = h->d_eps;
-    LatticeOps::release(h, v);
-    h->d_eps = nullptr;
-    ++h->hier_gen;
-    if (counts_out != nullptr) counts_out[0] = counts_out[1] = counts_out[2] = 0;
-    if (status[0] == 1) return fail(h, HLBM_E_BAD_STATE, "a transfer stencil reached a node that is not stored");
-    if (status[1]) return fail(h, HLBM_E_NONFINITE, "%d particle positions are not finite (ignored)", status[1]);
-    return HLBM_OK;
+    return keep_installed();
   }
 
   // 4. neighbour tables and interface node lists; with the spatial-hash block
@@ -451,6 +487,7 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
   ML_CUDA(h, cudaStreamSynchronize(st));
   const int64_t refined = int64_t(changes[0]), coarsened = int64_t(changes[1]), deleted = int64_t(changes[2]);
   const int bad = status[1];
+  adopt_occupancy();
   cleanup();
   for (auto& X : h->lv) LatticeOps::free_level(h, X);
   for (int l = 0; l < L; ++l) {
