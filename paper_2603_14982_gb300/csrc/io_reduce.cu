@@ -591,6 +591,12 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_reencode(T* buf, const Scales* from, const Scales* to,
                                                   const int32_t* __restrict__ dom) {
   const int d = dom != nullptr ? dom[blockIdx.x] : 0;
+  // unchanged scales leave the codes as they are (decoding to S and encoding
+  // S - u u again would only add a rounding)
+  bool same = true;
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) same = same && from[d].enc[r] == to[d].enc[r];
+  if (same) return;
   const Mom<float> m = load_node<T>(buf, blockIdx.x, threadIdx.x, from + d);
   store_node<T>(buf, blockIdx.x, threadIdx.x, m, to + d);
 }
