@@ -588,18 +588,25 @@ __global__ void k_set_scales(const unsigned* amax, Scales* sc_all, int n_dom) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_reencode(T* buf, const Scales* from, const Scales* to,
+__global__ void __launch_bounds__(512) k_reencode(T* buf, int64_t nb, const Scales* from, const Scales* to,
                                                   const int32_t* __restrict__ dom) {
-  const int d = dom != nullptr ? dom[blockIdx.x] : 0;
-  // unchanged scales leave the codes as they are (decoding to S and encoding
-  // S - u u again would only add a rounding)
-  bool same = true;
+  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int d = dom != nullptr ? dom[b] : 0;
+    // unchanged scales leave the codes as they are (decoding to S and
+    // encoding S - u u again would only add a rounding)
+    bool same = true;
 #pragma unroll
-  for (int r = 0; r < kRows; ++r) same = same && from[d].enc[r] == to[d].enc[r];
-  if (same) return;
-  const Mom<float> m = load_node<T>(buf, blockIdx.x, threadIdx.x, from + d);
-  store_node<T>(buf, blockIdx.x, threadIdx.x, m, to + d);
+    for (int r = 0; r < kRows; ++r) same = same && from[d].enc[r] == to[d].enc[r];
+    if (same) {
+      if (dom == nullptr) return;  // one set of scales: nothing to do anywhere
+      continue;
+    }
+    const Mom<float> m = load_node<T>(buf, b, threadIdx.x, from + d);
+    store_node<T>(buf, b, threadIdx.x, m, to + d);
+  }
 }
+
+inline unsigned reencode_grid(int64_t nb) { return unsigned(nb < 2048 ? nb : 2048); }
 
 // other (optional): a second buffer encoded with the same scales (the other
 // ping-pong buffer of a level), re-encoded with the new scales as well.
@@ -611,8 +618,8 @@ cudaError_t rescale_typed(void* buf, int64_t nb, const int32_t* dom, int n_dom, 
   if (e != cudaSuccess) return e;
   k_amax_storage<T><<<unsigned(nb), 512, 0, s>>>(static_cast<const T*>(buf), cur, amax, dom);
   k_set_scales<<<unsigned((n_dom * kRows + 255) / 256), 256, 0, s>>>(amax, tmp, n_dom);
-  k_reencode<T><<<unsigned(nb), 512, 0, s>>>(static_cast<T*>(buf), cur, tmp, dom);
-  if (other != nullptr) k_reencode<T><<<unsigned(nb), 512, 0, s>>>(static_cast<T*>(other), cur, tmp, dom);
+  k_reencode<T><<<reencode_grid(nb), 512, 0, s>>>(static_cast<T*>(buf), nb, cur, tmp, dom);
+  if (other != nullptr) k_reencode<T><<<reencode_grid(nb), 512, 0, s>>>(static_cast<T*>(other), nb, cur, tmp, dom);
   e = cudaMemcpyAsync(cur, tmp, size_t(n_dom) * sizeof(Scales), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
