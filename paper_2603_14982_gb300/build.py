@@ -18,7 +18,7 @@ SOURCES = ["api.cu", "stream_collide.cu", "stream_collide_f2.cu", "io_reduce.cu"
            "ml_host.cu", "adjoint.cu", "adjoint_ml.cu", "batch.cu", "coupling.cu", "boundary.cu",
            "deposit.cu"]
 HEADERS = ["hlbm_internal.h", "lbm_math.cuh", "storage.cuh", "io_reduce.h", "lattice_state.h", "hierarchy.cuh",
-           "multilevel.cuh", "v2.cuh", "adjoint_math.cuh", "f2_common.cuh"]
+           "multilevel.cuh", "v2.cuh", "adjoint_math.cuh", "f2_common.cuh", "fp64_bits.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -26,6 +26,7 @@
 
 #include "adjoint_math.cuh"
 #include "f2_common.cuh"
+#include "fp64_bits.cuh"
 #include "hierarchy.cuh"
 #include "hlbm_internal.h"
 #include "lattice_state.h"
@@ -213,7 +214,9 @@ __global__ void k_down_adj_seed(DownAdjArgs a) {
   for (int ax = 0; ax < 3; ++ax) stencil_axis(p[ax], n[ax], a.periodic[ax], lo[ax], hi[ax]);
   const int nx = hi[0] != lo[0] ? 2 : 1, ny = hi[1] != lo[1] ? 2 : 1, nz = hi[2] != lo[2] ? 2 : 1;
   const int nq = nx * ny * nz;
-  const float w = 1.f / float(nq);
+  // weight 1/nq = 2^-e, halved at s = 2 (old and new state each count half)
+  const int e = (nx - 1) + (ny - 1) + (nz - 1) + (a.avg ? 1 : 0);
+  const double w = e == 0 ? 1.0 : e == 1 ? 0.5 : e == 2 ? 0.25 : e == 3 ? 0.125 : 0.0625;
   int64_t cb[8];
   int cc[8];
   bool ok = true;
@@ -243,13 +246,16 @@ __global__ void k_down_adj_seed(DownAdjArgs a) {
       float o[kRows];
       load_f32(a.coarse.mom_other, cb[q], cc[q], o);
       load_f32(a.coarse.mom, cb[q], cc[q], m);
-      for (int ax = 0; ax < 3; ++ax) su[ax] += 0.5 * double(w) * (double(o[1 + ax]) + double(m[1 + ax]));
+      for (int ax = 0; ax < 3; ++ax) {
+        su[ax] += w * to64(o[1 + ax]);
+        su[ax] += w * to64(m[1 + ax]);
+      }
     } else {
       load_f32(a.coarse.mom_other, cb[q], cc[q], m);
-      for (int ax = 0; ax < 3; ++ax) su[ax] += double(w) * double(m[1 + ax]);
+      for (int ax = 0; ax < 3; ++ax) su[ax] += w * to64(m[1 + ax]);
     }
   }
-  const float ux = float(su[0]), uy = float(su[1]), uz = float(su[2]);
+  const float ux = to32(su[0]), uy = to32(su[1]), uz = to32(su[2]);
   // adjoint of stored S = k sn + u u and of u
   lf[kCells] = L[1] + 2.f * ux * L[4] + uy * L[7] + uz * L[8];
   lf[2 * kCells] = L[2] + 2.f * uy * L[5] + ux * L[7] + uz * L[9];
@@ -823,7 +829,7 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         t.fine = level_view(h, l, cur[l], nullptr);
         t.coarse = level_view(h, l + 1, cur[l + 1], prev[l + 1]);
         t.out = cur[l];
-        t.nodes = F.d_down;
+        t.nodes = F.d_down_t;
         t.n_nodes = F.n_down;
         t.avg = op.s == 2 ? 1 : 0;
         t.use_other = op.s == 1 ? 1 : 0;
@@ -886,7 +892,7 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         DownAdjArgs d{};
         d.fine = level_view(h, l, op.in, nullptr);
         d.coarse = level_view(h, l + 1, op.c_new, op.c_old);
-        d.nodes = F.d_down;
+        d.nodes = F.d_down_t;  // the seeds are per node: transfer order (uniform stencil shape per warp)
         d.n_nodes = F.n_down;
         d.avg = op.s == 2 ? 1 : 0;
         d.k = float(h->kdown[l]);

@@ -505,6 +505,127 @@ cudaError_t interface_scatter(const int32_t* nbr, const uint8_t* skip, int64_t n
   return cudaGetLastError();
 }
 
+namespace {
+
+// Transfer order of an interface list ------------------------------------------
+// The downward transfer's stencil has 1, 2, 4 or 8 coarse nodes depending on
+// the parity of the fine node's coordinates (even: one node on that axis, odd:
+// two).  Listed in block order, one warp mixes all eight parity classes and
+// runs as long as its widest stencil; ordered by class, a warp's lanes share
+// one stencil shape.  The order is stable within a class (block order), so
+// that neighbouring lanes still read neighbouring coarse nodes.
+
+constexpr int kOrdThreads = 256, kOrdPer = 8, kOrdTile = kOrdThreads * kOrdPer;
+
+__device__ __forceinline__ int parity_class(int32_t v) {
+  const int c = v & 511;  // cell = x + 8 y + 64 z: the parities are bits 0, 3 and 6
+  return (c & 1) | ((c >> 2) & 2) | ((c >> 4) & 4);
+}
+
+// counts[c * n_tile + t] = entries of class c in tile t (kOrdTile entries).
+__global__ void __launch_bounds__(kOrdThreads) k_order_count(const int32_t* __restrict__ nodes, int64_t n,
+                                                             int64_t n_tile, int64_t* __restrict__ counts) {
+  __shared__ int s_cnt[8];
+  if (threadIdx.x < 8) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = int64_t(blockIdx.x) * kOrdTile;
+#pragma unroll
+  for (int i = 0; i < kOrdPer; ++i) {
+    const int64_t e = base + i * kOrdThreads + threadIdx.x;
+    if (e < n) atomicAdd(&s_cnt[parity_class(nodes[e])], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) counts[threadIdx.x * n_tile + blockIdx.x] = s_cnt[threadIdx.x];
+}
+
+// Exclusive scan of m values in place, total to *total: one CTA, each thread
+// a contiguous run.
+__global__ void __launch_bounds__(1024) k_scan_runs(int64_t* __restrict__ v, int64_t m, int64_t* __restrict__ total) {
+  __shared__ int64_t s_w[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+  const int64_t per = (m + blockDim.x - 1) / blockDim.x;
+  const int64_t b0 = min(m, int64_t(t) * per), b1 = min(m, b0 + per);
+  int64_t own = 0;
+  for (int64_t i = b0; i < b1; ++i) own += v[i];
+  int64_t inc = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t x = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += x;
+  }
+  if (lane == 31) s_w[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int64_t x = lane < nw ? s_w[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    s_w[lane] = x;
+  }
+  __syncthreads();
+  int64_t run = (w > 0 ? s_w[w - 1] : 0) + inc - own;
+  for (int64_t i = b0; i < b1; ++i) {
+    const int64_t c = v[i];
+    v[i] = run;
+    run += c;
+  }
+  if (t == 0) *total = s_w[nw - 1];
+}
+
+// Scatter in class-major, then list order: entry order within a tile is
+// (i, warp, lane), the order of the count pass.
+__global__ void __launch_bounds__(kOrdThreads) k_order_scatter(const int32_t* __restrict__ nodes, int64_t n,
+                                                               int64_t n_tile, const int64_t* __restrict__ offs,
+                                                               int32_t* __restrict__ out) {
+  constexpr int kW = kOrdThreads / 32;
+  __shared__ int s_cnt[kW][8];
+  __shared__ int64_t s_off[kW][8];
+  __shared__ int64_t s_run[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x < 8) s_run[threadIdx.x] = offs[threadIdx.x * n_tile + blockIdx.x];
+  const int64_t base = int64_t(blockIdx.x) * kOrdTile;
+  for (int i = 0; i < kOrdPer; ++i) {
+    const int64_t e = base + i * kOrdThreads + threadIdx.x;
+    const bool valid = e < n;
+    const int32_t v = valid ? nodes[e] : 0;
+    const int c = valid ? parity_class(v) : -1;
+    int rank = 0;
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const unsigned bal = __ballot_sync(0xffffffffu, c == cc);
+      if (c == cc) rank = __popc(bal & ((1u << lane) - 1u));
+      if (lane == 0) s_cnt[w][cc] = __popc(bal);
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      int64_t run = s_run[threadIdx.x];
+      for (int ww = 0; ww < kW; ++ww) {
+        s_off[ww][threadIdx.x] = run;
+        run += s_cnt[ww][threadIdx.x];
+      }
+      s_run[threadIdx.x] = run;
+    }
+    __syncthreads();
+    if (valid) out[s_off[w][c] + rank] = v;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+cudaError_t transfer_order(const int32_t* nodes, int64_t n, int64_t* scratch, int32_t* out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t n_tile = (n + kOrdTile - 1) / kOrdTile;
+  k_order_count<<<unsigned(n_tile), kOrdThreads, 0, s>>>(nodes, n, n_tile, scratch);
+  k_scan_runs<<<1, 1024, 0, s>>>(scratch, 8 * n_tile, scratch + 8 * n_tile);
+  k_order_scatter<<<unsigned(n_tile), kOrdThreads, 0, s>>>(nodes, n, n_tile, scratch, out);
+  return cudaGetLastError();
+}
+
+int64_t transfer_order_scratch(int64_t n) { return 8 * ((n + kOrdTile - 1) / kOrdTile) + 1; }
+
 cudaError_t count_changes(const uint8_t* H_new, const uint8_t* H_old, const uint8_t* stored_new,
                           const uint8_t* stored_old, int64_t slots, unsigned long long* counts_dev, cudaStream_t s) {
   if (slots == 0) return cudaSuccess;

@@ -106,6 +106,13 @@ cudaError_t interface_count(const int32_t* nbr, const uint8_t* skip, int64_t nb,
 cudaError_t interface_scatter(const int32_t* nbr, const uint8_t* skip, int64_t nb, const int64_t* scratch,
                               int32_t* down, int32_t* up, cudaStream_t s);
 
+// Transfer order of a downward interface list: the same n entries grouped by
+// the parity class of the node (x, y, z odd or even: the shape of its
+// downward stencil), stable within a class.  scratch holds
+// transfer_order_scratch(n) int64.
+cudaError_t transfer_order(const int32_t* nodes, int64_t n, int64_t* scratch, int32_t* out, cudaStream_t s);
+int64_t transfer_order_scratch(int64_t n);
+
 // Adds to *count the positions where a and b (n bytes each) differ.
 cudaError_t count_diff(const uint8_t* a, const uint8_t* b, int64_t n, unsigned long long* count, cudaStream_t s);
 

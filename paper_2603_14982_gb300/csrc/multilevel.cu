@@ -11,6 +11,7 @@
 // accumulation: on GB300 the FP64 pipe runs at a small fraction of the FP32
 // rate, so the widening and the narrowing conversions run on the integer
 // pipes.
+#include "fp64_bits.cuh"
 #include "hlbm_internal.h"
 #include "multilevel.cuh"
 
@@ -20,43 +21,6 @@ namespace {
 struct Node64 {
   double drho, ux, uy, uz, s[6];  // drho = rho - 1; s = S^neq (xx, yy, zz, xy, xz, yz)
 };
-
-// Widening float -> double on the integer pipes.  The conversion is exact:
-// for a normal binary32 number the binary64 encoding keeps the sign, rebiases
-// the exponent by 1023 - 127 = 896 and appends 29 zero bits to the 23-bit
-// fraction, i.e. bits64 = sign | ((bits32 & 0x7fffffff) + (896 << 23)) << 29.
-// Zeros map to signed zeros; subnormals, infinities and NaNs (never seen on
-// a healthy lattice) take the conversion instruction.  The transfers are
-// bound by the FP64 pipe, which the conversion instruction also occupies.
-__device__ __forceinline__ double to64(double v) { return v; }
-__device__ __forceinline__ double to64(float v) {
-  const unsigned b = __float_as_uint(v);
-  const unsigned a = b & 0x7fffffffu;
-  const unsigned long long sign = static_cast<unsigned long long>(b & 0x80000000u) << 32;
-  if (a >= 0x7f800000u || (a != 0u && a < 0x00800000u)) return double(v);
-  const unsigned long long mag = a == 0u ? 0ull : (static_cast<unsigned long long>(a) + (896ull << 23)) << 29;
-  return __longlong_as_double(static_cast<long long>(sign | mag));
-}
-
-// Narrowing binary64 -> binary32 with round-to-nearest-even on the integer
-// pipes (IEEE 754): for results in the normal binary32 range the 52-bit
-// fraction is cut to 23 bits and rounded on the 29 dropped bits, ties to
-// even; the carry of a round-up propagates into the exponent (up to
-// infinity).  Zeros keep their sign; all other inputs (binary32 subnormal or
-// overflow range, infinities, NaNs) take the conversion instruction.
-__device__ __forceinline__ float to32(double v) {
-  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
-  const unsigned hi = unsigned(bits >> 32), lo = unsigned(bits);
-  const unsigned ex = (hi >> 20) & 0x7ffu;
-  if (ex - 897u > 253u) {  // biased exponent outside [897, 1150]
-    if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
-    return __double2float_rn(v);
-  }
-  const unsigned keep = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const unsigned rem = lo & 0x1fffffffu;
-  const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u))) ? 1u : 0u;
-  return __uint_as_float(((hi & 0x80000000u) | ((ex - 896u) << 23) | keep) + up);
-}
 
 template <typename R>
 __device__ __forceinline__ R narrow(double v) {
@@ -88,7 +52,7 @@ __device__ __forceinline__ void store64(void* base, int64_t blk, int cell, const
                                         const Scales* sc) {
   using R = typename StorageTraits<T>::R;
   Mom<R> m;
-  const R ux = narrow<R>(n.ux), uy = narrow<R>(n.uy), uz = narrow<R>(n.uz), kk = R(k);
+  const R ux = narrow<R>(n.ux), uy = narrow<R>(n.uy), uz = narrow<R>(n.uz), kk = narrow<R>(k);
   m.drho = narrow<R>(n.drho);
   m.ux = ux;
   m.uy = uy;
@@ -154,7 +118,10 @@ __global__ void k_down(TransferArgs a) {
   // 1), an odd one two (weight 1/2 each); the weights are exact in FP64
   const int nx = hi[0] != lo[0] ? 2 : 1, ny = hi[1] != lo[1] ? 2 : 1, nz = hi[2] != lo[2] ? 2 : 1;
   const int nq = nx * ny * nz;
-  const double w = nq == 1 ? 1.0 : (nq == 2 ? 0.5 : (nq == 4 ? 0.25 : 0.125));  // 1/nq, exact
+  // weight 1/nq = 2^-e, halved once more when the new state's sums are added
+  // to half the kept ones (step 2) or averaged with the old state's
+  const int e = (nx - 1) + (ny - 1) + (nz - 1) + (a.avg ? 1 : 0);
+  const double wt = e == 0 ? 1.0 : e == 1 ? 0.5 : e == 2 ? 0.25 : e == 3 ? 0.125 : 0.0625;
   // all stencil lookups first (independent loads), then the node loads two
   // corners at a time so that their latencies overlap
   int64_t cb[8];
@@ -180,15 +147,14 @@ __global__ void k_down(TransferArgs a) {
   const bool reuse = a.avg && a.acc_old != nullptr;
   if (reuse) {
     const double* o = a.acc_old + k * 10;
-    acc.drho = 0.5 * o[0];
-    acc.ux = 0.5 * o[1];
-    acc.uy = 0.5 * o[2];
-    acc.uz = 0.5 * o[3];
+    acc.drho = half64(o[0]);
+    acc.ux = half64(o[1]);
+    acc.uy = half64(o[2]);
+    acc.uz = half64(o[3]);
 #pragma unroll
-    for (int r = 0; r < 6; ++r) acc.s[r] = 0.5 * o[4 + r];
+    for (int r = 0; r < 6; ++r) acc.s[r] = half64(o[4 + r]);
     cur = a.coarse.mom;
   }
-  const double wt = reuse ? 0.5 * w : w;
 #pragma unroll
   for (int q = 0; q < 8; q += 2) {
     if (q >= nq) break;
@@ -203,11 +169,11 @@ __global__ void k_down(TransferArgs a) {
         o1 = load64<T>(a.coarse.mom_other, cb[q + 1], cc[q + 1], a.coarse.sc);
         n1 = load64<T>(a.coarse.mom, cb[q + 1], cc[q + 1], a.coarse.sc);
       }
-      axpy(acc, 0.5 * w, o0);
-      axpy(acc, 0.5 * w, n0);
+      axpy(acc, wt, o0);
+      axpy(acc, wt, n0);
       if (two) {
-        axpy(acc, 0.5 * w, o1);
-        axpy(acc, 0.5 * w, n1);
+        axpy(acc, wt, o1);
+        axpy(acc, wt, n1);
       }
     } else {
       const Node64 v0 = load64<T>(cur, cb[q], cc[q], a.coarse.sc);
