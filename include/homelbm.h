@@ -323,8 +323,14 @@ int32_t hlbm_reduce(hlbm_lattice *h, double out[7]);
    buffer, public layout [nb][10][512], rho row = d/d rho; multi-level: every
    level's blocks in level order, level 0 first) and writes dL/dF (float32
    device [nb0][3][512], the layout of hlbm_set_force) by recomputing each
-   checkpoint segment and stepping backwards; the force sums are FP64.
-   Device memory during the call, single level: with FP32 storage, the K =
+   checkpoint segment and stepping backwards; the force sums are FP64.  With
+   FP32 storage hlbm_forward_record runs its last segment the way the adjoint
+   recomputes one and keeps it (the tape), so hlbm_adjoint recomputes every
+   segment but that one; the tape's buffers are the segment buffers listed
+   below, allocated by hlbm_forward_record and held until the next
+   hlbm_adjoint, which takes them over and frees them (a further hlbm_adjoint
+   on the same recording recomputes every segment).
+   Device memory of the segment buffers, single level: with FP32 storage, the K =
    ckpt_every states and pre-collision moment fields of one segment (2 K x 40
    B per node) plus four float32 moment-sized buffers and the FP64 dL/dF sum
    (24 B per node); with FP64 storage, K - 1 states (80 B per node each) and

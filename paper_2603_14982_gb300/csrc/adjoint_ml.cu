@@ -495,19 +495,7 @@ inline unsigned grid_for(int64_t n) { return unsigned((n + 255) / 256); }
 
 // ---------------------------------------------------------------- host driver
 
-enum OpKind { kSC, kDown, kUp };
-
-struct Op {
-  OpKind kind;
-  int l, s;
-  // pointers as the forward recomputation used them
-  void* in = nullptr;       // SC: input state; DOWN: fine state written; UP: coarse state written
-  void* out = nullptr;      // SC: output state
-  float* pre = nullptr;     // SC: pre-collision moments
-  void* c_old = nullptr;    // DOWN: P_{l+1}
-  void* c_new = nullptr;    // DOWN: A_{l+1}; UP: the fine state read (A_l)
-  float* undo = nullptr;    // DOWN / UP: overwritten values
-};
+using Op = AdjOp;  // pointers as the forward recomputation used them
 
 // The operations of one coarse step, in the order of AdvanceLBM (Algorithm 1).
 void coarse_step_ops(int L, int l, int s, std::vector<Op>& ops) {
@@ -557,6 +545,117 @@ StepArgs level_args(const hlbm_lattice* h, int l) {
   return a;
 }
 
+// The operations of one checkpoint segment (k_coarse coarse steps) with
+// their buffers, the per-level working copies of the segment's start state
+// and the FP64 sums of the recomputed downward transfers.  get(bytes, &p)
+// allocates and keeps the allocation.
+template <class Get>
+int alloc_segment(hlbm_lattice* h, int k_coarse, Get&& get, std::vector<Op>& seg_ops, std::vector<void*>& work,
+                  std::vector<double*>& acc) {
+  const int L = h->cfg.num_levels;
+  std::vector<Op> step_ops;
+  coarse_step_ops(L, L - 1, 1, step_ops);
+  seg_ops.clear();
+  for (int c = 0; c < k_coarse; ++c) seg_ops.insert(seg_ops.end(), step_ops.begin(), step_ops.end());
+  work.assign(size_t(L), nullptr);
+  acc.assign(size_t(L), nullptr);
+  void* p;
+  for (int l = 0; l < L; ++l)
+    if (int rc = get(size_t(h->lv[l].nb) * kBlockVals * sizeof(float), &work[size_t(l)])) return rc;
+  for (int l = 0; l + 1 < L; ++l) {
+    if (int rc = get((size_t(h->lv[l].n_down) * 10 + 1) * sizeof(double), &p)) return rc;
+    acc[size_t(l)] = static_cast<double*>(p);
+  }
+  for (Op& op : seg_ops) {
+    if (op.kind == kSC) {
+      if (int rc = get(size_t(h->lv[op.l].nb) * kBlockVals * sizeof(float), &op.out)) return rc;
+      if (int rc = get(size_t(h->lv[op.l].nb) * kBlockVals * sizeof(float), &p)) return rc;
+      op.pre = static_cast<float*>(p);
+    } else {
+      const int64_t n = op.kind == kDown ? h->lv[op.l].n_down : h->lv[op.l + 1].n_up;
+      if (int rc = get(size_t(n) * kRows * sizeof(float), &p)) return rc;
+      op.undo = static_cast<float*>(p);
+    }
+  }
+  return HLBM_OK;
+}
+
+// Runs the first n_ops operations of a segment from the per-level start
+// states start[l] (copied into work first), recording every SC's p, logging
+// what the transfers overwrite and keeping each operation's buffers in its
+// record; cur[l] ends as the level's final state.
+cudaError_t recompute_segment(hlbm_lattice* h, std::vector<Op>& seg_ops, size_t n_ops, const std::vector<void*>& start,
+                              const std::vector<void*>& work, const std::vector<double*>& acc, std::vector<void*>& cur) {
+  const int L = h->cfg.num_levels;
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  std::vector<void*> prev(size_t(L), nullptr);
+  cur.assign(size_t(L), nullptr);
+  for (int l = 0; l < L && e == cudaSuccess; ++l) {
+    const size_t vals = size_t(h->lv[l].nb) * kBlockVals;
+    if (vals) e = cudaMemcpyAsync(work[size_t(l)], start[size_t(l)], vals * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    cur[size_t(l)] = work[size_t(l)];
+  }
+  for (size_t i = 0; i < n_ops && e == cudaSuccess; ++i) {
+    Op& op = seg_ops[i];
+    const int l = op.l;
+    if (op.kind == kSC) {
+      if (h->lv[l].nb == 0) {
+        prev[l] = cur[l];
+        continue;
+      }
+      StepArgs a = level_args(h, l);
+      a.in = cur[l];
+      a.out = op.out;
+      a.pre_out = op.pre;
+      e = launch_stream_collide_record(a, st);
+      op.in = cur[l];
+      prev[l] = cur[l];
+      cur[l] = op.out;
+    } else if (op.kind == kDown) {
+      const LevelData& F = h->lv[l];
+      op.in = cur[l];
+      op.c_old = prev[l + 1];
+      op.c_new = cur[l + 1];
+      if (F.n_down == 0) continue;
+      k_gather_nodes<<<grid_for(F.n_down), 256, 0, st>>>(static_cast<const float*>(cur[l]), F.d_down, F.n_down,
+                                                         op.undo);
+      TransferArgs t{};
+      t.fine = level_view(h, l, cur[l], nullptr);
+      t.coarse = level_view(h, l + 1, cur[l + 1], prev[l + 1]);
+      t.out = cur[l];
+      t.nodes = F.d_down_t;
+      t.n_nodes = F.n_down;
+      t.avg = op.s == 2 ? 1 : 0;
+      t.use_other = op.s == 1 ? 1 : 0;
+      t.acc_old = acc[size_t(l)];
+      t.k = h->kdown[l];
+      for (int ax = 0; ax < 3; ++ax) t.periodic[ax] = h->cfg.periodic[ax];
+      t.status = h->d_status;
+      e = transfer_down(HLBM_STORE_F32, t, st);
+    } else {
+      const LevelData& C = h->lv[l + 1];
+      op.in = cur[l + 1];
+      op.c_new = cur[l];
+      if (C.n_up == 0) continue;
+      k_gather_nodes<<<grid_for(C.n_up), 256, 0, st>>>(static_cast<const float*>(cur[l + 1]), C.d_up, C.n_up,
+                                                       op.undo);
+      TransferArgs t{};
+      t.fine = level_view(h, l, cur[l], nullptr);
+      t.coarse = level_view(h, l + 1, cur[l + 1], nullptr);
+      t.out = cur[l + 1];
+      t.nodes = C.d_up;
+      t.n_nodes = C.n_up;
+      t.k = h->kup[l];
+      for (int ax = 0; ax < 3; ++ax) t.periodic[ax] = h->cfg.periodic[ax];
+      t.status = h->d_status;
+      e = transfer_up(HLBM_STORE_F32, t, st);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
+  return e;
+}
+
 }  // namespace
 
 int ml_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every) {
@@ -575,7 +674,18 @@ int ml_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every) {
       if ((rc = LatticeOps::alloc(h, &p, size_t(h->lv[l].nb) * kBlockVals * sizeof(float)))) return rc;
       h->ckpt.push_back(p);
     }
-  for (int32_t t = 0; t < n_coarse; ++t) {
+  // the tape of the last segment, allocated before anything runs
+  AdjTape* tape = new AdjTape();
+  h->tape = tape;
+  auto get = [&](size_t bytes, void** out) -> int {
+    *out = nullptr;
+    const int r = LatticeOps::alloc(h, out, bytes);
+    if (r == HLBM_OK && *out != nullptr) tape->bufs.push_back(*out);
+    return r;
+  };
+  if ((rc = alloc_segment(h, k_coarse, get, tape->ops, tape->work, tape->acc))) return rc;
+  const int32_t t_last = (n_ck - 1) * k_coarse;
+  for (int32_t t = 0; t <= t_last; ++t) {
     if (t % k_coarse == 0)
       for (int l = 0; l < L; ++l) {
         const LevelData& Lv = h->lv[l];
@@ -585,8 +695,24 @@ int ml_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every) {
                                               h->stream);
         if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "checkpoint copy: %s", cudaGetErrorString(e));
       }
-    if ((rc = ml_advance_coarse(h, 1))) return rc;
+    if (t < t_last && (rc = ml_advance_coarse(h, 1))) return rc;
   }
+  // the last segment: the adjoint's recomputation, from the last checkpoint,
+  // kept as the tape; its final states become the lattice's state
+  tape->n = n_coarse - t_last;
+  std::vector<Op> step_ops;
+  coarse_step_ops(L, L - 1, 1, step_ops);
+  std::vector<void*> start(static_cast<size_t>(L)), cur;
+  for (int l = 0; l < L; ++l) start[size_t(l)] = h->ckpt[size_t(n_ck - 1) * L + l];
+  cudaError_t e = recompute_segment(h, tape->ops, size_t(tape->n) * step_ops.size(), start, tape->work, tape->acc, cur);
+  for (int l = 0; l < L && e == cudaSuccess; ++l) {
+    LevelData& Lv = h->lv[l];
+    if (Lv.nb)
+      e = cudaMemcpyAsync(Lv.d_mom[Lv.cur], cur[size_t(l)], size_t(Lv.nb) * kBlockVals * sizeof(float),
+                          cudaMemcpyDeviceToDevice, h->stream);
+  }
+  if (e != cudaSuccess) return fail(h, HLBM_E_CUDA, "recording the last segment: %s", cudaGetErrorString(e));
+  h->l0_steps += int64_t(tape->n) * per;
   h->rec_steps = n_steps;
   h->rec_every = ckpt_every;
   return ml_check_status(h);
@@ -643,17 +769,20 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
     get(size_t(h->lv[0].nb) * 3 * kCells * sizeof(float), &p);
     dFs = static_cast<float*>(p);
   }
-  // segment buffers: working copies of the checkpoint, one output and one
-  // pre-collision buffer per SC operation, undo logs per transfer
-  std::vector<void*> work(L, nullptr);
-  for (int l = 0; l < L; ++l) get(vals[l] * sizeof(float), &work[l]);
-  // FP64 stencil sums of the old coarse state kept from step 1 to step 2 of
-  // the recomputed downward transfers, as in the forward advance
-  std::vector<double*> acc(L, nullptr);
-  for (int l = 0; l + 1 < L; ++l) {
-    void* p;
-    get((size_t(h->lv[l].n_down) * 10 + 1) * sizeof(double), &p);
-    acc[l] = static_cast<double*>(p);
+  // segment buffers (working copies of the checkpoint, one output and one
+  // pre-collision buffer per SC operation, undo logs per transfer, the FP64
+  // sums of the recomputed downward transfers): the recording's tape when
+  // there is one, else allocated here
+  std::vector<Op> seg_ops;
+  std::vector<void*> work;
+  std::vector<double*> acc;
+  AdjTape* tape = h->tape;
+  if (tape != nullptr) {
+    seg_ops = tape->ops;
+    work = tape->work;
+    acc = tape->acc;
+  } else {
+    alloc_segment(h, k_coarse, get, seg_ops, work, acc);
   }
   // lambda at the pass-through nodes of a fused level, and the pass-through bits
   std::vector<float*> raw(L, nullptr);
@@ -665,8 +794,6 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
     get(size_t(h->lv[l].nb) * (kCells / 32) * sizeof(uint32_t) + sizeof(uint32_t), &p);
     ptb[l] = static_cast<uint32_t*>(p);
   }
-  std::vector<Op> seg_ops;
-  for (int c = 0; c < k_coarse; ++c) seg_ops.insert(seg_ops.end(), step_ops.begin(), step_ops.end());
   // the level's previous SC in the segment, for every SC (-1: the first)
   std::vector<int> prev_sc(seg_ops.size(), -1);
   {
@@ -676,18 +803,6 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         prev_sc[i] = last[seg_ops[i].l];
         last[seg_ops[i].l] = int(i);
       }
-  }
-  for (Op& op : seg_ops) {
-    void* p;
-    if (op.kind == kSC) {
-      get(vals[op.l] * sizeof(float), &op.out);
-      get(vals[op.l] * sizeof(float), &p);
-      op.pre = static_cast<float*>(p);
-    } else {
-      const int64_t n = op.kind == kDown ? h->lv[op.l].n_down : h->lv[op.l + 1].n_up;
-      get(size_t(n) * kRows * sizeof(float), &p);
-      op.undo = static_cast<float*>(p);
-    }
   }
   if (rc != HLBM_OK) {
     release_all();
@@ -763,6 +878,14 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
       return rc;
     }
   }
+  // every allocation went through: the adjoint takes the tape over (its
+  // reverse walk changes the tape's buffers; they are released with the rest)
+  const bool taped = tape != nullptr;
+  if (taped) {
+    tmp.insert(tmp.end(), tape->bufs.begin(), tape->bufs.end());
+    delete tape;
+    h->tape = nullptr;
+  }
   // Per level: plain (lamA holds lambda) or fused (lamA holds mu, raw holds
   // lambda at the pass-through nodes; fpre is the recorded p of the level's
   // next SC to reverse, whose transposed collision mu already includes).
@@ -793,70 +916,12 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
   for (int sgi = n_seg - 1; sgi >= 0 && e == cudaSuccess; --sgi) {
     const int nc = (n_coarse - sgi * k_coarse) < k_coarse ? (n_coarse - sgi * k_coarse) : k_coarse;
     const size_t n_ops = size_t(nc) * step_ops.size();
-    // 1. recompute the segment from its checkpoint, logging what every operation read
-    std::vector<void*> cur(L), prev(L, nullptr);
-    for (int l = 0; l < L && e == cudaSuccess; ++l) {
-      if (vals[l])
-        e = cudaMemcpyAsync(work[l], h->ckpt[size_t(sgi) * L + l], vals[l] * sizeof(float),
-                            cudaMemcpyDeviceToDevice, st);
-      cur[l] = work[l];
-    }
-    for (size_t i = 0; i < n_ops && e == cudaSuccess; ++i) {
-      Op& op = seg_ops[i];
-      const int l = op.l;
-      if (op.kind == kSC) {
-        if (h->lv[l].nb == 0) {
-          prev[l] = cur[l];
-          continue;
-        }
-        StepArgs a = level_args(h, l);
-        a.in = cur[l];
-        a.out = op.out;
-        a.pre_out = op.pre;
-        e = launch_stream_collide_record(a, st);
-        op.in = cur[l];
-        prev[l] = cur[l];
-        cur[l] = op.out;
-      } else if (op.kind == kDown) {
-        const LevelData& F = h->lv[l];
-        op.in = cur[l];
-        op.c_old = prev[l + 1];
-        op.c_new = cur[l + 1];
-        if (F.n_down == 0) continue;
-        k_gather_nodes<<<grid_for(F.n_down), 256, 0, st>>>(static_cast<const float*>(cur[l]), F.d_down, F.n_down,
-                                                           op.undo);
-        TransferArgs t{};
-        t.fine = level_view(h, l, cur[l], nullptr);
-        t.coarse = level_view(h, l + 1, cur[l + 1], prev[l + 1]);
-        t.out = cur[l];
-        t.nodes = F.d_down_t;
-        t.n_nodes = F.n_down;
-        t.avg = op.s == 2 ? 1 : 0;
-        t.use_other = op.s == 1 ? 1 : 0;
-        t.acc_old = acc[l];
-        t.k = h->kdown[l];
-        for (int ax = 0; ax < 3; ++ax) t.periodic[ax] = h->cfg.periodic[ax];
-        t.status = h->d_status;
-        e = transfer_down(HLBM_STORE_F32, t, st);
-      } else {
-        const LevelData& C = h->lv[l + 1];
-        op.in = cur[l + 1];
-        op.c_new = cur[l];
-        if (C.n_up == 0) continue;
-        k_gather_nodes<<<grid_for(C.n_up), 256, 0, st>>>(static_cast<const float*>(cur[l + 1]), C.d_up, C.n_up,
-                                                         op.undo);
-        TransferArgs t{};
-        t.fine = level_view(h, l, cur[l], nullptr);
-        t.coarse = level_view(h, l + 1, cur[l + 1], nullptr);
-        t.out = cur[l + 1];
-        t.nodes = C.d_up;
-        t.n_nodes = C.n_up;
-        t.k = h->kup[l];
-        for (int ax = 0; ax < 3; ++ax) t.periodic[ax] = h->cfg.periodic[ax];
-        t.status = h->d_status;
-        e = transfer_up(HLBM_STORE_F32, t, st);
-      }
-      if (e == cudaSuccess) e = cudaGetLastError();
+    // 1. recompute the segment from its checkpoint, logging what every
+    // operation read (the last segment: the recording's tape holds it)
+    if (!(taped && sgi == n_seg - 1)) {
+      std::vector<void*> start(static_cast<size_t>(L)), cur;
+      for (int l = 0; l < L; ++l) start[size_t(l)] = h->ckpt[size_t(sgi) * L + l];
+      e = recompute_segment(h, seg_ops, n_ops, start, work, acc, cur);
     }
     // 2. walk the operations backwards
     for (size_t i = n_ops; i-- > 0 && e == cudaSuccess;) {

@@ -158,6 +158,13 @@ void LatticeOps::release(hlbm_lattice* h, void*& p) {
   p = nullptr;
 }
 
+void LatticeOps::release_tape(hlbm_lattice* h) {
+  if (h->tape == nullptr) return;
+  for (void*& p : h->tape->bufs) release(h, p);
+  delete h->tape;
+  h->tape = nullptr;
+}
+
 void LatticeOps::free_level(hlbm_lattice* h, LevelData& L) {
   release(h, L.d_mom[0]);
   release(h, L.d_mom[1]);
@@ -376,6 +383,7 @@ int32_t hlbm_destroy(hlbm_lattice* h) {
   for (auto& L : h->lv) LatticeOps::free_level(h, L);
   LatticeOps::release(h, h->d_stage);
   for (void*& c : h->ckpt) LatticeOps::release(h, c);
+  LatticeOps::release_tape(h);
   void* v = h->d_status;
   LatticeOps::release(h, v);
   v = h->d_prev_occ;
@@ -774,14 +782,16 @@ int32_t hlbm_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every
   ProfScope prof_scope(h, kProfAdjoint);
   for (void*& c : h->ckpt) LatticeOps::release(h, c);
   h->ckpt.clear();
+  LatticeOps::release_tape(h);
   h->rec_steps = h->rec_every = 0;
   h->rec_gen = -1;
   if (h->drag_every > 0)
     return fail(h, HLBM_E_UNSUPPORTED, "the adjoint takes the force field as fixed: disable the live drag first");
   if (h->open_mask() != 0u) return fail(h, HLBM_E_UNSUPPORTED, "the adjoint does not cover open faces");
-  auto drop = [h](int r) {  // a failed recording keeps no checkpoints
+  auto drop = [h](int r) {  // a failed recording keeps no checkpoints and no tape
     for (void*& c : h->ckpt) LatticeOps::release(h, c);
     h->ckpt.clear();
+    LatticeOps::release_tape(h);
     h->rec_steps = h->rec_every = 0;
     return r;
   };
@@ -798,13 +808,51 @@ int32_t hlbm_forward_record(hlbm_lattice* h, int32_t n_steps, int32_t ckpt_every
     if ((rc = LatticeOps::alloc(h, &p, bytes))) return drop(rc);
     h->ckpt.push_back(p);
   }
+  // FP32 storage: the last segment runs as the adjoint would recompute it
+  // (states and pre-collision moments of every step kept as the tape; the
+  // buffers are sized for a whole segment, so that the adjoint uses them for
+  // every segment)
+  const bool taped = h->cfg.storage == HLBM_STORE_F32;
+  const int32_t t_last = (n_ck - 1) * ckpt_every;
+  if (taped) {
+    AdjTape* tape = new AdjTape();
+    h->tape = tape;
+    tape->n = n_steps - t_last;
+    tape->seg.assign(size_t(ckpt_every) + 1, nullptr);
+    tape->pre.assign(size_t(ckpt_every), nullptr);
+    for (int i = 0; i < ckpt_every; ++i) {
+      void* p = nullptr;
+      if ((rc = LatticeOps::alloc(h, &p, bytes))) return drop(rc);
+      tape->bufs.push_back(p);
+      tape->seg[size_t(i) + 1] = p;
+      if ((rc = LatticeOps::alloc(h, &p, bytes))) return drop(rc);
+      tape->bufs.push_back(p);
+      tape->pre[size_t(i)] = p;
+    }
+  }
   for (int32_t t = 0; t < n_steps; ++t) {
     if (t % ckpt_every == 0) {
       const cudaError_t e = cudaMemcpyAsync(h->ckpt[t / ckpt_every], L.d_mom[L.cur], bytes,
                                             cudaMemcpyDeviceToDevice, h->stream);
       if (e != cudaSuccess) return drop(fail(h, HLBM_E_CUDA, "checkpoint copy: %s", cudaGetErrorString(e)));
     }
+    if (taped && t >= t_last) break;
     if ((rc = hlbm_step(h, 1))) return drop(rc);
+  }
+  if (taped) {
+    AdjTape* tape = h->tape;
+    StepArgs a = level0_args(h);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < tape->n && e == cudaSuccess; ++i) {
+      a.in = i == 0 ? h->ckpt[size_t(n_ck) - 1] : tape->seg[size_t(i)];
+      a.out = tape->seg[size_t(i) + 1];
+      a.pre_out = static_cast<float*>(tape->pre[size_t(i)]);
+      e = launch_stream_collide_record(a, h->stream);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(L.d_mom[L.cur], tape->seg[size_t(tape->n)], bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return drop(fail(h, HLBM_E_CUDA, "recording the last segment: %s", cudaGetErrorString(e)));
+    h->l0_steps += tape->n;
   }
   h->rec_steps = n_steps;
   h->rec_every = ckpt_every;
@@ -849,16 +897,31 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
     release_all();
     return rc;
   }
-  for (int i = 1; i <= (record ? K : K - 1); ++i)
-    if ((rc = get(bytes, &seg[i]))) {
-      release_all();
-      return rc;
-    }
-  for (int i = 0; i < int(pre.size()); ++i)
-    if ((rc = get(lam_elems * 4, &pre[i]))) {
-      release_all();
-      return rc;
-    }
+  // segment buffers: the recording's tape when there is one (it holds the
+  // last segment already), else allocated here
+  AdjTape* tape = record ? h->tape : nullptr;
+  if (tape != nullptr) {
+    for (int i = 1; i <= K; ++i) seg[size_t(i)] = tape->seg[size_t(i)];
+    for (int i = 0; i < K; ++i) pre[size_t(i)] = tape->pre[size_t(i)];
+  } else {
+    for (int i = 1; i <= (record ? K : K - 1); ++i)
+      if ((rc = get(bytes, &seg[i]))) {
+        release_all();
+        return rc;
+      }
+    for (int i = 0; i < int(pre.size()); ++i)
+      if ((rc = get(lam_elems * 4, &pre[i]))) {
+        release_all();
+        return rc;
+      }
+  }
+  // every allocation went through: the adjoint takes the tape over
+  const bool taped = tape != nullptr;
+  if (taped) {
+    tmp.insert(tmp.end(), tape->bufs.begin(), tape->bufs.end());
+    delete tape;
+    h->tape = nullptr;
+  }
   float* lam[2] = {static_cast<float*>(lam0), static_cast<float*>(lam1)};
   int c = 0;
   cudaError_t e = cudaMemcpyAsync(lam[0], dL_dM_dev, lam_elems * 4, cudaMemcpyDeviceToDevice, h->stream);
@@ -878,7 +941,8 @@ int32_t hlbm_adjoint(hlbm_lattice* h, const float* dL_dM_dev, float* dL_dF_dev) 
       // only dL/dF is returned).
       float* lp[2] = {static_cast<float*>(lamp), static_cast<float*>(lamp2)};
       int q = 0;
-      for (int i = 0; i < ns && e == cudaSuccess; ++i) {  // recompute the segment, keeping states and p
+      for (int i = 0; i < ns && e == cudaSuccess && !(taped && s == n_seg - 1); ++i) {
+        // recompute the segment, keeping states and p (the last one: taped)
         a.in = seg[i];
         a.out = seg[i + 1];
         a.pre_out = static_cast<float*>(pre[i]);

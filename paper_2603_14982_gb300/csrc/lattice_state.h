@@ -38,6 +38,38 @@ struct Profile {
   int64_t count[kProfClasses] = {};
 };
 
+// One operation of a multi-level coarse step in the order of Algorithm 1,
+// with the buffers a recorded or recomputed run gave it.
+enum AdjOpKind { kSC, kDown, kUp };
+struct AdjOp {
+  AdjOpKind kind;
+  int l, s;
+  void* in = nullptr;       // SC: input state; DOWN: fine state written; UP: coarse state written
+  void* out = nullptr;      // SC: output state
+  float* pre = nullptr;     // SC: pre-collision moments
+  void* c_old = nullptr;    // DOWN: P_{l+1}
+  void* c_new = nullptr;    // DOWN: A_{l+1}; UP: the fine state read (A_l)
+  float* undo = nullptr;    // DOWN / UP: overwritten values
+};
+
+// Reverse-mode tape of the last checkpoint segment (FP32 storage).  The
+// recording pass runs that segment with the adjoint's own recomputation, so
+// the adjoint starts its reverse walk there without recomputing it; its
+// buffers then serve the adjoint as the segment buffers of every other
+// segment.  One adjoint consumes the tape (the multi-level reverse walk puts
+// the undo logs back into these buffers).
+struct AdjTape {
+  std::vector<void*> bufs;     // every allocation of the tape
+  int n = 0;                   // recorded steps: fine steps (one level), coarse steps (multi-level)
+  // one level: seg[i + 1] = state after step i of the segment, pre[i] = its p
+  std::vector<void*> seg, pre;
+  // multi-level: the segment's operations, the per-level working copy of its
+  // start state (the transfers write in place) and the FP64 downward sums
+  std::vector<AdjOp> ops;
+  std::vector<void*> work;
+  std::vector<double*> acc;
+};
+
 struct LevelData {
   int64_t nb = 0;                  // stored blocks
   std::vector<int32_t> coords;     // host copy [nb][3] (bx, by, bz), ascending slot id (see host_lists)
@@ -101,6 +133,7 @@ struct hlbm_lattice {
   // forward run recorded for the adjoint: states at steps 0, K, 2K, ...
   // (multi-level: one buffer per level and checkpoint, [c * L + l])
   std::vector<void*> ckpt;
+  hlbm::AdjTape* tape = nullptr;  // the recorded run's last segment, until an adjoint takes it
   int32_t rec_steps = 0, rec_every = 0;
   int64_t hier_gen = 0;  // bumped whenever the block layout changes
   // live drag of the coupled step (coupling.cu): every drag_every-th level-0
@@ -193,6 +226,7 @@ struct LatticeOps {
   static int alloc(hlbm_lattice* h, void** p, size_t bytes);
   static void release(hlbm_lattice* h, void*& p);
   static void free_level(hlbm_lattice* h, LevelData& L);
+  static void release_tape(hlbm_lattice* h);
   // Allocate the scale state of a reduced-precision level (scales for amax 0).
   static int init_scales(hlbm_lattice* h, LevelData& L);
   // Re-derive a reduced-precision level's scales every kRescaleEvery steps.
