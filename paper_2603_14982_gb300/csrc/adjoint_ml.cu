@@ -463,19 +463,9 @@ __global__ void k_up_adj(UpAdjArgs a) {
   add_lambda(a.lam_fine, fb, fc, dl);
 }
 
-// Undo log of the transfers: the 10 stored values of each listed node.
-__global__ void k_gather_nodes(const float* __restrict__ buf, const int32_t* __restrict__ nodes, int64_t n,
-                               float* __restrict__ log) {
-  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const int32_t v = nodes[k];
-  const float* p = buf + int64_t(v >> 9) * kBlockVals + node_offset<float>(v & 511);
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) log[k * kRows + r] = p[r * kCells];
-}
-
-// Puts the logged values back; lam, if set, is zeroed at the same nodes
-// (natural order).
+// Undo log of the transfers (written by the transfer kernels during the
+// recomputation, [n][10] in the order of nodes): puts the logged values back;
+// lam, if set, is zeroed at the same nodes (natural order).
 __global__ void k_scatter_nodes(float* __restrict__ buf, const int32_t* __restrict__ nodes, int64_t n,
                                 const float* __restrict__ log, float* __restrict__ lam) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -618,9 +608,8 @@ cudaError_t recompute_segment(hlbm_lattice* h, std::vector<Op>& seg_ops, size_t 
       op.c_old = prev[l + 1];
       op.c_new = cur[l + 1];
       if (F.n_down == 0) continue;
-      k_gather_nodes<<<grid_for(F.n_down), 256, 0, st>>>(static_cast<const float*>(cur[l]), F.d_down, F.n_down,
-                                                         op.undo);
       TransferArgs t{};
+      t.undo = op.undo;  // in transfer order
       t.fine = level_view(h, l, cur[l], nullptr);
       t.coarse = level_view(h, l + 1, cur[l + 1], prev[l + 1]);
       t.out = cur[l];
@@ -638,9 +627,8 @@ cudaError_t recompute_segment(hlbm_lattice* h, std::vector<Op>& seg_ops, size_t 
       op.in = cur[l + 1];
       op.c_new = cur[l];
       if (C.n_up == 0) continue;
-      k_gather_nodes<<<grid_for(C.n_up), 256, 0, st>>>(static_cast<const float*>(cur[l + 1]), C.d_up, C.n_up,
-                                                       op.undo);
       TransferArgs t{};
+      t.undo = op.undo;
       t.fine = level_view(h, l, cur[l], nullptr);
       t.coarse = level_view(h, l + 1, cur[l + 1], nullptr);
       t.out = cur[l + 1];
@@ -967,7 +955,7 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         d.lam_old = lamP[l + 1];
         k_down_adj_seed<<<grid_for(F.n_down), 256, 0, st>>>(d);
         if (n_tgt[l] > 0) k_down_adj_gather<<<grid_for(n_tgt[l]), 256, 0, st>>>(d, tgt[l], n_tgt[l], fbits[l]);
-        k_scatter_nodes<<<grid_for(F.n_down), 256, 0, st>>>(static_cast<float*>(op.in), F.d_down, F.n_down,
+        k_scatter_nodes<<<grid_for(F.n_down), 256, 0, st>>>(static_cast<float*>(op.in), F.d_down_t, F.n_down,
                                                             op.undo, d.lam_fine);
       } else {
         const LevelData& C = h->lv[l + 1];

@@ -30,9 +30,8 @@ __device__ __forceinline__ R narrow(double v) {
     return to32(v);
 }
 
-template <typename T>
-__device__ __forceinline__ Node64 load64(const void* base, int64_t blk, int cell, const Scales* sc) {
-  const auto m = load_node<T>(static_cast<const T*>(base), blk, cell, sc);
+template <typename M>
+__device__ __forceinline__ Node64 split64(const M& m) {
   Node64 n;
   n.drho = to64(m.drho);
   n.ux = to64(m.ux);
@@ -45,6 +44,11 @@ __device__ __forceinline__ Node64 load64(const void* base, int64_t blk, int cell
   n.s[4] = to64(mad(-m.ux, m.uz, m.sxz));
   n.s[5] = to64(mad(-m.uy, m.uz, m.syz));
   return n;
+}
+
+template <typename T>
+__device__ __forceinline__ Node64 load64(const void* base, int64_t blk, int cell, const Scales* sc) {
+  return split64(load_node<T>(static_cast<const T*>(base), blk, cell, sc));
 }
 
 template <typename T>
@@ -101,6 +105,18 @@ __device__ __forceinline__ void pair(int p, int n, int periodic, int& lo, int& h
   if (hi >= n) hi = periodic ? hi - n : n - 1;
 }
 
+// The adjoint's undo log: the node's stored values before a transfer
+// overwrites them (FP32 storage).
+template <typename T>
+__device__ __forceinline__ void log_node(const TransferArgs& a, int64_t k, int64_t blk, int cell) {
+  if constexpr (sizeof(T) == 4) {
+    if (a.undo == nullptr) return;
+    const T* p = static_cast<const T*>(a.out) + blk * (kRows * kCells) + node_offset<T>(cell);
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) a.undo[k * kRows + r] = p[r * kCells];
+  }
+}
+
 template <typename T>
 __global__ void k_down(TransferArgs a) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -155,32 +171,30 @@ __global__ void k_down(TransferArgs a) {
     for (int r = 0; r < 6; ++r) acc.s[r] = half64(o[4 + r]);
     cur = a.coarse.mom;
   }
+  if (a.avg && !reuse) {
+    // temporal midpoint of the old (other) and new (current) coarse states,
+    // taken per field on rho, u and S^neq (no sums kept from step 1)
 #pragma unroll
-  for (int q = 0; q < 8; q += 2) {
-    if (q >= nq) break;
-    const bool two = q + 1 < nq;
-    if (a.avg && !reuse) {
-      // temporal midpoint of the old (other) and new (current) coarse states,
-      // taken per field on rho, u and S^neq
-      const Node64 o0 = load64<T>(a.coarse.mom_other, cb[q], cc[q], a.coarse.sc);
-      const Node64 n0 = load64<T>(a.coarse.mom, cb[q], cc[q], a.coarse.sc);
-      Node64 o1 = zero64(), n1 = zero64();
-      if (two) {
-        o1 = load64<T>(a.coarse.mom_other, cb[q + 1], cc[q + 1], a.coarse.sc);
-        n1 = load64<T>(a.coarse.mom, cb[q + 1], cc[q + 1], a.coarse.sc);
-      }
-      axpy(acc, wt, o0);
-      axpy(acc, wt, n0);
-      if (two) {
-        axpy(acc, wt, o1);
-        axpy(acc, wt, n1);
-      }
-    } else {
-      const Node64 v0 = load64<T>(cur, cb[q], cc[q], a.coarse.sc);
-      Node64 v1 = zero64();
-      if (two) v1 = load64<T>(cur, cb[q + 1], cc[q + 1], a.coarse.sc);
-      axpy(acc, wt, v0);
-      if (two) axpy(acc, wt, v1);
+    for (int q = 0; q < 8; ++q) {
+      if (q >= nq) break;
+      axpy(acc, wt, load64<T>(a.coarse.mom_other, cb[q], cc[q], a.coarse.sc));
+      axpy(acc, wt, load64<T>(a.coarse.mom, cb[q], cc[q], a.coarse.sc));
+    }
+  } else {
+    // the stencil nodes' moments four at a time (nq is the same for the
+    // whole warp: the list is in transfer order), then their sums
+    using R = typename StorageTraits<T>::R;
+    constexpr int G = 4;
+#pragma unroll
+    for (int q0 = 0; q0 < 8; q0 += G) {
+      if (q0 >= nq) break;
+      Mom<R> mv[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j)
+        if (q0 + j < nq) mv[j] = load_node<T>(static_cast<const T*>(cur), cb[q0 + j], cc[q0 + j], a.coarse.sc);
+#pragma unroll
+      for (int j = 0; j < G; ++j)
+        if (q0 + j < nq) axpy(acc, wt, split64(mv[j]));
     }
   }
   if (a.use_other && a.acc_old != nullptr) {  // step 1: keep the old state's sums for step 2
@@ -192,6 +206,7 @@ __global__ void k_down(TransferArgs a) {
 #pragma unroll
     for (int r = 0; r < 6; ++r) o[4 + r] = acc.s[r];
   }
+  log_node<T>(a, k, b, cell);
   store64<T>(a.out, b, cell, acc, a.k, a.out_sc);
 }
 
@@ -209,7 +224,9 @@ __global__ void k_up(TransferArgs a) {
     atomicExch(a.status, 1);
     return;
   }
-  store64<T>(a.out, b, cell, load64<T>(a.fine.mom, fb, cell_of(x, y, z), a.fine.sc), a.k, a.out_sc);
+  const Node64 n = load64<T>(a.fine.mom, fb, cell_of(x, y, z), a.fine.sc);
+  log_node<T>(a, k, b, cell);
+  store64<T>(a.out, b, cell, n, a.k, a.out_sc);
 }
 
 // U_l(i): the stored value at level l, else the upward rule applied to U_{l-1}(2i).

@@ -34,6 +34,8 @@ struct TransferArgs {
   double k;                   // S^neq factor
   int periodic[3];
   int* status;                // set to 1 if a stencil node is not stored
+  float* undo;                // optional (FP32 storage): the written nodes' previous stored values,
+                              // [n_nodes][10] in the order of nodes (the adjoint's undo log)
   double* acc_old;            // down, optional [n_nodes][10]: step 1 stores the FP64 stencil sums of the
                               // old coarse state there; step 2 reuses them instead of re-reading the
                               // old state (it is the same state: the coarse level does not step between)
