@@ -614,6 +614,7 @@ cudaError_t recompute_segment(hlbm_lattice* h, std::vector<Op>& seg_ops, size_t 
       t.coarse = level_view(h, l + 1, cur[l + 1], prev[l + 1]);
       t.out = cur[l];
       t.nodes = F.d_down_t;
+      t.stencil = F.d_down_stc;
       t.n_nodes = F.n_down;
       t.avg = op.s == 2 ? 1 : 0;
       t.use_other = op.s == 1 ? 1 : 0;

@@ -187,7 +187,7 @@ void LatticeOps::free_level(hlbm_lattice* h, LevelData& L) {
   release(h, v);
   L.d_skip = nullptr;
   for (void** q : {(void**)&L.d_coords, (void**)&L.d_slot, (void**)&L.d_H, (void**)&L.d_stored, (void**)&L.d_down,
-                   (void**)&L.d_down_t, (void**)&L.d_up, (void**)&L.d_down_acc, (void**)&L.d_list_flags, (void**)&L.d_scales, (void**)&L.d_amax, (void**)&L.d_hkeys, (void**)&L.d_hvals}) {
+                   (void**)&L.d_down_t, (void**)&L.d_down_stc, (void**)&L.d_up, (void**)&L.d_down_acc, (void**)&L.d_list_flags, (void**)&L.d_scales, (void**)&L.d_amax, (void**)&L.d_hkeys, (void**)&L.d_hvals}) {
     release(h, *q);
   }
   L.hcap = 0;

@@ -98,6 +98,7 @@ struct LevelData {
   int64_t n_down = 0, n_up = 0;    // interface node counts (I^d, I^u)
   int32_t* d_down = nullptr;       // [n_down] (block << 9) | cell
   int32_t* d_down_t = nullptr;     // [n_down] the same nodes in transfer order (grouped by stencil shape)
+  int32_t* d_down_stc = nullptr;   // [8][n_down] their coarse stencil nodes, (block << 9) | cell
   int32_t* d_up = nullptr;         // [n_up]
   double* d_down_acc = nullptr;    // [n_down][10] FP64 stencil sums of the old coarse state (step s = 1,
                                    // reused at s = 2), in transfer order

@@ -69,6 +69,7 @@ int downward(hlbm_lattice* h, int l, int s, bool refresh) {
   a.out = F.d_mom[F.cur];
   a.out_sc = F.d_scales;
   a.nodes = F.d_down_t;
+  a.stencil = F.d_down_stc;
   a.n_nodes = F.n_down;
   a.avg = (!refresh && s == 2) ? 1 : 0;
   a.use_other = (!refresh && s == 1) ? 1 : 0;
@@ -420,6 +421,7 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
     if ((rc = alloc_t(h, &nl[l].d_up, size_t(nl[l].n_up) + 1))) break;
     if (l + 1 < L && (rc = alloc_t(h, &nl[l].d_down_acc, size_t(nl[l].n_down) * 10 + 1))) break;
     if (l + 1 < L && (rc = alloc_t(h, &nl[l].d_down_t, size_t(nl[l].n_down) + 1))) break;
+    if (l + 1 < L && (rc = alloc_t(h, &nl[l].d_down_stc, size_t(nl[l].n_down) * 8 + 1))) break;
     cudaError_t e = interface_scatter(nl[l].d_nbr, nl[l].d_skip, nb[l], d_ioff[l], nl[l].d_down, nl[l].d_up, st);
     if (e != cudaSuccess) {
       rc = fail(h, HLBM_E_CUDA, "interface scatter: %s", cudaGetErrorString(e));
@@ -430,6 +432,16 @@ int ml_rebuild(hlbm_lattice* h, const float* pos, int64_t n_pos, int pos_on_devi
       if ((rc = alloc_t(h, &d_ord, size_t(transfer_order_scratch(nl[l].n_down))))) break;
       tmp.push_back(d_ord);
       e = transfer_order(nl[l].d_down, nl[l].n_down, d_ord, nl[l].d_down_t, st);
+      if (e == cudaSuccess) {
+        TransferArgs t{};
+        t.fine = view_of(nl[l], dims_of(h, l));
+        t.coarse = view_of(nl[l + 1], dims_of(h, l + 1));
+        t.nodes = nl[l].d_down_t;
+        t.n_nodes = nl[l].n_down;
+        for (int ax = 0; ax < 3; ++ax) t.periodic[ax] = h->cfg.periodic[ax];
+        t.status = h->d_status;
+        e = down_stencil(t, nl[l].d_down_stc, st);
+      }
       if (e != cudaSuccess) rc = fail(h, HLBM_E_CUDA, "transfer order: %s", cudaGetErrorString(e));
     }
   }

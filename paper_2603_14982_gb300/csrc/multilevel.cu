@@ -117,8 +117,11 @@ __device__ __forceinline__ void log_node(const TransferArgs& a, int64_t k, int64
   }
 }
 
-template <typename T>
-__global__ void k_down(TransferArgs a) {
+// Stencil table of a downward transfer: per fine node, the distinct coarse
+// stencil nodes (an even fine index has one coarse node on that axis, an odd
+// one two; ceil wraps on a periodic axis and is clamped on a wall axis), in
+// the order x fastest, then y, then z.
+__global__ void k_down_stencil(TransferArgs a, int32_t* __restrict__ out) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= a.n_nodes) return;
   const int32_t v = a.nodes[k];
@@ -130,32 +133,59 @@ __global__ void k_down(TransferArgs a) {
   int lo[3], hi[3];
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) pair(p[ax], n[ax], a.periodic[ax], lo[ax], hi[ax]);
-  // distinct stencil nodes only: an even fine index has one coarse node (weight
-  // 1), an odd one two (weight 1/2 each); the weights are exact in FP64
   const int nx = hi[0] != lo[0] ? 2 : 1, ny = hi[1] != lo[1] ? 2 : 1, nz = hi[2] != lo[2] ? 2 : 1;
   const int nq = nx * ny * nz;
-  // weight 1/nq = 2^-e, halved once more when the new state's sums are added
-  // to half the kept ones (step 2) or averaged with the old state's
-  const int e = (nx - 1) + (ny - 1) + (nz - 1) + (a.avg ? 1 : 0);
-  const double wt = e == 0 ? 1.0 : e == 1 ? 0.5 : e == 2 ? 0.25 : e == 3 ? 0.125 : 0.0625;
-  // all stencil lookups first (independent loads), then the node loads two
-  // corners at a time so that their latencies overlap
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    int32_t e = -1;
+    if (q < nq) {
+      const int qx = q % nx, qy = (q / nx) % ny, qz = q / (nx * ny);
+      const int x = qx ? hi[0] : lo[0], y = qy ? hi[1] : lo[1], z = qz ? hi[2] : lo[2];
+      const int64_t cb = lookup(a.coarse, x, y, z);
+      ok = ok && cb >= 0;
+      e = cb >= 0 ? int32_t((cb << 9) | cell_of(x, y, z)) : -2;
+    }
+    out[q * a.n_nodes + k] = e;
+  }
+  if (!ok) atomicExch(a.status, 1);
+}
+
+template <typename T>
+__global__ void k_down(TransferArgs a) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= a.n_nodes) return;
+  const int32_t v = a.nodes[k];
+  const int64_t b = v >> 9;
+  const int cell = v & 511;
+  // the stencil from the table (built with the hierarchy): at most
+  // 2^(odd coordinates) entries, the same number for the whole warp
+  const int nmax = (1 + (cell & 1)) * (1 + ((cell >> 3) & 1)) * (1 + ((cell >> 6) & 1));
+  int32_t st[8];
+  int nq = 0;
+  bool bad = false;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    st[q] = q < nmax ? a.stencil[q * a.n_nodes + k] : -1;
+    nq += st[q] >= 0 ? 1 : 0;
+    bad = bad || st[q] == -2;
+  }
+  if (bad) {
+    atomicExch(a.status, 1);
+    return;
+  }
   int64_t cb[8];
   int cc[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const int qx = q % nx, qy = (q / nx) % ny, qz = q / (nx * ny);
-    const int x = qx ? hi[0] : lo[0], y = qy ? hi[1] : lo[1], z = qz ? hi[2] : lo[2];
-    cb[q] = q < nq ? lookup(a.coarse, x, y, z) : 0;
-    cc[q] = cell_of(x, y, z);
+    cb[q] = st[q] >= 0 ? (st[q] >> 9) : 0;
+    cc[q] = st[q] & 511;
   }
-  bool ok = true;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) ok = ok && cb[q] >= 0;
-  if (!ok) {
-    atomicExch(a.status, 1);
-    return;
-  }
+  // weight 1/nq = 2^-e (exact in FP64), halved once more when the new
+  // state's sums are added to half the kept ones (step 2) or averaged with
+  // the old state's
+  const int e = (nq >= 2 ? 1 : 0) + (nq >= 4 ? 1 : 0) + (nq >= 8 ? 1 : 0) + (a.avg ? 1 : 0);
+  const double wt = e == 0 ? 1.0 : e == 1 ? 0.5 : e == 2 ? 0.25 : e == 3 ? 0.125 : 0.0625;
   Node64 acc = zero64();
   const void* cur = a.use_other ? a.coarse.mom_other : a.coarse.mom;
   // step 2 with the old state's sums kept from step 1: half of them plus half
@@ -312,6 +342,7 @@ inline unsigned blocks_for(int64_t n) { return unsigned((n + kTransferThreads - 
 template <typename T>
 cudaError_t down_typed(const TransferArgs& a, cudaStream_t s) {
   if (a.n_nodes == 0) return cudaSuccess;
+  if (a.stencil == nullptr) return cudaErrorInvalidValue;
   k_down<T><<<blocks_for(a.n_nodes), kTransferThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -355,6 +386,12 @@ cudaError_t test_narrow(const double* in, float* out, float* hw, int64_t n, cuda
     case HLBM_STORE_BF16S: return fn<__nv_bfloat16>(__VA_ARGS__); \
     default: return cudaErrorNotSupported;                        \
   }
+
+cudaError_t down_stencil(const TransferArgs& a, int32_t* out, cudaStream_t s) {
+  if (a.n_nodes == 0) return cudaSuccess;
+  k_down_stencil<<<blocks_for(a.n_nodes), kTransferThreads, 0, s>>>(a, out);
+  return cudaGetLastError();
+}
 
 cudaError_t transfer_down(int storage, const TransferArgs& a, cudaStream_t s) {
   HLBM_ML_DISPATCH(storage, down_typed, a, s)

@@ -34,6 +34,8 @@ struct TransferArgs {
   double k;                   // S^neq factor
   int periodic[3];
   int* status;                // set to 1 if a stencil node is not stored
+  const int32_t* stencil;     // down: [8][n_nodes] (coarse block << 9) | cell of each stencil node of
+                              // nodes[k], -1 past its stencil, -2 where the coarse node is not stored
   float* undo;                // optional (FP32 storage): the written nodes' previous stored values,
                               // [n_nodes][10] in the order of nodes (the adjoint's undo log)
   double* acc_old;            // down, optional [n_nodes][10]: step 1 stores the FP64 stencil sums of the
@@ -41,6 +43,11 @@ struct TransferArgs {
                               // old state (it is the same state: the coarse level does not step between)
 };
 
+// The stencil table of a downward transfer (a.stencil written through
+// `out`): per node of a.nodes its coarse stencil nodes, in the order the
+// transfer sums them; sets *a.status to 1 for a coarse node that is not
+// stored.  Depends on the hierarchy only.
+cudaError_t down_stencil(const TransferArgs& a, int32_t* out, cudaStream_t s);
 // DownwardTransfer of Algorithm 1 (Eq. downward_rescale) into I^d nodes of the fine level.
 cudaError_t transfer_down(int storage, const TransferArgs& a, cudaStream_t s);
 // UpwardTransfer of Algorithm 1 (Eq. upload_S) into I^u nodes of the coarse level.
