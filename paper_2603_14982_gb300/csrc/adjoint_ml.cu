@@ -176,6 +176,7 @@ __device__ __forceinline__ void add_lambda(const LamTarget& g, int64_t blk, int 
 struct DownAdjArgs {
   LevelView fine, coarse;  // coarse.mom = A_{l+1} (new), coarse.mom_other = P_{l+1} (old)
   const int32_t* nodes;    // I^d_l: (block << 9) | cell
+  const int32_t* stencil;  // seeds: the forward transfer's stencil table, in the order of nodes
   int64_t n_nodes;
   int avg;                 // 1: s = 2 (temporal midpoint), 0: s = 1 (old state only)
   float k;                 // S^neq factor of the transfer
@@ -206,33 +207,28 @@ __global__ void k_down_adj_seed(DownAdjArgs a) {
   const int64_t b = v >> 9;
   const int cell = v & 511;
   float* lf = a.lam_fine + b * kBlockVals + cell;
-  const int32_t* c = a.fine.coords + 3 * b;
-  const int p[3] = {c[0] * 8 + (cell & 7), c[1] * 8 + ((cell >> 3) & 7), c[2] * 8 + (cell >> 6)};
-  const int n[3] = {a.coarse.d.nx * 8, a.coarse.d.ny * 8, a.coarse.d.nz * 8};
-  int lo[3], hi[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) stencil_axis(p[ax], n[ax], a.periodic[ax], lo[ax], hi[ax]);
-  const int nx = hi[0] != lo[0] ? 2 : 1, ny = hi[1] != lo[1] ? 2 : 1, nz = hi[2] != lo[2] ? 2 : 1;
-  const int nq = nx * ny * nz;
-  // weight 1/nq = 2^-e, halved at s = 2 (old and new state each count half)
-  const int e = (nx - 1) + (ny - 1) + (nz - 1) + (a.avg ? 1 : 0);
-  const double w = e == 0 ? 1.0 : e == 1 ? 0.5 : e == 2 ? 0.25 : e == 3 ? 0.125 : 0.0625;
+  // the stencil from the forward transfer's table (same order as nodes)
+  const int nmax = (1 + (cell & 1)) * (1 + ((cell >> 3) & 1)) * (1 + ((cell >> 6) & 1));
   int64_t cb[8];
   int cc[8];
+  int nq = 0;
   bool ok = true;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const int qx = q % nx, qy = (q / nx) % ny, qz = q / (nx * ny);
-    const int x = qx ? hi[0] : lo[0], y = qy ? hi[1] : lo[1], z = qz ? hi[2] : lo[2];
-    cb[q] = q < nq ? find_block(a.coarse, x, y, z) : 0;
-    cc[q] = node_cell(x, y, z);
-    ok = ok && cb[q] >= 0;
+    const int32_t st = q < nmax ? a.stencil[q * a.n_nodes + k] : -1;
+    nq += st >= 0 ? 1 : 0;
+    ok = ok && st != -2;
+    cb[q] = st >= 0 ? (st >> 9) : 0;
+    cc[q] = st & 511;
   }
   if (!ok) {  // the forward transfer reported this already
 #pragma unroll
     for (int r = 0; r < kRows; ++r) lf[r * kCells] = 0.f;
     return;
   }
+  // weight 1/nq = 2^-e, halved at s = 2 (old and new state each count half)
+  const int e = (nq >= 2 ? 1 : 0) + (nq >= 4 ? 1 : 0) + (nq >= 8 ? 1 : 0) + (a.avg ? 1 : 0);
+  const double w = e == 0 ? 1.0 : e == 1 ? 0.5 : e == 2 ? 0.25 : e == 3 ? 0.125 : 0.0625;
   float L[kRows];
 #pragma unroll
   for (int r = 0; r < kRows; ++r) L[r] = lf[r * kCells];
@@ -300,25 +296,41 @@ __global__ void k_down_adj_gather(DownAdjArgs a, const int32_t* __restrict__ tar
   fine_candidates(X[0], n[0], a.periodic[0], px, wx, okx);
   fine_candidates(X[1], n[1], a.periodic[1], py, wy, oky);
   fine_candidates(X[2], n[2], a.periodic[2], pz, wz, okz);
+  // The candidates 2X and 2X + 1 of an axis share a block (2X is even); only
+  // 2X - 1 may lie in another one.  So the 27 candidates lie in at most 8
+  // blocks: look those up first, then test all candidates' I^d bits, then
+  // load the seeds of the candidates that hold one (independent loads in
+  // each phase).
+  int64_t fbk[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int sx = j & 1, sy = (j >> 1) & 1, sz = j >> 2;  // 0: the block of 2X - 1, 1: of 2X
+    const bool need = (sx || okx[0]) && (sy || oky[0]) && (sz || okz[0]);
+    fbk[j] = need ? find_block(a.fine, px[sx ? 1 : 0], py[sy ? 1 : 0], pz[sz ? 1 : 0]) : -1;
+  }
+  uint32_t hit = 0;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const int ix = q % 3, iy = (q / 3) % 3, iz = q / 9;
+    const int64_t fb = fbk[(ix ? 1 : 0) | (iy ? 2 : 0) | (iz ? 4 : 0)];
+    if (!(okx[ix] && oky[iy] && okz[iz]) || fb < 0) continue;
+    const int fc = node_cell(px[ix], py[iy], pz[iz]);
+    if ((__ldg(fine_bits + fb * (kCells / 32) + (fc >> 5)) >> (fc & 31)) & 1u) hit |= 1u << q;
+  }
   float acc[kRows];
 #pragma unroll
   for (int r = 0; r < kRows; ++r) acc[r] = 0.f;
 #pragma unroll
-  for (int iz = 0; iz < 3; ++iz)
+  for (int q = 0; q < 27; ++q) {
+    if (!((hit >> q) & 1u)) continue;
+    const int ix = q % 3, iy = (q / 3) % 3, iz = q / 9;
+    const int64_t fb = fbk[(ix ? 1 : 0) | (iy ? 2 : 0) | (iz ? 4 : 0)];
+    const int fc = node_cell(px[ix], py[iy], pz[iz]);
+    const float w = 1.f / float(wx[ix] * wy[iy] * wz[iz]);
+    const float* sd = a.lam_fine + fb * kBlockVals + fc;
 #pragma unroll
-    for (int iy = 0; iy < 3; ++iy)
-#pragma unroll
-      for (int ix = 0; ix < 3; ++ix) {
-        if (!(okx[ix] && oky[iy] && okz[iz])) continue;
-        const int64_t fb = find_block(a.fine, px[ix], py[iy], pz[iz]);
-        if (fb < 0) continue;
-        const int fc = node_cell(px[ix], py[iy], pz[iz]);
-        if (!((__ldg(fine_bits + fb * (kCells / 32) + (fc >> 5)) >> (fc & 31)) & 1u)) continue;
-        const float w = 1.f / float(wx[ix] * wy[iy] * wz[iz]);
-        const float* sd = a.lam_fine + fb * kBlockVals + fc;
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) acc[r] = fmaf(w, sd[r * kCells], acc[r]);
-      }
+    for (int r = 0; r < kRows; ++r) acc[r] = fmaf(w, sd[r * kCells], acc[r]);
+  }
   const float lu[3] = {acc[1], acc[2], acc[3]};
   const float lsn[6] = {acc[4], acc[5], acc[6], acc[7], acc[8], acc[9]};
   float m[kRows], dl[kRows];
@@ -947,6 +959,7 @@ int ml_adjoint(hlbm_lattice* h, const float* dL_dM, float* dL_dF) {
         d.fine = level_view(h, l, op.in, nullptr);
         d.coarse = level_view(h, l + 1, op.c_new, op.c_old);
         d.nodes = F.d_down_t;  // the seeds are per node: transfer order (uniform stencil shape per warp)
+        d.stencil = F.d_down_stc;
         d.n_nodes = F.n_down;
         d.avg = op.s == 2 ? 1 : 0;
         d.k = float(h->kdown[l]);
